@@ -1,0 +1,232 @@
+/*
+ * esi.h -- C ABI of libesi: the GB300 (sm_103a) hot path of time-domain extended-source
+ * waveform inversion (ESI), after P. Yang & W. Zhou, "Algorithmic analysis towards
+ * time-domain extended source waveform inversion" (arXiv 2211.06300).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  Grid      : nz x ny x nx cells (ny = 1 in 2D), spacing dx on every axis, x fastest.
+ *              Cell (iz, iy, ix) sits at (x, y, z) = (ix dx, iy dx, iz dx).  The grid
+ *              includes the absorbing sponge of nb cells on every side.  N = nz*ny*nx.
+ *  Physics   : (1/v^2) u_tt - Lap u = q  (Eq. "wave"), discretised O(dt^2, dx^8) with a
+ *              damping sponge (Numerical tests section).  Step n (0 <= n < nt) consumes
+ *              the source q_n (time n dt) and produces u_{n+1}; u_0 = u_{-1} = 0.
+ *  Sampling  : R (Eq. "fwi") uses bilinear (2D) / trilinear (3D) weights; trace sample n
+ *              is R u_{n+1}.  A point source injects f_n * w / dx^d at the same nodes.
+ *  Traces    : "seismogram" buffers are CSR-packed per shot, time-major:
+ *              shot s occupies nt * nrec(s) values starting at nt * rec_offset[s],
+ *              element (s, n, r) at nt * rec_offset[s] + n * nrec(s) + r.
+ *  Fields    : space-time buffers (extended sources, adjoint outputs, CG solutions) are
+ *              [shot][n][iz][iy][ix], dense, element type = the context precision.
+ *  Precision : ESI_F32 (float) or ESI_F64 (double) for fields and traces; CG scalars,
+ *              dot products and misfits are always accumulated in double.
+ *  Memory    : every *_dev pointer is CUDA device memory owned by the caller (the Python
+ *              binding passes PyTorch tensors); host pointers are plain host memory.  The
+ *              library never frees caller memory.  The context owns its scratch (wave
+ *              states, checkpoints, CG work vectors), allocated on first use and released
+ *              by esi_destroy.
+ *  Streams   : all work is enqueued on the stream given to esi_create (or
+ *              esi_set_stream).  Calls return after enqueueing, except where stated
+ *              (esi_cg_solve, esi_gradient's misfit, esi_dft_extract's scales), which
+ *              synchronise the stream to read a few scalars back.
+ *  Errors    : every call returns an esi_status; nothing is thrown across the ABI.  On
+ *              failure esi_last_error(ctx) gives a message.  A context whose call failed
+ *              with ESI_ERR_CUDA should be destroyed.
+ */
+#ifndef ESI_H
+#define ESI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define ESI_API __attribute__((visibility("default")))
+#else
+#define ESI_API
+#endif
+
+typedef enum esi_status {
+    ESI_OK = 0,
+    ESI_ERR_ARG = 1,            /* invalid argument (NULL, size, point outside the grid) */
+    ESI_ERR_CFL = 2,            /* v_max dt / dx above the stability limit of the scheme */
+    ESI_ERR_OOM = 3,            /* device allocation failed */
+    ESI_ERR_CUDA = 4,           /* a CUDA call failed (message in esi_last_error) */
+    ESI_ERR_BREAKDOWN = 5,      /* CG: p^T A p <= 0 or a non-finite scalar */
+    ESI_ERR_TIMEOUT = 6,        /* a bounded device wait expired */
+    ESI_ERR_NOT_CONVERGED = 7,  /* CG stopped at max_iter above tol (outputs valid) */
+    ESI_ERR_UNSUPPORTED = 8     /* option combination not implemented */
+} esi_status;
+
+typedef enum esi_dtype { ESI_F32 = 0, ESI_F64 = 1 } esi_dtype;
+
+typedef struct esi_ctx esi_ctx;
+
+typedef struct esi_grid {
+    int ndim;            /* 2 or 3 */
+    int nz, ny, nx;      /* cells; ny must be 1 when ndim == 2 */
+    double dx;           /* metres */
+    int nb;              /* sponge width in cells on every side (0 = rigid edges) */
+    double sponge_R;     /* target reflection coefficient of the sponge, e.g. 1e-3 */
+    double sponge_vref;  /* velocity used in the damping profile (> 0, m/s) */
+    int dtype;           /* esi_dtype */
+} esi_grid;
+
+typedef struct esi_geometry {
+    int ns;                        /* number of shots */
+    const double *src_xyz;         /* host [ns][3]: source (x, y, z) in metres */
+    const long long *rec_offset;   /* host [ns + 1]: CSR offsets into rec_xyz */
+    const double *rec_xyz;         /* host [rec_offset[ns]][3]: receivers, metres */
+} esi_geometry;
+
+/*
+ * esi_create -- set up the discrete wave operator A(m) on a velocity model
+ * (Eq. "wave": constant-density acoustic, m = v) with the shots' sampling operators R
+ * (Eq. "fwi") and source positions.
+ *   out          : receives the new context
+ *   grid         : grid description (copied)
+ *   geom         : acquisition (copied)
+ *   velocity_dev : device [nz][ny][nx] velocity in m/s, element type = grid->dtype
+ *   dt           : time step in seconds;  nt : number of steps (>= 1)
+ *   stream       : cudaStream_t (NULL = legacy default stream)
+ * Rejects a time step above the stability limit with ESI_ERR_CFL:
+ *   v_max dt / dx <= sqrt(4 / (ndim * 6.5015873...)), the Nyquist symbol of the 8th-order
+ *   Laplacian.  Points outside the grid give ESI_ERR_ARG.  Synchronises the stream once.
+ */
+ESI_API esi_status esi_create(esi_ctx **out, const esi_grid *grid, const esi_geometry *geom,
+                              const void *velocity_dev, double dt, int nt, void *stream);
+
+ESI_API void esi_destroy(esi_ctx *ctx);
+
+/* Replace the context's stream (cudaStream_t). */
+ESI_API esi_status esi_set_stream(esi_ctx *ctx, void *stream);
+
+/* Replace the velocity model (same grid, same sponge reference); device pointer. */
+ESI_API esi_status esi_set_velocity(esi_ctx *ctx, const void *velocity_dev);
+
+/*
+ * esi_forward -- forward modelling d = R A^{-1} q for every shot (Eq. "fwi", "wave").
+ *   wavelet_dev : device [ns][nt] point-source time functions f_n, or NULL
+ *   ext_src_dev : device [ns][nt][N] extended source q (Eq. "newq2"), or NULL
+ *                 (both may be given; they add)
+ *   traces_dev  : device seismogram buffer (CSR layout above), written
+ */
+ESI_API esi_status esi_forward(esi_ctx *ctx, const void *wavelet_dev, const void *ext_src_dev,
+                               void *traces_dev);
+
+/*
+ * esi_adjoint -- exact discrete adjoint S^T e = A^{-T} R^T e (Eq. "FWI_lambda"; the
+ * right-hand side b = S^H d of the CG section), the transpose of esi_forward's map from
+ * the extended source to the traces.
+ *   traces_dev  : device seismogram-layout adjoint data e
+ *   ext_out_dev : device [ns][nt][N] receives (S^T e), or NULL
+ *   wavelet_out_dev : device [ns][nt] receives the adjoint of the point-source injection
+ *                 (the transpose of esi_forward's wavelet -> traces map), or NULL
+ */
+ESI_API esi_status esi_adjoint(esi_ctx *ctx, const void *traces_dev, void *ext_out_dev,
+                               void *wavelet_out_dev);
+
+typedef enum esi_grad_mode {
+    ESI_GRAD_ADJOINT_STATE = 0,  /* back-propagate a data residual (Eq. "gradient") */
+    ESI_GRAD_SADDLE_POINT = 1    /* Algorithm 2: lambda = beta B^H B q, no adjoint run */
+} esi_grad_mode;
+
+typedef enum esi_param { ESI_PARAM_C = 0, ESI_PARAM_V = 1, ESI_PARAM_M = 2 } esi_param;
+
+typedef enum esi_ckpt_kind {
+    ESI_CKPT_F32 = 0,            /* checkpoints stored in the field precision */
+    ESI_CKPT_F16 = 1,            /* IEEE half with a per-snapshot scale */
+    ESI_CKPT_BF16 = 2            /* bfloat16 with a per-snapshot scale */
+} esi_ckpt_kind;
+
+typedef struct esi_grad_opts {
+    int mode;          /* esi_grad_mode */
+    int param;         /* esi_param: c = v^2 dt^2, v, or m = 1/v^2 */
+    int ckpt_every;    /* checkpoint interval in steps (>= 1) */
+    int ckpt_kind;     /* esi_ckpt_kind */
+    double beta;       /* penalty weight (saddle-point mode) */
+    double eps;        /* annihilator offset in metres (<= 0: dx) */
+} esi_grad_opts;
+
+/*
+ * esi_gradient -- zero-lag cross-correlation gradient (Eq. "gradient", "gradewi").
+ * Adjoint-state mode: u = A^{-1}(wavelet, ext_src); the adjoint field of the data
+ *   residual e is correlated with Lap u_n + q_n over all steps.  e is adj_src_dev when
+ *   given (a vector-Jacobian product, J = <e, d>), otherwise e = R u - dobs and
+ *   *misfit = 1/2 ||e||^2 (Eq. "fwi").  The forward states are recomputed per segment of
+ *   ckpt_every steps from stored (optionally compressed) checkpoints.
+ * Saddle-point mode (Algorithm 2): ext_src is the ESI solution q, the
+ *   adjoint field is lambda = beta B^H B q with B = ||x - x_s|| + eps; one forward run.
+ *   grad_dev    : device [N], written (sum over all shots) in the chosen parameter
+ *   misfit      : host double, written in adjoint-state mode with dobs (may be NULL)
+ */
+ESI_API esi_status esi_gradient(esi_ctx *ctx, const void *wavelet_dev, const void *ext_src_dev,
+                                const void *dobs_dev, const void *adj_src_dev,
+                                const esi_grad_opts *opts, void *grad_dev, double *misfit);
+
+typedef enum esi_dft_out { ESI_DFT_C64 = 0, ESI_DFT_C32_HALF = 1 } esi_dft_out;
+
+/*
+ * esi_dft_extract -- forward modelling with the on-the-fly DTFT of the wavefield
+ * (Eq. "dtft"): U_m(x) = sum_{n=0}^{nt-1} u_{n+1}(x) exp(+j 2 pi f_m (n+1) dt).
+ *   freqs_hz    : host [nf] frequencies
+ *   out_dev     : device [ns][nf][N] complex: float2/double2 pairs (ESI_DFT_C64 means
+ *                 the context precision) or __half2 pairs (ESI_DFT_C32_HALF, each
+ *                 frequency scaled by 1/scales[s*nf+m])
+ *   scales_host : host [ns*nf] decode scales for the half output (may be NULL otherwise)
+ *   traces_dev  : optional seismogram output of the same run (may be NULL)
+ */
+ESI_API esi_status esi_dft_extract(esi_ctx *ctx, const void *wavelet_dev, const void *ext_src_dev,
+                                   const double *freqs_hz, int nf, void *out_dev, int out_kind,
+                                   float *scales_host, void *traces_dev);
+
+typedef enum esi_precond { ESI_PC_NONE = 0, ESI_PC_DIAG = 1, ESI_PC_LEARNED = 2 } esi_precond;
+
+typedef struct esi_cg_report {
+    int iters_max;           /* largest iteration count over shots */
+    int converged;           /* 1 when every shot met tol */
+    int max_hist;            /* capacity of rel_res (entries per shot), set by caller */
+    int *iters;              /* host [ns] iterations per shot (may be NULL) */
+    double *rel_res;         /* host [ns][max_hist] ||r_{k+1}|| / ||r_0|| (may be NULL) */
+    double ms_matvec, ms_vector, ms_precond, ms_total;   /* wall-clock split */
+} esi_cg_report;
+
+/*
+ * esi_cg_solve -- Algorithm 1 (CG) on the ESI normal equation (Eq. "normalewi"):
+ *   (S^T S + lambda B^T B) q = S^T d,   B = ||x - x_s|| + eps  (per shot),
+ * with the north-star's name lambda for the paper's penalty beta.  Every matrix-vector
+ * product is one forward modelling with p as the extended source and one adjoint
+ * modelling of its traces (CG section, second bullet), plus lambda B^2 p.  Shots are
+ * independent systems, each with its own scalars; a shot stops at
+ * ||r_{k+1}|| < tol ||r_0|| or after max_iter iterations.
+ *   dobs_dev  : device seismogram-layout observed data d
+ *   q_out_dev : device [ns][nt][N] receives the solution x = q
+ *   precond   : esi_precond; ESI_PC_DIAG uses z = r / (lambda B^2) (flexible CG),
+ *               ESI_PC_LEARNED the network loaded by esi_pc_load
+ *   eps       : annihilator offset in metres (<= 0: dx)
+ *   report    : may be NULL
+ * Synchronises every iteration (reads 8 bytes per shot).  Returns ESI_ERR_NOT_CONVERGED
+ * (q valid) when some shot did not reach tol.
+ */
+ESI_API esi_status esi_cg_solve(esi_ctx *ctx, double lambda, double tol, int max_iter,
+                                const void *dobs_dev, void *q_out_dev, int precond, double eps,
+                                esi_cg_report *report);
+
+/* Load the learned preconditioner's weights (layout documented in esi_pc.h). */
+ESI_API esi_status esi_pc_load(esi_ctx *ctx, const void *weights_dev, size_t bytes);
+
+/* Static string for a status code. */
+ESI_API const char *esi_status_string(esi_status s);
+
+/* Last error message of a context ("" when none); valid until the next call. */
+ESI_API const char *esi_last_error(const esi_ctx *ctx);
+
+/* Number of kernels this context has launched since creation (for accounting). */
+ESI_API long long esi_launch_count(const esi_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ESI_H */

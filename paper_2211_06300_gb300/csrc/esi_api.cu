@@ -1,0 +1,1041 @@
+// C-ABI entry points of libesi: context set-up (operator, sponge, geometry lists), the
+// time loops of forward / adjoint modelling, the checkpointed gradient, the on-the-fly
+// DTFT and Algorithm 1 (CG) on the ESI normal equation.  Host code here only enqueues
+// kernels and moves a few scalars; every arithmetic step of the path runs on the GPU.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "esi_internal.h"
+
+using namespace esi;
+
+namespace {
+
+// 8th-order weights at offsets 1 and 3 (Fornberg 1988).  The Nyquist symbol of the
+// second difference is -4 (W1 + W3) / dx^2 per axis, which fixes the leapfrog CFL bound.
+constexpr double CFL_W1 = 8.0 / 5.0, CFL_W3 = 8.0 / 315.0;
+constexpr int ZCH3_HOST = 64;  // z chunk of the 3D kernel (must match fd3d.cu)
+
+struct DBuf {
+    void *p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    ~DBuf() {
+        if (p) cudaFree(p);
+    }
+    cudaError_t ensure(size_t bytes) {
+        if (bytes <= n && p) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+        cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+        if (e == cudaSuccess) n = bytes;
+        return e;
+    }
+    template <typename U>
+    U *as() const { return reinterpret_cast<U *>(p); }
+};
+
+struct HostPoint {
+    std::vector<long long> node;  // global dense node index (z, y, x)
+    std::vector<int> iz, iy, ix;
+    std::vector<double> w;        // interpolation weight
+};
+
+struct DevInj {
+    DBuf tile_ptr, cell, cptr, off0, tstride, w;
+    bool empty = true;
+};
+struct DevSmp {
+    DBuf tile_ptr, idx, gidx, w, off0, tstride, shot;
+    int nrec = 0;
+};
+
+}  // namespace
+
+struct esi_ctx {
+    esi_grid g{};
+    int ns = 0, nt = 0;
+    double dt = 0;
+    cudaStream_t st = nullptr;
+    long long N = 0, sst = 0;
+    int px = 0, esz = 0;
+    std::vector<double> src_xyz;
+    std::vector<long long> rec_off;
+    std::vector<double> rec_xyz;
+    double vmax = 0, vref = 0, kappa_max = 0;
+    int ntx = 0, nty = 1, ntz = 0, nzc = 1, ntiles = 0;
+    DBuf cc, kz, ky, kx, src_pos;
+    DevInj inj_src, inj_rec;
+    DevSmp smp_rec, smp_src;
+    DBuf u0, u1, a0, a1;           // forward / adjoint state pairs [ns][sst]
+    DBuf part, part2, scal;        // reduction partials, per-shot scalars
+    DBuf traces;                   // scratch seismogram [nt * total receivers]
+    DBuf cg_r, cg_p, cg_ap;        // CG work vectors
+    DBuf ckpt, ckpt_scale, absbits, stash, gacc, twid, dftacc;
+    long long total_rec = 0;
+    std::string err;
+    long long launches = 0;
+
+    esi_status fail(esi_status s, const std::string &m) {
+        err = m;
+        return s;
+    }
+};
+
+#define CK(expr)                                                                           \
+    do {                                                                                   \
+        cudaError_t _e = (expr);                                                           \
+        if (_e != cudaSuccess)                                                             \
+            return ctx->fail(_e == cudaErrorMemoryAllocation ? ESI_ERR_OOM : ESI_ERR_CUDA,  \
+                             std::string(#expr) + ": " + cudaGetErrorString(_e));         \
+    } while (0)
+
+#define CKL(expr)        \
+    do {                 \
+        CK(expr);        \
+        ++ctx->launches; \
+    } while (0)
+
+namespace {
+
+template <typename U>
+cudaError_t upload(DBuf &b, const std::vector<U> &v, cudaStream_t st) {
+    cudaError_t e = b.ensure(std::max<size_t>(v.size() * sizeof(U), 16));
+    if (e != cudaSuccess || v.empty()) return e;
+    return cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(U), cudaMemcpyHostToDevice, st);
+}
+
+// bilinear / trilinear weights of a point; nodes in z-major order; zero weights dropped
+bool point_weights(const esi_grid &g, const double *xyz, HostPoint &hp, int &iz0, int &iy0,
+                   int &ix0) {
+    hp = HostPoint();
+    double pos[3] = {xyz[2], xyz[1], xyz[0]};  // (z, y, x)
+    int n[3] = {g.nz, g.ny, g.nx};
+    int base[3] = {0, 0, 0};
+    std::vector<std::pair<int, double>> ax[3];
+    for (int a = 0; a < 3; ++a) {
+        if (a == 1 && g.ndim == 2) {
+            ax[a].push_back({0, 1.0});
+            continue;
+        }
+        const double f = pos[a] / g.dx;
+        const double fl = std::floor(f);
+        const int i0 = (int)fl;
+        const double w1 = f - fl;
+        base[a] = i0;
+        if (1.0 - w1 != 0.0) ax[a].push_back({i0, 1.0 - w1});
+        if (w1 != 0.0) ax[a].push_back({i0 + 1, w1});
+        for (auto &pw : ax[a])
+            if (pw.first < 0 || pw.first >= n[a]) return false;
+    }
+    iz0 = base[0];
+    iy0 = base[1];
+    ix0 = base[2];
+    for (auto &pz : ax[0])
+        for (auto &py : ax[1])
+            for (auto &pxw : ax[2]) {
+                hp.iz.push_back(pz.first);
+                hp.iy.push_back(py.first);
+                hp.ix.push_back(pxw.first);
+                hp.node.push_back(((long long)pz.first * g.ny + py.first) * g.nx + pxw.first);
+                hp.w.push_back(pz.second * py.second * pxw.second);
+            }
+    return true;
+}
+
+struct Contrib {
+    long long off0;
+    int tstride;
+    double w;
+};
+
+// tile index and local cell of a node for the step kernels
+void tile_of(const esi_ctx *c, int s, int iz, int iy, int ix, int &tile, int &cell) {
+    if (c->g.ndim == 2) {
+        const int bz = iz / TZ, bx = ix / TX;
+        tile = (s * c->ntz + bz) * c->ntx + bx;
+        cell = (iz - bz * TZ) * TX + (ix - bx * TX);
+    } else {
+        const int zc = iz / ZCH3_HOST, by = iy / TY3, bx = ix / TX3;
+        tile = ((s * c->nzc + zc) * c->nty + by) * c->ntx + bx;
+        cell = iz * (TX3 * TY3) + (iy - by * TY3) * TX3 + (ix - bx * TX3);
+    }
+}
+
+template <typename T>
+esi_status build_inj(esi_ctx *ctx, DevInj &out,
+                     const std::vector<std::vector<std::pair<HostPoint, Contrib>>> &per_shot) {
+    // per (tile) -> ordered map cell -> contributions
+    const int ntt = ctx->ns * ctx->ntiles;
+    std::vector<std::map<int, std::vector<Contrib>>> tiles(ntt);
+    for (int s = 0; s < ctx->ns; ++s)
+        for (auto &pc : per_shot[s]) {
+            const HostPoint &hp = pc.first;
+            for (size_t k = 0; k < hp.node.size(); ++k) {
+                int tile, cell;
+                tile_of(ctx, s, hp.iz[k], hp.iy[k], hp.ix[k], tile, cell);
+                Contrib c = pc.second;
+                c.w *= hp.w[k];
+                tiles[tile][cell].push_back(c);
+            }
+        }
+    std::vector<int> tile_ptr(ntt + 1, 0), cell, cptr(1, 0), tstr;
+    std::vector<long long> off0;
+    std::vector<T> w;
+    for (int t = 0; t < ntt; ++t) {
+        for (auto &kv : tiles[t]) {  // std::map: cells ascending (z-sorted in 3D)
+            cell.push_back(kv.first);
+            for (auto &c : kv.second) {
+                off0.push_back(c.off0);
+                tstr.push_back(c.tstride);
+                w.push_back(T(c.w));
+            }
+            cptr.push_back((int)off0.size());
+        }
+        tile_ptr[t + 1] = (int)cell.size();
+    }
+    out.empty = cell.empty();
+    CK(upload(out.tile_ptr, tile_ptr, ctx->st));
+    CK(upload(out.cell, cell, ctx->st));
+    CK(upload(out.cptr, cptr, ctx->st));
+    CK(upload(out.off0, off0, ctx->st));
+    CK(upload(out.tstride, tstr, ctx->st));
+    CK(upload(out.w, w, ctx->st));
+    return ESI_OK;
+}
+
+struct SmpHost {
+    int s;
+    HostPoint hp;
+    int iz0, iy0, ix0;
+    long long off0;
+    int tstride;
+    double scale;
+};
+
+template <typename T>
+esi_status build_smp(esi_ctx *ctx, DevSmp &out, const std::vector<SmpHost> &recs) {
+    const int ntt = ctx->ns * ctx->ntiles;
+    std::vector<std::vector<int>> by_tile(ntt);
+    for (size_t r = 0; r < recs.size(); ++r) {
+        int tile, cell;
+        tile_of(ctx, recs[r].s, recs[r].iz0, recs[r].iy0, recs[r].ix0, tile, cell);
+        by_tile[tile].push_back((int)r);
+    }
+    std::vector<int> tile_ptr(ntt + 1, 0), idx, tstr, shot;
+    std::vector<long long> gidx, off0;
+    std::vector<T> w;
+    for (int t = 0; t < ntt; ++t) {
+        for (int r : by_tile[t]) {
+            const SmpHost &h = recs[r];
+            const int lz0 = h.iz0 % TZ, lx0 = h.ix0 % TX;
+            const long long gbase = ((long long)h.iz0 * ctx->g.ny + h.iy0) * ctx->px + h.ix0;
+            const int sbase = (lz0 + HALO) * SW + (lx0 + HALO);
+            for (int j = 0; j < MAXP; ++j) {
+                if (j < (int)h.hp.node.size()) {
+                    const int dz = h.hp.iz[j] - h.iz0, dy = h.hp.iy[j] - h.iy0, dxx = h.hp.ix[j] - h.ix0;
+                    idx.push_back(sbase + dz * SW + dxx);
+                    gidx.push_back(((long long)h.hp.iz[j] * ctx->g.ny + h.hp.iy[j]) * ctx->px +
+                                   h.hp.ix[j]);
+                    (void)dy;
+                    w.push_back(T(h.hp.w[j] * h.scale));
+                } else {
+                    idx.push_back(sbase);
+                    gidx.push_back(gbase);
+                    w.push_back(T(0));
+                }
+            }
+            off0.push_back(h.off0);
+            tstr.push_back(h.tstride);
+            shot.push_back(h.s);
+        }
+        tile_ptr[t + 1] = (int)off0.size();
+    }
+    // 2D in-kernel sampling uses 4 points in (z0,x0),(z0,x1),(z1,x0),(z1,x1) order; the
+    // host lists hold only the nonzero ones in that order, padded with zero weights, so
+    // the sum order matches the node order of the definition.
+    out.nrec = (int)off0.size();
+    CK(upload(out.tile_ptr, tile_ptr, ctx->st));
+    CK(upload(out.idx, idx, ctx->st));
+    CK(upload(out.gidx, gidx, ctx->st));
+    CK(upload(out.w, w, ctx->st));
+    CK(upload(out.off0, off0, ctx->st));
+    CK(upload(out.tstride, tstr, ctx->st));
+    CK(upload(out.shot, shot, ctx->st));
+    return ESI_OK;
+}
+
+template <typename T>
+InjList<T> inj_view(const DevInj &d) {
+    InjList<T> l;
+    l.tile_ptr = d.tile_ptr.as<int>();
+    l.cell = d.cell.as<int>();
+    l.cptr = d.cptr.as<int>();
+    l.off0 = d.off0.as<long long>();
+    l.tstride = d.tstride.as<int>();
+    l.w = d.w.as<T>();
+    return l;
+}
+
+template <typename T>
+SmpList<T> smp_view(const DevSmp &d) {
+    SmpList<T> l;
+    l.tile_ptr = d.tile_ptr.as<int>();
+    l.idx = d.idx.as<int>();
+    l.gidx = d.gidx.as<long long>();
+    l.w = d.w.as<T>();
+    l.off0 = d.off0.as<long long>();
+    l.tstride = d.tstride.as<int>();
+    l.shot = d.shot.as<int>();
+    l.nrec = d.nrec;
+    return l;
+}
+
+template <typename T>
+StepArgs<T> base_args(esi_ctx *ctx) {
+    StepArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.nz = ctx->g.nz;
+    a.ny = ctx->g.ny;
+    a.nx = ctx->g.nx;
+    a.px = ctx->px;
+    a.sst = ctx->sst;
+    a.N = ctx->N;
+    a.fst = ctx->N * ctx->nt;
+    a.ntx = ctx->ntx;
+    a.nty = ctx->nty;
+    a.ntz = ctx->ntz;
+    a.cc = ctx->cc.as<T>();
+    a.kz = ctx->kz.as<T>();
+    a.ky = ctx->ky.as<T>();
+    a.kx = ctx->kx.as<T>();
+    a.dx2 = T(ctx->g.dx * ctx->g.dx);
+    a.dx = T(ctx->g.dx);
+    a.src_pos = ctx->src_pos.as<double>();
+    a.ns = ctx->ns;
+    a.tout = -1;
+    return a;
+}
+
+// One step of either kernel.  In 3D the sampling of the input state is a gather launch.
+template <typename T>
+esi_status step(esi_ctx *ctx, unsigned flags, const StepArgs<T> &a) {
+    if (ctx->g.ndim == 2) {
+        CKL(launch_step2<T>(flags, a, ctx->ns, ctx->st));
+    } else {
+        if ((flags & F_SMP) && a.tout >= 0)
+            CKL(launch_sample_global<T>(a.smp, a.cur, ctx->sst, a.smp_out, a.tout, ctx->st));
+        CKL(launch_step3<T>(flags & ~F_SMP, a, ctx->ns, ctx->st));
+    }
+    return ESI_OK;
+}
+
+template <typename T>
+esi_status setup_model(esi_ctx *ctx, const void *vel, bool first) {
+    const int nblk = 1024;
+    CK(ctx->part.ensure(sizeof(double) * std::max<long long>(nblk, 1)));
+    CK(cudaMemsetAsync(ctx->cc.p, 0, ctx->sst * sizeof(T), ctx->st));
+    CKL(launch_setup_cc<T>(reinterpret_cast<const T *>(vel), ctx->cc.as<T>(), ctx->g.nz, ctx->g.ny,
+                           ctx->g.nx, ctx->px, ctx->dt, ctx->g.dx, ctx->part.as<double>(), nblk,
+                           ctx->st));
+    std::vector<double> vm(nblk);
+    CK(cudaMemcpyAsync(vm.data(), ctx->part.p, nblk * sizeof(double), cudaMemcpyDeviceToHost,
+                       ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    double vmax = 0;
+    for (double v : vm) vmax = std::max(vmax, v);
+    if (!(vmax > 0) || !std::isfinite(vmax))
+        return ctx->fail(ESI_ERR_ARG, "velocity must be positive and finite");
+    const double limit = std::sqrt(1.0 / (ctx->g.ndim * (CFL_W1 + CFL_W3)));
+    if (vmax * ctx->dt / ctx->g.dx > limit)
+        return ctx->fail(ESI_ERR_CFL, "v_max dt / dx = " + std::to_string(vmax * ctx->dt / ctx->g.dx) +
+                                          " exceeds the stability limit " + std::to_string(limit));
+    ctx->vmax = vmax;
+    if (first) {
+        ctx->vref = ctx->g.sponge_vref > 0 ? ctx->g.sponge_vref : vmax;
+        // sponge: kappa = eta dt / 2, eta = eta_max sum_axes (d / nb)^2,
+        // eta_max = 3 vref ln(1/R) / (2 nb dx)
+        const int nb = ctx->g.nb;
+        const double eta_max =
+            nb > 0 ? 3.0 * ctx->vref * std::log(1.0 / ctx->g.sponge_R) / (2.0 * nb * ctx->g.dx) : 0.0;
+        ctx->kappa_max = eta_max * ctx->dt / 2.0;
+        auto prof = [&](int n, bool used) {
+            std::vector<T> p(std::max(n, 1), T(0));
+            if (!used || nb <= 0) return p;
+            for (int i = 0; i < n; ++i) {
+                const int d = std::max(std::max(nb - i, i - (n - 1 - nb)), 0);
+                const double r = double(d) / nb;
+                p[i] = T(ctx->kappa_max * r * r);
+            }
+            return p;
+        };
+        CK(upload(ctx->kz, prof(ctx->g.nz, true), ctx->st));
+        CK(upload(ctx->ky, prof(ctx->g.ny, ctx->g.ndim == 3), ctx->st));
+        CK(upload(ctx->kx, prof(ctx->g.nx, true), ctx->st));
+    }
+    return ESI_OK;
+}
+
+template <typename T>
+esi_status setup_geometry(esi_ctx *ctx) {
+    const esi_grid &g = ctx->g;
+    const int d = g.ndim;
+    std::vector<std::vector<std::pair<HostPoint, Contrib>>> src_inj(ctx->ns), rec_inj(ctx->ns);
+    std::vector<SmpHost> rec_smp, src_smp;
+    for (int s = 0; s < ctx->ns; ++s) {
+        HostPoint hp;
+        int iz0, iy0, ix0;
+        if (!point_weights(g, &ctx->src_xyz[3 * s], hp, iz0, iy0, ix0))
+            return ctx->fail(ESI_ERR_ARG, "source " + std::to_string(s) + " outside the grid");
+        // forward injection carries f_n w / dx^d; the kernel adds dx^2 * q
+        src_inj[s].push_back({hp, Contrib{(long long)s * ctx->nt, 1, std::pow(g.dx, 2 - d)}});
+        src_smp.push_back(SmpHost{s, hp, iz0, iy0, ix0, (long long)s * ctx->nt, 1, std::pow(g.dx, -d)});
+        const int nr = (int)(ctx->rec_off[s + 1] - ctx->rec_off[s]);
+        for (int r = 0; r < nr; ++r) {
+            const double *xyz = &ctx->rec_xyz[3 * (ctx->rec_off[s] + r)];
+            if (!point_weights(g, xyz, hp, iz0, iy0, ix0))
+                return ctx->fail(ESI_ERR_ARG, "receiver " + std::to_string(r) + " of shot " +
+                                                  std::to_string(s) + " outside the grid");
+            const long long off0 = (long long)ctx->nt * ctx->rec_off[s] + r;
+            rec_inj[s].push_back({hp, Contrib{off0, nr, g.dx * g.dx}});
+            rec_smp.push_back(SmpHost{s, hp, iz0, iy0, ix0, off0, nr, 1.0});
+        }
+    }
+    esi_status e;
+    if ((e = build_inj<T>(ctx, ctx->inj_src, src_inj)) != ESI_OK) return e;
+    if ((e = build_inj<T>(ctx, ctx->inj_rec, rec_inj)) != ESI_OK) return e;
+    if ((e = build_smp<T>(ctx, ctx->smp_rec, rec_smp)) != ESI_OK) return e;
+    if ((e = build_smp<T>(ctx, ctx->smp_src, src_smp)) != ESI_OK) return e;
+    CK(upload(ctx->src_pos, ctx->src_xyz, ctx->st));
+    return ESI_OK;
+}
+
+template <typename T>
+esi_status ensure_states(esi_ctx *ctx, bool adj) {
+    const size_t b = (size_t)ctx->ns * ctx->sst * sizeof(T);
+    CK(ctx->u0.ensure(b));
+    CK(ctx->u1.ensure(b));
+    if (adj) {
+        CK(ctx->a0.ensure(b));
+        CK(ctx->a1.ensure(b));
+    }
+    return ESI_OK;
+}
+
+// ------------------------------------------------------------------ forward modelling
+// Runs steps [n0, n1) starting from states (cur, po) = (u_{n0}, u_{n0-1}); on return
+// cur holds u_{n1}.  Sampling of the inputs writes traces[n-1].
+template <typename T>
+esi_status fwd_loop(esi_ctx *ctx, StepArgs<T> a, unsigned flags, T *&cur, T *&po, int n0,
+                    int n1, std::vector<std::pair<int, int>> *ckpt_at = nullptr) {
+    (void)ckpt_at;
+    for (int n = n0; n < n1; ++n) {
+        a.cur = cur;
+        a.po = po;
+        a.n = n;
+        a.tin = n;
+        a.tout = n - 1;
+        a.slot_w = n - n0;
+        esi_status e = step<T>(ctx, flags, a);
+        if (e != ESI_OK) return e;
+        std::swap(cur, po);
+    }
+    return ESI_OK;
+}
+
+template <typename T>
+esi_status forward_impl(esi_ctx *ctx, const void *wavelet, const void *ext, void *traces,
+                        const double *freqs, int nf, T *dft_acc) {
+    esi_status e = ensure_states<T>(ctx, false);
+    if (e != ESI_OK) return e;
+    CK(cudaMemsetAsync(ctx->u0.p, 0, ctx->u0.n, ctx->st));
+    CK(cudaMemsetAsync(ctx->u1.p, 0, ctx->u1.n, ctx->st));
+    StepArgs<T> a = base_args<T>(ctx);
+    unsigned flags = F_SMP;
+    if (wavelet) {
+        flags |= F_PT;
+        a.inj = inj_view<T>(ctx->inj_src);
+        a.inj_trace = reinterpret_cast<const T *>(wavelet);
+    }
+    if (ext) {
+        flags |= F_EXT;
+        a.ext = reinterpret_cast<const T *>(ext);
+    }
+    if (!wavelet && !ext) return ctx->fail(ESI_ERR_ARG, "no source given");
+    a.smp = smp_view<T>(ctx->smp_rec);
+    T *tr = reinterpret_cast<T *>(traces);
+    if (!tr) {
+        CK(ctx->traces.ensure(std::max<size_t>((size_t)ctx->total_rec * ctx->nt * sizeof(T), 16)));
+        tr = ctx->traces.as<T>();
+    }
+    a.smp_out = tr;
+    if (nf > 0) {
+        flags |= F_DFT;
+        std::vector<T> tw((size_t)ctx->nt * nf * 2);
+        for (int n = 0; n < ctx->nt; ++n)
+            for (int m = 0; m < nf; ++m) {
+                const double ph = 2.0 * M_PI * freqs[m] * (n + 1) * ctx->dt;
+                tw[((size_t)n * nf + m) * 2] = T(std::cos(ph));
+                tw[((size_t)n * nf + m) * 2 + 1] = T(std::sin(ph));
+            }
+        CK(upload(ctx->twid, tw, ctx->st));
+        a.nf = nf;
+        a.twid = ctx->twid.as<T>();
+        a.dft = dft_acc;
+    }
+    T *cur = ctx->u0.as<T>(), *po = ctx->u1.as<T>();
+    e = fwd_loop<T>(ctx, a, flags, cur, po, 0, ctx->nt);
+    if (e != ESI_OK) return e;
+    CKL(launch_sample_global<T>(a.smp, cur, ctx->sst, tr, ctx->nt - 1, ctx->st));
+    return ESI_OK;
+}
+
+// ------------------------------------------------------------------ adjoint modelling
+// Time-reversed run: for j = j1 .. j0+1 computes lambda_j from (lambda_{j+1}, lambda_{j+2})
+// with source R^T e_{j-1}.  Epilogue writes index j-1 of the dense outputs.
+template <typename T>
+esi_status adj_loop(esi_ctx *ctx, StepArgs<T> a, unsigned flags, T *&cur, T *&po, int j1,
+                    int j0, bool sample_src) {
+    for (int j = j1; j > j0; --j) {
+        a.cur = cur;
+        a.po = po;
+        a.n = j - 1;
+        a.tin = j - 1;
+        a.nout = j - 1;
+        a.tout = (sample_src && j <= ctx->nt - 1) ? j : -1;
+        a.slot_r = (j - 1) - j0;
+        esi_status e = step<T>(ctx, flags, a);
+        if (e != ESI_OK) return e;
+        std::swap(cur, po);
+    }
+    return ESI_OK;
+}
+
+template <typename T>
+esi_status adjoint_impl(esi_ctx *ctx, const void *traces, void *ext_out, void *wav_out) {
+    esi_status e = ensure_states<T>(ctx, true);
+    if (e != ESI_OK) return e;
+    CK(cudaMemsetAsync(ctx->a0.p, 0, ctx->a0.n, ctx->st));
+    CK(cudaMemsetAsync(ctx->a1.p, 0, ctx->a1.n, ctx->st));
+    StepArgs<T> a = base_args<T>(ctx);
+    unsigned flags = F_PT;
+    a.inj = inj_view<T>(ctx->inj_rec);
+    a.inj_trace = reinterpret_cast<const T *>(traces);
+    if (ext_out) {
+        flags |= F_OUT;
+        a.fout = reinterpret_cast<T *>(ext_out);
+    }
+    if (wav_out) {
+        flags |= F_SMP;
+        a.smp = smp_view<T>(ctx->smp_src);
+        a.smp_out = reinterpret_cast<T *>(wav_out);
+    }
+    T *cur = ctx->a0.as<T>(), *po = ctx->a1.as<T>();
+    e = adj_loop<T>(ctx, a, flags, cur, po, ctx->nt, 0, wav_out != nullptr);
+    if (e != ESI_OK) return e;
+    if (wav_out)
+        CKL(launch_sample_global<T>(a.smp, cur, ctx->sst, a.smp_out, 0, ctx->st));
+    return ESI_OK;
+}
+
+// ------------------------------------------------------------------ gradient
+template <typename T>
+esi_status ckpt_store(esi_ctx *ctx, int kind, int slot, const T *cur, const T *prev) {
+    const long long len = ctx->sst;
+    const int ns = ctx->ns;
+    const T *src[2] = {cur, prev};
+    for (int h = 0; h < 2; ++h) {
+        const long long idx = (long long)(2 * slot + h) * ns;  // in units of shot states
+        if (kind == ESI_CKPT_F32) {
+            CK(cudaMemcpyAsync(ctx->ckpt.as<T>() + idx * len, src[h], ns * len * sizeof(T),
+                               cudaMemcpyDeviceToDevice, ctx->st));
+        } else {
+            CKL(launch_absmax<T>(src[h], len, len, ns, ctx->absbits.as<unsigned>(), ctx->st));
+            CKL(launch_encode<T>(src[h], len, len, ns, kind, ctx->absbits.as<unsigned>(),
+                                 ctx->ckpt.as<uint16_t>() + idx * len,
+                                 ctx->ckpt_scale.as<float>() + idx, ctx->st));
+        }
+    }
+    return ESI_OK;
+}
+
+template <typename T>
+esi_status ckpt_load(esi_ctx *ctx, int kind, int slot, T *cur, T *prev) {
+    const long long len = ctx->sst;
+    const int ns = ctx->ns;
+    T *dst[2] = {cur, prev};
+    for (int h = 0; h < 2; ++h) {
+        const long long idx = (long long)(2 * slot + h) * ns;
+        if (kind == ESI_CKPT_F32) {
+            CK(cudaMemcpyAsync(dst[h], ctx->ckpt.as<T>() + idx * len, ns * len * sizeof(T),
+                               cudaMemcpyDeviceToDevice, ctx->st));
+        } else {
+            CKL(launch_decode<T>(ctx->ckpt.as<uint16_t>() + idx * len, len, len, ns, kind,
+                                 ctx->ckpt_scale.as<float>() + idx, dst[h], ctx->st));
+        }
+    }
+    return ESI_OK;
+}
+
+template <typename T>
+esi_status gradient_impl(esi_ctx *ctx, const void *wavelet, const void *ext, const void *dobs,
+                         const void *adj, const esi_grad_opts *o, void *grad, double *misfit) {
+    const long long N = ctx->N;
+    const int ns = ctx->ns, nt = ctx->nt;
+    esi_status e = ensure_states<T>(ctx, true);
+    if (e != ESI_OK) return e;
+    CK(ctx->gacc.ensure((size_t)ns * N * sizeof(T)));
+    CK(cudaMemsetAsync(ctx->gacc.p, 0, (size_t)ns * N * sizeof(T), ctx->st));
+    const T eps = T(o->eps > 0 ? o->eps : ctx->g.dx);
+    double extra = 1.0;
+    if (o->mode == ESI_GRAD_SADDLE_POINT) {
+        if (!ext) return ctx->fail(ESI_ERR_ARG, "saddle-point gradient needs the extended source q");
+        CK(cudaMemsetAsync(ctx->u0.p, 0, ctx->u0.n, ctx->st));
+        CK(cudaMemsetAsync(ctx->u1.p, 0, ctx->u1.n, ctx->st));
+        StepArgs<T> a = base_args<T>(ctx);
+        a.ext = reinterpret_cast<const T *>(ext);
+        a.grad = ctx->gacc.as<T>();
+        a.eps = eps;
+        T *cur = ctx->u0.as<T>(), *po = ctx->u1.as<T>();
+        e = fwd_loop<T>(ctx, a, F_EXT | F_SAD, cur, po, 0, nt);
+        if (e != ESI_OK) return e;
+        extra = -o->beta;
+    } else {
+        if (!wavelet && !ext) return ctx->fail(ESI_ERR_ARG, "no source given");
+        if (!adj && !dobs) return ctx->fail(ESI_ERR_ARG, "need observed data or an adjoint source");
+        const int K = std::max(1, o->ckpt_every);
+        const int nseg = (nt + K - 1) / K;
+        const int kind = o->ckpt_kind;
+        const size_t csz = kind == ESI_CKPT_F32 ? sizeof(T) : 2;
+        CK(ctx->ckpt.ensure((size_t)nseg * 2 * ns * ctx->sst * csz));
+        CK(ctx->ckpt_scale.ensure(sizeof(float) * nseg * 2 * ns));
+        CK(ctx->absbits.ensure(sizeof(unsigned) * ns));
+        CK(ctx->stash.ensure((size_t)K * ns * N * sizeof(T)));
+        CK(ctx->traces.ensure(std::max<size_t>((size_t)ctx->total_rec * nt * sizeof(T), 16)));
+        // 1) forward with checkpoints (u_{n0}, u_{n0-1}) at n0 = k K, traces into scratch
+        CK(cudaMemsetAsync(ctx->u0.p, 0, ctx->u0.n, ctx->st));
+        CK(cudaMemsetAsync(ctx->u1.p, 0, ctx->u1.n, ctx->st));
+        StepArgs<T> a = base_args<T>(ctx);
+        unsigned fflags = 0;
+        if (wavelet) {
+            fflags |= F_PT;
+            a.inj = inj_view<T>(ctx->inj_src);
+            a.inj_trace = reinterpret_cast<const T *>(wavelet);
+        }
+        if (ext) {
+            fflags |= F_EXT;
+            a.ext = reinterpret_cast<const T *>(ext);
+        }
+        T *tr = ctx->traces.as<T>();
+        T *cur = ctx->u0.as<T>(), *po = ctx->u1.as<T>();
+        a.smp = smp_view<T>(ctx->smp_rec);  // in VJP mode the traces are not used
+        a.smp_out = tr;
+        for (int sg = 0; sg < nseg; ++sg) {
+            const int n0 = sg * K, n1 = std::min(nt, n0 + K);
+            e = ckpt_store<T>(ctx, kind, sg, cur, po);
+            if (e != ESI_OK) return e;
+            if (adj && sg + 1 == nseg) break;  // the last segment is recomputed anyway
+            e = fwd_loop<T>(ctx, a, fflags | F_SMP, cur, po, n0, n1);
+            if (e != ESI_OK) return e;
+        }
+        const T *eres = reinterpret_cast<const T *>(adj);
+        if (!adj) {
+            CKL(launch_sample_global<T>(a.smp, cur, ctx->sst, tr, nt - 1, ctx->st));
+            const long long len = ctx->total_rec * nt;
+            const int nblk = 1024;
+            CK(ctx->part.ensure(sizeof(double) * nblk));
+            CK(ctx->scal.ensure(sizeof(double) * 8));
+            CKL(launch_residual<T>(tr, reinterpret_cast<const T *>(dobs), len, ctx->part.as<double>(),
+                                   nblk, ctx->st));
+            CKL(launch_reduce_partials(ctx->part.as<double>(), nblk, 1, ctx->scal.as<double>(), ctx->st));
+            eres = tr;
+        }
+        // 2) backward: per segment, recompute with stash, then adjoint with correlation
+        CK(cudaMemsetAsync(ctx->a0.p, 0, ctx->a0.n, ctx->st));
+        CK(cudaMemsetAsync(ctx->a1.p, 0, ctx->a1.n, ctx->st));
+        T *acur = ctx->a0.as<T>(), *apo = ctx->a1.as<T>();
+        StepArgs<T> b = base_args<T>(ctx);
+        b.inj = inj_view<T>(ctx->inj_rec);
+        b.inj_trace = eres;
+        b.grad = ctx->gacc.as<T>();
+        b.stash_r = ctx->stash.as<T>();
+        a.stash_w = ctx->stash.as<T>();
+        a.smp = SmpList<T>();
+        for (int sg = nseg - 1; sg >= 0; --sg) {
+            const int n0 = sg * K, n1 = std::min(nt, n0 + K);
+            T *fc = ctx->u0.as<T>(), *fp = ctx->u1.as<T>();
+            e = ckpt_load<T>(ctx, kind, sg, fc, fp);
+            if (e != ESI_OK) return e;
+            e = fwd_loop<T>(ctx, a, fflags | F_STW, fc, fp, n0, n1);
+            if (e != ESI_OK) return e;
+            e = adj_loop<T>(ctx, b, F_PT | F_GRD, acur, apo, n1, n0, false);
+            if (e != ESI_OK) return e;
+        }
+        if (misfit && !adj) {
+            CK(cudaMemcpyAsync(misfit, ctx->scal.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+        }
+    }
+    CKL(launch_grad_finalize<T>(ctx->gacc.as<T>(), ns, N, ctx->cc.as<T>(), ctx->g.nz, ctx->g.ny,
+                                ctx->g.nx, ctx->px, nullptr, ctx->dt, ctx->g.dx, extra, o->param,
+                                reinterpret_cast<T *>(grad), ctx->st));
+    if (misfit && !adj && o->mode != ESI_GRAD_SADDLE_POINT) CK(cudaStreamSynchronize(ctx->st));
+    return ESI_OK;
+}
+
+// ------------------------------------------------------------------ DTFT
+template <typename T>
+esi_status dft_impl(esi_ctx *ctx, const void *wavelet, const void *ext, const double *freqs,
+                    int nf, void *out, int kind, float *scales, void *traces) {
+    if (nf <= 0 || !freqs || !out) return ctx->fail(ESI_ERR_ARG, "need frequencies and an output");
+    const size_t accb = (size_t)ctx->ns * nf * ctx->N * 2 * sizeof(T);
+    T *acc;
+    if (kind == ESI_DFT_C64) {
+        acc = reinterpret_cast<T *>(out);
+    } else if (kind == ESI_DFT_C32_HALF) {
+        if (!scales) return ctx->fail(ESI_ERR_ARG, "half output needs a scales array");
+        CK(ctx->dftacc.ensure(accb));
+        acc = ctx->dftacc.as<T>();
+    } else {
+        return ctx->fail(ESI_ERR_ARG, "unknown DTFT output kind");
+    }
+    CK(cudaMemsetAsync(acc, 0, accb, ctx->st));
+    esi_status e = forward_impl<T>(ctx, wavelet, ext, traces, freqs, nf, acc);
+    if (e != ESI_OK) return e;
+    if (kind == ESI_DFT_C32_HALF) {
+        CK(ctx->absbits.ensure(sizeof(unsigned) * ctx->ns * nf));
+        CK(ctx->ckpt_scale.ensure(std::max(ctx->ckpt_scale.n, sizeof(float) * ctx->ns * nf)));
+        CKL(launch_dft_to_half<T>(acc, ctx->N, ctx->ns, nf, out, ctx->absbits.as<unsigned>(),
+                                  ctx->ckpt_scale.as<float>(), ctx->st));
+        ++ctx->launches;
+        CK(cudaMemcpyAsync(scales, ctx->ckpt_scale.p, sizeof(float) * ctx->ns * nf,
+                           cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+    }
+    return ESI_OK;
+}
+
+// ------------------------------------------------------------------ CG (Algorithm 1)
+template <typename T>
+esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const void *dobs,
+                   void *q_out, int precond, double eps_in, esi_cg_report *rep) {
+    using clk = std::chrono::steady_clock;
+    const auto t_start = clk::now();
+    double ms_mv = 0, ms_vec = 0;
+    const int ns = ctx->ns, nt = ctx->nt;
+    const long long len = ctx->N * nt;  // one space-time vector per shot
+    if (precond != ESI_PC_NONE)
+        return ctx->fail(ESI_ERR_UNSUPPORTED, "only the unpreconditioned solver is available");
+    if (max_iter < 1) return ctx->fail(ESI_ERR_ARG, "max_iter must be >= 1");
+    esi_status e = ensure_states<T>(ctx, true);
+    if (e != ESI_OK) return e;
+    const size_t vb = (size_t)ns * len * sizeof(T);
+    CK(ctx->cg_r.ensure(vb));
+    CK(ctx->cg_p.ensure(vb));
+    CK(ctx->cg_ap.ensure(vb));
+    CK(ctx->traces.ensure(std::max<size_t>((size_t)ctx->total_rec * nt * sizeof(T), 16)));
+    const int nblk_step = ctx->g.ndim == 2 ? ctx->ntx * ctx->ntz : ctx->ntx * ctx->nty * ctx->nzc;
+    const int nblk_vec = 1184;  // 8 x 148
+    CK(ctx->part.ensure(sizeof(double) * (size_t)ns * std::max(nblk_step, nblk_vec)));
+    // scalars: rr_old[ns] rr_new[ns] pap[ns] alpha[ns] beta[ns] | ints: active[ns] bad[ns]
+    CK(ctx->scal.ensure(sizeof(double) * 5 * ns + sizeof(int) * 2 * ns));
+    double *rr_old = ctx->scal.as<double>(), *rr_new = rr_old + ns, *pap = rr_new + ns,
+           *alpha = pap + ns, *beta = alpha + ns;
+    int *active = reinterpret_cast<int *>(beta + ns), *bad = active + ns;
+    T *x = reinterpret_cast<T *>(q_out), *r = ctx->cg_r.as<T>(), *p = ctx->cg_p.as<T>(),
+      *ap = ctx->cg_ap.as<T>(), *tr = ctx->traces.as<T>();
+    const T eps = T(eps_in > 0 ? eps_in : ctx->g.dx);
+    std::vector<int> h_active(ns, 1), h_bad(ns, 0), iters(ns, 0);
+    CK(cudaMemcpyAsync(active, h_active.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemsetAsync(bad, 0, sizeof(int) * ns, ctx->st));
+    CK(cudaMemsetAsync(x, 0, vb, ctx->st));
+    // b = S^T d, written straight into r (x0 = 0, r0 = b)
+    e = adjoint_impl<T>(ctx, dobs, r, nullptr);
+    if (e != ESI_OK) return e;
+    CKL(launch_dot<T>(r, r, len, len, ns, ctx->part.as<double>(), nblk_vec, nullptr, ctx->st));
+    CKL(launch_reduce_partials(ctx->part.as<double>(), nblk_vec, ns, rr_old, ctx->st));
+    std::vector<double> rr0(ns), rrn(ns);
+    CK(cudaMemcpyAsync(rr0.data(), rr_old, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    const int hist_cap = rep ? rep->max_hist : 0;
+    for (int s = 0; s < ns; ++s)
+        if (!(rr0[s] > 0)) h_active[s] = 0;  // b = 0: x = 0 is exact
+    CK(cudaMemcpyAsync(active, h_active.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, ctx->st));
+    int k;
+    bool any_bad = false;
+    for (k = 0; k < max_iter; ++k) {
+        const auto t0 = clk::now();
+        // forward half of the product, fused with p = r + beta p (p0 = r0)
+        CK(cudaMemsetAsync(ctx->u0.p, 0, ctx->u0.n, ctx->st));
+        CK(cudaMemsetAsync(ctx->u1.p, 0, ctx->u1.n, ctx->st));
+        StepArgs<T> a = base_args<T>(ctx);
+        a.active = active;
+        a.cg_r = r;
+        a.cg_p = p;
+        a.cg_beta = beta;
+        a.cg_first = k == 0;
+        a.smp = smp_view<T>(ctx->smp_rec);
+        a.smp_out = tr;
+        T *cur = ctx->u0.as<T>(), *po = ctx->u1.as<T>();
+        e = fwd_loop<T>(ctx, a, F_CGP | F_SMP, cur, po, 0, nt);
+        if (e != ESI_OK) return e;
+        CKL(launch_sample_global<T>(a.smp, cur, ctx->sst, tr, nt - 1, ctx->st));
+        // adjoint half: Ap = S^T (S p) + lambda B^2 p, with <p, Ap> partials
+        CK(cudaMemsetAsync(ctx->a0.p, 0, ctx->a0.n, ctx->st));
+        CK(cudaMemsetAsync(ctx->a1.p, 0, ctx->a1.n, ctx->st));
+        CK(cudaMemsetAsync(ctx->part.p, 0, sizeof(double) * (size_t)ns * nblk_step, ctx->st));
+        StepArgs<T> b = base_args<T>(ctx);
+        b.active = active;
+        b.inj = inj_view<T>(ctx->inj_rec);
+        b.inj_trace = tr;
+        b.ap = ap;
+        b.ap_p = p;
+        b.dot_part = ctx->part.as<double>();
+        b.pen = T(lambda);
+        b.eps = eps;
+        T *acur = ctx->a0.as<T>(), *apo = ctx->a1.as<T>();
+        e = adj_loop<T>(ctx, b, F_PT | F_AP, acur, apo, nt, 0, false);
+        if (e != ESI_OK) return e;
+        CKL(launch_reduce_partials(ctx->part.as<double>(), nblk_step, ns, pap, ctx->st));
+        CKL(launch_cg_alpha(rr_old, pap, alpha, bad, active, ns, ctx->st));
+        const auto t1 = clk::now();
+        CKL(launch_cg_update<T>(x, r, p, ap, len, len, ns, alpha, active, ctx->part.as<double>(),
+                                nblk_vec, ctx->st));
+        CKL(launch_reduce_partials(ctx->part.as<double>(), nblk_vec, ns, rr_new, ctx->st));
+        CK(cudaMemcpyAsync(rrn.data(), rr_new, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaMemcpyAsync(h_bad.data(), bad, sizeof(int) * ns, cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        const auto t2 = clk::now();
+        ms_mv += std::chrono::duration<double, std::milli>(t1 - t0).count();
+        ms_vec += std::chrono::duration<double, std::milli>(t2 - t1).count();
+        bool any = false;
+        for (int s = 0; s < ns; ++s) {
+            if (!h_active[s]) continue;
+            if (h_bad[s]) {
+                any_bad = true;
+                h_active[s] = 0;
+                continue;
+            }
+            iters[s] = k + 1;
+            const double rel = std::sqrt(rrn[s] / rr0[s]);
+            if (rep && rep->rel_res && k < hist_cap) rep->rel_res[(size_t)s * hist_cap + k] = rel;
+            if (std::sqrt(rrn[s]) < tol * std::sqrt(rr0[s]) || k == max_iter - 1)
+                h_active[s] = 0;  // exit loop for this shot (Algorithm 1's stopping test)
+            else
+                any = true;
+        }
+        if (!any) break;
+        CK(cudaMemcpyAsync(active, h_active.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, ctx->st));
+        CKL(launch_cg_beta(rr_old, rr_new, beta, active, ns, ctx->st));
+    }
+    bool conv = true;
+    for (int s = 0; s < ns; ++s)
+        if (rr0[s] > 0 && !(iters[s] > 0 && std::sqrt(rrn[s]) < tol * std::sqrt(rr0[s]))) conv = false;
+    if (rep) {
+        int mx = 0;
+        for (int s = 0; s < ns; ++s) {
+            mx = std::max(mx, iters[s]);
+            if (rep->iters) rep->iters[s] = iters[s];
+        }
+        rep->iters_max = mx;
+        rep->converged = conv ? 1 : 0;
+        rep->ms_matvec = ms_mv;
+        rep->ms_vector = ms_vec;
+        rep->ms_precond = 0;
+        rep->ms_total = std::chrono::duration<double, std::milli>(clk::now() - t_start).count();
+    }
+    if (any_bad) return ctx->fail(ESI_ERR_BREAKDOWN, "CG breakdown: p^T A p <= 0 or non-finite");
+    return conv ? ESI_OK : ESI_ERR_NOT_CONVERGED;
+}
+
+template <typename T>
+esi_status create_impl(esi_ctx *ctx, const void *vel) {
+    esi_status e = setup_model<T>(ctx, vel, true);
+    if (e != ESI_OK) return e;
+    e = setup_geometry<T>(ctx);
+    if (e != ESI_OK) return e;
+    CK(cudaStreamSynchronize(ctx->st));
+    return ESI_OK;
+}
+
+}  // namespace
+
+#define DISPATCH(ctx, call)                                          \
+    ((ctx)->g.dtype == ESI_F64 ? call<double> : call<float>)
+
+extern "C" {
+
+ESI_API const char *esi_status_string(esi_status s) {
+    switch (s) {
+        case ESI_OK: return "ok";
+        case ESI_ERR_ARG: return "invalid argument";
+        case ESI_ERR_CFL: return "time step above the stability limit";
+        case ESI_ERR_OOM: return "device allocation failed";
+        case ESI_ERR_CUDA: return "CUDA error";
+        case ESI_ERR_BREAKDOWN: return "CG breakdown";
+        case ESI_ERR_TIMEOUT: return "device wait timed out";
+        case ESI_ERR_NOT_CONVERGED: return "CG did not reach the tolerance";
+        case ESI_ERR_UNSUPPORTED: return "unsupported option";
+    }
+    return "unknown status";
+}
+
+namespace {
+thread_local std::string g_create_error;  // message of the last failed esi_create
+}
+
+ESI_API const char *esi_last_error(const esi_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+ESI_API long long esi_launch_count(const esi_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+ESI_API esi_status esi_create(esi_ctx **out, const esi_grid *grid, const esi_geometry *geom,
+                              const void *velocity_dev, double dt, int nt, void *stream) {
+    g_create_error.clear();
+    if (!out || !grid || !geom || !velocity_dev) return ESI_ERR_ARG;
+    *out = nullptr;
+    const esi_grid &g = *grid;
+    if ((g.ndim != 2 && g.ndim != 3) || g.nz < 1 || g.nx < 1 || g.ny < 1 ||
+        (g.ndim == 2 && g.ny != 1) || !(g.dx > 0) || g.nb < 0 ||
+        (g.nb > 0 && !(g.sponge_R > 0 && g.sponge_R < 1)) ||
+        (g.dtype != ESI_F32 && g.dtype != ESI_F64) || !(dt > 0) || nt < 1 || geom->ns < 1 ||
+        !geom->src_xyz || !geom->rec_offset || (geom->rec_offset[geom->ns] > 0 && !geom->rec_xyz))
+        return ESI_ERR_ARG;
+    for (int s = 0; s < geom->ns; ++s)
+        if (geom->rec_offset[s + 1] < geom->rec_offset[s]) return ESI_ERR_ARG;
+    std::unique_ptr<esi_ctx> ctx(new esi_ctx());
+    ctx->g = g;
+    ctx->ns = geom->ns;
+    ctx->nt = nt;
+    ctx->dt = dt;
+    ctx->st = reinterpret_cast<cudaStream_t>(stream);
+    ctx->esz = g.dtype == ESI_F64 ? 8 : 4;
+    ctx->N = (long long)g.nz * g.ny * g.nx;
+    ctx->px = (g.nx + 31) / 32 * 32;
+    ctx->sst = (long long)g.nz * g.ny * ctx->px;
+    ctx->src_xyz.assign(geom->src_xyz, geom->src_xyz + 3 * geom->ns);
+    ctx->rec_off.assign(geom->rec_offset, geom->rec_offset + geom->ns + 1);
+    ctx->total_rec = ctx->rec_off[ctx->ns];
+    ctx->rec_xyz.assign(geom->rec_xyz, geom->rec_xyz + 3 * ctx->total_rec);
+    if (g.ndim == 2) {
+        ctx->ntx = (g.nx + TX - 1) / TX;
+        ctx->ntz = (g.nz + TZ - 1) / TZ;
+        ctx->nty = 1;
+        ctx->nzc = 1;
+        ctx->ntiles = ctx->ntx * ctx->ntz;
+    } else {
+        ctx->ntx = (g.nx + TX3 - 1) / TX3;
+        ctx->nty = (g.ny + TY3 - 1) / TY3;
+        ctx->nzc = (g.nz + ZCH3_HOST - 1) / ZCH3_HOST;
+        ctx->ntz = ctx->nzc;
+        ctx->ntiles = ctx->ntx * ctx->nty * ctx->nzc;
+    }
+    esi_ctx *c = ctx.get();
+    {
+        esi_ctx *ctx = c;  // for CK
+        CK(ctx->cc.ensure(ctx->sst * ctx->esz));
+    }
+    esi_status e = DISPATCH(c, create_impl)(c, velocity_dev);
+    if (e != ESI_OK) {
+        g_create_error = c->err;  // readable through esi_last_error(NULL)
+        return e;
+    }
+    *out = ctx.release();
+    return ESI_OK;
+}
+
+ESI_API void esi_destroy(esi_ctx *ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->st);
+    delete ctx;
+}
+
+ESI_API esi_status esi_set_stream(esi_ctx *ctx, void *stream) {
+    if (!ctx) return ESI_ERR_ARG;
+    ctx->st = reinterpret_cast<cudaStream_t>(stream);
+    return ESI_OK;
+}
+
+ESI_API esi_status esi_set_velocity(esi_ctx *ctx, const void *velocity_dev) {
+    if (!ctx || !velocity_dev) return ESI_ERR_ARG;
+    return ctx->g.dtype == ESI_F64 ? setup_model<double>(ctx, velocity_dev, false)
+                                   : setup_model<float>(ctx, velocity_dev, false);
+}
+
+ESI_API esi_status esi_forward(esi_ctx *ctx, const void *wavelet_dev, const void *ext_src_dev,
+                               void *traces_dev) {
+    if (!ctx) return ESI_ERR_ARG;
+    if (!traces_dev) return ctx->fail(ESI_ERR_ARG, "traces_dev is NULL");
+    ctx->err.clear();
+    return ctx->g.dtype == ESI_F64
+               ? forward_impl<double>(ctx, wavelet_dev, ext_src_dev, traces_dev, nullptr, 0, nullptr)
+               : forward_impl<float>(ctx, wavelet_dev, ext_src_dev, traces_dev, nullptr, 0, nullptr);
+}
+
+ESI_API esi_status esi_adjoint(esi_ctx *ctx, const void *traces_dev, void *ext_out_dev,
+                               void *wavelet_out_dev) {
+    if (!ctx) return ESI_ERR_ARG;
+    if (!traces_dev || (!ext_out_dev && !wavelet_out_dev))
+        return ctx->fail(ESI_ERR_ARG, "need adjoint data and at least one output");
+    ctx->err.clear();
+    return ctx->g.dtype == ESI_F64 ? adjoint_impl<double>(ctx, traces_dev, ext_out_dev, wavelet_out_dev)
+                                   : adjoint_impl<float>(ctx, traces_dev, ext_out_dev, wavelet_out_dev);
+}
+
+ESI_API esi_status esi_gradient(esi_ctx *ctx, const void *wavelet_dev, const void *ext_src_dev,
+                                const void *dobs_dev, const void *adj_src_dev,
+                                const esi_grad_opts *opts, void *grad_dev, double *misfit) {
+    if (!ctx) return ESI_ERR_ARG;
+    if (!opts || !grad_dev) return ctx->fail(ESI_ERR_ARG, "need options and a gradient buffer");
+    if (opts->param < ESI_PARAM_C || opts->param > ESI_PARAM_M ||
+        opts->ckpt_kind < ESI_CKPT_F32 || opts->ckpt_kind > ESI_CKPT_BF16)
+        return ctx->fail(ESI_ERR_ARG, "bad gradient options");
+    ctx->err.clear();
+    return ctx->g.dtype == ESI_F64
+               ? gradient_impl<double>(ctx, wavelet_dev, ext_src_dev, dobs_dev, adj_src_dev, opts,
+                                       grad_dev, misfit)
+               : gradient_impl<float>(ctx, wavelet_dev, ext_src_dev, dobs_dev, adj_src_dev, opts,
+                                      grad_dev, misfit);
+}
+
+ESI_API esi_status esi_dft_extract(esi_ctx *ctx, const void *wavelet_dev, const void *ext_src_dev,
+                                   const double *freqs_hz, int nf, void *out_dev, int out_kind,
+                                   float *scales_host, void *traces_dev) {
+    if (!ctx) return ESI_ERR_ARG;
+    ctx->err.clear();
+    return ctx->g.dtype == ESI_F64
+               ? dft_impl<double>(ctx, wavelet_dev, ext_src_dev, freqs_hz, nf, out_dev, out_kind,
+                                  scales_host, traces_dev)
+               : dft_impl<float>(ctx, wavelet_dev, ext_src_dev, freqs_hz, nf, out_dev, out_kind,
+                                 scales_host, traces_dev);
+}
+
+ESI_API esi_status esi_cg_solve(esi_ctx *ctx, double lambda, double tol, int max_iter,
+                                const void *dobs_dev, void *q_out_dev, int precond, double eps,
+                                esi_cg_report *report) {
+    if (!ctx) return ESI_ERR_ARG;
+    if (!dobs_dev || !q_out_dev || !(lambda >= 0) || !(tol >= 0))
+        return ctx->fail(ESI_ERR_ARG, "bad CG arguments");
+    ctx->err.clear();
+    return ctx->g.dtype == ESI_F64
+               ? cg_impl<double>(ctx, lambda, tol, max_iter, dobs_dev, q_out_dev, precond, eps, report)
+               : cg_impl<float>(ctx, lambda, tol, max_iter, dobs_dev, q_out_dev, precond, eps, report);
+}
+
+ESI_API esi_status esi_pc_load(esi_ctx *ctx, const void *weights_dev, size_t bytes) {
+    if (!ctx) return ESI_ERR_ARG;
+    (void)weights_dev;
+    (void)bytes;
+    return ctx->fail(ESI_ERR_UNSUPPORTED, "learned preconditioner not loaded in this build");
+}
+
+}  // extern "C"

@@ -1,0 +1,200 @@
+// Internal declarations of libesi (not part of the C ABI).
+//
+// Discrete scheme shared by every propagation kernel (forward and adjoint):
+//   new = cur + gamma (cur - old) + alpha * cc * (L(cur) + dx^2 src)
+// with L the dimensionless 8th-order Laplacian sum (Lap8 u = L / dx^2), cc = v^2 dt^2 / dx^2,
+// alpha = 1 / (1 + kappa), gamma = (1 - kappa) / (1 + kappa), kappa = eta dt / 2 the
+// sponge coefficient.  This is the centred discretisation of
+//   (1/v^2)(u_tt + eta u_t) - Lap u = q,
+// rearranged from (1+kappa) u_{n+1} = 2 u_n - (1-kappa) u_{n-1} + c (Lap8 u_n + q_n).
+//
+// The adjoint uses the same kernel run backward in time: the blocks of the discrete
+// operator A = C^{-1} M (C = diag(c), M the block lower-triangular time-stepping
+// matrix) are spatially symmetric, so A^T is A with the time axis reversed, and
+// S^T e = A^{-T} R^T e is the same recurrence driven by R^T e from t = T down to 0.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "esi.h"
+
+namespace esi {
+
+// ----------------------------------------------------------------------------- tiling
+constexpr int HALO = 4;           // stencil radius (8th order)
+constexpr int TX = 32;            // tile width (x) of the 2D step kernel
+constexpr int TZ = 32;            // tile height (z)
+constexpr int BX = 32, BY = 8;    // threads per block (x, y)
+constexpr int RZ = TZ / BY;       // cells per thread along z
+constexpr int SW = TX + 2 * HALO; // shared tile width incl. halo
+constexpr int SH = TZ + 2 * HALO; // shared tile height incl. halo
+constexpr int MAXP = 8;           // interpolation points per receiver (4 in 2D, 8 in 3D)
+
+// 3D kernel tile (xy plane, marching along z)
+constexpr int TX3 = 32, TY3 = 16;
+constexpr int SW3 = TX3 + 2 * HALO, SH3 = TY3 + 2 * HALO;
+
+// ----------------------------------------------------------------------------- feature flags
+enum : unsigned {
+    F_EXT = 1u << 0,  // add a dense extended source field q_n
+    F_CGP = 1u << 1,  // source p' = r + beta p (CG direction update), written back to p
+    F_PT = 1u << 2,   // point injection (wavelet at sources, or R^T e at receivers)
+    F_SMP = 1u << 3,  // sample the *input* state into a trace buffer
+    F_OUT = 1u << 4,  // write the new state to a dense space-time output
+    F_AP = 1u << 5,   // CG product epilogue Ap = new + beta B^2 p and <p, Ap> partials
+    F_STW = 1u << 6,  // write the stash s = L + dx^2 q (gradient recompute)
+    F_GRD = 1u << 7,  // gradient: G += new * stash
+    F_SAD = 1u << 8,  // saddle-point gradient: G += B^2 q s
+    F_DFT = 1u << 9,  // on-the-fly DTFT of the new state
+};
+
+// Point lists on the device, CSR over (shot, tile).  Injection lists hold unique nodes
+// with their contributing traces; sampling lists hold receivers with MAXP points each.
+template <typename T>
+struct InjList {
+    const int *tile_ptr = nullptr;     // [ns * ntiles + 1]
+    const int *cell = nullptr;         // [nodes] local cell index inside the tile (no halo)
+    const int *cptr = nullptr;         // [nodes + 1] range into contributions
+    const long long *off0 = nullptr;   // [contribs] trace offset at time 0
+    const int *tstride = nullptr;      // [contribs] trace stride per time step
+    const T *w = nullptr;              // [contribs] weight (dx^2 folded in)
+};
+
+template <typename T>
+struct SmpList {
+    const int *tile_ptr = nullptr;     // [ns * ntiles + 1]
+    const int *idx = nullptr;          // [recs * MAXP] shared-tile index (incl. halo)
+    const long long *gidx = nullptr;   // [recs * MAXP] global index into a shot's state
+    const T *w = nullptr;              // [recs * MAXP]
+    const long long *off0 = nullptr;   // [recs] output offset at time 0
+    const int *tstride = nullptr;      // [recs]
+    const int *shot = nullptr;         // [recs] shot of each receiver
+    int nrec = 0;
+};
+
+template <typename T>
+struct StepArgs {
+    int nz, ny, nx, px;        // grid and pitch (elements) of the state arrays
+    long long sst;             // shot stride of state arrays
+    long long N;               // dense field size nz*ny*nx
+    long long fst;             // shot stride of dense space-time fields (nt * N)
+    int ntx, nty, ntz;         // tiles per shot
+    const T *cur;              // input state
+    T *po;                     // in: older state, out: new state
+    const T *cc;               // [nz][ny][px] v^2 dt^2 / dx^2
+    const T *kz, *ky, *kx;     // sponge kappa per row / column
+    T dx2;
+    int n;                     // time index of dense sources (ext / CG / stash slot base)
+    const int *active;         // per-shot flag or null
+    // extended source at time n: ext + s*fst + n*N
+    const T *ext;
+    // CG: r, p at time n
+    const T *cg_r;
+    T *cg_p;
+    const double *cg_beta;
+    int cg_first;
+    // point injection at trace time tin
+    InjList<T> inj;
+    const T *inj_trace;
+    int tin;
+    // sampling of the input state at trace time tout (skipped when tout < 0)
+    SmpList<T> smp;
+    T *smp_out;
+    int tout;
+    // dense output of the new state at time nout: fout + s*fst + nout*N
+    T *fout;
+    int nout;
+    // CG product: ap/ap_p at time nout; <p,Ap> block partials per shot
+    T *ap;
+    const T *ap_p;
+    double *dot_part;
+    T pen;                     // penalty beta
+    const double *src_pos;     // [ns][3] source (x, y, z) metres
+    T eps, dx;
+    // stash [slot][ns][N] dense; write slot sw, read slot sr
+    T *stash_w;
+    const T *stash_r;
+    int slot_w, slot_r, ns;
+    // gradient accumulators [ns][N] dense
+    T *grad;
+    // DTFT: twiddles [nt][nf][2] (cos, sin) of the new state's time; acc [ns][nf][N][2]
+    int nf;
+    const T *twid;
+    T *dft;
+};
+
+// ----------------------------------------------------------------------------- launchers
+template <typename T>
+cudaError_t launch_step2(unsigned flags, const StepArgs<T> &a, int ns, cudaStream_t st);
+template <typename T>
+cudaError_t launch_step3(unsigned flags, const StepArgs<T> &a, int ns, cudaStream_t st);
+
+// sample a whole state (global memory) for every receiver of a list at time tout
+template <typename T>
+cudaError_t launch_sample_global(const SmpList<T> &l, const T *state, long long sst, T *out,
+                                 int tout, cudaStream_t st);
+
+// c = v^2 dt^2 / dx^2 into a pitched array; per-block max |v| partials
+template <typename T>
+cudaError_t launch_setup_cc(const T *v, T *cc, int nz, int ny, int nx, int px, double dt,
+                            double dx, double *vmax_part, int nblk, cudaStream_t st);
+
+// per-shot reductions of dense [ns][len] vectors into block partials [ns][nblk]
+template <typename T>
+cudaError_t launch_dot(const T *a, const T *b, long long len, long long sstride, int ns,
+                       double *part, int nblk, const int *active, cudaStream_t st);
+cudaError_t launch_reduce_partials(const double *part, int nblk, int ns, double *out,
+                                   cudaStream_t st);
+
+// x += alpha p ; r -= alpha Ap ; partial ||r||^2
+template <typename T>
+cudaError_t launch_cg_update(T *x, T *r, const T *p, const T *ap, long long len,
+                             long long sstride, int ns, const double *alpha,
+                             const int *active, double *part, int nblk, cudaStream_t st);
+// alpha = rr / pAp ; flags breakdown
+cudaError_t launch_cg_alpha(const double *rr, const double *pap, double *alpha, int *bad,
+                            const int *active, int ns, cudaStream_t st);
+// beta = rr_new / rr_old ; rr_old = rr_new
+cudaError_t launch_cg_beta(double *rr_old, const double *rr_new, double *beta,
+                           const int *active, int ns, cudaStream_t st);
+// z = r / (pen B^2) (diagonal preconditioner) over [ns][nt][N]
+template <typename T>
+cudaError_t launch_diag_pc(const T *r, T *z, long long N, int nt, int ns, int nz, int ny,
+                           int nx, const double *src_pos, T pen, T eps, T dx,
+                           const int *active, cudaStream_t st);
+
+// misfit: e = d - dobs (in place into d), per-block partial 1/2 e^2
+template <typename T>
+cudaError_t launch_residual(T *d, const T *dobs, long long len, double *part, int nblk,
+                            cudaStream_t st);
+
+// gradient finalisation: g[i] = scale_i * sum_s G[s][i]
+template <typename T>
+cudaError_t launch_grad_finalize(const T *G, int ns, long long N, const T *cc, int nz, int ny,
+                                 int nx, int px, const T *vel, double dt, double dx,
+                                 double extra, int param, T *g, cudaStream_t st);
+
+// checkpoint codec: per-shot max |u|, encode and decode
+template <typename T>
+cudaError_t launch_absmax(const T *u, long long len, long long sstride, int ns,
+                          unsigned *bits_out, cudaStream_t st);
+template <typename T>
+cudaError_t launch_encode(const T *u, long long len, long long sstride, int ns, int kind,
+                          const unsigned *absmax_bits, void *codes, float *dec_scale,
+                          cudaStream_t st);
+template <typename T>
+cudaError_t launch_decode(const void *codes, long long len, long long sstride, int ns, int kind,
+                          const float *dec_scale, T *u, cudaStream_t st);
+
+// DTFT output: complex accumulators [ns][nf][N][2] -> half2 with per (shot, f) scale
+template <typename T>
+cudaError_t launch_dft_to_half(const T *acc, long long N, int ns, int nf, void *out,
+                               unsigned *absmax_bits, float *scales_dev, cudaStream_t st);
+
+}  // namespace esi

@@ -1,0 +1,410 @@
+// Streaming kernels around the propagators: model set-up, per-shot reductions with a
+// deterministic two-stage sum, the CG vector updates of Algorithm 1, misfit, gradient
+// finalisation, and the scaled FP16/BF16 snapshot codec.
+#include "esi_internal.h"
+
+namespace esi {
+namespace {
+
+constexpr int RT = 256;  // threads per block of the streaming kernels
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// block-wide sum in double; result valid in thread 0
+__device__ __forceinline__ double block_sum_d(double v) {
+    __shared__ double red[RT / 32];
+    v = warp_sum_d(v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (warp == 0) {
+        t = lane < RT / 32 ? red[lane] : 0.0;
+        t = warp_sum_d(t);
+    }
+    return t;
+}
+
+template <typename T>
+__global__ void setup_cc_kernel(const T *v, T *cc, int nz, int ny, int nx, int px, double dt,
+                                double dx, double *vmax_part) {
+    const long long N = (long long)nz * ny * nx;
+    const double s = dt * dt / (dx * dx);
+    double vm = 0.0;
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < N;
+         i += (long long)gridDim.x * RT) {
+        const long long row = i / nx, x = i - row * nx;
+        const double vv = double(v[i]);
+        cc[row * px + x] = T(vv * vv * s);
+        vm = fmax(vm, fabs(vv));
+    }
+    __shared__ double red[RT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) vm = fmax(vm, __shfl_xor_sync(0xffffffffu, vm, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = vm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < RT / 32; ++w) t = fmax(t, red[w]);
+        vmax_part[blockIdx.x] = t;
+    }
+}
+
+template <typename T>
+__global__ void dot_kernel(const T *a, const T *b, long long len, long long sstride,
+                           double *part, const int *active) {
+    const int s = blockIdx.y;
+    if (active && !active[s]) return;
+    const T *x = a + s * sstride, *y = b + s * sstride;
+    double acc = 0.0;
+    T local = T(0);
+    int cnt = 0;
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < len;
+         i += (long long)gridDim.x * RT) {
+        local += x[i] * y[i];
+        if (++cnt == 64) {  // bound the length of each field-precision partial sum
+            acc += double(local);
+            local = T(0);
+            cnt = 0;
+        }
+    }
+    acc += double(local);
+    const double t = block_sum_d(acc);
+    if (threadIdx.x == 0) part[(long long)s * gridDim.x + blockIdx.x] = t;
+}
+
+__global__ void reduce_partials_kernel(const double *part, int nblk, int ns, double *out) {
+    const int s = blockIdx.x;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += RT) acc += part[(long long)s * nblk + i];
+    const double t = block_sum_d(acc);
+    if (threadIdx.x == 0) out[s] = t;
+}
+
+template <typename T>
+__global__ void cg_update_kernel(T *x, T *r, const T *p, const T *ap, long long len,
+                                 long long sstride, const double *alpha, const int *active,
+                                 double *part) {
+    const int s = blockIdx.y;
+    if (active && !active[s]) return;
+    const T al = T(alpha[s]);
+    T *xs = x + s * sstride, *rs = r + s * sstride;
+    const T *ps = p + s * sstride, *as = ap + s * sstride;
+    double acc = 0.0;
+    T local = T(0);
+    int cnt = 0;
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < len;
+         i += (long long)gridDim.x * RT) {
+        xs[i] += al * ps[i];
+        const T rn = rs[i] - al * as[i];
+        rs[i] = rn;
+        local += rn * rn;
+        if (++cnt == 64) {
+            acc += double(local);
+            local = T(0);
+            cnt = 0;
+        }
+    }
+    acc += double(local);
+    const double t = block_sum_d(acc);
+    if (threadIdx.x == 0) part[(long long)s * gridDim.x + blockIdx.x] = t;
+}
+
+__global__ void cg_alpha_kernel(const double *rr, const double *pap, double *alpha, int *bad,
+                                const int *active, int ns) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= ns) return;
+    if (active && !active[s]) {
+        alpha[s] = 0.0;
+        return;
+    }
+    const double a = rr[s] / pap[s];
+    if (!(pap[s] > 0.0) || !isfinite(a)) {
+        bad[s] = 1;
+        alpha[s] = 0.0;
+    } else {
+        alpha[s] = a;
+    }
+}
+
+__global__ void cg_beta_kernel(double *rr_old, const double *rr_new, double *beta,
+                               const int *active, int ns) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= ns) return;
+    if (active && !active[s]) return;
+    beta[s] = rr_new[s] / rr_old[s];
+    rr_old[s] = rr_new[s];
+}
+
+template <typename T>
+__global__ void diag_pc_kernel(const T *r, T *z, long long N, int nt, int nz, int ny, int nx,
+                               const double *src_pos, T pen, T eps, T dx, const int *active) {
+    const int s = blockIdx.y;
+    if (active && !active[s]) return;
+    const long long len = N * nt;
+    const T xs = T(src_pos[3 * s]), ys = T(src_pos[3 * s + 1]), zs = T(src_pos[3 * s + 2]);
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < len;
+         i += (long long)gridDim.x * RT) {
+        const long long c = i % N;
+        const long long ix = c % nx, rest = c / nx;
+        const long long iy = rest % ny, iz = rest / ny;
+        const T ex = T(ix) * dx - xs, ey = ny > 1 ? T(iy) * dx - ys : T(0), ez = T(iz) * dx - zs;
+        const T B = sqrt(ex * ex + ey * ey + ez * ez) + eps;
+        z[s * len + i] = r[s * len + i] / (pen * B * B);
+    }
+}
+
+template <typename T>
+__global__ void residual_kernel(T *d, const T *dobs, long long len, double *part) {
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < len;
+         i += (long long)gridDim.x * RT) {
+        const T e = d[i] - dobs[i];
+        d[i] = e;
+        acc += double(e) * double(e);
+    }
+    const double t = block_sum_d(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = 0.5 * t;
+}
+
+template <typename T>
+__global__ void grad_finalize_kernel(const T *G, int ns, long long N, const T *cc, int ny,
+                                     int nx, int px, double dt, double dx, double extra,
+                                     int param, T *g) {
+    const double dx2 = dx * dx;
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < N;
+         i += (long long)gridDim.x * RT) {
+        double sum = 0.0;
+        for (int s = 0; s < ns; ++s) sum += double(G[(long long)s * N + i]);
+        const long long row = i / nx, x = i - row * nx;
+        const double c = double(cc[row * px + x]) * dx2;  // v^2 dt^2
+        double gc = extra * sum / (c * dx2);
+        if (param == ESI_PARAM_V) gc *= 2.0 * sqrt(c) * dt;
+        else if (param == ESI_PARAM_M) gc *= -(c * c) / (dt * dt);
+        g[i] = T(gc);
+    }
+}
+
+// ---------------------------------------------------------------- snapshot codec
+constexpr float CODEC_RANGE = 32768.0f;  // max |u| of a snapshot maps to this magnitude
+
+template <typename T>
+__global__ void absmax_kernel(const T *u, long long len, long long sstride, unsigned *bits) {
+    const int s = blockIdx.y;
+    float m = 0.0f;
+    const T *x = u + s * sstride;
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < len;
+         i += (long long)gridDim.x * RT)
+        m = fmaxf(m, fabsf(float(x[i])));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    // non-negative floats order like their bit patterns
+    if ((threadIdx.x & 31) == 0) atomicMax(bits + s, __float_as_uint(m));
+}
+
+template <typename T>
+__global__ void encode_kernel(const T *u, long long len, long long sstride, int kind,
+                              const unsigned *bits, void *codes, float *dec_scale) {
+    const int s = blockIdx.y;
+    const float mx = __uint_as_float(bits[s]);
+    const float inv = mx > 0.0f ? __fdiv_rn(CODEC_RANGE, mx) : 0.0f;
+    if (blockIdx.x == 0 && threadIdx.x == 0) dec_scale[s] = __fdiv_rn(mx, CODEC_RANGE);
+    const T *x = u + s * sstride;
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < len;
+         i += (long long)gridDim.x * RT) {
+        const float y = __fmul_rn(float(x[i]), inv);
+        if (kind == ESI_CKPT_F16)
+            reinterpret_cast<__half *>(codes)[s * sstride + i] = __float2half_rn(y);
+        else
+            reinterpret_cast<__nv_bfloat16 *>(codes)[s * sstride + i] = __float2bfloat16_rn(y);
+    }
+}
+
+template <typename T>
+__global__ void decode_kernel(const void *codes, long long len, long long sstride, int kind,
+                              const float *dec_scale, T *u) {
+    const int s = blockIdx.y;
+    const float d = dec_scale[s];
+    T *x = u + s * sstride;
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < len;
+         i += (long long)gridDim.x * RT) {
+        float h;
+        if (kind == ESI_CKPT_F16)
+            h = __half2float(reinterpret_cast<const __half *>(codes)[s * sstride + i]);
+        else
+            h = __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(codes)[s * sstride + i]);
+        x[i] = T(__fmul_rn(h, d));
+    }
+}
+
+template <typename T>
+__global__ void dft_absmax_kernel(const T *acc, long long N, int nf, unsigned *bits) {
+    const int sm = blockIdx.y;  // shot * nf + m
+    const T *a = acc + (long long)sm * N * 2;
+    float m = 0.0f;
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < 2 * N;
+         i += (long long)gridDim.x * RT)
+        m = fmaxf(m, fabsf(float(a[i])));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(bits + sm, __float_as_uint(m));
+}
+
+template <typename T>
+__global__ void dft_half_kernel(const T *acc, long long N, const unsigned *bits, __half *out,
+                                float *scales) {
+    const int sm = blockIdx.y;
+    const float mx = __uint_as_float(bits[sm]);
+    const float inv = mx > 0.0f ? __fdiv_rn(CODEC_RANGE, mx) : 0.0f;
+    if (blockIdx.x == 0 && threadIdx.x == 0) scales[sm] = __fdiv_rn(mx, CODEC_RANGE);
+    const T *a = acc + (long long)sm * N * 2;
+    __half *o = out + (long long)sm * N * 2;
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < 2 * N;
+         i += (long long)gridDim.x * RT)
+        o[i] = __float2half_rn(__fmul_rn(float(a[i]), inv));
+}
+
+inline int blocks_for(long long len, int cap) {
+    long long b = (len + RT - 1) / RT;
+    return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_setup_cc(const T *v, T *cc, int nz, int ny, int nx, int px, double dt,
+                            double dx, double *vmax_part, int nblk, cudaStream_t st) {
+    setup_cc_kernel<T><<<nblk, RT, 0, st>>>(v, cc, nz, ny, nx, px, dt, dx, vmax_part);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_dot(const T *a, const T *b, long long len, long long sstride, int ns,
+                       double *part, int nblk, const int *active, cudaStream_t st) {
+    dot_kernel<T><<<dim3(nblk, ns), RT, 0, st>>>(a, b, len, sstride, part, active);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_partials(const double *part, int nblk, int ns, double *out,
+                                   cudaStream_t st) {
+    reduce_partials_kernel<<<ns, RT, 0, st>>>(part, nblk, ns, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cg_update(T *x, T *r, const T *p, const T *ap, long long len,
+                             long long sstride, int ns, const double *alpha,
+                             const int *active, double *part, int nblk, cudaStream_t st) {
+    cg_update_kernel<T><<<dim3(nblk, ns), RT, 0, st>>>(x, r, p, ap, len, sstride, alpha, active,
+                                                       part);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_alpha(const double *rr, const double *pap, double *alpha, int *bad,
+                            const int *active, int ns, cudaStream_t st) {
+    cg_alpha_kernel<<<(ns + 127) / 128, 128, 0, st>>>(rr, pap, alpha, bad, active, ns);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_beta(double *rr_old, const double *rr_new, double *beta,
+                           const int *active, int ns, cudaStream_t st) {
+    cg_beta_kernel<<<(ns + 127) / 128, 128, 0, st>>>(rr_old, rr_new, beta, active, ns);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_diag_pc(const T *r, T *z, long long N, int nt, int ns, int nz, int ny,
+                           int nx, const double *src_pos, T pen, T eps, T dx,
+                           const int *active, cudaStream_t st) {
+    diag_pc_kernel<T><<<dim3(blocks_for(N * nt, 4096), ns), RT, 0, st>>>(
+        r, z, N, nt, nz, ny, nx, src_pos, pen, eps, dx, active);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_residual(T *d, const T *dobs, long long len, double *part, int nblk,
+                            cudaStream_t st) {
+    residual_kernel<T><<<nblk, RT, 0, st>>>(d, dobs, len, part);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_grad_finalize(const T *G, int ns, long long N, const T *cc, int nz, int ny,
+                                 int nx, int px, const T *vel, double dt, double dx,
+                                 double extra, int param, T *g, cudaStream_t st) {
+    (void)nz;
+    (void)vel;
+    grad_finalize_kernel<T><<<blocks_for(N, 8192), RT, 0, st>>>(G, ns, N, cc, ny, nx, px, dt, dx,
+                                                                extra, param, g);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_absmax(const T *u, long long len, long long sstride, int ns, unsigned *bits,
+                          cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(unsigned) * ns, st);
+    if (e != cudaSuccess) return e;
+    absmax_kernel<T><<<dim3(blocks_for(len, 1024), ns), RT, 0, st>>>(u, len, sstride, bits);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_encode(const T *u, long long len, long long sstride, int ns, int kind,
+                          const unsigned *bits, void *codes, float *dec_scale, cudaStream_t st) {
+    encode_kernel<T><<<dim3(blocks_for(len, 1024), ns), RT, 0, st>>>(u, len, sstride, kind, bits,
+                                                                      codes, dec_scale);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_decode(const void *codes, long long len, long long sstride, int ns, int kind,
+                          const float *dec_scale, T *u, cudaStream_t st) {
+    decode_kernel<T><<<dim3(blocks_for(len, 1024), ns), RT, 0, st>>>(codes, len, sstride, kind,
+                                                                      dec_scale, u);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_dft_to_half(const T *acc, long long N, int ns, int nf, void *out,
+                               unsigned *bits, float *scales_dev, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(unsigned) * ns * nf, st);
+    if (e != cudaSuccess) return e;
+    dft_absmax_kernel<T><<<dim3(blocks_for(2 * N, 1024), ns * nf), RT, 0, st>>>(acc, N, nf, bits);
+    dft_half_kernel<T><<<dim3(blocks_for(2 * N, 1024), ns * nf), RT, 0, st>>>(
+        acc, N, bits, reinterpret_cast<__half *>(out), scales_dev);
+    return cudaGetLastError();
+}
+
+#define ESI_INST(T)                                                                              \
+    template cudaError_t launch_setup_cc<T>(const T *, T *, int, int, int, int, double, double,  \
+                                            double *, int, cudaStream_t);                        \
+    template cudaError_t launch_dot<T>(const T *, const T *, long long, long long, int, double *, \
+                                       int, const int *, cudaStream_t);                          \
+    template cudaError_t launch_cg_update<T>(T *, T *, const T *, const T *, long long,          \
+                                             long long, int, const double *, const int *,        \
+                                             double *, int, cudaStream_t);                       \
+    template cudaError_t launch_diag_pc<T>(const T *, T *, long long, int, int, int, int, int,   \
+                                           const double *, T, T, T, const int *, cudaStream_t);  \
+    template cudaError_t launch_residual<T>(T *, const T *, long long, double *, int,            \
+                                            cudaStream_t);                                       \
+    template cudaError_t launch_grad_finalize<T>(const T *, int, long long, const T *, int, int, \
+                                                 int, int, const T *, double, double, double,    \
+                                                 int, T *, cudaStream_t);                        \
+    template cudaError_t launch_absmax<T>(const T *, long long, long long, int, unsigned *,      \
+                                          cudaStream_t);                                         \
+    template cudaError_t launch_encode<T>(const T *, long long, long long, int, int,             \
+                                          const unsigned *, void *, float *, cudaStream_t);      \
+    template cudaError_t launch_decode<T>(const void *, long long, long long, int, int,          \
+                                          const float *, T *, cudaStream_t);                     \
+    template cudaError_t launch_dft_to_half<T>(const T *, long long, int, int, void *,           \
+                                               unsigned *, float *, cudaStream_t);
+
+ESI_INST(float)
+ESI_INST(double)
+#undef ESI_INST
+
+}  // namespace esi

@@ -1,0 +1,284 @@
+"""Thin ctypes binding of libesi (the C ABI in include/esi.h).
+
+Argument marshalling only: PyTorch provides device memory and the stream; every
+arithmetic step runs in the library's CUDA kernels.  There is no CPU fallback: loading
+fails loudly when the library is missing or no CUDA device is available.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libesi.so")
+
+ESI_OK, ESI_ERR_ARG, ESI_ERR_CFL, ESI_ERR_OOM, ESI_ERR_CUDA = 0, 1, 2, 3, 4
+ESI_ERR_BREAKDOWN, ESI_ERR_TIMEOUT, ESI_ERR_NOT_CONVERGED, ESI_ERR_UNSUPPORTED = 5, 6, 7, 8
+ESI_F32, ESI_F64 = 0, 1
+GRAD_ADJOINT_STATE, GRAD_SADDLE_POINT = 0, 1
+PARAMS = {"c": 0, "v": 1, "m": 2}
+CKPT = {"f32": 0, "f16": 1, "bf16": 2}
+DFT_C64, DFT_C32_HALF = 0, 1
+PC = {"none": 0, "diag": 1, "learned": 2}
+
+# every symbol the header declares (checked by the CPU test-suite)
+EXPORTS = ["esi_create", "esi_destroy", "esi_set_stream", "esi_set_velocity", "esi_forward",
+           "esi_adjoint", "esi_gradient", "esi_dft_extract", "esi_cg_solve", "esi_pc_load",
+           "esi_status_string", "esi_last_error", "esi_launch_count"]
+
+
+class EsiGrid(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("nz", ctypes.c_int), ("ny", ctypes.c_int),
+                ("nx", ctypes.c_int), ("dx", ctypes.c_double), ("nb", ctypes.c_int),
+                ("sponge_R", ctypes.c_double), ("sponge_vref", ctypes.c_double),
+                ("dtype", ctypes.c_int)]
+
+
+class EsiGeometry(ctypes.Structure):
+    _fields_ = [("ns", ctypes.c_int), ("src_xyz", ctypes.POINTER(ctypes.c_double)),
+                ("rec_offset", ctypes.POINTER(ctypes.c_longlong)),
+                ("rec_xyz", ctypes.POINTER(ctypes.c_double))]
+
+
+class EsiGradOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("param", ctypes.c_int), ("ckpt_every", ctypes.c_int),
+                ("ckpt_kind", ctypes.c_int), ("beta", ctypes.c_double), ("eps", ctypes.c_double)]
+
+
+class EsiCgReport(ctypes.Structure):
+    _fields_ = [("iters_max", ctypes.c_int), ("converged", ctypes.c_int),
+                ("max_hist", ctypes.c_int), ("iters", ctypes.POINTER(ctypes.c_int)),
+                ("rel_res", ctypes.POINTER(ctypes.c_double)), ("ms_matvec", ctypes.c_double),
+                ("ms_vector", ctypes.c_double), ("ms_precond", ctypes.c_double),
+                ("ms_total", ctypes.c_double)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def load_library(require_gpu: bool = True) -> ctypes.CDLL:
+    """Load libesi.so (built by paper_2211_06300_gb300.build).  Raises when missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libesi.so not built ({LIB_PATH}); run paper_2211_06300_gb300.build")
+    if require_gpu:
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libesi needs a CUDA device; none is available")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.esi_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(EsiGrid),
+                             ctypes.POINTER(EsiGeometry), vp, d, i, vp]
+    L.esi_destroy.argtypes = [vp]
+    L.esi_destroy.restype = None
+    L.esi_set_stream.argtypes = [vp, vp]
+    L.esi_set_velocity.argtypes = [vp, vp]
+    L.esi_forward.argtypes = [vp, vp, vp, vp]
+    L.esi_adjoint.argtypes = [vp, vp, vp, vp]
+    L.esi_gradient.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(EsiGradOpts), vp,
+                               ctypes.POINTER(d)]
+    L.esi_dft_extract.argtypes = [vp, vp, vp, ctypes.POINTER(d), i, vp, i,
+                                  ctypes.POINTER(ctypes.c_float), vp]
+    L.esi_cg_solve.argtypes = [vp, d, d, i, vp, vp, i, d, ctypes.POINTER(EsiCgReport)]
+    L.esi_pc_load.argtypes = [vp, vp, ctypes.c_size_t]
+    L.esi_status_string.argtypes = [i]
+    L.esi_status_string.restype = ctypes.c_char_p
+    L.esi_last_error.argtypes = [vp]
+    L.esi_last_error.restype = ctypes.c_char_p
+    L.esi_launch_count.argtypes = [vp]
+    L.esi_launch_count.restype = ctypes.c_longlong
+    for name in ("esi_create", "esi_set_stream", "esi_set_velocity", "esi_forward",
+                 "esi_adjoint", "esi_gradient", "esi_dft_extract", "esi_cg_solve",
+                 "esi_pc_load"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+class EsiError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libesi takes CUDA tensors")
+    if not t.is_contiguous():
+        raise ValueError("libesi takes contiguous tensors")
+    return t.data_ptr()
+
+
+class Context:
+    """An ESI operator on one velocity model and acquisition (``esi_create``).
+
+    ``v``: CUDA tensor (nz, nx) or (nz, ny, nx), float32 or float64 (the precision of
+    every field of this context).  ``geom``: a ``synth.Geometry`` (positions in metres).
+    """
+
+    def __init__(self, v, dx: float, dt: float, nt: int, nb: int, geom, sponge_R: float = 1e-3,
+                 vref: float = 0.0, stream=None):
+        import torch
+        self.L = load_library()
+        self.torch = torch
+        if v.dim() not in (2, 3):
+            raise ValueError("velocity must be 2D or 3D")
+        self.dtype = v.dtype
+        if v.dtype not in (torch.float32, torch.float64):
+            raise ValueError("velocity must be float32 or float64")
+        self.device = v.device
+        self.shape = tuple(v.shape)
+        self.ndim = v.dim()
+        self.N = int(np.prod(self.shape))
+        self.nt, self.dx, self.dt, self.nb = int(nt), float(dx), float(dt), int(nb)
+        self.geom = geom
+        self.ns = geom.ns
+        self.total_rec = int(geom.rec_offset[-1])
+        g = EsiGrid()
+        g.ndim = self.ndim
+        if self.ndim == 2:
+            g.nz, g.ny, g.nx = self.shape[0], 1, self.shape[1]
+        else:
+            g.nz, g.ny, g.nx = self.shape
+        g.dx, g.nb, g.sponge_R, g.sponge_vref = self.dx, self.nb, sponge_R, vref
+        g.dtype = ESI_F64 if v.dtype == torch.float64 else ESI_F32
+        self._src = np.ascontiguousarray(geom.src_xyz, dtype=np.float64)
+        self._off = np.ascontiguousarray(geom.rec_offset, dtype=np.int64)
+        self._rec = np.ascontiguousarray(geom.rec_xyz, dtype=np.float64).reshape(-1, 3)
+        if self._rec.size == 0:
+            self._rec = np.zeros((1, 3))
+        gm = EsiGeometry()
+        gm.ns = self.ns
+        gm.src_xyz = self._src.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        gm.rec_offset = self._off.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))
+        gm.rec_xyz = self._rec.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        self._v = v.contiguous()
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = self.L.esi_create(ctypes.byref(h), ctypes.byref(g), ctypes.byref(gm),
+                                   _ptr(self._v), self.dt, self.nt,
+                                   ctypes.c_void_p(stream.cuda_stream))
+        if st != ESI_OK:
+            raise EsiError(st, self.L.esi_last_error(None).decode() or
+                           self.L.esi_status_string(st).decode())
+        self.h = h
+
+    # ---------------------------------------------------------------- helpers
+    def _check(self, st: int, allow=(ESI_OK,)):
+        if st not in allow:
+            raise EsiError(st, self.L.esi_last_error(self.h).decode() or
+                           self.L.esi_status_string(st).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.esi_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def empty_traces(self):
+        return self.torch.empty(self.nt * self.total_rec, dtype=self.dtype, device=self.device)
+
+    def empty_field(self, ns: Optional[int] = None):
+        ns = self.ns if ns is None else ns
+        return self.torch.empty((ns, self.nt) + self.shape, dtype=self.dtype, device=self.device)
+
+    def traces_of(self, traces, s: int):
+        """View of shot s in a CSR seismogram buffer as (nt, nrec)."""
+        o0, o1 = int(self.geom.rec_offset[s]), int(self.geom.rec_offset[s + 1])
+        return traces[self.nt * o0:self.nt * o1].view(self.nt, o1 - o0)
+
+    @property
+    def launches(self) -> int:
+        return int(self.L.esi_launch_count(self.h))
+
+    # ---------------------------------------------------------------- operators
+    def set_velocity(self, v):
+        self._v = v.contiguous()
+        self._check(self.L.esi_set_velocity(self.h, _ptr(self._v)))
+
+    def forward(self, wavelet=None, ext=None, out=None):
+        out = self.empty_traces() if out is None else out
+        self._check(self.L.esi_forward(self.h, _ptr(wavelet), _ptr(ext), _ptr(out)))
+        return out
+
+    def adjoint(self, traces, want_field: bool = True, want_wavelet: bool = False, out=None):
+        f = (self.empty_field() if out is None else out) if want_field else None
+        w = self.torch.empty((self.ns, self.nt), dtype=self.dtype, device=self.device) \
+            if want_wavelet else None
+        self._check(self.L.esi_adjoint(self.h, _ptr(traces), _ptr(f), _ptr(w)))
+        return f, w
+
+    def gradient(self, wavelet=None, ext=None, dobs=None, adj_src=None, mode: str = "adjoint",
+                 param: str = "v", ckpt_every: int = 20, ckpt: str = "f32", beta: float = 0.0,
+                 eps: float = 0.0, out=None):
+        o = EsiGradOpts()
+        o.mode = GRAD_SADDLE_POINT if mode == "saddle" else GRAD_ADJOINT_STATE
+        o.param = PARAMS[param]
+        o.ckpt_every = int(ckpt_every)
+        o.ckpt_kind = CKPT[ckpt]
+        o.beta = float(beta)
+        o.eps = float(eps)
+        g = self.torch.empty(self.shape, dtype=self.dtype, device=self.device) if out is None else out
+        mis = ctypes.c_double(0.0)
+        self._check(self.L.esi_gradient(self.h, _ptr(wavelet), _ptr(ext), _ptr(dobs), _ptr(adj_src),
+                                        ctypes.byref(o), _ptr(g), ctypes.byref(mis)))
+        return g, float(mis.value)
+
+    def dft_extract(self, freqs: Sequence[float], wavelet=None, ext=None, half: bool = False,
+                    traces=None):
+        f = np.ascontiguousarray(freqs, dtype=np.float64)
+        nf = f.size
+        if half:
+            out = self.torch.empty((self.ns, nf) + self.shape + (2,), dtype=self.torch.float16,
+                                   device=self.device)
+            scales = np.zeros(self.ns * nf, dtype=np.float32)
+            sp = scales.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+            kind = DFT_C32_HALF
+        else:
+            out = self.torch.empty((self.ns, nf) + self.shape + (2,), dtype=self.dtype,
+                                   device=self.device)
+            scales, sp, kind = None, None, DFT_C64
+        self._check(self.L.esi_dft_extract(self.h, _ptr(wavelet), _ptr(ext),
+                                           f.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nf,
+                                           _ptr(out), kind, sp, _ptr(traces)))
+        return out, (scales.reshape(self.ns, nf) if scales is not None else None)
+
+    def cg_solve(self, dobs, lam: float, tol: float, max_iter: int, precond: str = "none",
+                 eps: float = 0.0, out=None, hist: int = 0):
+        q = self.empty_field() if out is None else out
+        rep = EsiCgReport()
+        hist = max(int(hist), int(max_iter))
+        rel = np.zeros((self.ns, hist), dtype=np.float64)
+        its = np.zeros(self.ns, dtype=np.int32)
+        rep.max_hist = hist
+        rep.iters = its.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        rep.rel_res = rel.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        st = self._check(self.L.esi_cg_solve(self.h, float(lam), float(tol), int(max_iter),
+                                             _ptr(dobs), _ptr(q), PC[precond], float(eps),
+                                             ctypes.byref(rep)),
+                         allow=(ESI_OK, ESI_ERR_NOT_CONVERGED))
+        report = {"iters": its.copy(), "rel_res": [rel[s, :its[s]].copy() for s in range(self.ns)],
+                  "converged": bool(rep.converged), "iters_max": int(rep.iters_max),
+                  "ms_matvec": rep.ms_matvec, "ms_vector": rep.ms_vector,
+                  "ms_total": rep.ms_total, "status": st}
+        return q, report

@@ -1,0 +1,280 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Sizes are small enough for the oracle to finish in seconds but span several tiles with
+ragged tails in every direction, several shots with uneven receiver counts, off-node
+points, and (3D) several z chunks.  Tolerances: FP64 1e-12 relative L2; FP32 fields and
+traces 1e-4 (the seismogram bound); compressed gradient checkpoints 1e-3.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2211_06300_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-4}
+
+
+def _esi():
+    from paper_2211_06300_gb300 import esi
+    return esi
+
+
+def _tdt(prec):
+    return torch.float64 if prec == "f64" else torch.float32
+
+
+def _dev(a, prec):
+    return torch.tensor(np.ascontiguousarray(a), dtype=_tdt(prec), device="cuda")
+
+
+def _ragged_case(shape=(45, 83), nt=120, dx=10.0, dt=1e-3, nb=6, ns=3, seed=5):
+    v = synth.dipping_layers(shape, dx, seed, nlayers=4, vmin=1500, vmax=2600, nanom=2,
+                             sigma=4 * dx)
+    nx, nz = shape[-1], shape[0]
+    rng = np.random.default_rng(seed)
+    src_x = [0.3 * nx * dx + 0.37 * dx, 0.55 * nx * dx, 0.8 * nx * dx + 0.5 * dx][:ns]
+    recs = []
+    for s in range(ns):
+        n = [nx, 1, 17][s % 3]
+        if n == nx:
+            xr = np.arange(nx) * dx                       # on-node, every column
+        elif n == 1:
+            xr = np.array([(nx - 1) * dx])                # last column only
+        else:
+            xr = np.sort(rng.uniform(0, (nx - 1.01) * dx, n))  # off-node
+        recs.append(xr)
+    geom = synth.surface_line(ns, src_x, 3.3 * dx, recs, 2.0 * dx + 0.25 * dx)
+    # move the second shot's receivers to the bottom row to cover edge nodes
+    off = geom.rec_offset
+    geom.rec_xyz[off[1]:off[2], 2] = (nz - 1) * dx
+    return v, geom, dict(dx=dx, dt=dt, nt=nt, nb=nb)
+
+
+def _ctx(v, geom, p, prec, vref=0.0):
+    esi = _esi()
+    return esi.Context(_dev(v, prec), p["dx"], p["dt"], p["nt"], p["nb"], geom, vref=vref)
+
+
+def _orc(v, geom, p, vref=None):
+    o = oracle.Oracle(v, p["dx"], p["dt"], p["nt"], p["nb"], vref=vref)
+    shots = [o.shot(geom.src_xyz[s], geom.receivers(s)) for s in range(geom.ns)]
+    return o, shots
+
+
+# ----------------------------------------------------------------------------- forward / adjoint
+def test_small_2d_fp64_forward_adjoint():
+    w = synth.workload_small_2d()
+    p = dict(dx=w.dx, dt=w.dt, nt=w.nt, nb=w.nb)
+    ctx = _ctx(w.v_true, w.geom, p, "f64")
+    o, (sh,) = _orc(w.v_true, w.geom, p)
+    wav = w.wavelets()
+    d = ctx.forward(wavelet=_dev(wav, "f64"))
+    ref = o.forward(sh, wavelet=wav[0])["traces"]
+    assert oracle.rel_l2(ctx.traces_of(d, 0).cpu().numpy(), ref) <= 1e-12
+    e = synth.normal(8, (w.nt, sh.nr))
+    f, wv = ctx.adjoint(_dev(e.ravel(), "f64"), want_wavelet=True)
+    ra = o.adjoint(sh, e, want_src=True)
+    assert oracle.rel_l2(f[0].reshape(w.nt, -1).cpu().numpy(), ra["out"]) <= 1e-12
+    assert oracle.rel_l2(wv[0].cpu().numpy(), ra["src"]) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_ragged_multishot_point_and_extended(prec):
+    v, geom, p = _ragged_case()
+    ctx = _ctx(v, geom, p, prec)
+    o, shots = _orc(v, geom, p)
+    nt, N = p["nt"], v.size
+    wav = np.stack([synth.ricker(nt, p["dt"], f) for f in (18.0, 22.0, 25.0)])
+    q = synth.normal(7, (geom.ns, nt, N)) * 1e-3
+    d = ctx.forward(wavelet=_dev(wav, prec), ext=_dev(q.reshape((geom.ns, nt) + v.shape), prec))
+    for s, sh in enumerate(shots):
+        ref = o.forward(sh, wavelet=wav[s], q_ext=q[s])["traces"]
+        assert oracle.rel_l2(ctx.traces_of(d, s).cpu().numpy(), ref) <= TOL[prec], s
+    e = synth.normal(9, (nt * geom.rec_offset[-1],))
+    f, wv = ctx.adjoint(_dev(e, prec), want_wavelet=True)
+    et = torch.tensor(e)
+    for s, sh in enumerate(shots):
+        es = ctx.traces_of(et, s).numpy()
+        ra = o.adjoint(sh, es, want_src=True)
+        assert oracle.rel_l2(f[s].reshape(nt, -1).cpu().numpy(), ra["out"]) <= TOL[prec], s
+        assert oracle.rel_l2(wv[s].cpu().numpy(), ra["src"]) <= TOL[prec], s
+
+
+@pytest.mark.parametrize("prec,bound", [("f64", 1e-12), ("f32", 1e-5)])
+def test_gpu_dot_product(prec, bound):
+    v, geom, p = _ragged_case()
+    ctx = _ctx(v, geom, p, prec)
+    nt, N = p["nt"], v.size
+    q = synth.normal(17, (geom.ns, nt) + v.shape)
+    e = synth.normal(18, (nt * geom.rec_offset[-1],))
+    Sq = ctx.forward(ext=_dev(q, prec)).double().cpu().numpy()
+    STe, _ = ctx.adjoint(_dev(e, prec))
+    STe = STe.double().cpu().numpy()
+    lhs, rhs = float(np.sum(Sq * e)), float(np.sum(q * STe))
+    assert abs(lhs - rhs) / (np.linalg.norm(Sq) * np.linalg.norm(e)) <= bound
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_3d_forward_adjoint(prec):
+    shape = (70, 21, 37)   # two z chunks, ragged x / y tiles
+    dx, dt, nt, nb = 10.0, 1e-3, 50, 4
+    v = synth.dipping_layers(shape, dx, 3, nlayers=3, vmin=1500, vmax=2500, nanom=1,
+                             sigma=3 * dx)
+    rx = np.array([35.0, 122.5, 300.0, 360.0])
+    ry = np.array([0.0, 101.0, 200.0])
+    geom = synth.surface_grid_3d((183.0, 96.5, 333.0), rx, ry, 655.5)
+    p = dict(dx=dx, dt=dt, nt=nt, nb=nb)
+    ctx = _ctx(v, geom, p, prec)
+    o, (sh,) = _orc(v, geom, p)
+    wav = synth.ricker(nt, dt, 30.0)[None, :]
+    q = synth.normal(3, (1, nt) + shape) * 1e-3
+    d = ctx.forward(wavelet=_dev(wav, prec), ext=_dev(q, prec))
+    ref = o.forward(sh, wavelet=wav[0], q_ext=q[0])["traces"]
+    assert oracle.rel_l2(ctx.traces_of(d, 0).cpu().numpy(), ref) <= TOL[prec]
+    e = synth.normal(4, (nt, sh.nr))
+    f, wv = ctx.adjoint(_dev(e.ravel(), prec), want_wavelet=True)
+    ra = o.adjoint(sh, e, want_src=True)
+    assert oracle.rel_l2(f[0].reshape(nt, -1).cpu().numpy(), ra["out"]) <= TOL[prec]
+    assert oracle.rel_l2(wv[0].cpu().numpy(), ra["src"]) <= TOL[prec]
+
+
+# ----------------------------------------------------------------------------- gradient
+def _grad_case():
+    shape, dx, dt, nt, nb = (36, 70), 10.0, 1e-3, 130, 8
+    v0 = synth.dipping_layers(shape, dx, 5, nlayers=4, vmin=1500, vmax=2500, nanom=2,
+                              sigma=30.0)
+    vt = v0 + synth.gaussian_blob(shape, dx, 21, amp=80.0, sigma=50.0)
+    recs = [np.arange(10.0, 690.0, 20.0), np.arange(5.0, 400.0, 12.5)]
+    geom = synth.surface_line(2, [215.0, 505.0], 40.0, recs, 40.0)
+    return v0, vt, geom, dict(dx=dx, dt=dt, nt=nt, nb=nb)
+
+
+@pytest.mark.parametrize("prec,ckpt,K,tol", [("f64", "f32", 7, 1e-12), ("f32", "f32", 20, 1e-4),
+                                            ("f32", "f16", 20, 1e-3), ("f32", "bf16", 20, 1e-3)])
+def test_adjoint_state_gradient(prec, ckpt, K, tol):
+    v0, vt, geom, p = _grad_case()
+    vref = 2700.0
+    ot, shots_t = _orc(vt, geom, p, vref=vref)
+    o, shots = _orc(v0, geom, p, vref=vref)
+    nt = p["nt"]
+    wav = np.stack([synth.ricker(nt, p["dt"], 20.0)] * geom.ns)
+    dobs = np.concatenate([ot.forward(sh, wavelet=wav[s])["traces"].ravel()
+                           for s, sh in enumerate(shots_t)])
+    g_ref = np.zeros(v0.size)
+    J_ref = 0.0
+    for s, sh in enumerate(shots):
+        o0, o1 = geom.rec_offset[s], geom.rec_offset[s + 1]
+        J, g = o.misfit_gradient(sh, dobs[nt * o0:nt * o1], wavelet=wav[s], param="v")
+        J_ref += J
+        g_ref += g
+    ctx = _ctx(v0, geom, p, prec, vref=vref)
+    g, J = ctx.gradient(wavelet=_dev(wav, prec), dobs=_dev(dobs, prec), param="v",
+                        ckpt_every=K, ckpt=ckpt)
+    assert oracle.rel_l2(g.double().cpu().numpy().ravel(), g_ref) <= tol
+    assert abs(J - J_ref) <= max(tol, 1e-6 if prec == "f32" else 0) * abs(J_ref)
+
+
+def test_gradient_vjp_and_saddle_fp64():
+    v0, vt, geom, p = _grad_case()
+    o, shots = _orc(v0, geom, p, vref=2700.0)
+    ctx = _ctx(v0, geom, p, "f64", vref=2700.0)
+    nt = p["nt"]
+    q = synth.normal(31, (geom.ns, nt) + v0.shape) * 1e-2
+    e = synth.normal(32, (nt * geom.rec_offset[-1],))
+    g, _ = ctx.gradient(ext=_dev(q, "f64"), adj_src=_dev(e, "f64"), param="c", ckpt_every=9)
+    g_ref = np.zeros(v0.size)
+    for s, sh in enumerate(shots):
+        o0, o1 = geom.rec_offset[s], geom.rec_offset[s + 1]
+        fw = o.forward(sh, q_ext=q[s].reshape(nt, -1), want_s=True)
+        g_ref += o.adjoint(sh, e[nt * o0:nt * o1], want_out=False, s_hist=fw["s"])["grad_c"]
+    assert oracle.rel_l2(g.cpu().numpy().ravel(), g_ref) <= 1e-12
+    beta = 0.37
+    gs, _ = ctx.gradient(ext=_dev(q, "f64"), mode="saddle", beta=beta, param="m")
+    gs_ref = sum(o.saddle_gradient(sh, q[s], beta, param="m") for s, sh in enumerate(shots))
+    assert oracle.rel_l2(gs.cpu().numpy().ravel(), gs_ref) <= 1e-12
+
+
+# ----------------------------------------------------------------------------- CG (Algorithm 1)
+def test_cg_small_2d_fp64_five_iterations():
+    w = synth.workload_small_2d()
+    p = dict(dx=w.dx, dt=w.dt, nt=w.nt, nb=w.nb)
+    o, (sh,) = _orc(w.v_true, w.geom, p)
+    d = o.forward(sh, wavelet=w.wavelets()[0])["traces"]
+    ref = o.cg(sh, d, beta=1.0, tol=0.0, n_cg=5)
+    ctx = _ctx(w.v_true, w.geom, p, "f64")
+    q, rep = ctx.cg_solve(_dev(d.ravel(), "f64"), lam=1.0, tol=0.0, max_iter=5)
+    assert rep["iters"][0] == 5
+    assert np.allclose(rep["rel_res"][0], ref["rel_res"], rtol=1e-12, atol=0)
+    assert oracle.rel_l2(q[0].reshape(w.nt, -1).cpu().numpy(), ref["x"]) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_cg_multishot_per_shot_stopping(prec):
+    v, geom, p = _ragged_case(nt=80)
+    o, shots = _orc(v, geom, p)
+    nt = p["nt"]
+    wav = np.stack([synth.ricker(nt, p["dt"], 25.0)] * geom.ns)
+    d = np.concatenate([o.forward(sh, wavelet=wav[s])["traces"].ravel()
+                        for s, sh in enumerate(shots)])
+    lam, tol, nmax = 2e-6, 0.05, 12
+    ctx = _ctx(v, geom, p, prec)
+    q, rep = ctx.cg_solve(_dev(d, prec), lam=lam, tol=tol, max_iter=nmax)
+    for s, sh in enumerate(shots):
+        o0, o1 = geom.rec_offset[s], geom.rec_offset[s + 1]
+        ref = o.cg(sh, d[nt * o0:nt * o1].reshape(nt, -1), lam, tol, nmax)
+        assert rep["iters"][s] == ref["iters"], s
+        assert np.allclose(rep["rel_res"][s], ref["rel_res"], rtol=TOL[prec], atol=0), s
+        assert oracle.rel_l2(q[s].reshape(nt, -1).double().cpu().numpy(), ref["x"]) <= \
+            (TOL[prec] if prec == "f64" else 1e-3), s
+
+
+# ----------------------------------------------------------------------------- DTFT
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_dft_extract(prec):
+    v, geom, p = _ragged_case(nt=150)
+    o, shots = _orc(v, geom, p)
+    nt = p["nt"]
+    wav = np.stack([synth.ricker(nt, p["dt"], 20.0)] * geom.ns)
+    freqs = [6.0, 11.0, 23.5]
+    out, _ = _ctx(v, geom, p, prec).dft_extract(freqs, wavelet=_dev(wav, prec))
+    hout, scales = _ctx(v, geom, p, prec).dft_extract(freqs, wavelet=_dev(wav, prec), half=True)
+    for s, sh in enumerate(shots):
+        ref = o.forward(sh, wavelet=wav[s], freqs=freqs)["dft"]
+        got = out[s].double().cpu().numpy().reshape(len(freqs), -1, 2)
+        gc = got[..., 0] + 1j * got[..., 1]
+        assert oracle.rel_l2(gc, ref) <= TOL[prec]
+        h = hout[s].float().cpu().numpy().reshape(len(freqs), -1, 2) * scales[s][:, None, None]
+        hc = h[..., 0] + 1j * h[..., 1]
+        for m in range(len(freqs)):
+            assert oracle.rel_l2(hc[m], ref[m]) <= 1e-3
+
+
+# ----------------------------------------------------------------------------- edge cases
+def test_rejects_cfl_and_outside_points():
+    esi = _esi()
+    v, geom, p = _ragged_case()
+    with pytest.raises(esi.EsiError) as ei:
+        _ctx(v * 4.0, geom, p, "f32")
+    assert ei.value.status == esi.ESI_ERR_CFL
+    bad = synth.surface_line(1, [1e6], 30.0, [np.array([10.0])], 20.0)
+    with pytest.raises(esi.EsiError) as ei:
+        _ctx(v, bad, p, "f32")
+    assert ei.value.status == esi.ESI_ERR_ARG
+
+
+def test_single_step_and_corner_points():
+    shape, dx, dt, nt, nb = (9, 11), 10.0, 1e-3, 3, 2
+    v = np.full(shape, 2000.0)
+    geom = synth.surface_line(1, [0.0], 0.0, [np.array([0.0, 100.0, 55.0, 10.0])], 0.0)
+    p = dict(dx=dx, dt=dt, nt=nt, nb=nb)
+    o, (sh,) = _orc(v, geom, p)
+    ctx = _ctx(v, geom, p, "f64")
+    wav = np.array([[1.0, -0.5, 0.25]])
+    d = ctx.forward(wavelet=_dev(wav, "f64"))
+    ref = o.forward(sh, wavelet=wav[0])["traces"]
+    assert np.allclose(ctx.traces_of(d, 0).cpu().numpy(), ref, rtol=1e-13, atol=1e-300)
