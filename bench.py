@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark of the ESI hot path on one GB300 (or N, one process per GPU).
+
+One step = the inner problem of Algorithm 2 for a batch of shots on the 801 x 241,
+nt = 3000, 16-shot FP32 workload (seeded dipping layers + anomalies, 8 Hz Ricker data):
+  set-up of c = v^2 dt^2 for the current model;
+  b = S^T d and Algorithm 1 (CG) on (S^T S + beta B^T B) q = S^T d to ||r|| < 1e-3 ||r_0||;
+  the saddle-point gradient of Algorithm 2 (u = A^{-1} q, lambda = beta B^H B q);
+  the on-the-fly DTFT of u = A^{-1} q at 2, 4, 6, 8 Hz into FP16.
+The metric is FD cell-updates per second over every forward and adjoint propagation of
+the step (Gcell/s), with the CG time to 1e-3 reported beside it.
+
+Multi-GPU: shots are independent systems, so each rank solves its own 16 shots (weak
+scaling) with no collective on the data path; ranks meet only at the timing barriers.
+
+--impl reference times the FP64 CPU oracle on the host cores (a bounded sample of the
+same workload: one shot's forward + adjoint over nt_sample steps per bench step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FD Gcell-updates/s fwd+adj; ESI CG time to 1e-3 residual, plain vs learned PC"
+UNIT = "Gcell-updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--ns", type=int, default=16, help="shots per GPU")
+    ap.add_argument("--nt", type=int, default=3000)
+    ap.add_argument("--tol", type=float, default=1e-3)
+    ap.add_argument("--max-iter", type=int, default=60)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ref-nt", type=int, default=1500, help="oracle sample: steps per bench step")
+    return ap.parse_args()
+
+
+def workload_name(ns, nt):
+    return f"esi2d-801x241-nt{nt}-{ns}shots-fp32"
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from paper_2211_06300_gb300 import synth
+    w = synth.workload_esi_2d(nt=args.ref_nt, ns=1)
+    o = oracle.Oracle(w.v_start, w.dx, w.dt, w.nt, w.nb, vref=float(w.v_true.max()))
+    sh = o.shot(w.geom.src_xyz[0], w.geom.receivers(0))
+    wav = w.wavelets()[0]
+
+    def step():
+        d = o.forward(sh, wavelet=wav)["traces"]
+        o.adjoint(sh, d)
+        return 2 * w.ncell * w.nt
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    cells = sum(step() for _ in range(args.steps))
+    dt = time.perf_counter() - t0
+    val = cells / dt / 1e9
+    sample = f"1 shot x {w.nt} steps forward + adjoint on the 801x241 grid, FP64 oracle"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(args.ns, args.nt), "reference_sample": sample},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def cpu_baseline(nt_sample=3000, shots=4):
+    """The oracle as it stands on the host cores: `shots` shots of the same workload, one
+    forward + one adjoint modelling each over nt_sample steps (about 10-20 s)."""
+    import oracle
+    from paper_2211_06300_gb300 import synth
+    w = synth.workload_esi_2d(nt=nt_sample, ns=shots)
+    o = oracle.Oracle(w.v_start, w.dx, w.dt, w.nt, w.nb, vref=float(w.v_true.max()))
+    wav = w.wavelets()
+    t0 = time.perf_counter()
+    for s in range(shots):
+        sh = o.shot(w.geom.src_xyz[s], w.geom.receivers(s))
+        d = o.forward(sh, wavelet=wav[s])["traces"]
+        o.adjoint(sh, d)
+    dt = time.perf_counter() - t0
+    return {"value": 2 * shots * w.ncell * w.nt / dt / 1e9, "unit": UNIT,
+            "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{shots} shots x {nt_sample} steps forward + adjoint (801x241, FP64), "
+                      f"{dt:.1f} s"}
+
+
+# ----------------------------------------------------------------------------- CUDA arm
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+    from paper_2211_06300_gb300 import esi, synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ns, nt = args.ns, args.nt
+    wl = synth.workload_esi_2d(nt=nt, ns=ns * world)
+    geom = wl.geom.select(range(rank * ns, (rank + 1) * ns))
+    vref = float(wl.v_true.max())
+    f32 = torch.float32
+    v_true = torch.tensor(wl.v_true, dtype=f32, device=dev)
+    v0 = torch.tensor(wl.v_start, dtype=f32, device=dev)
+    wav = torch.tensor(wl.wavelets()[:ns], dtype=f32, device=dev)
+    # observed data: forward modelling on the true model (untimed set-up)
+    ctx_t = esi.Context(v_true, wl.dx, wl.dt, nt, wl.nb, geom, vref=vref)
+    dobs = ctx_t.forward(wavelet=wav)
+    ctx_t.close()
+    del ctx_t
+    ctx = esi.Context(v0, wl.dx, wl.dt, nt, wl.nb, geom, vref=vref)
+    # penalty: beta = 1e-2 lambda_max(S^T S) / max B^2 (power iterations on the first shot)
+    g1 = geom.select([0])
+    c1 = esi.Context(v0, wl.dx, wl.dt, nt, wl.nb, g1, vref=vref)
+    torch.manual_seed(0)
+    p = torch.randn((1, nt) + wl.shape, dtype=f32, device=dev)
+    lam = 0.0
+    for _ in range(8):
+        p = p / p.norm()
+        f, _ = c1.adjoint(c1.forward(ext=p))
+        lam = float((f * p).sum())
+        p = f
+    del p, f
+    c1.close()
+    del c1
+    nz, nx = wl.shape
+    far = max(math.hypot(x, z) for x in (0.0, (nx - 1) * wl.dx) for z in (0.0, (nz - 1) * wl.dx))
+    beta = 1e-2 * lam / (far + wl.dx) ** 2
+    freqs = [2.0, 4.0, 6.0, 8.0]
+    q = torch.empty((ns, nt) + wl.shape, dtype=f32, device=dev)
+    N = wl.ncell
+
+    def step(d_obs):
+        ctx.set_velocity(v0)
+        _, rep = ctx.cg_solve(d_obs, lam=beta, tol=args.tol, max_iter=args.max_iter, out=q)
+        g, _ = ctx.gradient(ext=q, mode="saddle", beta=beta, param="v")
+        U, _ = ctx.dft_extract(freqs, ext=q, half=True)
+        props = sum(1 + 2 * int(k) + 2 for k in rep["iters"])   # b, CG products, grad, DTFT
+        return g, rep, props * N * nt
+
+    for _ in range(args.warmup):
+        step(dobs)
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = ctx.launches
+    ctx.set_profiling(True)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    cells, reps = 0, []
+    for _ in range(args.steps):
+        _, rep, c = step(dobs)
+        cells += c
+        reps.append(rep)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    prof = ctx.profile()
+    ctx.set_profiling(False)
+    launches = ctx.launches - l0
+    clk = clocks.stop()
+    t_max = ms
+    cells_all = cells
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t)
+        c = torch.tensor([float(cells)], dtype=torch.float64, device=dev)
+        dist.all_reduce(c)
+        cells_all = float(c)
+    value = cells_all / (t_max * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers: pinned d_obs in, gradient out
+    e2e = None
+    if not args.no_e2e:
+        d_host = dobs.cpu().pin_memory()
+        d_dev = torch.empty_like(dobs)
+        barrier()
+        t0 = time.perf_counter()
+        ce = 0
+        g_host = None
+        for _ in range(args.steps):
+            d_dev.copy_(d_host, non_blocking=True)
+            g, rep, c = step(d_dev)
+            g_host = g.cpu()
+            ce += c
+        barrier()
+        te = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([te], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t)
+            c = torch.tensor([float(ce)], dtype=torch.float64, device=dev)
+            dist.all_reduce(c)
+            ce = float(c)
+        e2e = {"value": ce / te / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(d_host.numel() * d_host.element_size()),
+               "d2h_bytes_per_step": int(g_host.numel() * g_host.element_size())}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    # dominant kernel = largest accumulated device time
+    roof = None
+    if prof:
+        top = max(prof, key=lambda k: k["ms"])
+        per_launch_ms = top["ms"] / max(top["launches"], 1)
+        bytes_per_launch = top["cells"] * top["bytes_per_cell"] / max(top["launches"], 1)
+        achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": top["name"], "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_src,
+                "traffic": None, "per_launch_us": 1e3 * per_launch_ms,
+                "bytes_per_launch": bytes_per_launch,
+                "share": top["ms"] / sum(k["ms"] for k in prof)}
+    iters = [int(max(r["iters"])) for r in reps]
+    cg_ms = [r["ms_total"] for r in reps]
+    cb = None
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            cb = cpu_baseline()
+        except Exception as ex:  # the baseline is a report, never a blocker
+            cb = {"error": str(ex)}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(ns, nt), "grid": "801x241 (z 241, x 801)",
+                   "nt": nt, "shots_per_gpu": ns, "tol": args.tol, "beta": beta,
+                   "freqs_hz": freqs, "precond": "none",
+                   "l2": "inputs larger than L2 (CG vectors 4 x 37 GB per GPU)"},
+        "cg": {"iters_max_per_step": iters, "time_to_tol_ms": cg_ms,
+               "converged": [bool(r["converged"]) for r in reps],
+               "rel_res_last": float(reps[-1]["rel_res"][0][-1]) if reps[-1]["rel_res"][0].size else None},
+        "roofline": roof, "kernels": prof, "cpu_baseline": cb, "e2e": e2e,
+        "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -226,6 +226,24 @@ ESI_API const char *esi_last_error(const esi_ctx *ctx);
 /* Number of kernels this context has launched since creation (for accounting). */
 ESI_API long long esi_launch_count(const esi_ctx *ctx);
 
+/*
+ * Kernel timing (tracing).  When enabled, every run of consecutive launches of one
+ * kernel variant (a propagation loop, a CG vector pass) is bracketed by CUDA events on
+ * the context stream and accumulated per variant.  esi_get_profile synchronises the
+ * stream, fills up to max entries and returns the number of variants seen; the
+ * counters reset when profiling is (re-)enabled.
+ */
+typedef struct esi_kernel_stat {
+    char name[48];       /* e.g. "fd2_step[CGP|SMP]" */
+    long long launches;  /* kernel launches */
+    long long cells;     /* cell updates (or vector elements) processed */
+    double bytes_per_cell;  /* algorithmic HBM bytes per cell update / element */
+    double ms;           /* accumulated device time between the bracketing events */
+} esi_kernel_stat;
+
+ESI_API esi_status esi_set_profiling(esi_ctx *ctx, int on);
+ESI_API int esi_get_profile(esi_ctx *ctx, esi_kernel_stat *out, int max);
+
 #ifdef __cplusplus
 }
 #endif

@@ -84,6 +84,32 @@ struct esi_ctx {
     long long total_rec = 0;
     std::string err;
     long long launches = 0;
+    // tracing: events bracketing runs of one kernel variant
+    struct Pending {
+        std::string name;
+        double bpc;
+        long long launches, cells;
+        cudaEvent_t a, b;
+    };
+    struct Stat {
+        std::string name;
+        double bpc = 0;
+        long long launches = 0, cells = 0;
+        double ms = 0;
+    };
+    bool prof = false;
+    int prof_active = 0;  // shots being advanced (cells per launch = prof_active * N)
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> evpool;
+    std::vector<Stat> stats;
+
+    ~esi_ctx() {
+        for (auto &p : pending) {
+            cudaEventDestroy(p.a);
+            cudaEventDestroy(p.b);
+        }
+        for (auto e : evpool) cudaEventDestroy(e);
+    }
 
     esi_status fail(esi_status s, const std::string &m) {
         err = m;
@@ -106,6 +132,59 @@ struct esi_ctx {
     } while (0)
 
 namespace {
+
+cudaEvent_t prof_mark(esi_ctx *ctx) {
+    if (!ctx->prof) return nullptr;
+    cudaEvent_t e = nullptr;
+    if (!ctx->evpool.empty()) {
+        e = ctx->evpool.back();
+        ctx->evpool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        return nullptr;
+    }
+    cudaEventRecord(e, ctx->st);
+    return e;
+}
+
+void prof_close(esi_ctx *ctx, cudaEvent_t a, const std::string &name, double bpc,
+                long long launches, long long cells) {
+    if (!a) return;
+    cudaEvent_t b = prof_mark(ctx);
+    if (!b) {
+        ctx->evpool.push_back(a);
+        return;
+    }
+    ctx->pending.push_back({name, bpc, launches, cells, a, b});
+}
+
+std::string step_name(const esi_ctx *ctx, unsigned f) {
+    static const char *names[] = {"EXT", "CGP", "PT", "SMP", "OUT", "AP", "STW", "GRD", "SAD", "DFT"};
+    std::string s = ctx->g.ndim == 2 ? "fd2_step[" : "fd3_step[";
+    bool first = true;
+    for (int i = 0; i < 10; ++i)
+        if (f & (1u << i)) {
+            if (!first) s += "|";
+            s += names[i];
+            first = false;
+        }
+    return s + "]";
+}
+
+// algorithmic HBM bytes per cell update of a step variant: the stencil reads u_n, u_{n-1}
+// and c and writes u_{n+1}; each fused stream adds its own reads / writes
+double step_bpc(const esi_ctx *ctx, unsigned f, int nf) {
+    const double e = ctx->esz;
+    double b = 4 * e;
+    if (f & F_EXT) b += e;
+    if (f & F_CGP) b += 3 * e;
+    if (f & F_OUT) b += e;
+    if (f & F_AP) b += 2 * e;
+    if (f & F_STW) b += e;
+    if (f & F_GRD) b += 3 * e;
+    if (f & F_SAD) b += 2 * e;
+    if (f & F_DFT) b += 4.0 * nf * e;
+    return b;
+}
 
 template <typename U>
 cudaError_t upload(DBuf &b, const std::vector<U> &v, cudaStream_t st) {
@@ -438,6 +517,7 @@ template <typename T>
 esi_status fwd_loop(esi_ctx *ctx, StepArgs<T> a, unsigned flags, T *&cur, T *&po, int n0,
                     int n1, std::vector<std::pair<int, int>> *ckpt_at = nullptr) {
     (void)ckpt_at;
+    cudaEvent_t ev = prof_mark(ctx);
     for (int n = n0; n < n1; ++n) {
         a.cur = cur;
         a.po = po;
@@ -449,12 +529,15 @@ esi_status fwd_loop(esi_ctx *ctx, StepArgs<T> a, unsigned flags, T *&cur, T *&po
         if (e != ESI_OK) return e;
         std::swap(cur, po);
     }
+    prof_close(ctx, ev, step_name(ctx, flags), step_bpc(ctx, flags, a.nf), n1 - n0,
+               (long long)(n1 - n0) * ctx->prof_active * ctx->N);
     return ESI_OK;
 }
 
 template <typename T>
 esi_status forward_impl(esi_ctx *ctx, const void *wavelet, const void *ext, void *traces,
                         const double *freqs, int nf, T *dft_acc) {
+    ctx->prof_active = ctx->ns;
     esi_status e = ensure_states<T>(ctx, false);
     if (e != ESI_OK) return e;
     CK(cudaMemsetAsync(ctx->u0.p, 0, ctx->u0.n, ctx->st));
@@ -505,6 +588,7 @@ esi_status forward_impl(esi_ctx *ctx, const void *wavelet, const void *ext, void
 template <typename T>
 esi_status adj_loop(esi_ctx *ctx, StepArgs<T> a, unsigned flags, T *&cur, T *&po, int j1,
                     int j0, bool sample_src) {
+    cudaEvent_t ev = prof_mark(ctx);
     for (int j = j1; j > j0; --j) {
         a.cur = cur;
         a.po = po;
@@ -517,11 +601,14 @@ esi_status adj_loop(esi_ctx *ctx, StepArgs<T> a, unsigned flags, T *&cur, T *&po
         if (e != ESI_OK) return e;
         std::swap(cur, po);
     }
+    prof_close(ctx, ev, step_name(ctx, flags), step_bpc(ctx, flags, a.nf), j1 - j0,
+               (long long)(j1 - j0) * ctx->prof_active * ctx->N);
     return ESI_OK;
 }
 
 template <typename T>
 esi_status adjoint_impl(esi_ctx *ctx, const void *traces, void *ext_out, void *wav_out) {
+    ctx->prof_active = ctx->ns;
     esi_status e = ensure_states<T>(ctx, true);
     if (e != ESI_OK) return e;
     CK(cudaMemsetAsync(ctx->a0.p, 0, ctx->a0.n, ctx->st));
@@ -591,6 +678,7 @@ esi_status gradient_impl(esi_ctx *ctx, const void *wavelet, const void *ext, con
                          const void *adj, const esi_grad_opts *o, void *grad, double *misfit) {
     const long long N = ctx->N;
     const int ns = ctx->ns, nt = ctx->nt;
+    ctx->prof_active = ns;
     esi_status e = ensure_states<T>(ctx, true);
     if (e != ESI_OK) return e;
     CK(ctx->gacc.ensure((size_t)ns * N * sizeof(T)));
@@ -773,6 +861,8 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
     bool any_bad = false;
     for (k = 0; k < max_iter; ++k) {
         const auto t0 = clk::now();
+        ctx->prof_active = 0;
+        for (int s = 0; s < ns; ++s) ctx->prof_active += h_active[s];
         // forward half of the product, fused with p = r + beta p (p0 = r0)
         CK(cudaMemsetAsync(ctx->u0.p, 0, ctx->u0.n, ctx->st));
         CK(cudaMemsetAsync(ctx->u1.p, 0, ctx->u1.n, ctx->st));
@@ -807,8 +897,10 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
         CKL(launch_reduce_partials(ctx->part.as<double>(), nblk_step, ns, pap, ctx->st));
         CKL(launch_cg_alpha(rr_old, pap, alpha, bad, active, ns, ctx->st));
         const auto t1 = clk::now();
+        cudaEvent_t ev = prof_mark(ctx);
         CKL(launch_cg_update<T>(x, r, p, ap, len, len, ns, alpha, active, ctx->part.as<double>(),
                                 nblk_vec, ctx->st));
+        prof_close(ctx, ev, "cg_update", 6.0 * sizeof(T), 1, (long long)ctx->prof_active * len);
         CKL(launch_reduce_partials(ctx->part.as<double>(), nblk_vec, ns, rr_new, ctx->st));
         CK(cudaMemcpyAsync(rrn.data(), rr_new, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->st));
         CK(cudaMemcpyAsync(h_bad.data(), bad, sizeof(int) * ns, cudaMemcpyDeviceToHost, ctx->st));
@@ -897,6 +989,53 @@ ESI_API const char *esi_last_error(const esi_ctx *ctx) {
 }
 
 ESI_API long long esi_launch_count(const esi_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+ESI_API esi_status esi_set_profiling(esi_ctx *ctx, int on) {
+    if (!ctx) return ESI_ERR_ARG;
+    cudaStreamSynchronize(ctx->st);
+    for (auto &p : ctx->pending) {
+        ctx->evpool.push_back(p.a);
+        ctx->evpool.push_back(p.b);
+    }
+    ctx->pending.clear();
+    ctx->stats.clear();
+    ctx->prof = on != 0;
+    return ESI_OK;
+}
+
+ESI_API int esi_get_profile(esi_ctx *ctx, esi_kernel_stat *out, int max) {
+    if (!ctx) return 0;
+    cudaStreamSynchronize(ctx->st);
+    for (auto &p : ctx->pending) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        esi_ctx::Stat *st = nullptr;
+        for (auto &x : ctx->stats)
+            if (x.name == p.name) st = &x;
+        if (!st) {
+            ctx->stats.push_back(esi_ctx::Stat());
+            st = &ctx->stats.back();
+            st->name = p.name;
+            st->bpc = p.bpc;
+        }
+        st->launches += p.launches;
+        st->cells += p.cells;
+        st->ms += ms;
+        ctx->evpool.push_back(p.a);
+        ctx->evpool.push_back(p.b);
+    }
+    ctx->pending.clear();
+    const int n = (int)ctx->stats.size();
+    for (int i = 0; i < n && i < max && out; ++i) {
+        std::memset(out[i].name, 0, sizeof(out[i].name));
+        std::strncpy(out[i].name, ctx->stats[i].name.c_str(), sizeof(out[i].name) - 1);
+        out[i].launches = ctx->stats[i].launches;
+        out[i].cells = ctx->stats[i].cells;
+        out[i].bytes_per_cell = ctx->stats[i].bpc;
+        out[i].ms = ctx->stats[i].ms;
+    }
+    return n;
+}
 
 ESI_API esi_status esi_create(esi_ctx **out, const esi_grid *grid, const esi_geometry *geom,
                               const void *velocity_dev, double dt, int nt, void *stream) {

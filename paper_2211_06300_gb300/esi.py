@@ -27,7 +27,8 @@ PC = {"none": 0, "diag": 1, "learned": 2}
 # every symbol the header declares (checked by the CPU test-suite)
 EXPORTS = ["esi_create", "esi_destroy", "esi_set_stream", "esi_set_velocity", "esi_forward",
            "esi_adjoint", "esi_gradient", "esi_dft_extract", "esi_cg_solve", "esi_pc_load",
-           "esi_status_string", "esi_last_error", "esi_launch_count"]
+           "esi_status_string", "esi_last_error", "esi_launch_count", "esi_set_profiling",
+           "esi_get_profile"]
 
 
 class EsiGrid(ctypes.Structure):
@@ -54,6 +55,12 @@ class EsiCgReport(ctypes.Structure):
                 ("rel_res", ctypes.POINTER(ctypes.c_double)), ("ms_matvec", ctypes.c_double),
                 ("ms_vector", ctypes.c_double), ("ms_precond", ctypes.c_double),
                 ("ms_total", ctypes.c_double)]
+
+
+class EsiKernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_longlong),
+                ("cells", ctypes.c_longlong), ("bytes_per_cell", ctypes.c_double),
+                ("ms", ctypes.c_double)]
 
 
 _lib = None
@@ -96,6 +103,10 @@ def load_library(require_gpu: bool = True) -> ctypes.CDLL:
     L.esi_last_error.restype = ctypes.c_char_p
     L.esi_launch_count.argtypes = [vp]
     L.esi_launch_count.restype = ctypes.c_longlong
+    L.esi_set_profiling.argtypes = [vp, i]
+    L.esi_set_profiling.restype = i
+    L.esi_get_profile.argtypes = [vp, ctypes.POINTER(EsiKernelStat), i]
+    L.esi_get_profile.restype = i
     for name in ("esi_create", "esi_set_stream", "esi_set_velocity", "esi_forward",
                  "esi_adjoint", "esi_gradient", "esi_dft_extract", "esi_cg_solve",
                  "esi_pc_load"):
@@ -210,6 +221,18 @@ class Context:
     @property
     def launches(self) -> int:
         return int(self.L.esi_launch_count(self.h))
+
+    def set_profiling(self, on: bool = True):
+        self._check(self.L.esi_set_profiling(self.h, 1 if on else 0))
+
+    def profile(self):
+        """Per kernel variant: launches, cells, algorithmic bytes per cell, device ms."""
+        n = self.L.esi_get_profile(self.h, None, 0)
+        arr = (EsiKernelStat * max(n, 1))()
+        n = self.L.esi_get_profile(self.h, arr, n)
+        return [{"name": arr[i].name.decode(), "launches": int(arr[i].launches),
+                 "cells": int(arr[i].cells), "bytes_per_cell": float(arr[i].bytes_per_cell),
+                 "ms": float(arr[i].ms)} for i in range(n)]
 
     # ---------------------------------------------------------------- operators
     def set_velocity(self, v):
