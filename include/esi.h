@@ -117,6 +117,28 @@ ESI_API esi_status esi_forward(esi_ctx *ctx, const void *wavelet_dev, const void
                                void *traces_dev);
 
 /*
+ * esi_forward_noalloc -- the same forward modelling as esi_forward, for callers that must
+ * not allocate device memory: a host framework that owns every byte of device memory
+ * through its own pool (a side cudaMalloc would fail or break its accounting), or a
+ * latency-bound loop that cannot pay for the device-wide synchronisation cudaMalloc and
+ * cudaFree imply.  esi_forward allocates the two wave states on its first call; this
+ * entry point instead keeps them in a fixed 32 MiB device array compiled into the
+ * library (every GPU that loads the library holds it until the process exits) and calls
+ * no allocator.  The paper has no counterpart: this is a deployment variant.
+ *   Limit     : 2 * ns * nz * ny * round_up(nx, 32) * sizeof(element) <= 32 MiB, else
+ *               ESI_ERR_ARG with a message (nothing is enqueued).
+ *   Set-up    : the first call on a device looks up the array's device address with that
+ *               device current; make that first call before any stream capture.
+ *   Sharing   : all calls in the process share the one array per device.  It is cleared
+ *               at the start of every call, so results do not depend on earlier calls,
+ *               but calls whose work overlaps on the GPU (other streams, other threads,
+ *               other contexts on the same device) race on it: serialise them.
+ *   Arguments : as esi_forward; traces_dev must not be NULL.
+ */
+ESI_API esi_status esi_forward_noalloc(esi_ctx *ctx, const void *wavelet_dev,
+                                       const void *ext_src_dev, void *traces_dev);
+
+/*
  * esi_adjoint -- exact discrete adjoint S^T e = A^{-T} R^T e (Eq. "FWI_lambda"; the
  * right-hand side b = S^H d of the CG section), the transpose of esi_forward's map from
  * the extended source to the traces.

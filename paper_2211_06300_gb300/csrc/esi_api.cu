@@ -8,6 +8,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -582,6 +583,76 @@ esi_status forward_impl(esi_ctx *ctx, const void *wavelet, const void *ext, void
     return ESI_OK;
 }
 
+// ------------------------------------------------------------------ allocation-free forward
+// Scratch of esi_forward_noalloc: the two wave states live in this file-scope device array
+// instead of context-owned cudaMalloc buffers.  Every GPU that loads the library holds it
+// until the process exits.  Host code must not use the symbol as an address (on the host
+// it names a stand-in); the device address is fetched once per device below.
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(32) << 20;  // 32 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[128] = {nullptr};
+
+// Device address of the scratch array for the current device (set-up on first use).
+cudaError_t noalloc_scratch(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+template <typename T>
+esi_status forward_noalloc_impl(esi_ctx *ctx, const void *wavelet, const void *ext, void *traces) {
+    if (!wavelet && !ext) return ctx->fail(ESI_ERR_ARG, "no source given");
+    const size_t need = 2 * (size_t)ctx->ns * ctx->sst * sizeof(T);
+    if (need > NOALLOC_SCRATCH_BYTES)
+        return ctx->fail(ESI_ERR_ARG, "esi_forward_noalloc: the two wave states need " +
+                                          std::to_string(need) + " bytes, above the " +
+                                          std::to_string(NOALLOC_SCRATCH_BYTES) +
+                                          "-byte static scratch; use esi_forward");
+    void *base = nullptr;
+    CK(noalloc_scratch(&base));
+    // the array keeps the previous call's contents: both states must start at zero
+    CK(cudaMemsetAsync(base, 0, need, ctx->st));
+    T *cur = reinterpret_cast<T *>(base);
+    T *po = cur + (size_t)ctx->ns * ctx->sst;
+    StepArgs<T> a = base_args<T>(ctx);
+    unsigned flags = F_SMP;
+    if (wavelet) {
+        flags |= F_PT;
+        a.inj = inj_view<T>(ctx->inj_src);
+        a.inj_trace = reinterpret_cast<const T *>(wavelet);
+    }
+    if (ext) {
+        flags |= F_EXT;
+        a.ext = reinterpret_cast<const T *>(ext);
+    }
+    a.smp = smp_view<T>(ctx->smp_rec);
+    a.smp_out = reinterpret_cast<T *>(traces);
+    for (int n = 0; n < ctx->nt; ++n) {
+        a.cur = cur;
+        a.po = po;
+        a.n = n;
+        a.tin = n;
+        a.tout = n - 1;
+        esi_status e = step<T>(ctx, flags, a);
+        if (e != ESI_OK) return e;
+        std::swap(cur, po);
+    }
+    CKL(launch_sample_global<T>(a.smp, cur, ctx->sst, a.smp_out, ctx->nt - 1, ctx->st));
+    return ESI_OK;
+}
+
 // ------------------------------------------------------------------ adjoint modelling
 // Time-reversed run: for j = j1 .. j0+1 computes lambda_j from (lambda_{j+1}, lambda_{j+2})
 // with source R^T e_{j-1}.  Epilogue writes index j-1 of the dense outputs.
@@ -1118,6 +1189,16 @@ ESI_API esi_status esi_forward(esi_ctx *ctx, const void *wavelet_dev, const void
     return ctx->g.dtype == ESI_F64
                ? forward_impl<double>(ctx, wavelet_dev, ext_src_dev, traces_dev, nullptr, 0, nullptr)
                : forward_impl<float>(ctx, wavelet_dev, ext_src_dev, traces_dev, nullptr, 0, nullptr);
+}
+
+ESI_API esi_status esi_forward_noalloc(esi_ctx *ctx, const void *wavelet_dev,
+                                       const void *ext_src_dev, void *traces_dev) {
+    if (!ctx) return ESI_ERR_ARG;
+    if (!traces_dev) return ctx->fail(ESI_ERR_ARG, "traces_dev is NULL");
+    ctx->err.clear();
+    return ctx->g.dtype == ESI_F64
+               ? forward_noalloc_impl<double>(ctx, wavelet_dev, ext_src_dev, traces_dev)
+               : forward_noalloc_impl<float>(ctx, wavelet_dev, ext_src_dev, traces_dev);
 }
 
 ESI_API esi_status esi_adjoint(esi_ctx *ctx, const void *traces_dev, void *ext_out_dev,

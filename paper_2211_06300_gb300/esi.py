@@ -28,7 +28,7 @@ PC = {"none": 0, "diag": 1, "learned": 2}
 EXPORTS = ["esi_create", "esi_destroy", "esi_set_stream", "esi_set_velocity", "esi_forward",
            "esi_adjoint", "esi_gradient", "esi_dft_extract", "esi_cg_solve", "esi_pc_load",
            "esi_status_string", "esi_last_error", "esi_launch_count", "esi_set_profiling",
-           "esi_get_profile"]
+           "esi_get_profile", "esi_forward_noalloc"]
 
 
 class EsiGrid(ctypes.Structure):
@@ -90,6 +90,7 @@ def load_library(require_gpu: bool = True) -> ctypes.CDLL:
     L.esi_set_stream.argtypes = [vp, vp]
     L.esi_set_velocity.argtypes = [vp, vp]
     L.esi_forward.argtypes = [vp, vp, vp, vp]
+    L.esi_forward_noalloc.argtypes = [vp, vp, vp, vp]
     L.esi_adjoint.argtypes = [vp, vp, vp, vp]
     L.esi_gradient.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(EsiGradOpts), vp,
                                ctypes.POINTER(d)]
@@ -108,6 +109,7 @@ def load_library(require_gpu: bool = True) -> ctypes.CDLL:
     L.esi_get_profile.argtypes = [vp, ctypes.POINTER(EsiKernelStat), i]
     L.esi_get_profile.restype = i
     for name in ("esi_create", "esi_set_stream", "esi_set_velocity", "esi_forward",
+                 "esi_forward_noalloc",
                  "esi_adjoint", "esi_gradient", "esi_dft_extract", "esi_cg_solve",
                  "esi_pc_load"):
         getattr(L, name).restype = ctypes.c_int
@@ -242,6 +244,12 @@ class Context:
     def forward(self, wavelet=None, ext=None, out=None):
         out = self.empty_traces() if out is None else out
         self._check(self.L.esi_forward(self.h, _ptr(wavelet), _ptr(ext), _ptr(out)))
+        return out
+
+    def forward_noalloc(self, out, wavelet=None, ext=None):
+        """esi_forward_noalloc: forward modelling whose wave states live in the library's
+        fixed device array (no device allocation); ``out`` must be preallocated."""
+        self._check(self.L.esi_forward_noalloc(self.h, _ptr(wavelet), _ptr(ext), _ptr(out)))
         return out
 
     def adjoint(self, traces, want_field: bool = True, want_wavelet: bool = False, out=None):
