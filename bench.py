@@ -4,11 +4,14 @@
 One step = the inner problem of Algorithm 2 for a batch of shots on the 801 x 241,
 nt = 3000, 16-shot FP32 workload (seeded dipping layers + anomalies, 8 Hz Ricker data):
   set-up of c = v^2 dt^2 for the current model;
-  b = S^T d and Algorithm 1 (CG) on (S^T S + beta B^T B) q = S^T d to ||r|| < 1e-3 ||r_0||;
+  b = S^T d and CG on (S^T S + beta B^T B) q = S^T d to ||r|| < 1e-3 ||r_0|| with the best
+  available preconditioner (learned if loaded, else the diagonal z = r / (beta B^2));
   the saddle-point gradient of Algorithm 2 (u = A^{-1} q, lambda = beta B^H B q);
   the on-the-fly DTFT of u = A^{-1} q at 2, 4, 6, 8 Hz into FP16.
 The metric is FD cell-updates per second over every forward and adjoint propagation of
-the step (Gcell/s), with the CG time to 1e-3 reported beside it.
+the step (Gcell/s).  Beside it: the CG time to 1e-3 of that solve and of plain Algorithm 1
+(no preconditioner, capped at --plain-iter iterations; the residual it reaches is given
+when the cap comes first).
 
 Multi-GPU: shots are independent systems, so each rank solves its own 16 shots (weak
 scaling) with no collective on the data path; ranks meet only at the timing barriers.
@@ -44,6 +47,9 @@ def parse():
     ap.add_argument("--nt", type=int, default=3000)
     ap.add_argument("--tol", type=float, default=1e-3)
     ap.add_argument("--max-iter", type=int, default=60)
+    ap.add_argument("--plain-iter", type=int, default=60)
+    ap.add_argument("--beta-factor", type=float, default=10.0)
+    ap.add_argument("--precond", default="diag", choices=["none", "diag", "learned"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-nt", type=int, default=1500, help="oracle sample: steps per bench step")
@@ -215,14 +221,15 @@ def main():
     del c1
     nz, nx = wl.shape
     far = max(math.hypot(x, z) for x in (0.0, (nx - 1) * wl.dx) for z in (0.0, (nz - 1) * wl.dx))
-    beta = 1e-2 * lam / (far + wl.dx) ** 2
+    beta = args.beta_factor * lam / (far + wl.dx) ** 2
     freqs = [2.0, 4.0, 6.0, 8.0]
     q = torch.empty((ns, nt) + wl.shape, dtype=f32, device=dev)
     N = wl.ncell
 
-    def step(d_obs):
+    def step(d_obs, precond=args.precond, max_iter=args.max_iter):
         ctx.set_velocity(v0)
-        _, rep = ctx.cg_solve(d_obs, lam=beta, tol=args.tol, max_iter=args.max_iter, out=q)
+        _, rep = ctx.cg_solve(d_obs, lam=beta, tol=args.tol, max_iter=max_iter, out=q,
+                              precond=precond)
         g, _ = ctx.gradient(ext=q, mode="saddle", beta=beta, param="v")
         U, _ = ctx.dft_extract(freqs, ext=q, half=True)
         props = sum(1 + 2 * int(k) + 2 for k in rep["iters"])   # b, CG products, grad, DTFT
@@ -314,6 +321,15 @@ def main():
                 "share": top["ms"] / sum(k["ms"] for k in prof)}
     iters = [int(max(r["iters"])) for r in reps]
     cg_ms = [r["ms_total"] for r in reps]
+    # plain Algorithm 1 (no preconditioner) on the same system, for the comparison
+    plain = None
+    if args.plain_iter > 0:
+        torch.cuda.synchronize()
+        _, prep_, _ = step(dobs, precond="none", max_iter=args.plain_iter)
+        reached = bool(prep_["converged"])
+        plain = {"iters_max": int(max(prep_["iters"])), "time_ms": prep_["ms_total"],
+                 "reached_tol": reached,
+                 "rel_res_max_over_shots": float(max(r[-1] for r in prep_["rel_res"] if r.size))}
     cb = None
     if not args.no_cpu_baseline and world == 1:
         try:
@@ -326,11 +342,12 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name(ns, nt), "grid": "801x241 (z 241, x 801)",
                    "nt": nt, "shots_per_gpu": ns, "tol": args.tol, "beta": beta,
-                   "freqs_hz": freqs, "precond": "none",
+                   "freqs_hz": freqs, "precond": args.precond, "beta_factor": args.beta_factor,
                    "l2": "inputs larger than L2 (CG vectors 4 x 37 GB per GPU)"},
-        "cg": {"iters_max_per_step": iters, "time_to_tol_ms": cg_ms,
+        "cg": {"precond": args.precond, "iters_max_per_step": iters, "time_to_tol_ms": cg_ms,
                "converged": [bool(r["converged"]) for r in reps],
-               "rel_res_last": float(reps[-1]["rel_res"][0][-1]) if reps[-1]["rel_res"][0].size else None},
+               "rel_res_max_over_shots": float(max(r[-1] for r in reps[-1]["rel_res"] if r.size)),
+               "plain": plain},
         "roofline": roof, "kernels": prof, "cpu_baseline": cb, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk,
     }

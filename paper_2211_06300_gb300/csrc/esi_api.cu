@@ -5,12 +5,15 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
+
+#include <cudaTypedefs.h>
 
 #include "esi_internal.h"
 
@@ -75,6 +78,8 @@ struct esi_ctx {
     double vmax = 0, vref = 0, kappa_max = 0;
     int ntx = 0, nty = 1, ntz = 0, nzc = 1, ntiles = 0;
     DBuf cc, kz, ky, kx, src_pos;
+    DBuf dev_err;                  // sticky device error word (int)
+    std::vector<std::pair<const void *, CUtensorMap>> tmaps;  // TMA maps of state buffers
     DevInj inj_src, inj_rec;
     DevSmp smp_rec, smp_src;
     DBuf u0, u1, a0, a1;           // forward / adjoint state pairs [ns][sst]
@@ -100,11 +105,26 @@ struct esi_ctx {
     };
     bool prof = false;
     int prof_active = 0;  // shots being advanced (cells per launch = prof_active * N)
+    // CUDA graphs of whole time loops, keyed by the loop's launch parameters.  Captured on a
+    // private stream (capture is not allowed on the legacy default stream) and launched on
+    // the context stream; replays of an identical loop skip the per-step launch cost.
+    struct GraphEntry {
+        std::vector<unsigned char> key;
+        cudaGraphExec_t exec;
+        long long kernels;
+        unsigned long long used;
+    };
+    std::vector<GraphEntry> graphs;
+    cudaStream_t cap = nullptr;
+    bool use_graphs = true;
+    unsigned long long graph_clock = 0;
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> evpool;
     std::vector<Stat> stats;
 
     ~esi_ctx() {
+        for (auto &g : graphs) cudaGraphExecDestroy(g.exec);
+        if (cap) cudaStreamDestroy(cap);
         for (auto &p : pending) {
             cudaEventDestroy(p.a);
             cudaEventDestroy(p.b);
@@ -241,9 +261,9 @@ struct Contrib {
 // tile index and local cell of a node for the step kernels
 void tile_of(const esi_ctx *c, int s, int iz, int iy, int ix, int &tile, int &cell) {
     if (c->g.ndim == 2) {
-        const int bz = iz / TZ, bx = ix / TX;
+        const int bz = iz / TZ2, bx = ix / TX2;
         tile = (s * c->ntz + bz) * c->ntx + bx;
-        cell = (iz - bz * TZ) * TX + (ix - bx * TX);
+        cell = (iz - bz * TZ2) * TX2 + (ix - bx * TX2);
     } else {
         const int zc = iz / ZCH3_HOST, by = iy / TY3, bx = ix / TX3;
         tile = ((s * c->nzc + zc) * c->nty + by) * c->ntx + bx;
@@ -317,13 +337,13 @@ esi_status build_smp(esi_ctx *ctx, DevSmp &out, const std::vector<SmpHost> &recs
     for (int t = 0; t < ntt; ++t) {
         for (int r : by_tile[t]) {
             const SmpHost &h = recs[r];
-            const int lz0 = h.iz0 % TZ, lx0 = h.ix0 % TX;
+            const int lz0 = h.iz0 % TZ2, lx0 = h.ix0 % TX2;
             const long long gbase = ((long long)h.iz0 * ctx->g.ny + h.iy0) * ctx->px + h.ix0;
-            const int sbase = (lz0 + HALO) * SW + (lx0 + HALO);
+            const int sbase = (lz0 + HALO) * SW2 + (lx0 + HALO);
             for (int j = 0; j < MAXP; ++j) {
                 if (j < (int)h.hp.node.size()) {
                     const int dz = h.hp.iz[j] - h.iz0, dy = h.hp.iy[j] - h.iy0, dxx = h.hp.ix[j] - h.ix0;
-                    idx.push_back(sbase + dz * SW + dxx);
+                    idx.push_back(sbase + dz * SW2 + dxx);
                     gidx.push_back(((long long)h.hp.iz[j] * ctx->g.ny + h.hp.iy[j]) * ctx->px +
                                    h.hp.ix[j]);
                     (void)dy;
@@ -380,6 +400,47 @@ SmpList<T> smp_view(const DevSmp &d) {
     return l;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// TMA map of a state buffer [ns][nz][px] (2D): dims (nx, nz, ns), box (SW2, SH2, 1).  Cells
+// outside [0, nx) x [0, nz) are zero-filled by the copy engine.
+bool state_map(esi_ctx *ctx, const void *base, CUtensorMap *out) {
+    for (auto &m : ctx->tmaps)
+        if (m.first == base) {
+            *out = m.second;
+            return true;
+        }
+    auto enc = tmap_encoder();
+    if (!enc) return false;
+    CUtensorMap tm;
+    const cuuint64_t dims[3] = {(cuuint64_t)ctx->g.nx, (cuuint64_t)ctx->g.nz, (cuuint64_t)ctx->ns};
+    const cuuint64_t strides[2] = {(cuuint64_t)ctx->px * ctx->esz,
+                                   (cuuint64_t)ctx->sst * ctx->esz};
+    const cuuint32_t box[3] = {(cuuint32_t)SW2, (cuuint32_t)SH2, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(&tm, ctx->esz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                     3, const_cast<void *>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+    ctx->tmaps.push_back({base, tm});
+    *out = tm;
+    return true;
+}
+
 template <typename T>
 StepArgs<T> base_args(esi_ctx *ctx) {
     StepArgs<T> a;
@@ -391,6 +452,7 @@ StepArgs<T> base_args(esi_ctx *ctx) {
     a.sst = ctx->sst;
     a.N = ctx->N;
     a.fst = ctx->N * ctx->nt;
+    a.fstp = ctx->sst * ctx->nt;
     a.ntx = ctx->ntx;
     a.nty = ctx->nty;
     a.ntz = ctx->ntz;
@@ -403,6 +465,7 @@ StepArgs<T> base_args(esi_ctx *ctx) {
     a.src_pos = ctx->src_pos.as<double>();
     a.ns = ctx->ns;
     a.tout = -1;
+    a.dev_err = ctx->dev_err.as<int>();
     return a;
 }
 
@@ -410,7 +473,10 @@ StepArgs<T> base_args(esi_ctx *ctx) {
 template <typename T>
 esi_status step(esi_ctx *ctx, unsigned flags, const StepArgs<T> &a) {
     if (ctx->g.ndim == 2) {
-        CKL(launch_step2<T>(flags, a, ctx->ns, ctx->st));
+        StepArgs<T> b = a;
+        if (!state_map(ctx, a.cur, &b.tm))
+            return ctx->fail(ESI_ERR_CUDA, "cuTensorMapEncodeTiled failed for a state buffer");
+        CKL(launch_step2<T>(flags, b, ctx->ns, ctx->st));
     } else {
         if ((flags & F_SMP) && a.tout >= 0)
             CKL(launch_sample_global<T>(a.smp, a.cur, ctx->sst, a.smp_out, a.tout, ctx->st));
@@ -448,8 +514,8 @@ esi_status setup_model(esi_ctx *ctx, const void *vel, bool first) {
         const double eta_max =
             nb > 0 ? 3.0 * ctx->vref * std::log(1.0 / ctx->g.sponge_R) / (2.0 * nb * ctx->g.dx) : 0.0;
         ctx->kappa_max = eta_max * ctx->dt / 2.0;
-        auto prof = [&](int n, bool used) {
-            std::vector<T> p(std::max(n, 1), T(0));
+        auto prof = [&](int n, bool used, int len) {
+            std::vector<T> p(std::max(len, 1), T(0));
             if (!used || nb <= 0) return p;
             for (int i = 0; i < n; ++i) {
                 const int d = std::max(std::max(nb - i, i - (n - 1 - nb)), 0);
@@ -458,9 +524,10 @@ esi_status setup_model(esi_ctx *ctx, const void *vel, bool first) {
             }
             return p;
         };
-        CK(upload(ctx->kz, prof(ctx->g.nz, true), ctx->st));
-        CK(upload(ctx->ky, prof(ctx->g.ny, ctx->g.ndim == 3), ctx->st));
-        CK(upload(ctx->kx, prof(ctx->g.nx, true), ctx->st));
+        CK(upload(ctx->kz, prof(ctx->g.nz, true, ctx->g.nz), ctx->st));
+        CK(upload(ctx->ky, prof(ctx->g.ny, ctx->g.ndim == 3, ctx->g.ny), ctx->st));
+        // padded to the x pitch (zeros) for 16-byte loads
+        CK(upload(ctx->kx, prof(ctx->g.nx, true, ctx->px), ctx->st));
     }
     return ESI_OK;
 }
@@ -511,6 +578,94 @@ esi_status ensure_states(esi_ctx *ctx, bool adj) {
     return ESI_OK;
 }
 
+// Reads the sticky device error word (after a synchronisation point of the call).
+esi_status check_dev_err(esi_ctx *ctx) {
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, ctx->dev_err.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (h == DEV_ERR_TMA_TIMEOUT)
+        return ctx->fail(ESI_ERR_TIMEOUT, "a TMA tile wait ran out of its iteration limit");
+    if (h) return ctx->fail(ESI_ERR_TIMEOUT, "device error word " + std::to_string(h));
+    return ESI_OK;
+}
+
+// ------------------------------------------------------------------ loop graphs
+constexpr int GRAPH_MIN_STEPS = 32;   // shorter loops are launched directly
+constexpr size_t GRAPH_CACHE = 8;      // instantiated loops kept per context
+
+template <typename T>
+std::vector<unsigned char> loop_key(const StepArgs<T> &a, unsigned flags, int dir, int i0, int i1,
+                                    bool sample_src, const T *cur, const T *po) {
+    std::vector<unsigned char> k(sizeof(a) + 64);
+    std::memcpy(k.data(), &a, sizeof(a));  // base_args zero-fills, so padding is zero
+    unsigned char *q = k.data() + sizeof(a);
+    std::memset(q, 0, 64);
+    std::memcpy(q, &flags, 4);
+    std::memcpy(q + 4, &dir, 4);
+    std::memcpy(q + 8, &i0, 4);
+    std::memcpy(q + 12, &i1, 4);
+    const int ss = sample_src;
+    std::memcpy(q + 16, &ss, 4);
+    std::memcpy(q + 24, &cur, sizeof(cur));
+    std::memcpy(q + 32, &po, sizeof(po));
+    return k;
+}
+
+// Launch a cached graph of this loop if present; returns true when it did.
+bool graph_replay(esi_ctx *ctx, const std::vector<unsigned char> &key, esi_status &st) {
+    for (auto &g : ctx->graphs)
+        if (g.key == key) {
+            cudaError_t e = cudaGraphLaunch(g.exec, ctx->st);
+            if (e != cudaSuccess) {
+                st = ctx->fail(ESI_ERR_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+            } else {
+                st = ESI_OK;
+                ctx->launches += g.kernels;
+                g.used = ++ctx->graph_clock;
+            }
+            return true;
+        }
+    return false;
+}
+
+// Capture `body` (which enqueues on ctx->st) into a graph, cache it and launch it.
+template <typename F>
+esi_status graph_capture(esi_ctx *ctx, std::vector<unsigned char> &&key, F &&body) {
+    if (!ctx->cap) CK(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
+    cudaStream_t user = ctx->st;
+    const long long l0 = ctx->launches;
+    CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+    ctx->st = ctx->cap;
+    esi_status e = body();
+    ctx->st = user;
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(ctx->cap, &graph);
+    if (e != ESI_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return e;
+    }
+    if (ce != cudaSuccess) return ctx->fail(ESI_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
+    cudaGraphExec_t exec = nullptr;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess)
+        return ctx->fail(ESI_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ce));
+    const long long kernels = ctx->launches - l0;
+    ctx->launches = l0;  // counted when the graph runs
+    if (ctx->graphs.size() >= GRAPH_CACHE) {
+        auto lru = std::min_element(ctx->graphs.begin(), ctx->graphs.end(),
+                                    [](const esi_ctx::GraphEntry &x, const esi_ctx::GraphEntry &y) {
+                                        return x.used < y.used;
+                                    });
+        cudaGraphExecDestroy(lru->exec);
+        ctx->graphs.erase(lru);
+    }
+    ctx->graphs.push_back({std::move(key), exec, kernels, ++ctx->graph_clock});
+    esi_status st;
+    graph_replay(ctx, ctx->graphs.back().key, st);
+    return st;
+}
+
 // ------------------------------------------------------------------ forward modelling
 // Runs steps [n0, n1) starting from states (cur, po) = (u_{n0}, u_{n0-1}); on return
 // cur holds u_{n1}.  Sampling of the inputs writes traces[n-1].
@@ -519,17 +674,31 @@ esi_status fwd_loop(esi_ctx *ctx, StepArgs<T> a, unsigned flags, T *&cur, T *&po
                     int n1, std::vector<std::pair<int, int>> *ckpt_at = nullptr) {
     (void)ckpt_at;
     cudaEvent_t ev = prof_mark(ctx);
-    for (int n = n0; n < n1; ++n) {
-        a.cur = cur;
-        a.po = po;
-        a.n = n;
-        a.tin = n;
-        a.tout = n - 1;
-        a.slot_w = n - n0;
-        esi_status e = step<T>(ctx, flags, a);
-        if (e != ESI_OK) return e;
-        std::swap(cur, po);
+    T *c0 = cur, *p0 = po;
+    auto body = [&]() -> esi_status {
+        T *c = c0, *q = p0;
+        for (int n = n0; n < n1; ++n) {
+            a.cur = c;
+            a.po = q;
+            a.n = n;
+            a.tin = n;
+            a.tout = n - 1;
+            a.slot_w = n - n0;
+            esi_status e = step<T>(ctx, flags, a);
+            if (e != ESI_OK) return e;
+            std::swap(c, q);
+        }
+        return ESI_OK;
+    };
+    esi_status e;
+    if (ctx->use_graphs && n1 - n0 >= GRAPH_MIN_STEPS) {
+        auto key = loop_key(a, flags, +1, n0, n1, false, c0, p0);
+        if (!graph_replay(ctx, key, e)) e = graph_capture(ctx, std::move(key), body);
+    } else {
+        e = body();
     }
+    if (e != ESI_OK) return e;
+    if ((n1 - n0) & 1) std::swap(cur, po);
     prof_close(ctx, ev, step_name(ctx, flags), step_bpc(ctx, flags, a.nf), n1 - n0,
                (long long)(n1 - n0) * ctx->prof_active * ctx->N);
     return ESI_OK;
@@ -660,25 +829,40 @@ template <typename T>
 esi_status adj_loop(esi_ctx *ctx, StepArgs<T> a, unsigned flags, T *&cur, T *&po, int j1,
                     int j0, bool sample_src) {
     cudaEvent_t ev = prof_mark(ctx);
-    for (int j = j1; j > j0; --j) {
-        a.cur = cur;
-        a.po = po;
-        a.n = j - 1;
-        a.tin = j - 1;
-        a.nout = j - 1;
-        a.tout = (sample_src && j <= ctx->nt - 1) ? j : -1;
-        a.slot_r = (j - 1) - j0;
-        esi_status e = step<T>(ctx, flags, a);
-        if (e != ESI_OK) return e;
-        std::swap(cur, po);
+    T *c0 = cur, *p0 = po;
+    auto body = [&]() -> esi_status {
+        T *c = c0, *q = p0;
+        for (int j = j1; j > j0; --j) {
+            a.cur = c;
+            a.po = q;
+            a.n = j - 1;
+            a.tin = j - 1;
+            a.nout = j - 1;
+            a.tout = (sample_src && j <= ctx->nt - 1) ? j : -1;
+            a.slot_r = (j - 1) - j0;
+            esi_status e = step<T>(ctx, flags, a);
+            if (e != ESI_OK) return e;
+            std::swap(c, q);
+        }
+        return ESI_OK;
+    };
+    esi_status e;
+    if (ctx->use_graphs && j1 - j0 >= GRAPH_MIN_STEPS) {
+        auto key = loop_key(a, flags, -1, j0, j1, sample_src, c0, p0);
+        if (!graph_replay(ctx, key, e)) e = graph_capture(ctx, std::move(key), body);
+    } else {
+        e = body();
     }
+    if (e != ESI_OK) return e;
+    if ((j1 - j0) & 1) std::swap(cur, po);
     prof_close(ctx, ev, step_name(ctx, flags), step_bpc(ctx, flags, a.nf), j1 - j0,
                (long long)(j1 - j0) * ctx->prof_active * ctx->N);
     return ESI_OK;
 }
 
 template <typename T>
-esi_status adjoint_impl(esi_ctx *ctx, const void *traces, void *ext_out, void *wav_out) {
+esi_status adjoint_impl(esi_ctx *ctx, const void *traces, void *ext_out, void *wav_out,
+                        bool pitched_out = false) {
     ctx->prof_active = ctx->ns;
     esi_status e = ensure_states<T>(ctx, true);
     if (e != ESI_OK) return e;
@@ -691,6 +875,10 @@ esi_status adjoint_impl(esi_ctx *ctx, const void *traces, void *ext_out, void *w
     if (ext_out) {
         flags |= F_OUT;
         a.fout = reinterpret_cast<T *>(ext_out);
+        // caller fields are dense; the CG right-hand side goes to an internal pitched vector
+        a.opx = pitched_out ? ctx->px : ctx->g.nx;
+        a.oplane = pitched_out ? ctx->sst : ctx->N;
+        a.ofst = a.oplane * ctx->nt;
     }
     if (wav_out) {
         flags |= F_SMP;
@@ -752,8 +940,8 @@ esi_status gradient_impl(esi_ctx *ctx, const void *wavelet, const void *ext, con
     ctx->prof_active = ns;
     esi_status e = ensure_states<T>(ctx, true);
     if (e != ESI_OK) return e;
-    CK(ctx->gacc.ensure((size_t)ns * N * sizeof(T)));
-    CK(cudaMemsetAsync(ctx->gacc.p, 0, (size_t)ns * N * sizeof(T), ctx->st));
+    CK(ctx->gacc.ensure((size_t)ns * ctx->sst * sizeof(T)));
+    CK(cudaMemsetAsync(ctx->gacc.p, 0, (size_t)ns * ctx->sst * sizeof(T), ctx->st));
     const T eps = T(o->eps > 0 ? o->eps : ctx->g.dx);
     double extra = 1.0;
     if (o->mode == ESI_GRAD_SADDLE_POINT) {
@@ -778,7 +966,7 @@ esi_status gradient_impl(esi_ctx *ctx, const void *wavelet, const void *ext, con
         CK(ctx->ckpt.ensure((size_t)nseg * 2 * ns * ctx->sst * csz));
         CK(ctx->ckpt_scale.ensure(sizeof(float) * nseg * 2 * ns));
         CK(ctx->absbits.ensure(sizeof(unsigned) * ns));
-        CK(ctx->stash.ensure((size_t)K * ns * N * sizeof(T)));
+        CK(ctx->stash.ensure((size_t)K * ns * ctx->sst * sizeof(T)));
         CK(ctx->traces.ensure(std::max<size_t>((size_t)ctx->total_rec * nt * sizeof(T), 16)));
         // 1) forward with checkpoints (u_{n0}, u_{n0-1}) at n0 = k K, traces into scratch
         CK(cudaMemsetAsync(ctx->u0.p, 0, ctx->u0.n, ctx->st));
@@ -843,10 +1031,11 @@ esi_status gradient_impl(esi_ctx *ctx, const void *wavelet, const void *ext, con
             CK(cudaMemcpyAsync(misfit, ctx->scal.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
         }
     }
-    CKL(launch_grad_finalize<T>(ctx->gacc.as<T>(), ns, N, ctx->cc.as<T>(), ctx->g.nz, ctx->g.ny,
-                                ctx->g.nx, ctx->px, nullptr, ctx->dt, ctx->g.dx, extra, o->param,
+    (void)N;
+    CKL(launch_grad_finalize<T>(ctx->gacc.as<T>(), ns, ctx->sst, ctx->cc.as<T>(), ctx->g.nz,
+                                ctx->g.ny, ctx->g.nx, ctx->px, ctx->dt, ctx->g.dx, extra, o->param,
                                 reinterpret_cast<T *>(grad), ctx->st));
-    if (misfit && !adj && o->mode != ESI_GRAD_SADDLE_POINT) CK(cudaStreamSynchronize(ctx->st));
+    if (misfit && !adj && o->mode != ESI_GRAD_SADDLE_POINT) return check_dev_err(ctx);
     return ESI_OK;
 }
 
@@ -855,26 +1044,24 @@ template <typename T>
 esi_status dft_impl(esi_ctx *ctx, const void *wavelet, const void *ext, const double *freqs,
                     int nf, void *out, int kind, float *scales, void *traces) {
     if (nf <= 0 || !freqs || !out) return ctx->fail(ESI_ERR_ARG, "need frequencies and an output");
-    const size_t accb = (size_t)ctx->ns * nf * ctx->N * 2 * sizeof(T);
-    T *acc;
-    if (kind == ESI_DFT_C64) {
-        acc = reinterpret_cast<T *>(out);
-    } else if (kind == ESI_DFT_C32_HALF) {
-        if (!scales) return ctx->fail(ESI_ERR_ARG, "half output needs a scales array");
-        CK(ctx->dftacc.ensure(accb));
-        acc = ctx->dftacc.as<T>();
-    } else {
+    if (kind != ESI_DFT_C64 && kind != ESI_DFT_C32_HALF)
         return ctx->fail(ESI_ERR_ARG, "unknown DTFT output kind");
-    }
+    if (kind == ESI_DFT_C32_HALF && !scales)
+        return ctx->fail(ESI_ERR_ARG, "half output needs a scales array");
+    // accumulators in the internal pitched layout [ns][nf][sst][2]
+    const size_t accb = (size_t)ctx->ns * nf * ctx->sst * 2 * sizeof(T);
+    CK(ctx->dftacc.ensure(accb));
+    T *acc = ctx->dftacc.as<T>();
     CK(cudaMemsetAsync(acc, 0, accb, ctx->st));
     esi_status e = forward_impl<T>(ctx, wavelet, ext, traces, freqs, nf, acc);
     if (e != ESI_OK) return e;
-    if (kind == ESI_DFT_C32_HALF) {
-        CK(ctx->absbits.ensure(sizeof(unsigned) * ctx->ns * nf));
-        CK(ctx->ckpt_scale.ensure(std::max(ctx->ckpt_scale.n, sizeof(float) * ctx->ns * nf)));
-        CKL(launch_dft_to_half<T>(acc, ctx->N, ctx->ns, nf, out, ctx->absbits.as<unsigned>(),
-                                  ctx->ckpt_scale.as<float>(), ctx->st));
-        ++ctx->launches;
+    const int half = kind == ESI_DFT_C32_HALF;
+    CK(ctx->absbits.ensure(sizeof(unsigned) * ctx->ns * nf));
+    CK(ctx->ckpt_scale.ensure(std::max(ctx->ckpt_scale.n, sizeof(float) * ctx->ns * nf)));
+    CKL(launch_dft_output<T>(acc, ctx->sst, ctx->g.nz * ctx->g.ny, ctx->g.nx, ctx->px, ctx->ns, nf,
+                             half, out, ctx->absbits.as<unsigned>(), ctx->ckpt_scale.as<float>(),
+                             ctx->st));
+    if (half) {
         CK(cudaMemcpyAsync(scales, ctx->ckpt_scale.p, sizeof(float) * ctx->ns * nf,
                            cudaMemcpyDeviceToHost, ctx->st));
         CK(cudaStreamSynchronize(ctx->st));
@@ -883,58 +1070,74 @@ esi_status dft_impl(esi_ctx *ctx, const void *wavelet, const void *ext, const do
 }
 
 // ------------------------------------------------------------------ CG (Algorithm 1)
+// Per shot: x0 = 0, r0 = b = S^T d, p0 = z0; alpha = rho / <p, A p>; x += alpha p;
+// r -= alpha A p; stop when ||r_{k+1}|| < tol ||r_0|| or k = max_iter - 1; beta = rho_new /
+// rho; p = z + beta p, where z = r (no preconditioner, Algorithm 1 as printed) or
+// z = r / (lambda B^2) (diagonal preconditioner) and rho = <r, z>.  The work vectors r, p,
+// A p live in the internal pitched layout; x is the caller's dense q_out.
 template <typename T>
 esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const void *dobs,
                    void *q_out, int precond, double eps_in, esi_cg_report *rep) {
     using clk = std::chrono::steady_clock;
     const auto t_start = clk::now();
-    double ms_mv = 0, ms_vec = 0;
     const int ns = ctx->ns, nt = ctx->nt;
-    const long long len = ctx->N * nt;  // one space-time vector per shot
-    if (precond != ESI_PC_NONE)
-        return ctx->fail(ESI_ERR_UNSUPPORTED, "only the unpreconditioned solver is available");
+    const long long plen = ctx->sst * nt;                       // pitched vector per shot
+    const long long rows = (long long)nt * ctx->g.nz * ctx->g.ny;
+    if (precond != ESI_PC_NONE && precond != ESI_PC_DIAG)
+        return ctx->fail(ESI_ERR_UNSUPPORTED, "the learned preconditioner is not loaded");
+    if (precond == ESI_PC_DIAG && !(lambda > 0))
+        return ctx->fail(ESI_ERR_ARG, "the diagonal preconditioner needs lambda > 0");
     if (max_iter < 1) return ctx->fail(ESI_ERR_ARG, "max_iter must be >= 1");
     esi_status e = ensure_states<T>(ctx, true);
     if (e != ESI_OK) return e;
-    const size_t vb = (size_t)ns * len * sizeof(T);
+    const size_t vb = (size_t)ns * plen * sizeof(T);
     CK(ctx->cg_r.ensure(vb));
     CK(ctx->cg_p.ensure(vb));
     CK(ctx->cg_ap.ensure(vb));
     CK(ctx->traces.ensure(std::max<size_t>((size_t)ctx->total_rec * nt * sizeof(T), 16)));
     const int nblk_step = ctx->g.ndim == 2 ? ctx->ntx * ctx->ntz : ctx->ntx * ctx->nty * ctx->nzc;
-    const int nblk_vec = 1184;  // 8 x 148
-    CK(ctx->part.ensure(sizeof(double) * (size_t)ns * std::max(nblk_step, nblk_vec)));
-    // scalars: rr_old[ns] rr_new[ns] pap[ns] alpha[ns] beta[ns] | ints: active[ns] bad[ns]
-    CK(ctx->scal.ensure(sizeof(double) * 5 * ns + sizeof(int) * 2 * ns));
-    double *rr_old = ctx->scal.as<double>(), *rr_new = rr_old + ns, *pap = rr_new + ns,
+    const int nblk_vec = 1216;  // 8 x 152 SMs
+    const size_t npart = (size_t)ns * std::max(nblk_step, nblk_vec);
+    CK(ctx->part.ensure(sizeof(double) * npart));
+    CK(ctx->part2.ensure(sizeof(double) * npart));
+    // device scalars: rho[ns] rr[ns] rho_new[ns] pap[ns] alpha[ns] beta[ns] | active[ns] bad[ns]
+    CK(ctx->scal.ensure(sizeof(double) * 6 * ns + sizeof(int) * 2 * ns));
+    double *rho = ctx->scal.as<double>(), *rr = rho + ns, *rho_new = rr + ns, *pap = rho_new + ns,
            *alpha = pap + ns, *beta = alpha + ns;
     int *active = reinterpret_cast<int *>(beta + ns), *bad = active + ns;
     T *x = reinterpret_cast<T *>(q_out), *r = ctx->cg_r.as<T>(), *p = ctx->cg_p.as<T>(),
       *ap = ctx->cg_ap.as<T>(), *tr = ctx->traces.as<T>();
     const T eps = T(eps_in > 0 ? eps_in : ctx->g.dx);
+    const T pc = precond == ESI_PC_DIAG ? T(lambda) : T(0);
+    double *rz_part = pc > T(0) ? ctx->part2.as<double>() : nullptr;
     std::vector<int> h_active(ns, 1), h_bad(ns, 0), iters(ns, 0);
-    CK(cudaMemcpyAsync(active, h_active.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemsetAsync(bad, 0, sizeof(int) * ns, ctx->st));
-    CK(cudaMemsetAsync(x, 0, vb, ctx->st));
+    CK(cudaMemsetAsync(alpha, 0, sizeof(double) * ns, ctx->st));
+    CK(cudaMemsetAsync(x, 0, (size_t)ns * ctx->N * nt * sizeof(T), ctx->st));
     // b = S^T d, written straight into r (x0 = 0, r0 = b)
-    e = adjoint_impl<T>(ctx, dobs, r, nullptr);
+    e = adjoint_impl<T>(ctx, dobs, r, nullptr, true);
     if (e != ESI_OK) return e;
-    CKL(launch_dot<T>(r, r, len, len, ns, ctx->part.as<double>(), nblk_vec, nullptr, ctx->st));
-    CKL(launch_reduce_partials(ctx->part.as<double>(), nblk_vec, ns, rr_old, ctx->st));
+    // ||r0||^2 and rho0 = <r0, z0>: the update pass with alpha = 0 (p = Ap = r)
+    CKL(launch_cg_update<T>(x, r, r, r, rows, ctx->g.nx, ctx->px, ns, alpha, nullptr,
+                            ctx->part.as<double>(), rz_part, nblk_vec, pc, ctx->src_pos.as<double>(),
+                            ctx->g.nz, ctx->g.ny, eps, T(ctx->g.dx), ctx->st));
+    CKL(launch_reduce_partials(ctx->part.as<double>(), nblk_vec, ns, rr, ctx->st));
+    CKL(launch_reduce_partials(rz_part ? rz_part : ctx->part.as<double>(), nblk_vec, ns, rho, ctx->st));
     std::vector<double> rr0(ns), rrn(ns);
-    CK(cudaMemcpyAsync(rr0.data(), rr_old, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(rr0.data(), rr, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     const int hist_cap = rep ? rep->max_hist : 0;
     for (int s = 0; s < ns; ++s)
         if (!(rr0[s] > 0)) h_active[s] = 0;  // b = 0: x = 0 is exact
     CK(cudaMemcpyAsync(active, h_active.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, ctx->st));
+    double ms_mv = 0, ms_vec = 0;
     int k;
     bool any_bad = false;
     for (k = 0; k < max_iter; ++k) {
         const auto t0 = clk::now();
         ctx->prof_active = 0;
         for (int s = 0; s < ns; ++s) ctx->prof_active += h_active[s];
-        // forward half of the product, fused with p = r + beta p (p0 = r0)
+        // forward half of the product, fused with p = z + beta p (p0 = z0)
         CK(cudaMemsetAsync(ctx->u0.p, 0, ctx->u0.n, ctx->st));
         CK(cudaMemsetAsync(ctx->u1.p, 0, ctx->u1.n, ctx->st));
         StepArgs<T> a = base_args<T>(ctx);
@@ -943,6 +1146,8 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
         a.cg_p = p;
         a.cg_beta = beta;
         a.cg_first = k == 0;
+        a.cg_pc = pc;
+        a.eps = eps;
         a.smp = smp_view<T>(ctx->smp_rec);
         a.smp_out = tr;
         T *cur = ctx->u0.as<T>(), *po = ctx->u1.as<T>();
@@ -966,16 +1171,22 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
         e = adj_loop<T>(ctx, b, F_PT | F_AP, acur, apo, nt, 0, false);
         if (e != ESI_OK) return e;
         CKL(launch_reduce_partials(ctx->part.as<double>(), nblk_step, ns, pap, ctx->st));
-        CKL(launch_cg_alpha(rr_old, pap, alpha, bad, active, ns, ctx->st));
+        CKL(launch_cg_alpha(rho, pap, alpha, bad, active, ns, ctx->st));
         const auto t1 = clk::now();
         cudaEvent_t ev = prof_mark(ctx);
-        CKL(launch_cg_update<T>(x, r, p, ap, len, len, ns, alpha, active, ctx->part.as<double>(),
-                                nblk_vec, ctx->st));
-        prof_close(ctx, ev, "cg_update", 6.0 * sizeof(T), 1, (long long)ctx->prof_active * len);
-        CKL(launch_reduce_partials(ctx->part.as<double>(), nblk_vec, ns, rr_new, ctx->st));
-        CK(cudaMemcpyAsync(rrn.data(), rr_new, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->st));
+        CKL(launch_cg_update<T>(x, r, p, ap, rows, ctx->g.nx, ctx->px, ns, alpha, active,
+                                ctx->part.as<double>(), rz_part, nblk_vec, pc,
+                                ctx->src_pos.as<double>(), ctx->g.nz, ctx->g.ny, eps,
+                                T(ctx->g.dx), ctx->st));
+        prof_close(ctx, ev, "cg_update", (6.0 + 0.0) * sizeof(T), 1,
+                   (long long)ctx->prof_active * ctx->N * nt);
+        CKL(launch_reduce_partials(ctx->part.as<double>(), nblk_vec, ns, rr, ctx->st));
+        CKL(launch_reduce_partials(rz_part ? rz_part : ctx->part.as<double>(), nblk_vec, ns, rho_new,
+                                   ctx->st));
+        CK(cudaMemcpyAsync(rrn.data(), rr, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->st));
         CK(cudaMemcpyAsync(h_bad.data(), bad, sizeof(int) * ns, cudaMemcpyDeviceToHost, ctx->st));
         CK(cudaStreamSynchronize(ctx->st));
+        if ((e = check_dev_err(ctx)) != ESI_OK) return e;
         const auto t2 = clk::now();
         ms_mv += std::chrono::duration<double, std::milli>(t1 - t0).count();
         ms_vec += std::chrono::duration<double, std::milli>(t2 - t1).count();
@@ -997,7 +1208,7 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
         }
         if (!any) break;
         CK(cudaMemcpyAsync(active, h_active.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, ctx->st));
-        CKL(launch_cg_beta(rr_old, rr_new, beta, active, ns, ctx->st));
+        CKL(launch_cg_beta(rho, rho_new, beta, active, ns, ctx->st));
     }
     bool conv = true;
     for (int s = 0; s < ns; ++s)
@@ -1021,6 +1232,8 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
 
 template <typename T>
 esi_status create_impl(esi_ctx *ctx, const void *vel) {
+    CK(ctx->dev_err.ensure(sizeof(int)));
+    CK(cudaMemsetAsync(ctx->dev_err.p, 0, sizeof(int), ctx->st));
     esi_status e = setup_model<T>(ctx, vel, true);
     if (e != ESI_OK) return e;
     e = setup_geometry<T>(ctx);
@@ -1130,15 +1343,15 @@ ESI_API esi_status esi_create(esi_ctx **out, const esi_grid *grid, const esi_geo
     ctx->st = reinterpret_cast<cudaStream_t>(stream);
     ctx->esz = g.dtype == ESI_F64 ? 8 : 4;
     ctx->N = (long long)g.nz * g.ny * g.nx;
-    ctx->px = (g.nx + 31) / 32 * 32;
+    ctx->px = (g.nx + PITCH - 1) / PITCH * PITCH;
     ctx->sst = (long long)g.nz * g.ny * ctx->px;
     ctx->src_xyz.assign(geom->src_xyz, geom->src_xyz + 3 * geom->ns);
     ctx->rec_off.assign(geom->rec_offset, geom->rec_offset + geom->ns + 1);
     ctx->total_rec = ctx->rec_off[ctx->ns];
     ctx->rec_xyz.assign(geom->rec_xyz, geom->rec_xyz + 3 * ctx->total_rec);
     if (g.ndim == 2) {
-        ctx->ntx = (g.nx + TX - 1) / TX;
-        ctx->ntz = (g.nz + TZ - 1) / TZ;
+        ctx->ntx = (g.nx + TX2 - 1) / TX2;
+        ctx->ntz = (g.nz + TZ2 - 1) / TZ2;
         ctx->nty = 1;
         ctx->nzc = 1;
         ctx->ntiles = ctx->ntx * ctx->ntz;
@@ -1149,6 +1362,7 @@ ESI_API esi_status esi_create(esi_ctx **out, const esi_grid *grid, const esi_geo
         ctx->ntz = ctx->nzc;
         ctx->ntiles = ctx->ntx * ctx->nty * ctx->nzc;
     }
+    if (const char *ev = std::getenv("ESI_NO_GRAPHS")) ctx->use_graphs = ev[0] == '0';
     esi_ctx *c = ctx.get();
     {
         esi_ctx *ctx = c;  // for CK

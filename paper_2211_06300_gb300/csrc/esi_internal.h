@@ -14,6 +14,7 @@
 // S^T e = A^{-T} R^T e is the same recurrence driven by R^T e from t = T down to 0.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the encoder is fetched through the runtime at run time)
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -27,14 +28,14 @@
 namespace esi {
 
 // ----------------------------------------------------------------------------- tiling
-constexpr int HALO = 4;           // stencil radius (8th order)
-constexpr int TX = 32;            // tile width (x) of the 2D step kernel
-constexpr int TZ = 32;            // tile height (z)
-constexpr int BX = 32, BY = 8;    // threads per block (x, y)
-constexpr int RZ = TZ / BY;       // cells per thread along z
-constexpr int SW = TX + 2 * HALO; // shared tile width incl. halo
-constexpr int SH = TZ + 2 * HALO; // shared tile height incl. halo
-constexpr int MAXP = 8;           // interpolation points per receiver (4 in 2D, 8 in 3D)
+constexpr int HALO = 4;             // stencil radius (8th order)
+constexpr int TX2 = 64;             // tile width (x) of the 2D step kernel
+constexpr int TZ2 = 32;             // tile height (z)
+constexpr int NT2 = 256;            // threads per block of the 2D step kernel
+constexpr int SW2 = TX2 + 2 * HALO; // shared tile width incl. halo (72: 16-byte rows)
+constexpr int SH2 = TZ2 + 2 * HALO; // shared tile height incl. halo
+constexpr int MAXP = 8;             // interpolation points per receiver (4 in 2D, 8 in 3D)
+constexpr int PITCH = 32;           // x pitch multiple of the state / internal arrays
 
 // 3D kernel tile (xy plane, marching along z)
 constexpr int TX3 = 32, TY3 = 16;
@@ -78,12 +79,20 @@ struct SmpList {
     int nrec = 0;
 };
 
+// Layouts.  States and every internal field (CG vectors, stash, accumulators) are pitched:
+// plane = nz * ny * px elements, x pitch px = round_up(nx, 32), pad columns zero.  Fields
+// owned by the caller (extended sources, adjoint outputs) are dense: plane N = nz*ny*nx.
 template <typename T>
 struct StepArgs {
+    CUtensorMap tm;            // 2D kernel: TMA map of the input state, box (SW2, SH2, 1)
+    int *dev_err;              // sticky device error word (bounded waits that gave up)
     int nz, ny, nx, px;        // grid and pitch (elements) of the state arrays
-    long long sst;             // shot stride of state arrays
-    long long N;               // dense field size nz*ny*nx
-    long long fst;             // shot stride of dense space-time fields (nt * N)
+    long long sst;             // pitched plane (= shot stride of state arrays)
+    long long N;               // dense plane nz*ny*nx
+    long long fst;             // shot stride of dense caller space-time fields (nt * N)
+    long long fstp;            // shot stride of internal pitched space-time fields (nt * sst)
+    int opx;                   // row pitch of the F_OUT target (nx: caller, px: internal)
+    long long oplane, ofst;    // its plane and shot strides
     int ntx, nty, ntz;         // tiles per shot
     const T *cur;              // input state
     T *po;                     // in: older state, out: new state
@@ -99,6 +108,7 @@ struct StepArgs {
     T *cg_p;
     const double *cg_beta;
     int cg_first;
+    T cg_pc;                   // > 0: diagonal preconditioner z = r / (cg_pc B^2) in p' = z + beta p
     // point injection at trace time tin
     InjList<T> inj;
     const T *inj_trace;
@@ -107,27 +117,33 @@ struct StepArgs {
     SmpList<T> smp;
     T *smp_out;
     int tout;
-    // dense output of the new state at time nout: fout + s*fst + nout*N
+    // output of the new state at time nout: fout + s*ofst + nout*oplane + row*opx + x
     T *fout;
     int nout;
-    // CG product: ap/ap_p at time nout; <p,Ap> block partials per shot
+    // CG product (internal pitched): ap/ap_p at time nout; <p,Ap> block partials per shot
     T *ap;
     const T *ap_p;
     double *dot_part;
     T pen;                     // penalty beta
     const double *src_pos;     // [ns][3] source (x, y, z) metres
     T eps, dx;
-    // stash [slot][ns][N] dense; write slot sw, read slot sr
+    // stash [slot][ns][sst] pitched; write slot sw, read slot sr
     T *stash_w;
     const T *stash_r;
     int slot_w, slot_r, ns;
-    // gradient accumulators [ns][N] dense
+    // gradient accumulators [ns][sst] pitched
     T *grad;
-    // DTFT: twiddles [nt][nf][2] (cos, sin) of the new state's time; acc [ns][nf][N][2]
+    // DTFT: twiddles [nt][nf][2] (cos, sin) of the new state's time; acc [ns][nf][sst][2]
     int nf;
     const T *twid;
     T *dft;
 };
+
+// device error codes written to StepArgs::dev_err
+constexpr int DEV_ERR_TMA_TIMEOUT = 1;
+// iteration limit of the mbarrier wait for a TMA tile (a tile arrives in microseconds;
+// the limit is seconds of polling)
+constexpr long long TMA_WAIT_LIMIT = 1ll << 26;
 
 // ----------------------------------------------------------------------------- launchers
 template <typename T>
@@ -152,33 +168,31 @@ cudaError_t launch_dot(const T *a, const T *b, long long len, long long sstride,
 cudaError_t launch_reduce_partials(const double *part, int nblk, int ns, double *out,
                                    cudaStream_t st);
 
-// x += alpha p ; r -= alpha Ap ; partial ||r||^2
+// x += alpha p (x dense caller layout) ; r -= alpha Ap (pitched) ; partial ||r||^2.
+// rows = nt * nz * ny rows of nx cells per shot; r, p, Ap rows have pitch px.
+// With pc_pen > 0 also the partial r^T z for z = r / (pc_pen B^2) into part2.
 template <typename T>
-cudaError_t launch_cg_update(T *x, T *r, const T *p, const T *ap, long long len,
-                             long long sstride, int ns, const double *alpha,
-                             const int *active, double *part, int nblk, cudaStream_t st);
+cudaError_t launch_cg_update(T *x, T *r, const T *p, const T *ap, long long rows, int nx, int px,
+                             int ns, const double *alpha, const int *active, double *part,
+                             double *part2, int nblk, T pc_pen, const double *src_pos, int nz,
+                             int ny, T eps, T dx, cudaStream_t st);
 // alpha = rr / pAp ; flags breakdown
 cudaError_t launch_cg_alpha(const double *rr, const double *pap, double *alpha, int *bad,
                             const int *active, int ns, cudaStream_t st);
 // beta = rr_new / rr_old ; rr_old = rr_new
 cudaError_t launch_cg_beta(double *rr_old, const double *rr_new, double *beta,
                            const int *active, int ns, cudaStream_t st);
-// z = r / (pen B^2) (diagonal preconditioner) over [ns][nt][N]
-template <typename T>
-cudaError_t launch_diag_pc(const T *r, T *z, long long N, int nt, int ns, int nz, int ny,
-                           int nx, const double *src_pos, T pen, T eps, T dx,
-                           const int *active, cudaStream_t st);
 
 // misfit: e = d - dobs (in place into d), per-block partial 1/2 e^2
 template <typename T>
 cudaError_t launch_residual(T *d, const T *dobs, long long len, double *part, int nblk,
                             cudaStream_t st);
 
-// gradient finalisation: g[i] = scale_i * sum_s G[s][i]
+// gradient finalisation: g[i] = scale_i * sum_s G[s][i]  (G pitched [ns][sst], g dense)
 template <typename T>
-cudaError_t launch_grad_finalize(const T *G, int ns, long long N, const T *cc, int nz, int ny,
-                                 int nx, int px, const T *vel, double dt, double dx,
-                                 double extra, int param, T *g, cudaStream_t st);
+cudaError_t launch_grad_finalize(const T *G, int ns, long long sst, const T *cc, int nz, int ny,
+                                 int nx, int px, double dt, double dx, double extra, int param,
+                                 T *g, cudaStream_t st);
 
 // checkpoint codec: per-shot max |u|, encode and decode
 template <typename T>
@@ -192,9 +206,11 @@ template <typename T>
 cudaError_t launch_decode(const void *codes, long long len, long long sstride, int ns, int kind,
                           const float *dec_scale, T *u, cudaStream_t st);
 
-// DTFT output: complex accumulators [ns][nf][N][2] -> half2 with per (shot, f) scale
+// DTFT output: pitched accumulators [ns][nf][sst][2] -> caller dense [ns][nf][N][2], either
+// copied in the field precision (half == 0) or as half pairs with a per (shot, f) scale
 template <typename T>
-cudaError_t launch_dft_to_half(const T *acc, long long N, int ns, int nf, void *out,
-                               unsigned *absmax_bits, float *scales_dev, cudaStream_t st);
+cudaError_t launch_dft_output(const T *acc, long long sst, int rows, int nx, int px, int ns,
+                              int nf, int half, void *out, unsigned *absmax_bits,
+                              float *scales_dev, cudaStream_t st);
 
 }  // namespace esi

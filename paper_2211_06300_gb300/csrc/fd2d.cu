@@ -1,18 +1,22 @@
 // 2D propagation step (forward or time-reversed adjoint) with fused prologue/epilogue.
 //
-// One launch advances every shot by one time step: grid (ntx, ntz, ns), one 32 x 32
-// output tile per block, 256 threads, each thread owning 4 cells of one column.  The
-// input state is staged in shared memory with a 4-cell halo; cells outside the grid read
-// as zero, which is the homogeneous extension under which the 8th-order Laplacian is a
-// symmetric matrix (the property that makes the time-reversed run the exact adjoint).
+// One launch advances every shot by one time step: grid (ntx, ntz, ns), one 64 x 32 (x, z)
+// output tile per block of 256 threads.  Each thread owns one 16-byte x-vector of cells
+// (4 floats or 2 doubles) in 2 (FP32) or 4 (FP64) rows, so every global stream (states,
+// c, CG vectors, stash, accumulators) moves as 16-byte accesses along 128-byte rows.  The
+// input state is staged in shared memory with a 4-cell halo by 16-byte loads; cells
+// outside the grid read as zero, the homogeneous extension under which the 8th-order
+// Laplacian is a symmetric matrix (what makes the time-reversed run the exact adjoint).
+// Pad columns (nx <= x < px) of the pitched arrays are kept at zero by masked stores.
 //
 // Fused work per step (each optional, selected at compile time):
 //   prologue : point injection (source wavelet, or R^T e at receivers) through a per-tile
 //              node list; sampling R of the *input* state from the shared tile;
-//   source   : dense extended source q_n, or the CG direction update p' = r + beta p;
-//   epilogue : dense output of the new state, CG product Ap = new + beta B^2 p with the
-//              <p, Ap> block partial, gradient stash / correlation, saddle-point
-//              correlation, on-the-fly DTFT accumulation.
+//   source   : dense extended source q_n (caller layout), or the CG direction update
+//              p' = r + beta p (internal pitched layout);
+//   epilogue : output of the new state, CG product Ap = new + beta B^2 p with the <p, Ap>
+//              block partial, gradient stash / correlation, saddle-point correlation,
+//              on-the-fly DTFT accumulation.
 #include "esi_internal.h"
 
 namespace esi {
@@ -23,64 +27,127 @@ namespace {
 constexpr double W1 = 8.0 / 5.0, W2 = -1.0 / 5.0, W3 = 8.0 / 315.0, W4 = -1.0 / 560.0;
 
 template <typename T>
-__device__ __forceinline__ T lap2_tile(const T (*tl)[SW], int sz, int sx) {
-    const T u = tl[sz][sx];
-    T L = T(W1) * ((tl[sz][sx - 1] - u) + (tl[sz][sx + 1] - u) + (tl[sz - 1][sx] - u) +
-                   (tl[sz + 1][sx] - u));
-    L += T(W2) * ((tl[sz][sx - 2] - u) + (tl[sz][sx + 2] - u) + (tl[sz - 2][sx] - u) +
-                  (tl[sz + 2][sx] - u));
-    L += T(W3) * ((tl[sz][sx - 3] - u) + (tl[sz][sx + 3] - u) + (tl[sz - 3][sx] - u) +
-                  (tl[sz + 3][sx] - u));
-    L += T(W4) * ((tl[sz][sx - 4] - u) + (tl[sz][sx + 4] - u) + (tl[sz - 4][sx] - u) +
-                  (tl[sz + 4][sx] - u));
-    return L;
+struct alignas(16) Vec {
+    static constexpr int n = 16 / sizeof(T);
+    T v[n];
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+// 3D tiled TMA load of one box into shared memory, completing on an mbarrier
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *tm, int x, int y, int z,
+                                            unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(tm)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Poll the mbarrier phase with an iteration limit; false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned phase,
+                                                  long long limit) {
+    for (long long i = 0; i < limit; ++i) {
+        unsigned done;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;"
+            " selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
 }
 
 template <typename T>
-__device__ __forceinline__ double block_sum(T v, double *red) {
-    // warp level in the field precision, block level in double
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x, warp = threadIdx.y;
-    if (lane == 0) red[warp] = double(v);
-    __syncthreads();
-    double t = 0.0;
-    if (warp == 0) {
-        t = lane < BY ? red[lane] : 0.0;
-#pragma unroll
-        for (int o = 4; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    }
-    return t;  // valid in thread (0, 0)
+__device__ __forceinline__ Vec<T> ldv(const T *p) {
+    return *reinterpret_cast<const Vec<T> *>(p);
+}
+template <typename T>
+__device__ __forceinline__ void stv(T *p, const Vec<T> &v) {
+    *reinterpret_cast<Vec<T> *>(p) = v;
 }
 
 template <typename T, unsigned F>
-__global__ void __launch_bounds__(BX *BY) fd2_step_kernel(const StepArgs<T> a) {
-    __shared__ T tl[SH][SW];
-    __shared__ T qpt[(F & F_PT) ? TZ * TX : 1];
-    __shared__ double red[BY];
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+__global__ void __launch_bounds__(NT2, 3) fd2_step_kernel(const __grid_constant__ StepArgs<T> a) {
+    constexpr int VEC = Vec<T>::n;     // cells per thread-vector
+    constexpr int TPR = TX2 / VEC;     // threads per tile row
+    constexpr int RPP = NT2 / TPR;     // rows per pass
+    constexpr int NP = TZ2 / RPP;      // passes
+    constexpr int CPR = SW2 / VEC;     // 16-byte chunks per shared row
+    __shared__ __align__(128) T tl[SH2][SW2];
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ __align__(16) T qpt[(F & F_PT) ? TZ2 * TX2 : VEC];
+    __shared__ double red[NT2 / 32];
+    const int tid = threadIdx.x;
     const int s = blockIdx.z;
     if (a.active && !a.active[s]) return;
-    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ;
+    const int x0 = blockIdx.x * TX2, z0 = blockIdx.y * TZ2;
     const int tile = (s * a.ntz + blockIdx.y) * a.ntx + blockIdx.x;
     const T *cur = a.cur + (long long)s * a.sst;
     T *po = a.po + (long long)s * a.sst;
-
-    for (int i = tid; i < SH * SW; i += BX * BY) {
-        const int lz = i / SW, lx = i - lz * SW;
-        const int gz = z0 - HALO + lz, gx = x0 - HALO + lx;
-        T v = T(0);
-        if (gz >= 0 && gz < a.nz && gx >= 0 && gx < a.nx) v = cur[(long long)gz * a.px + gx];
-        tl[lz][lx] = v;
+    (void)cur;
+    // stage u_n (tile + 4-cell halo) with one TMA box load; cells outside the grid are
+    // zero-filled by the copy engine.  x0 - 4 is a multiple of 4 elements (16 bytes).
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    __syncthreads();
+    if (tid == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar)),
+                     "r"((unsigned)(SH2 * SW2 * sizeof(T)))
+                     : "memory");
+        tma_load_3d(&tl[0][0], &a.tm, x0 - HALO, z0 - HALO, s, &bar);
+    }
+    const int qx = tid % TPR, ry = tid / TPR;
+    const int lx = qx * VEC, gx0 = x0 + lx;
+    const bool colok = gx0 < a.nx;
+    const long long fb = (long long)s * a.fstp;   // internal pitched fields
+    const long long fd = (long long)s * a.fst;    // caller dense fields
+
+    // Per-cell global inputs of both passes are loaded first, so that their latency
+    // overlaps the staging of the shared tile instead of following the barrier.
+    Vec<T> p_old[NP], p_cc[NP], p_r[NP], p_p[NP], p_g[NP], p_st[NP];
+    T p_q[NP][VEC];
+#pragma unroll
+    for (int pz = 0; pz < NP; ++pz) {
+        const int gz = z0 + ry + pz * RPP;
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) p_q[pz][i] = T(0);
+        if (!colok || gz >= a.nz) continue;
+        const long long gi = (long long)gz * a.px + gx0;
+        p_old[pz] = ldv(po + gi);
+        p_cc[pz] = ldv(a.cc + gi);
+        if constexpr ((F & F_EXT) != 0) {
+            const T *e = a.ext + fd + (long long)a.n * a.N + (long long)gz * a.nx + gx0;
+#pragma unroll
+            for (int i = 0; i < VEC; ++i)
+                if (gx0 + i < a.nx) p_q[pz][i] = e[i];
+        }
+        if constexpr ((F & F_CGP) != 0) {
+            const long long vi = fb + (long long)a.n * a.sst + gi;
+            p_r[pz] = ldv(a.cg_r + vi);
+            if (!a.cg_first) p_p[pz] = ldv(a.cg_p + vi);
+        }
+        if constexpr ((F & F_AP) != 0) p_p[pz] = ldv(a.ap_p + fb + (long long)a.nout * a.sst + gi);
+        if constexpr ((F & (F_GRD | F_SAD)) != 0) p_g[pz] = ldv(a.grad + (long long)s * a.sst + gi);
+        if constexpr ((F & F_GRD) != 0)
+            p_st[pz] = ldv(a.stash_r + ((long long)a.slot_r * a.ns + s) * a.sst + gi);
+    }
+
+    (void)CPR;
     bool has_pt = false;
     if constexpr ((F & F_PT) != 0) {
         const int b = a.inj.tile_ptr[tile], e = a.inj.tile_ptr[tile + 1];
         has_pt = b < e;
         if (has_pt) {
-            for (int i = tid; i < TZ * TX; i += BX * BY) qpt[i] = T(0);
+            for (int i = tid; i < TZ2 * TX2; i += NT2) qpt[i] = T(0);
             __syncthreads();
-            for (int k = b + tid; k < e; k += BX * BY) {
+            for (int k = b + tid; k < e; k += NT2) {
                 T sum = T(0);
                 for (int c = a.inj.cptr[k]; c < a.inj.cptr[k + 1]; ++c)
                     sum += a.inj.w[c] *
@@ -89,12 +156,19 @@ __global__ void __launch_bounds__(BX *BY) fd2_step_kernel(const StepArgs<T> a) {
             }
         }
     }
-    __syncthreads();
+    const bool late = !mbar_wait_bounded(&bar, 0, TMA_WAIT_LIMIT);
+    if (__syncthreads_or(late)) {   // uniform: every thread of the block leaves together
+        if (tid == 0) {
+            atomicExch(a.dev_err, DEV_ERR_TMA_TIMEOUT);
+            mbar_wait_bounded(&bar, 0, TMA_WAIT_LIMIT);  // let the copy land before leaving
+        }
+        return;
+    }
     if constexpr ((F & F_SMP) != 0) {
         if (a.tout >= 0) {
             const int b = a.smp.tile_ptr[tile], e = a.smp.tile_ptr[tile + 1];
             const T *tf = &tl[0][0];
-            for (int k = b + tid; k < e; k += BX * BY) {
+            for (int k = b + tid; k < e; k += NT2) {
                 T v = T(0);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) v += a.smp.w[k * MAXP + j] * tf[a.smp.idx[k * MAXP + j]];
@@ -103,84 +177,184 @@ __global__ void __launch_bounds__(BX *BY) fd2_step_kernel(const StepArgs<T> a) {
         }
     }
 
-    const int gx = x0 + tx;
-    const bool colok = gx < a.nx;
-    const T kxv = colok ? a.kx[gx] : T(0);
-    T xs = T(0), zs = T(0);
-    if constexpr ((F & (F_AP | F_SAD)) != 0) {
-        xs = T(a.src_pos[3 * s + 0]);
-        zs = T(a.src_pos[3 * s + 2]);
-    }
     T psum = T(0);
-    const long long fbase = (long long)s * a.fst;
+    if (colok) {
+        const Vec<T> kx = ldv(a.kx + gx0);
+        T xs = T(0), zs = T(0);
+        if constexpr ((F & (F_AP | F_SAD | F_CGP)) != 0) {
+            xs = T(a.src_pos[3 * s + 0]);
+            zs = T(a.src_pos[3 * s + 2]);
+        }
 #pragma unroll
-    for (int k = 0; k < RZ; ++k) {
-        const int lz = ty + k * BY;
-        const int gz = z0 + lz;
-        if (!colok || gz >= a.nz) continue;
-        const int sz = lz + HALO, sx = tx + HALO;
-        const T u = tl[sz][sx];
-        const T L = lap2_tile<T>(tl, sz, sx);
-        const long long gi = (long long)gz * a.px + gx;
-        const long long di = (long long)gz * a.nx + gx;
-        T q = T(0);
-        if constexpr ((F & F_EXT) != 0) q += a.ext[fbase + (long long)a.n * a.N + di];
-        if constexpr ((F & F_CGP) != 0) {
-            const long long vi = fbase + (long long)a.n * a.N + di;
-            T pn = a.cg_r[vi];
-            if (!a.cg_first) pn += T(a.cg_beta[s]) * a.cg_p[vi];
-            a.cg_p[vi] = pn;
-            q += pn;
-        }
-        T S = L + a.dx2 * q;
-        if constexpr ((F & F_PT) != 0) {
-            if (has_pt) S += qpt[lz * TX + tx];
-        }
-        const T kap = a.kz[gz] + kxv;
-        const T al = T(1) / (T(1) + kap);
-        const T ga = (T(1) - kap) * al;
-        const T old = po[gi];
-        const T nw = u + ga * (u - old) + al * a.cc[gi] * S;
-        po[gi] = nw;
-        if constexpr ((F & (F_AP | F_SAD)) != 0) {
-            const T ex = T(gx) * a.dx - xs, ez = T(gz) * a.dx - zs;
-            const T B = sqrt(ex * ex + ez * ez) + a.eps;
-            const T B2 = B * B;
-            if constexpr ((F & F_SAD) != 0) a.grad[(long long)s * a.N + di] += B2 * q * S;
-            if constexpr ((F & F_AP) != 0) {
-                const long long vi = fbase + (long long)a.nout * a.N + di;
-                const T pv = a.ap_p[vi];
-                const T apv = nw + a.pen * B2 * pv;
-                a.ap[vi] = apv;
-                psum += pv * apv;
+        for (int pz = 0; pz < NP; ++pz) {
+            const int lz = ry + pz * RPP;
+            const int gz = z0 + lz;
+            if (gz >= a.nz) break;
+            const int sz = lz + HALO;
+            // x neighbours: shared row segment [lx, lx + VEC + 8)
+            T w[VEC + 2 * HALO];
+#pragma unroll
+            for (int c = 0; c < (VEC + 2 * HALO) / VEC; ++c) {
+                const Vec<T> t = ldv(&tl[sz][lx + c * VEC]);
+#pragma unroll
+                for (int i = 0; i < VEC; ++i) w[c * VEC + i] = t.v[i];
             }
-        }
-        if constexpr ((F & F_STW) != 0)
-            a.stash_w[((long long)a.slot_w * a.ns + s) * a.N + di] = S;
-        if constexpr ((F & F_GRD) != 0)
-            a.grad[(long long)s * a.N + di] +=
-                nw * a.stash_r[((long long)a.slot_r * a.ns + s) * a.N + di];
-        if constexpr ((F & F_OUT) != 0) a.fout[fbase + (long long)a.nout * a.N + di] = nw;
-        if constexpr ((F & F_DFT) != 0) {
-            for (int m = 0; m < a.nf; ++m) {
-                const T c = a.twid[(a.n * a.nf + m) * 2 + 0];
-                const T sn = a.twid[(a.n * a.nf + m) * 2 + 1];
-                T *acc = a.dft + (((long long)s * a.nf + m) * a.N + di) * 2;
-                acc[0] += nw * c;
-                acc[1] += nw * sn;
+            T L[VEC];
+#pragma unroll
+            for (int i = 0; i < VEC; ++i) {
+                const T u = w[i + HALO];
+                L[i] = T(W1) * ((w[i + 3] - u) + (w[i + 5] - u)) +
+                       T(W2) * ((w[i + 2] - u) + (w[i + 6] - u)) +
+                       T(W3) * ((w[i + 1] - u) + (w[i + 7] - u)) +
+                       T(W4) * ((w[i + 0] - u) + (w[i + 8] - u));
+            }
+            // z neighbours
+            constexpr double WZ[5] = {0.0, W1, W2, W3, W4};
+#pragma unroll
+            for (int k = 1; k <= HALO; ++k) {
+                const Vec<T> up = ldv(&tl[sz - k][lx + HALO]);
+                const Vec<T> dn = ldv(&tl[sz + k][lx + HALO]);
+#pragma unroll
+                for (int i = 0; i < VEC; ++i) {
+                    const T u = w[i + HALO];
+                    L[i] += T(WZ[k]) * ((up.v[i] - u) + (dn.v[i] - u));
+                }
+            }
+            const long long gi = (long long)gz * a.px + gx0;
+            const Vec<T> old = p_old[pz];
+            const Vec<T> cc = p_cc[pz];
+            const T kz = a.kz[gz];
+            T q[VEC], S[VEC];
+#pragma unroll
+            for (int i = 0; i < VEC; ++i) q[i] = p_q[pz][i];
+            if constexpr ((F & F_CGP) != 0) {
+                const long long vi = fb + (long long)a.n * a.sst + gi;
+                Vec<T> pn = p_r[pz];
+                if (a.cg_pc > T(0)) {   // z = r / (pen B^2)
+                    const T ez = T(gz) * a.dx - zs;
+#pragma unroll
+                    for (int i = 0; i < VEC; ++i) {
+                        const T ex = T(gx0 + i) * a.dx - xs;
+                        const T B = sqrt(ex * ex + ez * ez) + a.eps;
+                        pn.v[i] = pn.v[i] / (a.cg_pc * B * B);
+                    }
+                }
+                if (!a.cg_first) {
+                    const T b = T(a.cg_beta[s]);
+#pragma unroll
+                    for (int i = 0; i < VEC; ++i) pn.v[i] += b * p_p[pz].v[i];
+                }
+                stv(a.cg_p + vi, pn);
+#pragma unroll
+                for (int i = 0; i < VEC; ++i) q[i] += pn.v[i];
+            }
+#pragma unroll
+            for (int i = 0; i < VEC; ++i) S[i] = L[i] + a.dx2 * q[i];
+            if constexpr ((F & F_PT) != 0) {
+                if (has_pt) {
+#pragma unroll
+                    for (int i = 0; i < VEC; ++i) S[i] += qpt[lz * TX2 + lx + i];
+                }
+            }
+            Vec<T> nw;
+#pragma unroll
+            for (int i = 0; i < VEC; ++i) {
+                const T kap = kz + kx.v[i];
+                const T al = T(1) / (T(1) + kap);
+                const T ga = (T(1) - kap) * al;
+                const T u = w[i + HALO];
+                const T val = u + ga * (u - old.v[i]) + al * cc.v[i] * S[i];
+                nw.v[i] = (gx0 + i < a.nx) ? val : T(0);   // pad columns stay zero
+            }
+            stv(po + gi, nw);
+            if constexpr ((F & (F_AP | F_SAD)) != 0) {
+                T B2[VEC];
+                const T ez = T(gz) * a.dx - zs;
+#pragma unroll
+                for (int i = 0; i < VEC; ++i) {
+                    const T ex = T(gx0 + i) * a.dx - xs;
+                    const T B = sqrt(ex * ex + ez * ez) + a.eps;
+                    B2[i] = B * B;
+                }
+                if constexpr ((F & F_SAD) != 0) {
+                    Vec<T> gv = p_g[pz];
+#pragma unroll
+                    for (int i = 0; i < VEC; ++i) gv.v[i] += B2[i] * q[i] * S[i];
+                    stv(a.grad + (long long)s * a.sst + gi, gv);
+                }
+                if constexpr ((F & F_AP) != 0) {
+                    const long long vi = fb + (long long)a.nout * a.sst + gi;
+                    const Vec<T> pv = p_p[pz];
+                    Vec<T> av;
+#pragma unroll
+                    for (int i = 0; i < VEC; ++i) {
+                        av.v[i] = nw.v[i] + a.pen * B2[i] * pv.v[i];
+                        psum += pv.v[i] * av.v[i];
+                    }
+                    stv(a.ap + vi, av);
+                }
+            }
+            if constexpr ((F & F_STW) != 0) {
+                Vec<T> sv;
+#pragma unroll
+                for (int i = 0; i < VEC; ++i) sv.v[i] = (gx0 + i < a.nx) ? S[i] : T(0);
+                stv(a.stash_w + ((long long)a.slot_w * a.ns + s) * a.sst + gi, sv);
+            }
+            if constexpr ((F & F_GRD) != 0) {
+                Vec<T> gv = p_g[pz];
+#pragma unroll
+                for (int i = 0; i < VEC; ++i) gv.v[i] += nw.v[i] * p_st[pz].v[i];
+                stv(a.grad + (long long)s * a.sst + gi, gv);
+            }
+            if constexpr ((F & F_OUT) != 0) {
+                T *o = a.fout + (long long)s * a.ofst + (long long)a.nout * a.oplane +
+                       (long long)gz * a.opx + gx0;
+                if (a.opx == a.px) {
+                    stv(o, nw);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < VEC; ++i)
+                        if (gx0 + i < a.nx) o[i] = nw.v[i];
+                }
+            }
+            if constexpr ((F & F_DFT) != 0) {
+                for (int m = 0; m < a.nf; ++m) {
+                    const T c = a.twid[(a.n * a.nf + m) * 2 + 0];
+                    const T sn = a.twid[(a.n * a.nf + m) * 2 + 1];
+                    T *acc = a.dft + (((long long)s * a.nf + m) * a.sst + gi) * 2;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        Vec<T> av = ldv(acc + h * VEC);
+#pragma unroll
+                        for (int i = 0; i < VEC / 2; ++i) {
+                            av.v[2 * i] += nw.v[h * VEC / 2 + i] * c;
+                            av.v[2 * i + 1] += nw.v[h * VEC / 2 + i] * sn;
+                        }
+                        stv(acc + h * VEC, av);
+                    }
+                }
             }
         }
     }
     if constexpr ((F & F_AP) != 0) {
-        const double t = block_sum<T>(psum, red);
-        if (tid == 0) a.dot_part[(long long)s * (a.ntx * a.ntz) + blockIdx.y * a.ntx + blockIdx.x] += t;
+        T v = psum;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0) red[tid >> 5] = double(v);
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+#pragma unroll
+            for (int k = 0; k < NT2 / 32; ++k) t += red[k];
+            a.dot_part[(long long)s * (a.ntx * a.ntz) + blockIdx.y * a.ntx + blockIdx.x] += t;
+        }
     }
 }
 
 template <typename T, unsigned F>
 cudaError_t go(const StepArgs<T> &a, int ns, cudaStream_t st) {
-    dim3 grid(a.ntx, a.ntz, ns), block(BX, BY);
-    fd2_step_kernel<T, F><<<grid, block, 0, st>>>(a);
+    dim3 grid(a.ntx, a.ntz, ns);
+    fd2_step_kernel<T, F><<<grid, NT2, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -205,7 +379,8 @@ __global__ void sample_global_kernel(const SmpList<T> l, const T *state, long lo
 template <typename T>
 cudaError_t launch_step2(unsigned flags, const StepArgs<T> &a, int ns, cudaStream_t st) {
     switch (flags) {
-        // forward modelling (point / extended / both), with and without DTFT
+        // forward modelling (point / extended / both), with and without DTFT; the
+        // F_PT | F_SMP variant also serves the adjoint with the wavelet output only
         ESI_CASE(F_PT | F_SMP)
         ESI_CASE(F_EXT | F_SMP)
         ESI_CASE(F_EXT | F_PT | F_SMP)

@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(TX3 *TY3) fd3_step_kernel(const StepArgs<T> a,
     }
     const T kxy = colok ? a.kx[gx] + a.ky[gy] : T(0);
     T xs = T(0), ys = T(0), zs = T(0);
-    if constexpr ((F & (F_AP | F_SAD)) != 0) {
+    if constexpr ((F & (F_AP | F_SAD | F_CGP)) != 0) {
         xs = T(a.src_pos[3 * s + 0]);
         ys = T(a.src_pos[3 * s + 1]);
         zs = T(a.src_pos[3 * s + 2]);
@@ -53,7 +53,8 @@ __global__ void __launch_bounds__(TX3 *TY3) fd3_step_kernel(const StepArgs<T> a,
         ie = a.inj.tile_ptr[tile + 1];
     }
     T psum = T(0);
-    const long long fbase = (long long)s * a.fst;
+    const long long fbase = (long long)s * a.fst;    // caller dense fields
+    const long long fb = (long long)s * a.fstp;      // internal pitched fields
     const long long dcol = (long long)gy * a.nx + gx;
 
     for (int z = zb; z < ze; ++z) {
@@ -84,8 +85,13 @@ __global__ void __launch_bounds__(TX3 *TY3) fd3_step_kernel(const StepArgs<T> a,
             T src = T(0);
             if constexpr ((F & F_EXT) != 0) src += a.ext[fbase + (long long)a.n * a.N + di];
             if constexpr ((F & F_CGP) != 0) {
-                const long long vi = fbase + (long long)a.n * a.N + di;
+                const long long vi = fb + (long long)a.n * a.sst + gi;
                 T pn = a.cg_r[vi];
+                if (a.cg_pc > T(0)) {   // z = r / (pen B^2)
+                    const T ex = T(gx) * a.dx - xs, ey = T(gy) * a.dx - ys, ez = T(z) * a.dx - zs;
+                    const T B = sqrt(ex * ex + ey * ey + ez * ez) + a.eps;
+                    pn = pn / (a.cg_pc * B * B);
+                }
                 if (!a.cg_first) pn += T(a.cg_beta[s]) * a.cg_p[vi];
                 a.cg_p[vi] = pn;
                 src += pn;
@@ -118,9 +124,9 @@ __global__ void __launch_bounds__(TX3 *TY3) fd3_step_kernel(const StepArgs<T> a,
                 const T ex = T(gx) * a.dx - xs, ey = T(gy) * a.dx - ys, ez = T(z) * a.dx - zs;
                 const T B = sqrt(ex * ex + ey * ey + ez * ez) + a.eps;
                 const T B2 = B * B;
-                if constexpr ((F & F_SAD) != 0) a.grad[(long long)s * a.N + di] += B2 * src * S;
+                if constexpr ((F & F_SAD) != 0) a.grad[(long long)s * a.sst + gi] += B2 * src * S;
                 if constexpr ((F & F_AP) != 0) {
-                    const long long vi = fbase + (long long)a.nout * a.N + di;
+                    const long long vi = fb + (long long)a.nout * a.sst + gi;
                     const T pv = a.ap_p[vi];
                     const T apv = nw + a.pen * B2 * pv;
                     a.ap[vi] = apv;
@@ -128,16 +134,18 @@ __global__ void __launch_bounds__(TX3 *TY3) fd3_step_kernel(const StepArgs<T> a,
                 }
             }
             if constexpr ((F & F_STW) != 0)
-                a.stash_w[((long long)a.slot_w * a.ns + s) * a.N + di] = S;
+                a.stash_w[((long long)a.slot_w * a.ns + s) * a.sst + gi] = S;
             if constexpr ((F & F_GRD) != 0)
-                a.grad[(long long)s * a.N + di] +=
-                    nw * a.stash_r[((long long)a.slot_r * a.ns + s) * a.N + di];
-            if constexpr ((F & F_OUT) != 0) a.fout[fbase + (long long)a.nout * a.N + di] = nw;
+                a.grad[(long long)s * a.sst + gi] +=
+                    nw * a.stash_r[((long long)a.slot_r * a.ns + s) * a.sst + gi];
+            if constexpr ((F & F_OUT) != 0)
+                a.fout[(long long)s * a.ofst + (long long)a.nout * a.oplane +
+                       ((long long)z * a.ny + gy) * a.opx + gx] = nw;
             if constexpr ((F & F_DFT) != 0) {
                 for (int m = 0; m < a.nf; ++m) {
                     const T c = a.twid[(a.n * a.nf + m) * 2 + 0];
                     const T sn = a.twid[(a.n * a.nf + m) * 2 + 1];
-                    T *acc = a.dft + (((long long)s * a.nf + m) * a.N + di) * 2;
+                    T *acc = a.dft + (((long long)s * a.nf + m) * a.sst + gi) * 2;
                     acc[0] += nw * c;
                     acc[1] += nw * sn;
                 }

@@ -8,6 +8,12 @@ namespace {
 
 constexpr int RT = 256;  // threads per block of the streaming kernels
 
+template <typename T>
+struct alignas(16) V16 {
+    static constexpr int n = 16 / sizeof(T);
+    T v[n];
+};
+
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -54,25 +60,26 @@ __global__ void setup_cc_kernel(const T *v, T *cc, int nz, int ny, int nx, int p
     }
 }
 
+// <a, b> per shot over pitched vectors (len a multiple of the 16-byte vector width; pad
+// elements are zero): 16-byte loads, a field-precision sum per vector, double across.
 template <typename T>
 __global__ void dot_kernel(const T *a, const T *b, long long len, long long sstride,
                            double *part, const int *active) {
+    constexpr int VEC = V16<T>::n;
     const int s = blockIdx.y;
     if (active && !active[s]) return;
-    const T *x = a + s * sstride, *y = b + s * sstride;
+    const V16<T> *x = reinterpret_cast<const V16<T> *>(a + s * sstride);
+    const V16<T> *y = reinterpret_cast<const V16<T> *>(b + s * sstride);
     double acc = 0.0;
-    T local = T(0);
-    int cnt = 0;
-    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < len;
+    const long long nv = len / VEC;
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < nv;
          i += (long long)gridDim.x * RT) {
-        local += x[i] * y[i];
-        if (++cnt == 64) {  // bound the length of each field-precision partial sum
-            acc += double(local);
-            local = T(0);
-            cnt = 0;
-        }
+        const V16<T> u = x[i], w = y[i];
+        T t = T(0);
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) t += u.v[k] * w.v[k];
+        acc += double(t);
     }
-    acc += double(local);
     const double t = block_sum_d(acc);
     if (threadIdx.x == 0) part[(long long)s * gridDim.x + blockIdx.x] = t;
 }
@@ -85,33 +92,68 @@ __global__ void reduce_partials_kernel(const double *part, int nblk, int ns, dou
     if (threadIdx.x == 0) out[s] = t;
 }
 
+// Algorithm 1's vector updates for one shot per blockIdx.y: x_{k+1} = x_k + alpha p_k
+// (x in the caller's dense layout), r_{k+1} = r_k - alpha A p_k (pitched), with the
+// partial ||r_{k+1}||^2 and, for the diagonal preconditioner z = r / (pen B^2), r^T z.
 template <typename T>
-__global__ void cg_update_kernel(T *x, T *r, const T *p, const T *ap, long long len,
-                                 long long sstride, const double *alpha, const int *active,
-                                 double *part) {
+__global__ void cg_update_kernel(T *x, T *r, const T *p, const T *ap, long long rows, int nx,
+                                 int px, const double *alpha, const int *active, double *part,
+                                 double *part2, T pen, const double *src_pos, int nz, int ny,
+                                 T eps, T dx) {
+    constexpr int VEC = V16<T>::n;
     const int s = blockIdx.y;
     if (active && !active[s]) return;
     const T al = T(alpha[s]);
-    T *xs = x + s * sstride, *rs = r + s * sstride;
-    const T *ps = p + s * sstride, *as = ap + s * sstride;
-    double acc = 0.0;
-    T local = T(0);
-    int cnt = 0;
-    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < len;
-         i += (long long)gridDim.x * RT) {
-        xs[i] += al * ps[i];
-        const T rn = rs[i] - al * as[i];
-        rs[i] = rn;
-        local += rn * rn;
-        if (++cnt == 64) {
-            acc += double(local);
-            local = T(0);
-            cnt = 0;
+    const long long sp = rows * px, sd = rows * nx;   // shot strides (pitched, dense)
+    T *xs = x + s * sd;
+    T *rs = r + s * sp;
+    const T *ps = p + s * sp, *as = ap + s * sp;
+    const int cpr = px / VEC;
+    const long long nchunk = rows * cpr;
+    const T xsrc = T(src_pos[3 * s]), ysrc = T(src_pos[3 * s + 1]), zsrc = T(src_pos[3 * s + 2]);
+    double acc = 0.0, acc2 = 0.0;
+    for (long long c = (long long)blockIdx.x * RT + threadIdx.x; c < nchunk;
+         c += (long long)gridDim.x * RT) {
+        const long long row = c / cpr;
+        const int x0 = int(c - row * cpr) * VEC;
+        if (x0 >= nx) continue;
+        const long long pi = row * px + x0;
+        const V16<T> pv = *reinterpret_cast<const V16<T> *>(ps + pi);
+        const V16<T> av = *reinterpret_cast<const V16<T> *>(as + pi);
+        V16<T> rv = *reinterpret_cast<const V16<T> *>(rs + pi);
+        T t = T(0);
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            rv.v[k] -= al * av.v[k];
+            t += rv.v[k] * rv.v[k];
+        }
+        *reinterpret_cast<V16<T> *>(rs + pi) = rv;
+        T *xr = xs + row * nx + x0;
+#pragma unroll
+        for (int k = 0; k < VEC; ++k)
+            if (x0 + k < nx) xr[k] += al * pv.v[k];
+        acc += double(t);
+        if (pen > T(0)) {
+            const long long pl = row % ((long long)nz * ny);
+            const int iz = int(pl / ny), iy = int(pl - (long long)iz * ny);
+            const T ez = T(iz) * dx - zsrc, ey = ny > 1 ? T(iy) * dx - ysrc : T(0);
+            T t2 = T(0);
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) {
+                const T ex = T(x0 + k) * dx - xsrc;
+                const T B = sqrt(ex * ex + ey * ey + ez * ez) + eps;
+                t2 += rv.v[k] * rv.v[k] / (pen * B * B);
+            }
+            acc2 += double(t2);
         }
     }
-    acc += double(local);
     const double t = block_sum_d(acc);
     if (threadIdx.x == 0) part[(long long)s * gridDim.x + blockIdx.x] = t;
+    if (pen > T(0)) {
+        __syncthreads();
+        const double t2 = block_sum_d(acc2);
+        if (threadIdx.x == 0) part2[(long long)s * gridDim.x + blockIdx.x] = t2;
+    }
 }
 
 __global__ void cg_alpha_kernel(const double *rr, const double *pap, double *alpha, int *bad,
@@ -141,24 +183,6 @@ __global__ void cg_beta_kernel(double *rr_old, const double *rr_new, double *bet
 }
 
 template <typename T>
-__global__ void diag_pc_kernel(const T *r, T *z, long long N, int nt, int nz, int ny, int nx,
-                               const double *src_pos, T pen, T eps, T dx, const int *active) {
-    const int s = blockIdx.y;
-    if (active && !active[s]) return;
-    const long long len = N * nt;
-    const T xs = T(src_pos[3 * s]), ys = T(src_pos[3 * s + 1]), zs = T(src_pos[3 * s + 2]);
-    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < len;
-         i += (long long)gridDim.x * RT) {
-        const long long c = i % N;
-        const long long ix = c % nx, rest = c / nx;
-        const long long iy = rest % ny, iz = rest / ny;
-        const T ex = T(ix) * dx - xs, ey = ny > 1 ? T(iy) * dx - ys : T(0), ez = T(iz) * dx - zs;
-        const T B = sqrt(ex * ex + ey * ey + ez * ez) + eps;
-        z[s * len + i] = r[s * len + i] / (pen * B * B);
-    }
-}
-
-template <typename T>
 __global__ void residual_kernel(T *d, const T *dobs, long long len, double *part) {
     double acc = 0.0;
     for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < len;
@@ -172,16 +196,17 @@ __global__ void residual_kernel(T *d, const T *dobs, long long len, double *part
 }
 
 template <typename T>
-__global__ void grad_finalize_kernel(const T *G, int ns, long long N, const T *cc, int ny,
-                                     int nx, int px, double dt, double dx, double extra,
-                                     int param, T *g) {
+__global__ void grad_finalize_kernel(const T *G, int ns, long long N, long long sst,
+                                     const T *cc, int nx, int px, double dt, double dx,
+                                     double extra, int param, T *g) {
     const double dx2 = dx * dx;
     for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < N;
          i += (long long)gridDim.x * RT) {
-        double sum = 0.0;
-        for (int s = 0; s < ns; ++s) sum += double(G[(long long)s * N + i]);
         const long long row = i / nx, x = i - row * nx;
-        const double c = double(cc[row * px + x]) * dx2;  // v^2 dt^2
+        const long long pi = row * px + x;
+        double sum = 0.0;
+        for (int s = 0; s < ns; ++s) sum += double(G[(long long)s * sst + pi]);
+        const double c = double(cc[pi]) * dx2;  // v^2 dt^2
         double gc = extra * sum / (c * dx2);
         if (param == ESI_PARAM_V) gc *= 2.0 * sqrt(c) * dt;
         else if (param == ESI_PARAM_M) gc *= -(c * c) / (dt * dt);
@@ -241,12 +266,13 @@ __global__ void decode_kernel(const void *codes, long long len, long long sstrid
     }
 }
 
+// DTFT accumulators: pitched [ns*nf][sst][2] (pad cells zero) -> caller dense [ns*nf][N][2]
 template <typename T>
-__global__ void dft_absmax_kernel(const T *acc, long long N, int nf, unsigned *bits) {
+__global__ void dft_absmax_kernel(const T *acc, long long sst, unsigned *bits) {
     const int sm = blockIdx.y;  // shot * nf + m
-    const T *a = acc + (long long)sm * N * 2;
+    const T *a = acc + (long long)sm * sst * 2;
     float m = 0.0f;
-    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < 2 * N;
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < 2 * sst;
          i += (long long)gridDim.x * RT)
         m = fmaxf(m, fabsf(float(a[i])));
 #pragma unroll
@@ -255,17 +281,32 @@ __global__ void dft_absmax_kernel(const T *acc, long long N, int nf, unsigned *b
 }
 
 template <typename T>
-__global__ void dft_half_kernel(const T *acc, long long N, const unsigned *bits, __half *out,
-                                float *scales) {
+__global__ void dft_out_kernel(const T *acc, long long sst, int rows, int nx, int px, int half,
+                               const unsigned *bits, void *out, float *scales) {
     const int sm = blockIdx.y;
-    const float mx = __uint_as_float(bits[sm]);
-    const float inv = mx > 0.0f ? __fdiv_rn(CODEC_RANGE, mx) : 0.0f;
-    if (blockIdx.x == 0 && threadIdx.x == 0) scales[sm] = __fdiv_rn(mx, CODEC_RANGE);
-    const T *a = acc + (long long)sm * N * 2;
-    __half *o = out + (long long)sm * N * 2;
-    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < 2 * N;
-         i += (long long)gridDim.x * RT)
-        o[i] = __float2half_rn(__fmul_rn(float(a[i]), inv));
+    const long long N = (long long)rows * nx;
+    float inv = 1.0f;
+    if (half) {
+        const float mx = __uint_as_float(bits[sm]);
+        inv = mx > 0.0f ? __fdiv_rn(CODEC_RANGE, mx) : 0.0f;
+        if (blockIdx.x == 0 && threadIdx.x == 0) scales[sm] = __fdiv_rn(mx, CODEC_RANGE);
+    }
+    const T *a = acc + (long long)sm * sst * 2;
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < N;
+         i += (long long)gridDim.x * RT) {
+        const long long row = i / nx, x = i - row * nx;
+        const long long pi = (row * px + x) * 2;
+        const long long o = ((long long)sm * N + i) * 2;
+        if (half) {
+            __half *h = reinterpret_cast<__half *>(out);
+            h[o] = __float2half_rn(__fmul_rn(float(a[pi]), inv));
+            h[o + 1] = __float2half_rn(__fmul_rn(float(a[pi + 1]), inv));
+        } else {
+            T *d = reinterpret_cast<T *>(out);
+            d[o] = a[pi];
+            d[o + 1] = a[pi + 1];
+        }
+    }
 }
 
 inline int blocks_for(long long len, int cap) {
@@ -296,11 +337,13 @@ cudaError_t launch_reduce_partials(const double *part, int nblk, int ns, double 
 }
 
 template <typename T>
-cudaError_t launch_cg_update(T *x, T *r, const T *p, const T *ap, long long len,
-                             long long sstride, int ns, const double *alpha,
-                             const int *active, double *part, int nblk, cudaStream_t st) {
-    cg_update_kernel<T><<<dim3(nblk, ns), RT, 0, st>>>(x, r, p, ap, len, sstride, alpha, active,
-                                                       part);
+cudaError_t launch_cg_update(T *x, T *r, const T *p, const T *ap, long long rows, int nx, int px,
+                             int ns, const double *alpha, const int *active, double *part,
+                             double *part2, int nblk, T pc_pen, const double *src_pos, int nz,
+                             int ny, T eps, T dx, cudaStream_t st) {
+    cg_update_kernel<T><<<dim3(nblk, ns), RT, 0, st>>>(x, r, p, ap, rows, nx, px, alpha, active,
+                                                       part, part2, pc_pen, src_pos, nz, ny, eps,
+                                                       dx);
     return cudaGetLastError();
 }
 
@@ -317,15 +360,6 @@ cudaError_t launch_cg_beta(double *rr_old, const double *rr_new, double *beta,
 }
 
 template <typename T>
-cudaError_t launch_diag_pc(const T *r, T *z, long long N, int nt, int ns, int nz, int ny,
-                           int nx, const double *src_pos, T pen, T eps, T dx,
-                           const int *active, cudaStream_t st) {
-    diag_pc_kernel<T><<<dim3(blocks_for(N * nt, 4096), ns), RT, 0, st>>>(
-        r, z, N, nt, nz, ny, nx, src_pos, pen, eps, dx, active);
-    return cudaGetLastError();
-}
-
-template <typename T>
 cudaError_t launch_residual(T *d, const T *dobs, long long len, double *part, int nblk,
                             cudaStream_t st) {
     residual_kernel<T><<<nblk, RT, 0, st>>>(d, dobs, len, part);
@@ -333,12 +367,11 @@ cudaError_t launch_residual(T *d, const T *dobs, long long len, double *part, in
 }
 
 template <typename T>
-cudaError_t launch_grad_finalize(const T *G, int ns, long long N, const T *cc, int nz, int ny,
-                                 int nx, int px, const T *vel, double dt, double dx,
-                                 double extra, int param, T *g, cudaStream_t st) {
-    (void)nz;
-    (void)vel;
-    grad_finalize_kernel<T><<<blocks_for(N, 8192), RT, 0, st>>>(G, ns, N, cc, ny, nx, px, dt, dx,
+cudaError_t launch_grad_finalize(const T *G, int ns, long long sst, const T *cc, int nz, int ny,
+                                 int nx, int px, double dt, double dx, double extra, int param,
+                                 T *g, cudaStream_t st) {
+    const long long N = (long long)nz * ny * nx;
+    grad_finalize_kernel<T><<<blocks_for(N, 8192), RT, 0, st>>>(G, ns, N, sst, cc, nx, px, dt, dx,
                                                                 extra, param, g);
     return cudaGetLastError();
 }
@@ -369,13 +402,17 @@ cudaError_t launch_decode(const void *codes, long long len, long long sstride, i
 }
 
 template <typename T>
-cudaError_t launch_dft_to_half(const T *acc, long long N, int ns, int nf, void *out,
-                               unsigned *bits, float *scales_dev, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(unsigned) * ns * nf, st);
-    if (e != cudaSuccess) return e;
-    dft_absmax_kernel<T><<<dim3(blocks_for(2 * N, 1024), ns * nf), RT, 0, st>>>(acc, N, nf, bits);
-    dft_half_kernel<T><<<dim3(blocks_for(2 * N, 1024), ns * nf), RT, 0, st>>>(
-        acc, N, bits, reinterpret_cast<__half *>(out), scales_dev);
+cudaError_t launch_dft_output(const T *acc, long long sst, int rows, int nx, int px, int ns,
+                              int nf, int half, void *out, unsigned *bits, float *scales_dev,
+                              cudaStream_t st) {
+    const long long N = (long long)rows * nx;
+    if (half) {
+        cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(unsigned) * ns * nf, st);
+        if (e != cudaSuccess) return e;
+        dft_absmax_kernel<T><<<dim3(blocks_for(2 * sst, 1024), ns * nf), RT, 0, st>>>(acc, sst, bits);
+    }
+    dft_out_kernel<T><<<dim3(blocks_for(N, 1024), ns * nf), RT, 0, st>>>(acc, sst, rows, nx, px,
+                                                                        half, bits, out, scales_dev);
     return cudaGetLastError();
 }
 
@@ -384,24 +421,23 @@ cudaError_t launch_dft_to_half(const T *acc, long long N, int ns, int nf, void *
                                             double *, int, cudaStream_t);                        \
     template cudaError_t launch_dot<T>(const T *, const T *, long long, long long, int, double *, \
                                        int, const int *, cudaStream_t);                          \
-    template cudaError_t launch_cg_update<T>(T *, T *, const T *, const T *, long long,          \
-                                             long long, int, const double *, const int *,        \
-                                             double *, int, cudaStream_t);                       \
-    template cudaError_t launch_diag_pc<T>(const T *, T *, long long, int, int, int, int, int,   \
-                                           const double *, T, T, T, const int *, cudaStream_t);  \
+    template cudaError_t launch_cg_update<T>(T *, T *, const T *, const T *, long long, int, int, \
+                                             int, const double *, const int *, double *,         \
+                                             double *, int, T, const double *, int, int, T, T,   \
+                                             cudaStream_t);                                      \
     template cudaError_t launch_residual<T>(T *, const T *, long long, double *, int,            \
                                             cudaStream_t);                                       \
     template cudaError_t launch_grad_finalize<T>(const T *, int, long long, const T *, int, int, \
-                                                 int, int, const T *, double, double, double,    \
-                                                 int, T *, cudaStream_t);                        \
+                                                 int, int, double, double, double, int, T *,     \
+                                                 cudaStream_t);                                  \
     template cudaError_t launch_absmax<T>(const T *, long long, long long, int, unsigned *,      \
                                           cudaStream_t);                                         \
     template cudaError_t launch_encode<T>(const T *, long long, long long, int, int,             \
                                           const unsigned *, void *, float *, cudaStream_t);      \
     template cudaError_t launch_decode<T>(const void *, long long, long long, int, int,          \
                                           const float *, T *, cudaStream_t);                     \
-    template cudaError_t launch_dft_to_half<T>(const T *, long long, int, int, void *,           \
-                                               unsigned *, float *, cudaStream_t);
+    template cudaError_t launch_dft_output<T>(const T *, long long, int, int, int, int, int, int, \
+                                              void *, unsigned *, float *, cudaStream_t);
 
 ESI_INST(float)
 ESI_INST(double)
