@@ -358,6 +358,35 @@ class Oracle:
         return {"x": x, "rel_res": np.asarray(hist), "alpha": np.asarray(alphas),
                 "beta": np.asarray(betas), "iters": k + 1, "b": b}
 
+    def pcg(self, sh: Shot, d: np.ndarray, beta: float, tol: float, n_cg: int,
+            minv: np.ndarray, eps: Optional[float] = None) -> Dict:
+        """Algorithm 1 with a fixed SPD preconditioner M^{-1} = diag(minv) (per cell, the same
+        at every time step): z = M^{-1} r, alpha = <r,z>/<p,Ap>, beta_k = <r',z'>/<r,z>,
+        p = z + beta_k p; stopping test on ||r|| as in Algorithm 1."""
+        b = self.ST(sh, d)
+        x = np.zeros_like(b)
+        r = b.copy()
+        z = r * minv[None, :]
+        p = z.copy()
+        rz = float(np.sum(r * z))
+        r0 = math.sqrt(float(np.sum(r * r)))
+        hist = []
+        k = 0
+        for k in range(n_cg):
+            Ap = self.normal_matvec(sh, p, beta, eps)
+            alpha = rz / float(np.sum(p * Ap))
+            x = x + alpha * p
+            r = r - alpha * Ap
+            rn = math.sqrt(float(np.sum(r * r)))
+            hist.append(rn / r0)
+            if rn < tol * r0 or k == n_cg - 1:
+                break
+            z = r * minv[None, :]
+            rz_new = float(np.sum(r * z))
+            p = z + (rz_new / rz) * p
+            rz = rz_new
+        return {"x": x, "rel_res": np.asarray(hist), "iters": k + 1}
+
     def assemble_normal(self, sh: Shot, beta: float, eps: Optional[float] = None) -> np.ndarray:
         """Dense normal matrix, column j = A e_j (tiny sizes only)."""
         n = self.nt * self.N

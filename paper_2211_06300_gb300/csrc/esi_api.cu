@@ -86,6 +86,7 @@ struct esi_ctx {
     DBuf part, part2, scal;        // reduction partials, per-shot scalars
     DBuf traces;                   // scratch seismogram [nt * total receivers]
     DBuf cg_r, cg_p, cg_ap;        // CG work vectors
+    DBuf pb2, ipb2;                // per-shot pen B^2 and 1 / (pen B^2) maps [ns][sst]
     DBuf ckpt, ckpt_scale, absbits, stash, gacc, twid, dftacc;
     long long total_rec = 0;
     std::string err;
@@ -407,8 +408,8 @@ PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
     std::call_once(once, [] {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) ==
-                cudaSuccess &&
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
             fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
     });
@@ -1110,6 +1111,16 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
     const T eps = T(eps_in > 0 ? eps_in : ctx->g.dx);
     const T pc = precond == ESI_PC_DIAG ? T(lambda) : T(0);
     double *rz_part = pc > T(0) ? ctx->part2.as<double>() : nullptr;
+    // lambda B^2 (and its inverse for the diagonal preconditioner), once per solve
+    CK(ctx->pb2.ensure((size_t)ns * ctx->sst * sizeof(T)));
+    T *ipb2 = nullptr;
+    if (pc > T(0)) {
+        CK(ctx->ipb2.ensure((size_t)ns * ctx->sst * sizeof(T)));
+        ipb2 = ctx->ipb2.as<T>();
+    }
+    CKL(launch_b2_maps<T>(ctx->pb2.as<T>(), ipb2, ns, ctx->g.nz, ctx->g.ny, ctx->g.nx, ctx->px,
+                          T(lambda), eps, T(ctx->g.dx), ctx->src_pos.as<double>(), ctx->st));
+    const int nzny = ctx->g.nz * ctx->g.ny;
     std::vector<int> h_active(ns, 1), h_bad(ns, 0), iters(ns, 0);
     CK(cudaMemsetAsync(bad, 0, sizeof(int) * ns, ctx->st));
     CK(cudaMemsetAsync(alpha, 0, sizeof(double) * ns, ctx->st));
@@ -1119,8 +1130,8 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
     if (e != ESI_OK) return e;
     // ||r0||^2 and rho0 = <r0, z0>: the update pass with alpha = 0 (p = Ap = r)
     CKL(launch_cg_update<T>(x, r, r, r, rows, ctx->g.nx, ctx->px, ns, alpha, nullptr,
-                            ctx->part.as<double>(), rz_part, nblk_vec, pc, ctx->src_pos.as<double>(),
-                            ctx->g.nz, ctx->g.ny, eps, T(ctx->g.dx), ctx->st));
+                            ctx->part.as<double>(), rz_part, nblk_vec, ipb2, ctx->sst, nzny,
+                            ctx->st));
     CKL(launch_reduce_partials(ctx->part.as<double>(), nblk_vec, ns, rr, ctx->st));
     CKL(launch_reduce_partials(rz_part ? rz_part : ctx->part.as<double>(), nblk_vec, ns, rho, ctx->st));
     std::vector<double> rr0(ns), rrn(ns);
@@ -1147,6 +1158,7 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
         a.cg_beta = beta;
         a.cg_first = k == 0;
         a.cg_pc = pc;
+        a.ipb2 = ipb2;
         a.eps = eps;
         a.smp = smp_view<T>(ctx->smp_rec);
         a.smp_out = tr;
@@ -1166,6 +1178,7 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
         b.ap_p = p;
         b.dot_part = ctx->part.as<double>();
         b.pen = T(lambda);
+        b.pb2 = ctx->pb2.as<T>();
         b.eps = eps;
         T *acur = ctx->a0.as<T>(), *apo = ctx->a1.as<T>();
         e = adj_loop<T>(ctx, b, F_PT | F_AP, acur, apo, nt, 0, false);
@@ -1175,9 +1188,8 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
         const auto t1 = clk::now();
         cudaEvent_t ev = prof_mark(ctx);
         CKL(launch_cg_update<T>(x, r, p, ap, rows, ctx->g.nx, ctx->px, ns, alpha, active,
-                                ctx->part.as<double>(), rz_part, nblk_vec, pc,
-                                ctx->src_pos.as<double>(), ctx->g.nz, ctx->g.ny, eps,
-                                T(ctx->g.dx), ctx->st));
+                                ctx->part.as<double>(), rz_part, nblk_vec, ipb2, ctx->sst, nzny,
+                                ctx->st));
         prof_close(ctx, ev, "cg_update", (6.0 + 0.0) * sizeof(T), 1,
                    (long long)ctx->prof_active * ctx->N * nt);
         CKL(launch_reduce_partials(ctx->part.as<double>(), nblk_vec, ns, rr, ctx->st));

@@ -108,7 +108,9 @@ struct StepArgs {
     T *cg_p;
     const double *cg_beta;
     int cg_first;
-    T cg_pc;                   // > 0: diagonal preconditioner z = r / (cg_pc B^2) in p' = z + beta p
+    T cg_pc;                   // > 0: diagonal preconditioner z = r * ipb2 in p' = z + beta p
+    // per-shot maps [ns][sst] (pitched) of pen B^2 and 1 / (pen B^2), B = |x - x_s| + eps
+    const T *pb2, *ipb2;
     // point injection at trace time tin
     InjList<T> inj;
     const T *inj_trace;
@@ -170,12 +172,17 @@ cudaError_t launch_reduce_partials(const double *part, int nblk, int ns, double 
 
 // x += alpha p (x dense caller layout) ; r -= alpha Ap (pitched) ; partial ||r||^2.
 // rows = nt * nz * ny rows of nx cells per shot; r, p, Ap rows have pitch px.
-// With pc_pen > 0 also the partial r^T z for z = r / (pc_pen B^2) into part2.
+// With ipb2 (per-shot [sst] map of 1 / (pen B^2)) also the partial r^T z, z = r * ipb2.
 template <typename T>
 cudaError_t launch_cg_update(T *x, T *r, const T *p, const T *ap, long long rows, int nx, int px,
                              int ns, const double *alpha, const int *active, double *part,
-                             double *part2, int nblk, T pc_pen, const double *src_pos, int nz,
-                             int ny, T eps, T dx, cudaStream_t st);
+                             double *part2, int nblk, const T *ipb2, long long sst, int nzny,
+                             cudaStream_t st);
+
+// per-shot maps pb2 = pen B^2 and ipb2 = 1 / pb2 over the pitched plane (pad cells 0)
+template <typename T>
+cudaError_t launch_b2_maps(T *pb2, T *ipb2, int ns, int nz, int ny, int nx, int px, T pen, T eps,
+                           T dx, const double *src_pos, cudaStream_t st);
 // alpha = rr / pAp ; flags breakdown
 cudaError_t launch_cg_alpha(const double *rr, const double *pap, double *alpha, int *bad,
                             const int *active, int ns, cudaStream_t st);

@@ -19,12 +19,18 @@
 //              on-the-fly DTFT accumulation.
 #include "esi_internal.h"
 
+// resident blocks per SM the register allocation must allow (256 threads each)
+#ifndef ESI_FD2_MINB
+#define ESI_FD2_MINB 4
+#endif
+
 namespace esi {
 namespace {
 
-// Fornberg (1988) 8th-order central weights of the second derivative, offsets 1..4
-// (the centre weight is minus twice their sum, so it is folded into differences).
-constexpr double W1 = 8.0 / 5.0, W2 = -1.0 / 5.0, W3 = 8.0 / 315.0, W4 = -1.0 / 560.0;
+// Fornberg (1988) 8th-order central weights of the second derivative, offsets 0..4; in
+// 2D the centre weight appears once per axis.
+constexpr double W0 = -205.0 / 72.0, W1 = 8.0 / 5.0, W2 = -1.0 / 5.0, W3 = 8.0 / 315.0,
+                 W4 = -1.0 / 560.0;
 
 template <typename T>
 struct alignas(16) Vec {
@@ -72,7 +78,7 @@ __device__ __forceinline__ void stv(T *p, const Vec<T> &v) {
 }
 
 template <typename T, unsigned F>
-__global__ void __launch_bounds__(NT2, 3) fd2_step_kernel(const __grid_constant__ StepArgs<T> a) {
+__global__ void __launch_bounds__(NT2, ESI_FD2_MINB) fd2_step_kernel(const __grid_constant__ StepArgs<T> a) {
     constexpr int VEC = Vec<T>::n;     // cells per thread-vector
     constexpr int TPR = TX2 / VEC;     // threads per tile row
     constexpr int RPP = NT2 / TPR;     // rows per pass
@@ -181,7 +187,7 @@ __global__ void __launch_bounds__(NT2, 3) fd2_step_kernel(const __grid_constant_
     if (colok) {
         const Vec<T> kx = ldv(a.kx + gx0);
         T xs = T(0), zs = T(0);
-        if constexpr ((F & (F_AP | F_SAD | F_CGP)) != 0) {
+        if constexpr ((F & F_SAD) != 0) {
             xs = T(a.src_pos[3 * s + 0]);
             zs = T(a.src_pos[3 * s + 2]);
         }
@@ -199,26 +205,18 @@ __global__ void __launch_bounds__(NT2, 3) fd2_step_kernel(const __grid_constant_
 #pragma unroll
                 for (int i = 0; i < VEC; ++i) w[c * VEC + i] = t.v[i];
             }
+            // Laplacian sum: 2 w0 u + sum_k w_k (4 neighbours at distance k)
             T L[VEC];
 #pragma unroll
-            for (int i = 0; i < VEC; ++i) {
-                const T u = w[i + HALO];
-                L[i] = T(W1) * ((w[i + 3] - u) + (w[i + 5] - u)) +
-                       T(W2) * ((w[i + 2] - u) + (w[i + 6] - u)) +
-                       T(W3) * ((w[i + 1] - u) + (w[i + 7] - u)) +
-                       T(W4) * ((w[i + 0] - u) + (w[i + 8] - u));
-            }
-            // z neighbours
+            for (int i = 0; i < VEC; ++i) L[i] = T(2.0 * W0) * w[i + HALO];
             constexpr double WZ[5] = {0.0, W1, W2, W3, W4};
 #pragma unroll
             for (int k = 1; k <= HALO; ++k) {
                 const Vec<T> up = ldv(&tl[sz - k][lx + HALO]);
                 const Vec<T> dn = ldv(&tl[sz + k][lx + HALO]);
 #pragma unroll
-                for (int i = 0; i < VEC; ++i) {
-                    const T u = w[i + HALO];
-                    L[i] += T(WZ[k]) * ((up.v[i] - u) + (dn.v[i] - u));
-                }
+                for (int i = 0; i < VEC; ++i)
+                    L[i] += T(WZ[k]) * ((w[i + HALO - k] + w[i + HALO + k]) + (up.v[i] + dn.v[i]));
             }
             const long long gi = (long long)gz * a.px + gx0;
             const Vec<T> old = p_old[pz];
@@ -231,13 +229,9 @@ __global__ void __launch_bounds__(NT2, 3) fd2_step_kernel(const __grid_constant_
                 const long long vi = fb + (long long)a.n * a.sst + gi;
                 Vec<T> pn = p_r[pz];
                 if (a.cg_pc > T(0)) {   // z = r / (pen B^2)
-                    const T ez = T(gz) * a.dx - zs;
+                    const Vec<T> ib = ldv(a.ipb2 + (long long)s * a.sst + gi);
 #pragma unroll
-                    for (int i = 0; i < VEC; ++i) {
-                        const T ex = T(gx0 + i) * a.dx - xs;
-                        const T B = sqrt(ex * ex + ez * ez) + a.eps;
-                        pn.v[i] = pn.v[i] / (a.cg_pc * B * B);
-                    }
+                    for (int i = 0; i < VEC; ++i) pn.v[i] *= ib.v[i];
                 }
                 if (!a.cg_first) {
                     const T b = T(a.cg_beta[s]);
@@ -257,17 +251,30 @@ __global__ void __launch_bounds__(NT2, 3) fd2_step_kernel(const __grid_constant_
                 }
             }
             Vec<T> nw;
+            bool sponge = kz != T(0);
 #pragma unroll
-            for (int i = 0; i < VEC; ++i) {
-                const T kap = kz + kx.v[i];
-                const T al = T(1) / (T(1) + kap);
-                const T ga = (T(1) - kap) * al;
-                const T u = w[i + HALO];
-                const T val = u + ga * (u - old.v[i]) + al * cc.v[i] * S[i];
-                nw.v[i] = (gx0 + i < a.nx) ? val : T(0);   // pad columns stay zero
+            for (int i = 0; i < VEC; ++i) sponge |= kx.v[i] != T(0);
+            if (sponge) {
+#pragma unroll
+                for (int i = 0; i < VEC; ++i) {
+                    const T kap = kz + kx.v[i];
+                    const T al = T(1) / (T(1) + kap);
+                    const T ga = (T(1) - kap) * al;
+                    const T u = w[i + HALO];
+                    nw.v[i] = u + ga * (u - old.v[i]) + al * cc.v[i] * S[i];
+                }
+            } else {   // interior: alpha = gamma = 1
+#pragma unroll
+                for (int i = 0; i < VEC; ++i) {
+                    const T u = w[i + HALO];
+                    nw.v[i] = u + (u - old.v[i]) + cc.v[i] * S[i];
+                }
             }
+#pragma unroll
+            for (int i = 0; i < VEC; ++i)
+                if (gx0 + i >= a.nx) nw.v[i] = T(0);   // pad columns stay zero
             stv(po + gi, nw);
-            if constexpr ((F & (F_AP | F_SAD)) != 0) {
+            if constexpr ((F & F_SAD) != 0) {
                 T B2[VEC];
                 const T ez = T(gz) * a.dx - zs;
 #pragma unroll
@@ -276,23 +283,24 @@ __global__ void __launch_bounds__(NT2, 3) fd2_step_kernel(const __grid_constant_
                     const T B = sqrt(ex * ex + ez * ez) + a.eps;
                     B2[i] = B * B;
                 }
-                if constexpr ((F & F_SAD) != 0) {
+                {
                     Vec<T> gv = p_g[pz];
 #pragma unroll
                     for (int i = 0; i < VEC; ++i) gv.v[i] += B2[i] * q[i] * S[i];
                     stv(a.grad + (long long)s * a.sst + gi, gv);
                 }
-                if constexpr ((F & F_AP) != 0) {
-                    const long long vi = fb + (long long)a.nout * a.sst + gi;
-                    const Vec<T> pv = p_p[pz];
-                    Vec<T> av;
+            }
+            if constexpr ((F & F_AP) != 0) {   // A p = S^T S p + pen B^2 p
+                const long long vi = fb + (long long)a.nout * a.sst + gi;
+                const Vec<T> pv = p_p[pz];
+                const Vec<T> b2 = ldv(a.pb2 + (long long)s * a.sst + gi);
+                Vec<T> av;
 #pragma unroll
-                    for (int i = 0; i < VEC; ++i) {
-                        av.v[i] = nw.v[i] + a.pen * B2[i] * pv.v[i];
-                        psum += pv.v[i] * av.v[i];
-                    }
-                    stv(a.ap + vi, av);
+                for (int i = 0; i < VEC; ++i) {
+                    av.v[i] = nw.v[i] + b2.v[i] * pv.v[i];
+                    psum += pv.v[i] * av.v[i];
                 }
+                stv(a.ap + vi, av);
             }
             if constexpr ((F & F_STW) != 0) {
                 Vec<T> sv;

@@ -87,11 +87,7 @@ __global__ void __launch_bounds__(TX3 *TY3) fd3_step_kernel(const StepArgs<T> a,
             if constexpr ((F & F_CGP) != 0) {
                 const long long vi = fb + (long long)a.n * a.sst + gi;
                 T pn = a.cg_r[vi];
-                if (a.cg_pc > T(0)) {   // z = r / (pen B^2)
-                    const T ex = T(gx) * a.dx - xs, ey = T(gy) * a.dx - ys, ez = T(z) * a.dx - zs;
-                    const T B = sqrt(ex * ex + ey * ey + ez * ez) + a.eps;
-                    pn = pn / (a.cg_pc * B * B);
-                }
+                if (a.cg_pc > T(0)) pn *= a.ipb2[(long long)s * a.sst + gi];   // z = r / (pen B^2)
                 if (!a.cg_first) pn += T(a.cg_beta[s]) * a.cg_p[vi];
                 a.cg_p[vi] = pn;
                 src += pn;
@@ -120,18 +116,17 @@ __global__ void __launch_bounds__(TX3 *TY3) fd3_step_kernel(const StepArgs<T> a,
             const T old = po[gi];
             const T nw = u + ga * (u - old) + al * a.cc[gi] * S;
             po[gi] = nw;
-            if constexpr ((F & (F_AP | F_SAD)) != 0) {
+            if constexpr ((F & F_SAD) != 0) {
                 const T ex = T(gx) * a.dx - xs, ey = T(gy) * a.dx - ys, ez = T(z) * a.dx - zs;
                 const T B = sqrt(ex * ex + ey * ey + ez * ez) + a.eps;
-                const T B2 = B * B;
-                if constexpr ((F & F_SAD) != 0) a.grad[(long long)s * a.sst + gi] += B2 * src * S;
-                if constexpr ((F & F_AP) != 0) {
-                    const long long vi = fb + (long long)a.nout * a.sst + gi;
-                    const T pv = a.ap_p[vi];
-                    const T apv = nw + a.pen * B2 * pv;
-                    a.ap[vi] = apv;
-                    psum += pv * apv;
-                }
+                a.grad[(long long)s * a.sst + gi] += B * B * src * S;
+            }
+            if constexpr ((F & F_AP) != 0) {   // A p = S^T S p + pen B^2 p
+                const long long vi = fb + (long long)a.nout * a.sst + gi;
+                const T pv = a.ap_p[vi];
+                const T apv = nw + a.pb2[(long long)s * a.sst + gi] * pv;
+                a.ap[vi] = apv;
+                psum += pv * apv;
             }
             if constexpr ((F & F_STW) != 0)
                 a.stash_w[((long long)a.slot_w * a.ns + s) * a.sst + gi] = S;

@@ -98,8 +98,7 @@ __global__ void reduce_partials_kernel(const double *part, int nblk, int ns, dou
 template <typename T>
 __global__ void cg_update_kernel(T *x, T *r, const T *p, const T *ap, long long rows, int nx,
                                  int px, const double *alpha, const int *active, double *part,
-                                 double *part2, T pen, const double *src_pos, int nz, int ny,
-                                 T eps, T dx) {
+                                 double *part2, const T *ipb2, long long sst, int nzny) {
     constexpr int VEC = V16<T>::n;
     const int s = blockIdx.y;
     if (active && !active[s]) return;
@@ -110,7 +109,7 @@ __global__ void cg_update_kernel(T *x, T *r, const T *p, const T *ap, long long 
     const T *ps = p + s * sp, *as = ap + s * sp;
     const int cpr = px / VEC;
     const long long nchunk = rows * cpr;
-    const T xsrc = T(src_pos[3 * s]), ysrc = T(src_pos[3 * s + 1]), zsrc = T(src_pos[3 * s + 2]);
+    const T *ib = ipb2 ? ipb2 + s * sst : nullptr;
     double acc = 0.0, acc2 = 0.0;
     for (long long c = (long long)blockIdx.x * RT + threadIdx.x; c < nchunk;
          c += (long long)gridDim.x * RT) {
@@ -133,23 +132,17 @@ __global__ void cg_update_kernel(T *x, T *r, const T *p, const T *ap, long long 
         for (int k = 0; k < VEC; ++k)
             if (x0 + k < nx) xr[k] += al * pv.v[k];
         acc += double(t);
-        if (pen > T(0)) {
-            const long long pl = row % ((long long)nz * ny);
-            const int iz = int(pl / ny), iy = int(pl - (long long)iz * ny);
-            const T ez = T(iz) * dx - zsrc, ey = ny > 1 ? T(iy) * dx - ysrc : T(0);
+        if (ib) {   // r^T z with z = r / (pen B^2)
+            const V16<T> bv = *reinterpret_cast<const V16<T> *>(ib + (row % nzny) * px + x0);
             T t2 = T(0);
 #pragma unroll
-            for (int k = 0; k < VEC; ++k) {
-                const T ex = T(x0 + k) * dx - xsrc;
-                const T B = sqrt(ex * ex + ey * ey + ez * ez) + eps;
-                t2 += rv.v[k] * rv.v[k] / (pen * B * B);
-            }
+            for (int k = 0; k < VEC; ++k) t2 += rv.v[k] * rv.v[k] * bv.v[k];
             acc2 += double(t2);
         }
     }
     const double t = block_sum_d(acc);
     if (threadIdx.x == 0) part[(long long)s * gridDim.x + blockIdx.x] = t;
-    if (pen > T(0)) {
+    if (ib) {
         __syncthreads();
         const double t2 = block_sum_d(acc2);
         if (threadIdx.x == 0) part2[(long long)s * gridDim.x + blockIdx.x] = t2;
@@ -339,11 +332,43 @@ cudaError_t launch_reduce_partials(const double *part, int nblk, int ns, double 
 template <typename T>
 cudaError_t launch_cg_update(T *x, T *r, const T *p, const T *ap, long long rows, int nx, int px,
                              int ns, const double *alpha, const int *active, double *part,
-                             double *part2, int nblk, T pc_pen, const double *src_pos, int nz,
-                             int ny, T eps, T dx, cudaStream_t st) {
+                             double *part2, int nblk, const T *ipb2, long long sst, int nzny,
+                             cudaStream_t st) {
     cg_update_kernel<T><<<dim3(nblk, ns), RT, 0, st>>>(x, r, p, ap, rows, nx, px, alpha, active,
-                                                       part, part2, pc_pen, src_pos, nz, ny, eps,
-                                                       dx);
+                                                       part, part2, ipb2, sst, nzny);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void b2_maps_kernel(T *pb2, T *ipb2, int nz, int ny, int nx, int px, T pen, T eps,
+                               T dx, const double *src_pos) {
+    const int s = blockIdx.y;
+    const long long plane = (long long)nz * ny * px;
+    const double xs = src_pos[3 * s], ys = src_pos[3 * s + 1], zs = src_pos[3 * s + 2];
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < plane;
+         i += (long long)gridDim.x * RT) {
+        const long long row = i / px;
+        const int x = int(i - row * px);
+        const int iy = int(row % ny), iz = int(row / ny);
+        T v = T(0), iv = T(0);
+        if (x < nx) {
+            const double ex = x * double(dx) - xs, ez = iz * double(dx) - zs;
+            const double ey = ny > 1 ? iy * double(dx) - ys : 0.0;
+            const double B = std::sqrt(ex * ex + ey * ey + ez * ez) + double(eps);
+            v = T(double(pen) * B * B);
+            iv = T(1.0 / (double(pen) * B * B));
+        }
+        pb2[(long long)s * plane + i] = v;
+        if (ipb2) ipb2[(long long)s * plane + i] = iv;
+    }
+}
+
+template <typename T>
+cudaError_t launch_b2_maps(T *pb2, T *ipb2, int ns, int nz, int ny, int nx, int px, T pen, T eps,
+                           T dx, const double *src_pos, cudaStream_t st) {
+    const long long plane = (long long)nz * ny * px;
+    b2_maps_kernel<T><<<dim3(blocks_for(plane, 2048), ns), RT, 0, st>>>(pb2, ipb2, nz, ny, nx, px,
+                                                                        pen, eps, dx, src_pos);
     return cudaGetLastError();
 }
 
@@ -423,8 +448,10 @@ cudaError_t launch_dft_output(const T *acc, long long sst, int rows, int nx, int
                                        int, const int *, cudaStream_t);                          \
     template cudaError_t launch_cg_update<T>(T *, T *, const T *, const T *, long long, int, int, \
                                              int, const double *, const int *, double *,         \
-                                             double *, int, T, const double *, int, int, T, T,   \
+                                             double *, int, const T *, long long, int,           \
                                              cudaStream_t);                                      \
+    template cudaError_t launch_b2_maps<T>(T *, T *, int, int, int, int, int, T, T, T,           \
+                                           const double *, cudaStream_t);                        \
     template cudaError_t launch_residual<T>(T *, const T *, long long, double *, int,            \
                                             cudaStream_t);                                       \
     template cudaError_t launch_grad_finalize<T>(const T *, int, long long, const T *, int, int, \

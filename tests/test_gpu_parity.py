@@ -287,3 +287,32 @@ def test_single_step_and_corner_points():
     d = ctx.forward(wavelet=_dev(wav, "f64"))
     ref = o.forward(sh, wavelet=wav[0])["traces"]
     assert np.allclose(ctx.traces_of(d, 0).cpu().numpy(), ref, rtol=1e-13, atol=1e-300)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_diag_pcg_matches_oracle(prec):
+    v, geom, p = _ragged_case(nt=80)
+    geom.rec_xyz[geom.rec_offset[1]] = (geom.src_xyz[1, 0] + 55.0, 0.0, 30.0)
+    o, shots = _orc(v, geom, p)
+    nt = p["nt"]
+    wav = np.stack([synth.ricker(nt, p["dt"], 25.0)] * geom.ns)
+    d = np.concatenate([o.forward(sh, wavelet=wav[s])["traces"].ravel()
+                        for s, sh in enumerate(shots)])
+    # This system is ill-conditioned (B^2 spans four decades), so rounding-order
+    # differences grow along the iteration as in any finite-precision CG: the iterates are
+    # compared over the first 5 iterations, convergence over a longer run.
+    lam, nmax = 2e-4, 5
+    ctx = _ctx(v, geom, p, prec)
+    q, rep = ctx.cg_solve(_dev(d, prec), lam=lam, tol=0.0, max_iter=nmax, precond="diag")
+    tol_hist = {"f64": 1e-9, "f32": 1e-3}[prec]
+    for s, sh in enumerate(shots):
+        o0, o1 = geom.rec_offset[s], geom.rec_offset[s + 1]
+        B = o.annihilator(sh.src_xyz)
+        ref = o.pcg(sh, d[nt * o0:nt * o1].reshape(nt, -1), lam, 0.0, nmax,
+                    minv=1.0 / (lam * B * B))
+        assert rep["iters"][s] == ref["iters"] == nmax, s
+        assert np.allclose(rep["rel_res"][s], ref["rel_res"], rtol=tol_hist, atol=0), s
+        assert oracle.rel_l2(q[s].reshape(nt, -1).double().cpu().numpy(), ref["x"]) <= \
+            tol_hist, s
+    q, rep = ctx.cg_solve(_dev(d, prec), lam=lam, tol=1e-3, max_iter=60, precond="diag")
+    assert rep["converged"] and max(rep["iters"]) < 60

@@ -455,3 +455,20 @@ def test_snapshot_codec_roundtrip_bound(kind, bound):
     # one rounding to the 16-bit format plus two FP32 roundings of the scale products
     assert np.max(rel) <= bound * (1 + 1e-3) + 3 * 2.0 ** -24
     assert np.max(np.abs(back)) <= s * (1 + bound)
+
+
+def test_pcg_reaches_the_cholesky_solution_and_reduces_to_cg():
+    orc, sh = _tiny_problem()
+    beta = 1e-3
+    A = orc.assemble_normal(sh, beta)
+    d = synth.normal(15, (orc.nt, sh.nr))
+    b = orc.ST(sh, d).ravel()
+    x_direct = np.linalg.solve(A, b)
+    B = orc.annihilator(sh.src_xyz)
+    res = orc.pcg(sh, d, beta, tol=1e-13, n_cg=3000, minv=1.0 / (beta * B * B))
+    assert oracle.rel_l2(res["x"].ravel(), x_direct) < 1e-9
+    # the identity preconditioner gives Algorithm 1's iterates
+    a = orc.pcg(sh, d, beta, tol=0.0, n_cg=6, minv=np.ones(orc.N))
+    c = orc.cg(sh, d, beta, tol=0.0, n_cg=6)
+    assert np.allclose(a["rel_res"], c["rel_res"], rtol=1e-12)
+    assert oracle.rel_l2(a["x"], c["x"]) < 1e-12
