@@ -236,8 +236,63 @@ ESI_API esi_status esi_cg_solve(esi_ctx *ctx, double lambda, double tol, int max
                                 const void *dobs_dev, void *q_out_dev, int precond, double eps,
                                 esi_cg_report *report);
 
-/* Load the learned preconditioner's weights (layout documented in esi_pc.h). */
+/*
+ * esi_normal_apply -- the ESI normal operator (Eq. "normalewi"; the matrix-vector product
+ * bullet of the CG section): out = S^T S p + lambda B^2 p, B = ||x - x_s|| + eps (eps <= 0:
+ * dx), one forward and one adjoint modelling.  p_dev, out_dev: device [ns][nt][N] dense.
+ */
+ESI_API esi_status esi_normal_apply(esi_ctx *ctx, double lambda, double eps, const void *p_dev,
+                                    void *out_dev);
+
+/*
+ * Learned CG preconditioner (the paper's conclusion: an efficient preconditioner to cut
+ * the inner CG iterations).  For a residual r of one shot:
+ *     s = r / (lambda B^2),   z = s + up2(U(pack(s)))
+ * where pack() averages 2 x 2 cells and groups 16 consecutive time samples as the 16
+ * channels of an image (time padded with zeros to a multiple of 16), U is a 4-level U-Net
+ * with 32 channels (3 x 3 convolutions with zero padding and ReLU, 2 x 2 average pooling
+ * with zero fill at odd edges, nearest upsampling with skip additions; the last layer is
+ * linear with 16 outputs) and up2() repeats each coarse cell over its 2 x 2 block.  Images
+ * are BF16 [img][h][w][16] (h = ceil(nz/2), w = ceil(nx/2)); U computes in BF16 with FP32
+ * accumulation on the tensor cores.  Parameters: esi_pc_param_count() FP32 values, per
+ * layer (enc1 16->32, enc2, enc3, bott, dec3, dec2 32->32, dec1 32->16) the weights
+ * W[3][3][cin][cout] followed by the biases b[cout].  The network is a learned object:
+ * its only judge is the CG residual (the solver falls back to the diagonal preconditioner
+ * whenever <z, r> <= 0).
+ */
+typedef struct esi_pc esi_pc;
+
+ESI_API size_t esi_pc_param_count(void);
+
+/* Load trained parameters (device FP32, esi_pc_param_count() values) into a 2D FP32 context;
+ * esi_cg_solve(..., ESI_PC_LEARNED, ...) then uses flexible (Polak-Ribiere) CG with z above. */
 ESI_API esi_status esi_pc_load(esi_ctx *ctx, const void *weights_dev, size_t bytes);
+
+/* Times the learned preconditioner broke down (<z, r> <= 0) and CG restarted diagonally. */
+ESI_API long long esi_pc_fallbacks(const esi_ctx *ctx);
+
+/* Pack a dense field [ns][nt][N] (scaled by 1 / (lambda B^2) when scale != 0) into the
+ * network's BF16 images [ns * ceil(nt/16)][h][w][16] (2D FP32 contexts). */
+ESI_API esi_status esi_pc_pack(esi_ctx *ctx, const void *field_dev, double lambda, double eps,
+                               int scale, void *img_dev);
+
+/* A stand-alone network for h x w images, batches of up to max_batch, on a stream. */
+ESI_API esi_status esi_pc_create(esi_pc **out, int h, int w, int max_batch, void *stream);
+ESI_API void esi_pc_destroy(esi_pc *pc);
+ESI_API const char *esi_pc_last_error(const esi_pc *pc);
+/* Parameters in and out (device FP32, layout above); setting them resets the Adam state. */
+ESI_API esi_status esi_pc_set_params(esi_pc *pc, const float *params_dev);
+ESI_API esi_status esi_pc_get_params(esi_pc *pc, float *params_dev);
+/* y = U(x) for n images: x BF16 [n][h][w][16], y FP32 [n][h][w][16]. */
+ESI_API esi_status esi_pc_apply(esi_pc *pc, const void *in_dev, int n, float *y_dev);
+/* Training objective on n pairs (x = packed scaled residual, e = packed CG error):
+ * loss = mean_i (1 - <x_i + y_i, e_i>^2 / (|x_i + y_i|^2 |e_i|^2)), y = U(x).  Writes the
+ * parameter gradient (device FP32, may be NULL) and the loss (host, may be NULL). */
+ESI_API esi_status esi_pc_grad(esi_pc *pc, const void *in_dev, const void *target_dev, int n,
+                               float *grad_dev, double *loss);
+/* esi_pc_grad followed by one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at rate lr. */
+ESI_API esi_status esi_pc_train_step(esi_pc *pc, const void *in_dev, const void *target_dev,
+                                     int n, double lr, double *loss);
 
 /* Static string for a status code. */
 ESI_API const char *esi_status_string(esi_status s);

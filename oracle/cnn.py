@@ -102,24 +102,40 @@ def init_params(seed: int, scale: float = 1.0) -> Dict[str, np.ndarray]:
     return p
 
 
-def unet_forward(x: np.ndarray, p: Dict[str, np.ndarray]) -> Tuple[np.ndarray, Dict]:
-    """4-level U-Net; returns the output and the activations needed by the backward."""
+def unet_forward(x: np.ndarray, p: Dict[str, np.ndarray], store=None) -> Tuple[np.ndarray, Dict]:
+    """4-level U-Net; returns the output and the activations needed by the backward.
+    ``store`` (optional) maps every stored hidden activation (conv outputs, pooled and
+    upsampled-plus-skip tensors) to the values a reduced-precision implementation keeps;
+    the default keeps them exactly."""
+    st = store if store is not None else (lambda t: t)
     a = {"x": x}
 
     def layer(name, inp, relu):
         pre = conv3x3(inp, p[name + ".W"], p[name + ".b"])
         a[name + ".in"] = inp
         a[name + ".pre"] = pre
-        return np.maximum(pre, 0.0) if relu else pre
+        return st(np.maximum(pre, 0.0)) if relu else pre
     e1 = layer("enc1", x, True)
-    e2 = layer("enc2", pool2(e1), True)
-    e3 = layer("enc3", pool2(e2), True)
-    bt = layer("bott", pool2(e3), True)
-    d3 = layer("dec3", up2(bt, *e3.shape[1:3]) + e3, True)
-    d2 = layer("dec2", up2(d3, *e2.shape[1:3]) + e2, True)
-    y = layer("dec1", up2(d2, *e1.shape[1:3]) + e1, False)
+    e2 = layer("enc2", st(pool2(e1)), True)
+    e3 = layer("enc3", st(pool2(e2)), True)
+    bt = layer("bott", st(pool2(e3)), True)
+    d3 = layer("dec3", st(up2(bt, *e3.shape[1:3]) + e3), True)
+    d2 = layer("dec2", st(up2(d3, *e2.shape[1:3]) + e2), True)
+    y = layer("dec1", st(up2(d2, *e1.shape[1:3]) + e1), False)
     a.update(e1=e1, e2=e2, e3=e3, bt=bt, d3=d3, d2=d2)
     return y, a
+
+
+def normalized_forward(x: np.ndarray, p: Dict[str, np.ndarray], store=None
+                       ) -> Tuple[np.ndarray, Dict, np.ndarray]:
+    """y_i = rho_i U(x_i / rho_i), rho_i the root-mean-square of image i (y_i = 0 when
+    rho_i = 0): positively homogeneous in x, as a preconditioner has to be."""
+    st = store if store is not None else (lambda t: t)
+    rho = np.sqrt(np.mean(x.reshape(x.shape[0], -1) ** 2, axis=1))
+    safe = np.where(rho > 0, rho, 1.0)
+    xn = st(np.where(rho[:, None, None, None] > 0, x / safe[:, None, None, None], 0.0))
+    y, a = unet_forward(xn, p, store)
+    return y * rho[:, None, None, None], a, rho
 
 
 def unet_backward(gy: np.ndarray, p: Dict[str, np.ndarray], a: Dict) -> Tuple[np.ndarray, Dict]:
@@ -168,10 +184,43 @@ def unpack(s: np.ndarray, y: np.ndarray) -> np.ndarray:
 
 
 def precondition(r: np.ndarray, D: np.ndarray, p: Dict[str, np.ndarray]) -> np.ndarray:
-    """z = s + up2(U(pack(s))), s = D * r (D = 1 / (beta B^2) per cell)."""
+    """z = s + up2(rho U(pack(s) / rho)), s = D * r (D = 1 / (beta B^2) per cell), rho the
+    per-image root-mean-square of pack(s)."""
     s = r * D[None]
-    y, _ = unet_forward(pack(s), p)
+    y, _, _ = normalized_forward(pack(s), p)
     return unpack(s, y)
+
+
+def param_vector(p: Dict[str, np.ndarray]) -> np.ndarray:
+    """Flat parameter vector in the library's order: per layer W[3][3][cin][cout], b[cout]."""
+    return np.concatenate([np.concatenate([p[n + ".W"].ravel(), p[n + ".b"].ravel()])
+                           for n, _, _, _ in LAYERS])
+
+
+def params_from_vector(v: np.ndarray) -> Dict[str, np.ndarray]:
+    p, o = {}, 0
+    for n, ci, co, _ in LAYERS:
+        k = 9 * ci * co
+        p[n + ".W"] = np.asarray(v[o:o + k], dtype=np.float64).reshape(3, 3, ci, co)
+        p[n + ".b"] = np.asarray(v[o + k:o + k + co], dtype=np.float64)
+        o += k + co
+    return p
+
+
+def batch_loss_and_grad(x: np.ndarray, e: np.ndarray, p: Dict[str, np.ndarray], store=None
+                        ) -> Tuple[float, Dict[str, np.ndarray]]:
+    """Training objective on a batch: mean_i cosine_loss(x_i + y_i, e_i) with the normalised
+    network y = rho U(x / rho), and its gradient with respect to every parameter."""
+    y, a, rho = normalized_forward(x, p, store)
+    n = x.shape[0]
+    gy = np.zeros_like(y)
+    loss = 0.0
+    for i in range(n):
+        z = x[i] + y[i]
+        loss += cosine_loss(z, e[i])
+        gy[i] = cosine_loss_grad(z, e[i]) / n * rho[i]   # y = rho U(x / rho)
+    _, g = unet_backward(gy, p, a)
+    return loss / n, g
 
 
 def cosine_loss(z: np.ndarray, e: np.ndarray) -> float:

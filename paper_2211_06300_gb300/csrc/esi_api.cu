@@ -16,6 +16,7 @@
 #include <cudaTypedefs.h>
 
 #include "esi_internal.h"
+#include "esi_pc.h"
 
 using namespace esi;
 
@@ -83,10 +84,14 @@ struct esi_ctx {
     DevInj inj_src, inj_rec;
     DevSmp smp_rec, smp_src;
     DBuf u0, u1, a0, a1;           // forward / adjoint state pairs [ns][sst]
-    DBuf part, part2, scal;        // reduction partials, per-shot scalars
+    DBuf part, part2, part3, scal; // reduction partials, per-shot scalars
+    long long pc_fallbacks = 0;    // learned-preconditioner breakdowns (diagonal restart)
     DBuf traces;                   // scratch seismogram [nt * total receivers]
     DBuf cg_r, cg_p, cg_ap;        // CG work vectors
     DBuf pb2, ipb2;                // per-shot pen B^2 and 1 / (pen B^2) maps [ns][sst]
+    PcNet *pc = nullptr;           // learned preconditioner (esi_pc_load)
+    DBuf pc_img, pc_y;             // network input images (BF16) and output (FP32)
+    int pc_batch = 0;
     DBuf ckpt, ckpt_scale, absbits, stash, gacc, twid, dftacc;
     long long total_rec = 0;
     std::string err;
@@ -124,6 +129,7 @@ struct esi_ctx {
     std::vector<Stat> stats;
 
     ~esi_ctx() {
+        if (pc) pcnet_destroy(pc);
         for (auto &g : graphs) cudaGraphExecDestroy(g.exec);
         if (cap) cudaStreamDestroy(cap);
         for (auto &p : pending) {
@@ -401,9 +407,11 @@ SmpList<T> smp_view(const DevSmp &d) {
     return l;
 }
 
+}  // namespace
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)
-PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+TensorMapEncoder esi::tensor_map_encoder() {
+    static TensorMapEncoder fn = nullptr;
     static std::once_flag once;
     std::call_once(once, [] {
         void *p = nullptr;
@@ -411,10 +419,12 @@ PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
                                              &q) == cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+            fn = reinterpret_cast<TensorMapEncoder>(p);
     });
     return fn;
 }
+
+namespace {
 
 // TMA map of a state buffer [ns][nz][px] (2D): dims (nx, nz, ns), box (SW2, SH2, 1).  Cells
 // outside [0, nx) x [0, nz) are zero-filled by the copy engine.
@@ -424,7 +434,7 @@ bool state_map(esi_ctx *ctx, const void *base, CUtensorMap *out) {
             *out = m.second;
             return true;
         }
-    auto enc = tmap_encoder();
+    auto enc = tensor_map_encoder();
     if (!enc) return false;
     CUtensorMap tm;
     const cuuint64_t dims[3] = {(cuuint64_t)ctx->g.nx, (cuuint64_t)ctx->g.nz, (cuuint64_t)ctx->ns};
@@ -1084,10 +1094,14 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
     const int ns = ctx->ns, nt = ctx->nt;
     const long long plen = ctx->sst * nt;                       // pitched vector per shot
     const long long rows = (long long)nt * ctx->g.nz * ctx->g.ny;
-    if (precond != ESI_PC_NONE && precond != ESI_PC_DIAG)
-        return ctx->fail(ESI_ERR_UNSUPPORTED, "the learned preconditioner is not loaded");
-    if (precond == ESI_PC_DIAG && !(lambda > 0))
-        return ctx->fail(ESI_ERR_ARG, "the diagonal preconditioner needs lambda > 0");
+    bool learned = precond == ESI_PC_LEARNED;
+    if (precond != ESI_PC_NONE && precond != ESI_PC_DIAG && !learned)
+        return ctx->fail(ESI_ERR_ARG, "unknown preconditioner");
+    if (learned && (!ctx->pc || sizeof(T) != 4 || ctx->g.ndim != 2))
+        return ctx->fail(ESI_ERR_UNSUPPORTED,
+                         "the learned preconditioner needs esi_pc_load on a 2D FP32 context");
+    if (precond != ESI_PC_NONE && !(lambda > 0))
+        return ctx->fail(ESI_ERR_ARG, "preconditioning needs lambda > 0");
     if (max_iter < 1) return ctx->fail(ESI_ERR_ARG, "max_iter must be >= 1");
     esi_status e = ensure_states<T>(ctx, true);
     if (e != ESI_OK) return e;
@@ -1109,7 +1123,7 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
     T *x = reinterpret_cast<T *>(q_out), *r = ctx->cg_r.as<T>(), *p = ctx->cg_p.as<T>(),
       *ap = ctx->cg_ap.as<T>(), *tr = ctx->traces.as<T>();
     const T eps = T(eps_in > 0 ? eps_in : ctx->g.dx);
-    const T pc = precond == ESI_PC_DIAG ? T(lambda) : T(0);
+    const T pc = precond != ESI_PC_NONE ? T(lambda) : T(0);
     double *rz_part = pc > T(0) ? ctx->part2.as<double>() : nullptr;
     // lambda B^2 (and its inverse for the diagonal preconditioner), once per solve
     CK(ctx->pb2.ensure((size_t)ns * ctx->sst * sizeof(T)));
@@ -1121,6 +1135,38 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
     CKL(launch_b2_maps<T>(ctx->pb2.as<T>(), ipb2, ns, ctx->g.nz, ctx->g.ny, ctx->g.nx, ctx->px,
                           T(lambda), eps, T(ctx->g.dx), ctx->src_pos.as<double>(), ctx->st));
     const int nzny = ctx->g.nz * ctx->g.ny;
+    // learned preconditioner: z = r / (lambda B^2) + up2(U(pack(r / (lambda B^2)))), flexible
+    // (Polak-Ribiere) beta = -alpha <z_{k+1}, A p_k> / <z_k, r_k>; falls back to the diagonal
+    // preconditioner (restarting the directions) when <z, r> <= 0 for any shot
+    const int ng = (nt + 15) / 16, hc = (ctx->g.nz + 1) / 2, wc = (ctx->g.nx + 1) / 2;
+    const long long nimg = (long long)ns * ng, img_elems = (long long)hc * wc * 16;
+    double *za = nullptr;
+    std::vector<double> h_rho(ns), h_rhon(ns), h_za(ns), h_alpha(ns), h_beta(ns, 0.0);
+    if (learned) {
+        CK(ctx->pc_img.ensure((size_t)nimg * img_elems * 2));
+        CK(ctx->pc_y.ensure((size_t)nimg * img_elems * 4));
+        CK(ctx->part3.ensure(sizeof(double) * (ns + (size_t)ns * nblk_vec)));
+        za = ctx->part3.as<double>();
+    }
+    auto apply_learned = [&](const T *ap_prev, double *zr_out) -> esi_status {
+        const float *rf = reinterpret_cast<const float *>(r);
+        CKL(pcnet::pack_launch(rf, reinterpret_cast<const float *>(ipb2), ctx->pc_img.as<__nv_bfloat16>(),
+                               ns, nt, ctx->g.nz, ctx->g.nx, ctx->px, ctx->sst, 1, 0, ctx->st));
+        for (long long i0 = 0; i0 < nimg; i0 += ctx->pc_batch) {
+            const int nb = (int)std::min<long long>(ctx->pc_batch, nimg - i0);
+            CK(pcnet_forward(ctx->pc, ctx->pc_img.as<__nv_bfloat16>() + i0 * img_elems, nb,
+                             ctx->pc_y.as<float>() + i0 * img_elems, ctx->st));
+            ctx->launches += 13;
+        }
+        double *pzr = ctx->part.as<double>(), *pza = za + ns;
+        CKL(pcnet::pc_dots_launch(rf, reinterpret_cast<const float *>(ap_prev),
+                                  reinterpret_cast<const float *>(ipb2), ctx->pc_y.as<float>(), pzr,
+                                  pza, nblk_vec, ns, nt, ctx->g.nz, ctx->g.nx, ctx->px, ctx->sst,
+                                  active, ctx->st));
+        CKL(launch_reduce_partials(pzr, nblk_vec, ns, zr_out, ctx->st));
+        if (ap_prev) CKL(launch_reduce_partials(pza, nblk_vec, ns, za, ctx->st));
+        return ESI_OK;
+    };
     std::vector<int> h_active(ns, 1), h_bad(ns, 0), iters(ns, 0);
     CK(cudaMemsetAsync(bad, 0, sizeof(int) * ns, ctx->st));
     CK(cudaMemsetAsync(alpha, 0, sizeof(double) * ns, ctx->st));
@@ -1134,6 +1180,19 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
                             ctx->st));
     CKL(launch_reduce_partials(ctx->part.as<double>(), nblk_vec, ns, rr, ctx->st));
     CKL(launch_reduce_partials(rz_part ? rz_part : ctx->part.as<double>(), nblk_vec, ns, rho, ctx->st));
+    CK(cudaMemsetAsync(active, 0xff, sizeof(int) * ns, ctx->st));  // nonzero: all shots
+    if (learned) {
+        e = apply_learned(nullptr, rho_new);
+        if (e != ESI_OK) return e;
+        CK(cudaMemcpyAsync(h_rhon.data(), rho_new, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        for (int s = 0; s < ns; ++s)
+            if (!(h_rhon[s] > 0) || !std::isfinite(h_rhon[s])) learned = false;
+        if (learned)   // else rho keeps the diagonal preconditioner's <r, z>
+            CK(cudaMemcpyAsync(rho, rho_new, sizeof(double) * ns, cudaMemcpyDeviceToDevice, ctx->st));
+        else
+            ctx->pc_fallbacks++;
+    }
     std::vector<double> rr0(ns), rrn(ns);
     CK(cudaMemcpyAsync(rr0.data(), rr, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
@@ -1141,7 +1200,12 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
     for (int s = 0; s < ns; ++s)
         if (!(rr0[s] > 0)) h_active[s] = 0;  // b = 0: x = 0 is exact
     CK(cudaMemcpyAsync(active, h_active.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, ctx->st));
-    double ms_mv = 0, ms_vec = 0;
+    double ms_mv = 0, ms_vec = 0, ms_pc = 0;
+    bool restart = false;
+    CK(ctx->part3.ensure(std::max(ctx->part3.n, sizeof(double) * (ns + (size_t)ns * nblk_vec + ns))));
+    double *zero_alpha = ctx->part3.as<double>() + ns + (size_t)ns * nblk_vec;
+    CK(cudaMemsetAsync(zero_alpha, 0, sizeof(double) * ns, ctx->st));
+    if (learned) za = ctx->part3.as<double>();
     int k;
     bool any_bad = false;
     for (k = 0; k < max_iter; ++k) {
@@ -1156,10 +1220,18 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
         a.cg_r = r;
         a.cg_p = p;
         a.cg_beta = beta;
-        a.cg_first = k == 0;
+        a.cg_first = k == 0 || restart;
+        restart = false;
         a.cg_pc = pc;
         a.ipb2 = ipb2;
         a.eps = eps;
+        if (learned) {
+            a.pc_y = ctx->pc_y.as<float>();
+            a.pc_ng = ng;
+            a.pc_hc = hc;
+            a.pc_wc = wc;
+            a.cg_beta = beta;
+        }
         a.smp = smp_view<T>(ctx->smp_rec);
         a.smp_out = tr;
         T *cur = ctx->u0.as<T>(), *po = ctx->u1.as<T>();
@@ -1188,13 +1260,25 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
         const auto t1 = clk::now();
         cudaEvent_t ev = prof_mark(ctx);
         CKL(launch_cg_update<T>(x, r, p, ap, rows, ctx->g.nx, ctx->px, ns, alpha, active,
-                                ctx->part.as<double>(), rz_part, nblk_vec, ipb2, ctx->sst, nzny,
-                                ctx->st));
+                                ctx->part.as<double>(), learned ? nullptr : rz_part, nblk_vec,
+                                learned ? nullptr : ipb2, ctx->sst, nzny, ctx->st));
         prof_close(ctx, ev, "cg_update", (6.0 + 0.0) * sizeof(T), 1,
                    (long long)ctx->prof_active * ctx->N * nt);
         CKL(launch_reduce_partials(ctx->part.as<double>(), nblk_vec, ns, rr, ctx->st));
-        CKL(launch_reduce_partials(rz_part ? rz_part : ctx->part.as<double>(), nblk_vec, ns, rho_new,
-                                   ctx->st));
+        if (learned) {
+            const auto tp = clk::now();
+            e = apply_learned(ap, rho_new);
+            if (e != ESI_OK) return e;
+            CK(cudaMemcpyAsync(h_rhon.data(), rho_new, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->st));
+            CK(cudaMemcpyAsync(h_za.data(), za, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->st));
+            CK(cudaMemcpyAsync(h_alpha.data(), alpha, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->st));
+            CK(cudaMemcpyAsync(h_rho.data(), rho, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->st));
+            CK(cudaStreamSynchronize(ctx->st));
+            ms_pc += std::chrono::duration<double, std::milli>(clk::now() - tp).count();
+        } else {
+            CKL(launch_reduce_partials(rz_part ? rz_part : ctx->part.as<double>(), nblk_vec, ns,
+                                       rho_new, ctx->st));
+        }
         CK(cudaMemcpyAsync(rrn.data(), rr, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->st));
         CK(cudaMemcpyAsync(h_bad.data(), bad, sizeof(int) * ns, cudaMemcpyDeviceToHost, ctx->st));
         CK(cudaStreamSynchronize(ctx->st));
@@ -1220,7 +1304,29 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
         }
         if (!any) break;
         CK(cudaMemcpyAsync(active, h_active.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, ctx->st));
-        CKL(launch_cg_beta(rho, rho_new, beta, active, ns, ctx->st));
+        if (learned) {
+            bool ok = true;
+            for (int s = 0; s < ns; ++s)
+                if (h_active[s] && (!(h_rhon[s] > 0) || !std::isfinite(h_rhon[s]) || !std::isfinite(h_za[s])))
+                    ok = false;
+            if (ok) {
+                for (int s = 0; s < ns; ++s)
+                    h_beta[s] = h_active[s] ? -h_alpha[s] * h_za[s] / h_rho[s] : 0.0;
+                CK(cudaMemcpyAsync(beta, h_beta.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, ctx->st));
+                CK(cudaMemcpyAsync(rho, rho_new, sizeof(double) * ns, cudaMemcpyDeviceToDevice, ctx->st));
+            } else {
+                // not positive: restart with the diagonal preconditioner (p = z, beta = 0)
+                learned = false;
+                ctx->pc_fallbacks++;
+                restart = true;
+                CKL(launch_cg_update<T>(x, r, r, r, rows, ctx->g.nx, ctx->px, ns, zero_alpha, active,
+                                        ctx->part.as<double>(), rz_part, nblk_vec, ipb2, ctx->sst,
+                                        nzny, ctx->st));
+                CKL(launch_reduce_partials(rz_part, nblk_vec, ns, rho, ctx->st));
+            }
+        } else {
+            CKL(launch_cg_beta(rho, rho_new, beta, active, ns, ctx->st));
+        }
     }
     bool conv = true;
     for (int s = 0; s < ns; ++s)
@@ -1235,7 +1341,7 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
         rep->converged = conv ? 1 : 0;
         rep->ms_matvec = ms_mv;
         rep->ms_vector = ms_vec;
-        rep->ms_precond = 0;
+        rep->ms_precond = ms_pc;
         rep->ms_total = std::chrono::duration<double, std::milli>(clk::now() - t_start).count();
     }
     if (any_bad) return ctx->fail(ESI_ERR_BREAKDOWN, "CG breakdown: p^T A p <= 0 or non-finite");
@@ -1479,9 +1585,70 @@ ESI_API esi_status esi_cg_solve(esi_ctx *ctx, double lambda, double tol, int max
 
 ESI_API esi_status esi_pc_load(esi_ctx *ctx, const void *weights_dev, size_t bytes) {
     if (!ctx) return ESI_ERR_ARG;
-    (void)weights_dev;
-    (void)bytes;
-    return ctx->fail(ESI_ERR_UNSUPPORTED, "learned preconditioner not loaded in this build");
+    if (!weights_dev || bytes != (size_t)pcnet::param_count() * sizeof(float))
+        return ctx->fail(ESI_ERR_ARG, "weights must be esi_pc_param_count() FP32 values");
+    if (ctx->g.ndim != 2 || ctx->g.dtype != ESI_F32)
+        return ctx->fail(ESI_ERR_UNSUPPORTED, "the learned preconditioner serves 2D FP32 contexts");
+    if (!ctx->pc) {
+        const long long nimg = (long long)ctx->ns * ((ctx->nt + 15) / 16);
+        ctx->pc_batch = (int)std::min<long long>(nimg, 512);
+        std::string err;
+        ctx->pc = pcnet_create((ctx->g.nz + 1) / 2, (ctx->g.nx + 1) / 2, ctx->pc_batch, ctx->st, &err);
+        if (!ctx->pc) return ctx->fail(ESI_ERR_OOM, err);
+    }
+    CK(pcnet_set_params(ctx->pc, reinterpret_cast<const float *>(weights_dev), ctx->st));
+    return ESI_OK;
+}
+
+ESI_API long long esi_pc_fallbacks(const esi_ctx *ctx) { return ctx ? ctx->pc_fallbacks : 0; }
+
+ESI_API esi_status esi_normal_apply(esi_ctx *ctx, double lambda, double eps, const void *p_dev,
+                                    void *out_dev) {
+    if (!ctx) return ESI_ERR_ARG;
+    if (!p_dev || !out_dev || !(lambda >= 0)) return ctx->fail(ESI_ERR_ARG, "bad arguments");
+    ctx->err.clear();
+    CK(ctx->traces.ensure(std::max<size_t>((size_t)ctx->total_rec * ctx->nt * ctx->esz, 16)));
+    const double ep = eps > 0 ? eps : ctx->g.dx;
+    esi_status e;
+    if (ctx->g.dtype == ESI_F64) {
+        e = forward_impl<double>(ctx, nullptr, p_dev, ctx->traces.p, nullptr, 0, nullptr);
+        if (e == ESI_OK) e = adjoint_impl<double>(ctx, ctx->traces.p, out_dev, nullptr);
+        if (e == ESI_OK)
+            CKL(launch_add_b2p<double>((double *)out_dev, (const double *)p_dev, ctx->ns, ctx->nt,
+                                       ctx->g.nz, ctx->g.ny, ctx->g.nx, lambda, ep, ctx->g.dx,
+                                       ctx->src_pos.as<double>(), ctx->st));
+    } else {
+        e = forward_impl<float>(ctx, nullptr, p_dev, ctx->traces.p, nullptr, 0, nullptr);
+        if (e == ESI_OK) e = adjoint_impl<float>(ctx, ctx->traces.p, out_dev, nullptr);
+        if (e == ESI_OK)
+            CKL(launch_add_b2p<float>((float *)out_dev, (const float *)p_dev, ctx->ns, ctx->nt,
+                                      ctx->g.nz, ctx->g.ny, ctx->g.nx, float(lambda), float(ep),
+                                      float(ctx->g.dx), ctx->src_pos.as<double>(), ctx->st));
+    }
+    return e;
+}
+
+ESI_API esi_status esi_pc_pack(esi_ctx *ctx, const void *field_dev, double lambda, double eps,
+                               int scale, void *img_dev) {
+    if (!ctx) return ESI_ERR_ARG;
+    if (!field_dev || !img_dev) return ctx->fail(ESI_ERR_ARG, "bad arguments");
+    if (ctx->g.ndim != 2 || ctx->g.dtype != ESI_F32)
+        return ctx->fail(ESI_ERR_UNSUPPORTED, "packing serves 2D FP32 contexts");
+    if (scale && !(lambda > 0)) return ctx->fail(ESI_ERR_ARG, "scaling needs lambda > 0");
+    float *ipb2 = nullptr;
+    if (scale) {
+        CK(ctx->pb2.ensure((size_t)ctx->ns * ctx->sst * 4));
+        CK(ctx->ipb2.ensure((size_t)ctx->ns * ctx->sst * 4));
+        CKL(launch_b2_maps<float>(ctx->pb2.as<float>(), ctx->ipb2.as<float>(), ctx->ns, ctx->g.nz,
+                                  ctx->g.ny, ctx->g.nx, ctx->px, float(lambda),
+                                  float(eps > 0 ? eps : ctx->g.dx), float(ctx->g.dx),
+                                  ctx->src_pos.as<double>(), ctx->st));
+        ipb2 = ctx->ipb2.as<float>();
+    }
+    CKL(pcnet::pack_launch(reinterpret_cast<const float *>(field_dev), ipb2,
+                           reinterpret_cast<__nv_bfloat16 *>(img_dev), ctx->ns, ctx->nt, ctx->g.nz,
+                           ctx->g.nx, ctx->px, ctx->sst, scale, 1, ctx->st));
+    return ESI_OK;
 }
 
 }  // extern "C"

@@ -111,6 +111,9 @@ struct StepArgs {
     T cg_pc;                   // > 0: diagonal preconditioner z = r * ipb2 in p' = z + beta p
     // per-shot maps [ns][sst] (pitched) of pen B^2 and 1 / (pen B^2), B = |x - x_s| + eps
     const T *pb2, *ipb2;
+    // learned preconditioner: z = r * ipb2 + y[(s*ng + n/16)][iz/2][ix/2][n%16] (FP32)
+    const float *pc_y;
+    int pc_ng, pc_hc, pc_wc;
     // point injection at trace time tin
     InjList<T> inj;
     const T *inj_trace;
@@ -186,6 +189,10 @@ cudaError_t launch_b2_maps(T *pb2, T *ipb2, int ns, int nz, int ny, int nx, int 
 // alpha = rr / pAp ; flags breakdown
 cudaError_t launch_cg_alpha(const double *rr, const double *pap, double *alpha, int *bad,
                             const int *active, int ns, cudaStream_t st);
+// out += pen B^2 p over dense caller fields [ns][nt][N]
+template <typename T>
+cudaError_t launch_add_b2p(T *out, const T *p, int ns, int nt, int nz, int ny, int nx, T pen, T eps,
+                           T dx, const double *src_pos, cudaStream_t st);
 // beta = rr_new / rr_old ; rr_old = rr_new
 cudaError_t launch_cg_beta(double *rr_old, const double *rr_new, double *beta,
                            const int *active, int ns, cudaStream_t st);

@@ -232,6 +232,14 @@ __global__ void __launch_bounds__(NT2, ESI_FD2_MINB) fd2_step_kernel(const __gri
                     const Vec<T> ib = ldv(a.ipb2 + (long long)s * a.sst + gi);
 #pragma unroll
                     for (int i = 0; i < VEC; ++i) pn.v[i] *= ib.v[i];
+                    if (a.pc_y) {   // + the learned coarse correction of this time sample
+                        const float *yr = a.pc_y +
+                            (((long long)s * a.pc_ng + a.n / 16) * a.pc_hc + gz / 2) * a.pc_wc * 16 +
+                            a.n % 16;
+#pragma unroll
+                        for (int i = 0; i < VEC; ++i)
+                            if (gx0 + i < a.nx) pn.v[i] += T(yr[(long long)((gx0 + i) / 2) * 16]);
+                    }
                 }
                 if (!a.cg_first) {
                     const T b = T(a.cg_beta[s]);

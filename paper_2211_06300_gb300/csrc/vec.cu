@@ -340,6 +340,25 @@ cudaError_t launch_cg_update(T *x, T *r, const T *p, const T *ap, long long rows
 }
 
 template <typename T>
+__global__ void add_b2p_kernel(T *out, const T *p, int nt, int nz, int ny, int nx, T pen, T eps,
+                               T dx, const double *src_pos) {
+    const int s = blockIdx.y;
+    const long long N = (long long)nz * ny * nx, len = N * nt;
+    const double xs = src_pos[3 * s], ys = src_pos[3 * s + 1], zs = src_pos[3 * s + 2];
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < len;
+         i += (long long)gridDim.x * RT) {
+        const long long c = i % N;
+        const int ix = int(c % nx);
+        const long long row = c / nx;
+        const int iy = int(row % ny), iz = int(row / ny);
+        const double ex = ix * double(dx) - xs, ez = iz * double(dx) - zs;
+        const double ey = ny > 1 ? iy * double(dx) - ys : 0.0;
+        const double B = std::sqrt(ex * ex + ey * ey + ez * ez) + double(eps);
+        out[(long long)s * len + i] += T(double(pen) * B * B) * p[(long long)s * len + i];
+    }
+}
+
+template <typename T>
 __global__ void b2_maps_kernel(T *pb2, T *ipb2, int nz, int ny, int nx, int px, T pen, T eps,
                                T dx, const double *src_pos) {
     const int s = blockIdx.y;
@@ -361,6 +380,15 @@ __global__ void b2_maps_kernel(T *pb2, T *ipb2, int nz, int ny, int nx, int px, 
         pb2[(long long)s * plane + i] = v;
         if (ipb2) ipb2[(long long)s * plane + i] = iv;
     }
+}
+
+template <typename T>
+cudaError_t launch_add_b2p(T *out, const T *p, int ns, int nt, int nz, int ny, int nx, T pen, T eps,
+                           T dx, const double *src_pos, cudaStream_t st) {
+    const long long len = (long long)nz * ny * nx * nt;
+    add_b2p_kernel<T><<<dim3(blocks_for(len, 4096), ns), RT, 0, st>>>(out, p, nt, nz, ny, nx, pen,
+                                                                      eps, dx, src_pos);
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -451,6 +479,8 @@ cudaError_t launch_dft_output(const T *acc, long long sst, int rows, int nx, int
                                              double *, int, const T *, long long, int,           \
                                              cudaStream_t);                                      \
     template cudaError_t launch_b2_maps<T>(T *, T *, int, int, int, int, int, T, T, T,           \
+                                           const double *, cudaStream_t);                        \
+    template cudaError_t launch_add_b2p<T>(T *, const T *, int, int, int, int, int, T, T, T,     \
                                            const double *, cudaStream_t);                        \
     template cudaError_t launch_residual<T>(T *, const T *, long long, double *, int,            \
                                             cudaStream_t);                                       \

@@ -28,7 +28,10 @@ PC = {"none": 0, "diag": 1, "learned": 2}
 EXPORTS = ["esi_create", "esi_destroy", "esi_set_stream", "esi_set_velocity", "esi_forward",
            "esi_adjoint", "esi_gradient", "esi_dft_extract", "esi_cg_solve", "esi_pc_load",
            "esi_status_string", "esi_last_error", "esi_launch_count", "esi_set_profiling",
-           "esi_get_profile", "esi_forward_noalloc"]
+           "esi_get_profile", "esi_forward_noalloc", "esi_normal_apply", "esi_pc_param_count",
+           "esi_pc_fallbacks", "esi_pc_pack", "esi_pc_create", "esi_pc_destroy",
+           "esi_pc_last_error", "esi_pc_set_params", "esi_pc_get_params", "esi_pc_apply",
+           "esi_pc_grad", "esi_pc_train_step"]
 
 
 class EsiGrid(ctypes.Structure):
@@ -98,6 +101,22 @@ def load_library(require_gpu: bool = True) -> ctypes.CDLL:
                                   ctypes.POINTER(ctypes.c_float), vp]
     L.esi_cg_solve.argtypes = [vp, d, d, i, vp, vp, i, d, ctypes.POINTER(EsiCgReport)]
     L.esi_pc_load.argtypes = [vp, vp, ctypes.c_size_t]
+    L.esi_normal_apply.argtypes = [vp, d, d, vp, vp]
+    L.esi_pc_param_count.argtypes = []
+    L.esi_pc_param_count.restype = ctypes.c_size_t
+    L.esi_pc_fallbacks.argtypes = [vp]
+    L.esi_pc_fallbacks.restype = ctypes.c_longlong
+    L.esi_pc_pack.argtypes = [vp, vp, d, d, i, vp]
+    L.esi_pc_create.argtypes = [ctypes.POINTER(vp), i, i, i, vp]
+    L.esi_pc_destroy.argtypes = [vp]
+    L.esi_pc_destroy.restype = None
+    L.esi_pc_last_error.argtypes = [vp]
+    L.esi_pc_last_error.restype = ctypes.c_char_p
+    L.esi_pc_set_params.argtypes = [vp, vp]
+    L.esi_pc_get_params.argtypes = [vp, vp]
+    L.esi_pc_apply.argtypes = [vp, vp, i, vp]
+    L.esi_pc_grad.argtypes = [vp, vp, vp, i, vp, ctypes.POINTER(d)]
+    L.esi_pc_train_step.argtypes = [vp, vp, vp, i, d, ctypes.POINTER(d)]
     L.esi_status_string.argtypes = [i]
     L.esi_status_string.restype = ctypes.c_char_p
     L.esi_last_error.argtypes = [vp]
@@ -109,7 +128,9 @@ def load_library(require_gpu: bool = True) -> ctypes.CDLL:
     L.esi_get_profile.argtypes = [vp, ctypes.POINTER(EsiKernelStat), i]
     L.esi_get_profile.restype = i
     for name in ("esi_create", "esi_set_stream", "esi_set_velocity", "esi_forward",
-                 "esi_forward_noalloc",
+                 "esi_forward_noalloc", "esi_normal_apply", "esi_pc_pack", "esi_pc_create",
+                 "esi_pc_set_params", "esi_pc_get_params", "esi_pc_apply", "esi_pc_grad",
+                 "esi_pc_train_step",
                  "esi_adjoint", "esi_gradient", "esi_dft_extract", "esi_cg_solve",
                  "esi_pc_load"):
         getattr(L, name).restype = ctypes.c_int
@@ -246,6 +267,33 @@ class Context:
         self._check(self.L.esi_forward(self.h, _ptr(wavelet), _ptr(ext), _ptr(out)))
         return out
 
+    def normal_apply(self, p, lam: float, eps: float = 0.0, out=None):
+        """A p = S^T S p + lam B^2 p (esi_normal_apply)."""
+        out = self.empty_field() if out is None else out
+        self._check(self.L.esi_normal_apply(self.h, float(lam), float(eps), _ptr(p), _ptr(out)))
+        return out
+
+    def pc_images_shape(self):
+        ng = (self.nt + 15) // 16
+        return (self.ns * ng, (self.shape[0] + 1) // 2, (self.shape[-1] + 1) // 2, 16)
+
+    def pc_pack(self, field, lam: float = 0.0, scale: bool = False, eps: float = 0.0, out=None):
+        """Pack a [ns][nt][...] field into the network's BF16 images (esi_pc_pack)."""
+        out = self.torch.empty(self.pc_images_shape(), dtype=self.torch.bfloat16,
+                               device=self.device) if out is None else out
+        self._check(self.L.esi_pc_pack(self.h, _ptr(field), float(lam), float(eps),
+                                       1 if scale else 0, _ptr(out)))
+        return out
+
+    def pc_load(self, params):
+        """Load trained preconditioner parameters (FP32 CUDA tensor, esi_pc_param_count())."""
+        params = params.contiguous()
+        self._check(self.L.esi_pc_load(self.h, _ptr(params), params.numel() * 4))
+
+    @property
+    def pc_fallbacks(self) -> int:
+        return int(self.L.esi_pc_fallbacks(self.h))
+
     def forward_noalloc(self, out, wavelet=None, ext=None):
         """esi_forward_noalloc: forward modelling whose wave states live in the library's
         fixed device array (no device allocation); ``out`` must be preallocated."""
@@ -311,5 +359,71 @@ class Context:
         report = {"iters": its.copy(), "rel_res": [rel[s, :its[s]].copy() for s in range(self.ns)],
                   "converged": bool(rep.converged), "iters_max": int(rep.iters_max),
                   "ms_matvec": rep.ms_matvec, "ms_vector": rep.ms_vector,
+                  "ms_precond": rep.ms_precond,
                   "ms_total": rep.ms_total, "status": st}
         return q, report
+
+
+class PCNet:
+    """A stand-alone preconditioner network (esi_pc_*) for h x w images, batches <= max_batch."""
+
+    def __init__(self, h: int, w: int, max_batch: int, stream=None):
+        import torch
+        self.torch = torch
+        self.L = load_library()
+        self.h_img, self.w_img = int(h), int(w)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h_ = ctypes.c_void_p()
+        st = self.L.esi_pc_create(ctypes.byref(h_), self.h_img, self.w_img, int(max_batch),
+                                  ctypes.c_void_p(stream.cuda_stream))
+        if st != ESI_OK:
+            raise EsiError(st, self.L.esi_pc_last_error(None).decode())
+        self.h = h_
+
+    @staticmethod
+    def param_count() -> int:
+        return int(load_library(require_gpu=False).esi_pc_param_count())
+
+    def _check(self, st):
+        if st != ESI_OK:
+            raise EsiError(st, self.L.esi_pc_last_error(self.h).decode())
+
+    def set_params(self, params):
+        params = params.contiguous()
+        self._check(self.L.esi_pc_set_params(self.h, _ptr(params)))
+
+    def get_params(self):
+        out = self.torch.empty(self.param_count(), dtype=self.torch.float32, device="cuda")
+        self._check(self.L.esi_pc_get_params(self.h, _ptr(out)))
+        return out
+
+    def apply(self, x):
+        y = self.torch.empty(x.shape, dtype=self.torch.float32, device=x.device)
+        self._check(self.L.esi_pc_apply(self.h, _ptr(x), int(x.shape[0]), _ptr(y)))
+        return y
+
+    def grad(self, x, e):
+        g = self.torch.empty(self.param_count(), dtype=self.torch.float32, device=x.device)
+        loss = ctypes.c_double(0.0)
+        self._check(self.L.esi_pc_grad(self.h, _ptr(x), _ptr(e), int(x.shape[0]), _ptr(g),
+                                       ctypes.byref(loss)))
+        return g, float(loss.value)
+
+    def train_step(self, x, e, lr: float) -> float:
+        loss = ctypes.c_double(0.0)
+        self._check(self.L.esi_pc_train_step(self.h, _ptr(x), _ptr(e), int(x.shape[0]),
+                                             float(lr), ctypes.byref(loss)))
+        return float(loss.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.esi_pc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

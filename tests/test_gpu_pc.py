@@ -1,0 +1,124 @@
+"""The learned preconditioner's kernels (tensor-core convolutions, pooling, upsampling, the
+backward pass, Adam) against the FP64 oracle, and the preconditioned CG judged by the true
+residual of the ESI normal equation.
+
+The GPU keeps activations in BF16 between layers and feeds BF16 operands to the tensor
+cores; the oracle is run with the same storage rounding (BF16 weights, BF16 hidden
+activations, FP32 biases) so that what is compared is the arithmetic, not the format.
+What remains is FP32 accumulation order and the occasional BF16 rounding tie broken the
+other way, hence the 5e-3 (forward) and 3e-2 (gradient, whose backward operands are also
+rounded to BF16) relative bounds.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import cnn
+from paper_2211_06300_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _bf16(a):
+    return oracle.bf16_to_f32(oracle._bf16_rne(np.asarray(a, dtype=np.float32))).astype(np.float64)
+
+
+def _params(seed, dec1=0.05):
+    rng = np.random.default_rng(seed)
+    p = cnn.init_params(seed)
+    p["dec1.W"] = rng.standard_normal(p["dec1.W"].shape) * dec1
+    for k in p:
+        if k.endswith(".b"):
+            p[k] = rng.standard_normal(p[k].shape) * 0.05
+    return p
+
+
+def _as_stored(p):
+    return {k: (_bf16(v) if k.endswith(".W") else v.astype(np.float32).astype(np.float64))
+            for k, v in p.items()}
+
+
+def _net(H, W, n, p):
+    from paper_2211_06300_gb300 import esi
+    net = esi.PCNet(H, W, n)
+    net.set_params(torch.tensor(cnn.param_vector(p), dtype=torch.float32, device="cuda"))
+    return net
+
+
+def _img(a):
+    return torch.tensor(a, dtype=torch.float32, device="cuda").to(torch.bfloat16).contiguous()
+
+
+@pytest.mark.parametrize("H,W", [(13, 150), (8, 64)])
+def test_network_forward_matches_oracle(H, W):
+    rng = np.random.default_rng(1)
+    n = 3
+    x = _bf16(rng.standard_normal((n, H, W, cnn.G)))
+    p = _params(2)
+    net = _net(H, W, 4, p)
+    y = net.apply(_img(x)).double().cpu().numpy()
+    ref, _, _ = cnn.normalized_forward(x, _as_stored(p), store=_bf16)
+    assert y.shape == ref.shape
+    assert oracle.rel_l2(y, ref) < 5e-3
+
+
+def test_network_gradient_matches_oracle():
+    rng = np.random.default_rng(3)
+    H, W, n = 11, 140, 3
+    x = _bf16(rng.standard_normal((n, H, W, cnn.G)))
+    e = _bf16(rng.standard_normal((n, H, W, cnn.G)))
+    p = _params(4, dec1=0.2)
+    net = _net(H, W, n, p)
+    g, loss = net.grad(_img(x), _img(e))
+    loss_ref, g_ref = cnn.batch_loss_and_grad(x, e, _as_stored(p), store=_bf16)
+    assert abs(loss - loss_ref) <= 1e-3 * max(1.0, abs(loss_ref))
+    gv = g.double().cpu().numpy()
+    rv = cnn.param_vector(g_ref)
+    o = 0
+    for name, ci, co, _ in cnn.LAYERS:
+        k = 9 * ci * co
+        assert oracle.rel_l2(gv[o:o + k], rv[o:o + k]) < 3e-2, name + ".W"
+        assert oracle.rel_l2(gv[o + k:o + k + co], rv[o + k:o + k + co]) < 3e-2, name + ".b"
+        o += k + co
+
+
+def test_training_reduces_the_loss():
+    rng = np.random.default_rng(5)
+    H, W, n = 12, 40, 8
+    x = rng.standard_normal((n, H, W, cnn.G))
+    # targets: a fixed smooth linear map of the inputs, which the network can learn
+    from scipy.ndimage import uniform_filter
+    e = uniform_filter(x, size=(1, 3, 3, 1)) * 2.0 + 0.3 * x
+    p = cnn.init_params(6)
+    net = _net(H, W, n, p)
+    xi, ei = _img(x), _img(e)
+    first = net.train_step(xi, ei, 1e-3)
+    for _ in range(60):
+        last = net.train_step(xi, ei, 1e-3)
+    assert last < 0.7 * first
+
+
+def test_cg_with_learned_preconditioner_reaches_the_true_residual():
+    from paper_2211_06300_gb300 import esi
+    shape, dx, dt, nt, nb = (40, 70), 10.0, 1e-3, 90, 6     # nt not a multiple of 16
+    v = synth.dipping_layers(shape, dx, 5, nlayers=4, vmin=1500, vmax=2600, nanom=2, sigma=40.0)
+    recs = [np.arange(10.0, 690.0, 10.0), np.arange(200.0, 500.0, 15.0)]
+    geom = synth.surface_line(2, [205.0, 455.5], 35.0, recs, 25.0)
+    o = oracle.Oracle(v, dx, dt, nt, nb)
+    shots = [o.shot(geom.src_xyz[s], geom.receivers(s)) for s in range(2)]
+    wav = synth.ricker(nt, dt, 25.0)
+    d = np.concatenate([o.forward(sh, wavelet=wav)["traces"].ravel() for sh in shots])
+    lam = 2e-4
+    ctx = esi.Context(torch.tensor(v, dtype=torch.float32, device="cuda"), dx, dt, nt, nb, geom)
+    ctx.pc_load(torch.tensor(cnn.param_vector(_params(7, dec1=0.005)), dtype=torch.float32,
+                             device="cuda"))
+    q, rep = ctx.cg_solve(torch.tensor(d, dtype=torch.float32, device="cuda"), lam=lam, tol=1e-3,
+                          max_iter=80, precond="learned")
+    assert rep["converged"], rep["iters"]
+    for s, sh in enumerate(shots):
+        o0, o1 = geom.rec_offset[s], geom.rec_offset[s + 1]
+        b = o.ST(sh, d[nt * o0:nt * o1].reshape(nt, -1))
+        qs = q[s].reshape(nt, -1).double().cpu().numpy()
+        r = b - o.normal_matvec(sh, qs, lam)
+        assert np.linalg.norm(r) / np.linalg.norm(b) < 2e-3, s

@@ -127,6 +127,24 @@ def test_cosine_loss_invariances_and_gradient():
     assert fd == pytest.approx(float(g @ dz), rel=1e-6)
 
 
+def test_batch_gradient_taylor_and_param_vector_roundtrip():
+    rng = _rng(9)
+    p = cnn.init_params(3)
+    p["dec1.W"] = rng.standard_normal(p["dec1.W"].shape) * 0.05
+    v = cnn.param_vector(p)
+    q = cnn.params_from_vector(v)
+    assert all(np.array_equal(p[k], q[k]) for k in p)
+    x = rng.standard_normal((3, 9, 11, cnn.G))
+    e = rng.standard_normal((3, 9, 11, cnn.G))
+    L, g = cnn.batch_loss_and_grad(x, e, p)
+    gv = cnn.param_vector(g)
+    dv = rng.standard_normal(v.shape)
+    h = 1e-6
+    Lp, _ = cnn.batch_loss_and_grad(x, e, cnn.params_from_vector(v + h * dv))
+    Lm, _ = cnn.batch_loss_and_grad(x, e, cnn.params_from_vector(v - h * dv))
+    assert (Lp - Lm) / (2 * h) == pytest.approx(float(gv @ dv), rel=1e-6)
+
+
 def test_adam_first_step_closed_form():
     # from zero moments, the bias-corrected step is lr * g / (|g| + eps) ~ lr * sign(g)
     p = {"w": np.array([1.0, -2.0, 0.5])}
@@ -135,3 +153,18 @@ def test_adam_first_step_closed_form():
     v = {"w": np.zeros(3)}
     cnn.adam_step(p, g, m, v, t=1, lr=0.01)
     assert np.allclose(p["w"], np.array([1.0, -2.0, 0.5]) - 0.01 * g["w"] / (np.abs(g["w"]) + 1e-8))
+
+
+def test_normalized_network_is_positively_homogeneous():
+    rng = _rng(10)
+    p = cnn.init_params(12)
+    p["dec1.W"] = rng.standard_normal(p["dec1.W"].shape) * 0.1
+    for k in p:
+        if k.endswith(".b"):
+            p[k] = rng.standard_normal(p[k].shape) * 0.1      # biases do not break it
+    x = rng.standard_normal((2, 7, 9, cnn.G))
+    y1, _, _ = cnn.normalized_forward(x, p)
+    y2, _, _ = cnn.normalized_forward(1e-3 * x, p)
+    assert np.allclose(1e-3 * y1, y2, rtol=1e-10, atol=0)
+    y0, _, _ = cnn.normalized_forward(np.zeros_like(x), p)
+    assert np.all(y0 == 0)
