@@ -9,9 +9,11 @@ nt = 3000, 16-shot FP32 workload (seeded dipping layers + anomalies, 8 Hz Ricker
   the saddle-point gradient of Algorithm 2 (u = A^{-1} q, lambda = beta B^H B q);
   the on-the-fly DTFT of u = A^{-1} q at 2, 4, 6, 8 Hz into FP16.
 The metric is FD cell-updates per second over every forward and adjoint propagation of
-the step (Gcell/s).  Beside it: the CG time to 1e-3 of that solve and of plain Algorithm 1
-(no preconditioner, capped at --plain-iter iterations; the residual it reaches is given
-when the cap comes first).
+the step (Gcell/s).  Beside it, outside the timed steps: the CG time to 1e-3 of the same
+system with each preconditioner -- none (plain Algorithm 1, capped at --plain-iter
+iterations; the residual it reaches is given when the cap comes first), the diagonal
+z = r / (beta B^2), and the learned network (when its weights are present) -- with the
+device time split into the product, the vector updates and the preconditioner.
 
 Multi-GPU: shots are independent systems, so each rank solves its own 16 shots (weak
 scaling) with no collective on the data path; ranks meet only at the timing barriers.
@@ -49,7 +51,10 @@ def parse():
     ap.add_argument("--max-iter", type=int, default=60)
     ap.add_argument("--plain-iter", type=int, default=60)
     ap.add_argument("--beta-factor", type=float, default=10.0)
-    ap.add_argument("--precond", default="diag", choices=["none", "diag", "learned"])
+    ap.add_argument("--precond", default="auto", choices=["auto", "none", "diag", "learned"],
+                    help="auto: the learned preconditioner when its weights are present")
+    ap.add_argument("--pc-weights", default=os.path.join(ROOT, "paper_2211_06300_gb300",
+                                                         "pc_weights.npy"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-nt", type=int, default=1500, help="oracle sample: steps per bench step")
@@ -58,6 +63,32 @@ def parse():
 
 def workload_name(ns, nt):
     return f"esi2d-801x241-nt{nt}-{ns}shots-fp32"
+
+
+# ----------------------------------------------------------------------------- DRAM traffic
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per cell update of a step-kernel variant,
+# from the capture summarised in profiles/ (16 shots of 801 x 241), valid only for the
+# kernel sources it was taken on: the SHA-256 of fd2d.cu and esi_internal.h at capture time.
+MEASURED_TRAFFIC = {}
+TRAFFIC_SOURCES = ("paper_2211_06300_gb300/csrc/fd2d.cu", "paper_2211_06300_gb300/csrc/esi_internal.h")
+
+
+def _sources_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def traffic_per_launch(entry):
+    """DRAM bytes of one launch of the profiled variant, scaled from the capture by the cell
+    updates the launch performs; None when not captured or the kernel changed since."""
+    m = MEASURED_TRAFFIC.get(entry["name"])
+    if m is None or m[1] != _sources_sha():
+        return None
+    return m[0] * entry["cells"] / max(entry["launches"], 1)
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -178,7 +209,7 @@ def main():
         return
     import numpy as np
     import torch
-    from paper_2211_06300_gb300 import esi, synth
+    from paper_2211_06300_gb300 import esi, pc_train, shard, synth
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     dist = None
@@ -193,7 +224,7 @@ def main():
 
     ns, nt = args.ns, args.nt
     wl = synth.workload_esi_2d(nt=nt, ns=ns * world)
-    geom = wl.geom.select(range(rank * ns, (rank + 1) * ns))
+    geom = wl.geom.select(range(*shard.shot_range(ns * world, rank, world)))
     vref = float(wl.v_true.max())
     f32 = torch.float32
     v_true = torch.tensor(wl.v_true, dtype=f32, device=dev)
@@ -205,28 +236,24 @@ def main():
     ctx_t.close()
     del ctx_t
     ctx = esi.Context(v0, wl.dx, wl.dt, nt, wl.nb, geom, vref=vref)
-    # penalty: beta = 1e-2 lambda_max(S^T S) / max B^2 (power iterations on the first shot)
-    g1 = geom.select([0])
-    c1 = esi.Context(v0, wl.dx, wl.dt, nt, wl.nb, g1, vref=vref)
-    torch.manual_seed(0)
-    p = torch.randn((1, nt) + wl.shape, dtype=f32, device=dev)
-    lam = 0.0
-    for _ in range(8):
-        p = p / p.norm()
-        f, _ = c1.adjoint(c1.forward(ext=p))
-        lam = float((f * p).sum())
-        p = f
-    del p, f
+    # penalty: beta = factor * lambda_max(S^T S) / max B^2 (power iterations on the first shot)
+    c1 = esi.Context(v0, wl.dx, wl.dt, nt, wl.nb, geom.select([0]), vref=vref)
+    beta = pc_train.penalty(c1, wl.shape, wl.dx, nt, dev, factor=args.beta_factor)
     c1.close()
     del c1
-    nz, nx = wl.shape
-    far = max(math.hypot(x, z) for x in (0.0, (nx - 1) * wl.dx) for z in (0.0, (nz - 1) * wl.dx))
-    beta = args.beta_factor * lam / (far + wl.dx) ** 2
+    have_pc = os.path.exists(args.pc_weights)
+    if have_pc:
+        ctx.pc_load(torch.tensor(np.load(args.pc_weights), dtype=f32, device=dev))
+    precond = args.precond
+    if precond == "auto":
+        precond = "learned" if have_pc else "diag"
+    if precond == "learned" and not have_pc:
+        raise SystemExit(f"--precond learned needs {args.pc_weights}")
     freqs = [2.0, 4.0, 6.0, 8.0]
     q = torch.empty((ns, nt) + wl.shape, dtype=f32, device=dev)
     N = wl.ncell
 
-    def step(d_obs, precond=args.precond, max_iter=args.max_iter):
+    def step(d_obs, precond=precond, max_iter=args.max_iter):
         ctx.set_velocity(v0)
         _, rep = ctx.cg_solve(d_obs, lam=beta, tol=args.tol, max_iter=max_iter, out=q,
                               precond=precond)
@@ -258,15 +285,8 @@ def main():
     ctx.set_profiling(False)
     launches = ctx.launches - l0
     clk = clocks.stop()
-    t_max = ms
-    cells_all = cells
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t)
-        c = torch.tensor([float(cells)], dtype=torch.float64, device=dev)
-        dist.all_reduce(c)
-        cells_all = float(c)
+    t_max = shard.max_over_ranks(ms, dist, dev)
+    cells_all = shard.sum_over_ranks(cells, dist, dev)
     value = cells_all / (t_max * 1e-3) / 1e9
 
     # end to end through the public API with host buffers: pinned d_obs in, gradient out
@@ -284,14 +304,8 @@ def main():
             g_host = g.cpu()
             ce += c
         barrier()
-        te = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([te], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t)
-            c = torch.tensor([float(ce)], dtype=torch.float64, device=dev)
-            dist.all_reduce(c)
-            ce = float(c)
+        te = shard.max_over_ranks(time.perf_counter() - t0, dist, dev)
+        ce = shard.sum_over_ranks(ce, dist, dev)
         e2e = {"value": ce / te / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(d_host.numel() * d_host.element_size()),
                "d2h_bytes_per_step": int(g_host.numel() * g_host.element_size())}
@@ -307,29 +321,40 @@ def main():
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    # dominant kernel = largest accumulated device time
+    # dominant kernel = largest accumulated device time among single-kernel entries
+    # ("pc_net" groups the preconditioner network's 13 launches per batch)
     roof = None
-    if prof:
-        top = max(prof, key=lambda k: k["ms"])
+    single = [k for k in prof if k["name"] != "pc_net"]
+    if single:
+        top = max(single, key=lambda k: k["ms"])
         per_launch_ms = top["ms"] / max(top["launches"], 1)
         bytes_per_launch = top["cells"] * top["bytes_per_cell"] / max(top["launches"], 1)
         achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": top["name"], "achieved": achieved, "peak": hbm,
                 "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_src,
-                "traffic": None, "per_launch_us": 1e3 * per_launch_ms,
+                "traffic": traffic_per_launch(top), "per_launch_us": 1e3 * per_launch_ms,
                 "bytes_per_launch": bytes_per_launch,
                 "share": top["ms"] / sum(k["ms"] for k in prof)}
     iters = [int(max(r["iters"])) for r in reps]
     cg_ms = [r["ms_total"] for r in reps]
-    # plain Algorithm 1 (no preconditioner) on the same system, for the comparison
-    plain = None
-    if args.plain_iter > 0:
+
+    # CG alone on the same system with each preconditioner (untimed by the steps above)
+    def cg_only(pc, cap):
         torch.cuda.synchronize()
-        _, prep_, _ = step(dobs, precond="none", max_iter=args.plain_iter)
-        reached = bool(prep_["converged"])
-        plain = {"iters_max": int(max(prep_["iters"])), "time_ms": prep_["ms_total"],
-                 "reached_tol": reached,
-                 "rel_res_max_over_shots": float(max(r[-1] for r in prep_["rel_res"] if r.size))}
+        ctx.set_velocity(v0)
+        _, r = ctx.cg_solve(dobs, lam=beta, tol=args.tol, max_iter=cap, out=q, precond=pc)
+        return {"iters_max": int(max(r["iters"])), "time_ms": r["ms_total"],
+                "reached_tol": bool(r["converged"]),
+                "rel_res_max_over_shots": float(max(x[-1] for x in r["rel_res"] if x.size)),
+                "device_ms": {"product": r["ms_matvec"], "vector": r["ms_vector"],
+                              "precond": r["ms_precond"]}}
+    compare = {}
+    if args.plain_iter > 0:
+        compare["none"] = cg_only("none", args.plain_iter)
+    compare["diag"] = cg_only("diag", args.max_iter)
+    if have_pc:
+        compare["learned"] = cg_only("learned", args.max_iter)
+        compare["learned"]["fallbacks"] = ctx.pc_fallbacks
     cb = None
     if not args.no_cpu_baseline and world == 1:
         try:
@@ -342,12 +367,12 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name(ns, nt), "grid": "801x241 (z 241, x 801)",
                    "nt": nt, "shots_per_gpu": ns, "tol": args.tol, "beta": beta,
-                   "freqs_hz": freqs, "precond": args.precond, "beta_factor": args.beta_factor,
+                   "freqs_hz": freqs, "precond": precond, "beta_factor": args.beta_factor,
                    "l2": "inputs larger than L2 (CG vectors 4 x 37 GB per GPU)"},
-        "cg": {"precond": args.precond, "iters_max_per_step": iters, "time_to_tol_ms": cg_ms,
+        "cg": {"precond": precond, "iters_max_per_step": iters, "time_to_tol_ms": cg_ms,
                "converged": [bool(r["converged"]) for r in reps],
                "rel_res_max_over_shots": float(max(r[-1] for r in reps[-1]["rel_res"] if r.size)),
-               "plain": plain},
+               "compare": compare},
         "roofline": roof, "kernels": prof, "cpu_baseline": cb, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk,
     }

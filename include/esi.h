@@ -212,7 +212,10 @@ typedef struct esi_cg_report {
     int max_hist;            /* capacity of rel_res (entries per shot), set by caller */
     int *iters;              /* host [ns] iterations per shot (may be NULL) */
     double *rel_res;         /* host [ns][max_hist] ||r_{k+1}|| / ||r_0|| (may be NULL) */
-    double ms_matvec, ms_vector, ms_precond, ms_total;   /* wall-clock split */
+    /* per-phase device time (CUDA events on the context stream), summed over iterations:
+     * the product S^T S p + lambda B^2 p, the vector updates and reductions, the learned
+     * preconditioner; ms_total is the host wall clock of the whole call (set-up, S^T d) */
+    double ms_matvec, ms_vector, ms_precond, ms_total;
 } esi_cg_report;
 
 /*
@@ -256,9 +259,13 @@ ESI_API esi_status esi_normal_apply(esi_ctx *ctx, double lambda, double eps, con
  * are BF16 [img][h][w][16] (h = ceil(nz/2), w = ceil(nx/2)); U computes in BF16 with FP32
  * accumulation on the tensor cores.  Parameters: esi_pc_param_count() FP32 values, per
  * layer (enc1 16->32, enc2, enc3, bott, dec3, dec2 32->32, dec1 32->16) the weights
- * W[3][3][cin][cout] followed by the biases b[cout].  The network is a learned object:
- * its only judge is the CG residual (the solver falls back to the diagonal preconditioner
- * whenever <z, r> <= 0).
+ * W[3][3][cin][cout] followed by the biases b[cout].  Each image is divided by its RMS
+ * before U and the output multiplied by it (y = rms U(x / rms), so the preconditioner is
+ * positively homogeneous).  The network is a learned object: its only judge is the CG
+ * residual.  In the solver the correction enters per shot as z = s + theta up2(y): theta = 1
+ * while <z, r> >= <s, r> / 2 (s the diagonal preconditioner's output); the first time that
+ * fails the shot drops the network (theta = 0 to the end of the solve) and restarts its
+ * directions from the diagonal preconditioner.
  */
 typedef struct esi_pc esi_pc;
 
@@ -268,7 +275,8 @@ ESI_API size_t esi_pc_param_count(void);
  * esi_cg_solve(..., ESI_PC_LEARNED, ...) then uses flexible (Polak-Ribiere) CG with z above. */
 ESI_API esi_status esi_pc_load(esi_ctx *ctx, const void *weights_dev, size_t bytes);
 
-/* Times the learned preconditioner broke down (<z, r> <= 0) and CG restarted diagonally. */
+/* How many shots dropped the learned correction (and restarted diagonally), summed over the
+ * context's learned solves. */
 ESI_API long long esi_pc_fallbacks(const esi_ctx *ctx);
 
 /* Pack a dense field [ns][nt][N] (scaled by 1 / (lambda B^2) when scale != 0) into the
@@ -283,10 +291,10 @@ ESI_API const char *esi_pc_last_error(const esi_pc *pc);
 /* Parameters in and out (device FP32, layout above); setting them resets the Adam state. */
 ESI_API esi_status esi_pc_set_params(esi_pc *pc, const float *params_dev);
 ESI_API esi_status esi_pc_get_params(esi_pc *pc, float *params_dev);
-/* y = U(x) for n images: x BF16 [n][h][w][16], y FP32 [n][h][w][16]. */
+/* y = rms(x) U(x / rms(x)) for n images: x BF16 [n][h][w][16], y FP32 [n][h][w][16]. */
 ESI_API esi_status esi_pc_apply(esi_pc *pc, const void *in_dev, int n, float *y_dev);
 /* Training objective on n pairs (x = packed scaled residual, e = packed CG error):
- * loss = mean_i (1 - <x_i + y_i, e_i>^2 / (|x_i + y_i|^2 |e_i|^2)), y = U(x).  Writes the
+ * loss = mean_i (1 - <x_i + y_i, e_i>^2 / (|x_i + y_i|^2 |e_i|^2)), y as in esi_pc_apply.  Writes the
  * parameter gradient (device FP32, may be NULL) and the loss (host, may be NULL). */
 ESI_API esi_status esi_pc_grad(esi_pc *pc, const void *in_dev, const void *target_dev, int n,
                                float *grad_dev, double *loss);

@@ -25,7 +25,6 @@ namespace {
 // 8th-order weights at offsets 1 and 3 (Fornberg 1988).  The Nyquist symbol of the
 // second difference is -4 (W1 + W3) / dx^2 per axis, which fixes the leapfrog CFL bound.
 constexpr double CFL_W1 = 8.0 / 5.0, CFL_W3 = 8.0 / 315.0;
-constexpr int ZCH3_HOST = 64;  // z chunk of the 3D kernel (must match fd3d.cu)
 
 struct DBuf {
     void *p = nullptr;
@@ -80,7 +79,12 @@ struct esi_ctx {
     int ntx = 0, nty = 1, ntz = 0, nzc = 1, ntiles = 0;
     DBuf cc, kz, ky, kx, src_pos;
     DBuf dev_err;                  // sticky device error word (int)
-    std::vector<std::pair<const void *, CUtensorMap>> tmaps;  // TMA maps of state buffers
+    struct TMap {
+        const void *base;
+        int kind;
+        CUtensorMap tm;
+    };
+    std::vector<TMap> tmaps;       // TMA maps of state buffers and of c (by address and box)
     DevInj inj_src, inj_rec;
     DevSmp smp_rec, smp_src;
     DBuf u0, u1, a0, a1;           // forward / adjoint state pairs [ns][sst]
@@ -91,6 +95,7 @@ struct esi_ctx {
     DBuf pb2, ipb2;                // per-shot pen B^2 and 1 / (pen B^2) maps [ns][sst]
     PcNet *pc = nullptr;           // learned preconditioner (esi_pc_load)
     DBuf pc_img, pc_y;             // network input images (BF16) and output (FP32)
+    DBuf pc_dev;                   // learned-PCG dot partials, sums and per-shot theta
     int pc_batch = 0;
     DBuf ckpt, ckpt_scale, absbits, stash, gacc, twid, dftacc;
     long long total_rec = 0;
@@ -272,7 +277,7 @@ void tile_of(const esi_ctx *c, int s, int iz, int iy, int ix, int &tile, int &ce
         tile = (s * c->ntz + bz) * c->ntx + bx;
         cell = (iz - bz * TZ2) * TX2 + (ix - bx * TX2);
     } else {
-        const int zc = iz / ZCH3_HOST, by = iy / TY3, bx = ix / TX3;
+        const int zc = iz / ZCH3, by = iy / TY3, bx = ix / TX3;
         tile = ((s * c->nzc + zc) * c->nty + by) * c->ntx + bx;
         cell = iz * (TX3 * TY3) + (iy - by * TY3) * TX3 + (ix - bx * TX3);
     }
@@ -426,28 +431,49 @@ TensorMapEncoder esi::tensor_map_encoder() {
 
 namespace {
 
-// TMA map of a state buffer [ns][nz][px] (2D): dims (nx, nz, ns), box (SW2, SH2, 1).  Cells
-// outside [0, nx) x [0, nz) are zero-filled by the copy engine.
-bool state_map(esi_ctx *ctx, const void *base, CUtensorMap *out) {
+// TMA maps (cells outside the grid are zero-filled by the copy engine):
+//   kind 0, a state buffer with the halo box: 2D [ns][nz][px] as dims (nx, nz, ns), box
+//     (SW2, SH2, 1); 3D [ns][nz][ny][px] as dims (nx, ny, nz, ns), box (SW3, SH3, 1, 1);
+//   kind 1, a 3D state buffer with the tile-interior box (TX3, TY3, 1, 1);
+//   kind 2, the 3D array c [nz][ny][px] as dims (nx, ny, nz), box (TX3, TY3, 1).
+bool state_map(esi_ctx *ctx, const void *base, CUtensorMap *out, int kind = 0) {
     for (auto &m : ctx->tmaps)
-        if (m.first == base) {
-            *out = m.second;
+        if (m.base == base && m.kind == kind) {
+            *out = m.tm;
             return true;
         }
     auto enc = tensor_map_encoder();
     if (!enc) return false;
     CUtensorMap tm;
-    const cuuint64_t dims[3] = {(cuuint64_t)ctx->g.nx, (cuuint64_t)ctx->g.nz, (cuuint64_t)ctx->ns};
-    const cuuint64_t strides[2] = {(cuuint64_t)ctx->px * ctx->esz,
-                                   (cuuint64_t)ctx->sst * ctx->esz};
-    const cuuint32_t box[3] = {(cuuint32_t)SW2, (cuuint32_t)SH2, 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
+    const cuuint64_t row = (cuuint64_t)ctx->px * ctx->esz, shot = (cuuint64_t)ctx->sst * ctx->esz;
+    const cuuint64_t nx = ctx->g.nx, ny = ctx->g.ny, nz = ctx->g.nz, ns = ctx->ns;
+    cuuint64_t dims[4];
+    cuuint64_t str[3];
+    cuuint32_t box[4];
+    cuuint32_t rank;
+    if (ctx->g.ndim == 2) {
+        rank = 3;
+        dims[0] = nx, dims[1] = nz, dims[2] = ns;
+        str[0] = row, str[1] = shot;
+        box[0] = SW2, box[1] = SH2, box[2] = 1;
+    } else if (kind == 2) {
+        rank = 3;
+        dims[0] = nx, dims[1] = ny, dims[2] = nz;
+        str[0] = row, str[1] = row * ny;
+        box[0] = TX3, box[1] = TY3, box[2] = 1;
+    } else {
+        rank = 4;
+        dims[0] = nx, dims[1] = ny, dims[2] = nz, dims[3] = ns;
+        str[0] = row, str[1] = row * ny, str[2] = shot;
+        box[0] = kind == 1 ? TX3 : SW3, box[1] = kind == 1 ? TY3 : SH3, box[2] = 1, box[3] = 1;
+    }
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = enc(&tm, ctx->esz == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                     3, const_cast<void *>(base), dims, strides, box, estr,
+                     rank, const_cast<void *>(base), dims, str, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return false;
-    ctx->tmaps.push_back({base, tm});
+    ctx->tmaps.push_back({base, kind, tm});
     *out = tm;
     return true;
 }
@@ -483,15 +509,16 @@ StepArgs<T> base_args(esi_ctx *ctx) {
 // One step of either kernel.  In 3D the sampling of the input state is a gather launch.
 template <typename T>
 esi_status step(esi_ctx *ctx, unsigned flags, const StepArgs<T> &a) {
+    StepArgs<T> b = a;
+    if (!state_map(ctx, a.cur, &b.tm) ||
+        (ctx->g.ndim == 3 && (!state_map(ctx, a.po, &b.tm_old, 1) || !state_map(ctx, a.cc, &b.tm_cc, 2))))
+        return ctx->fail(ESI_ERR_CUDA, "cuTensorMapEncodeTiled failed for a state buffer");
     if (ctx->g.ndim == 2) {
-        StepArgs<T> b = a;
-        if (!state_map(ctx, a.cur, &b.tm))
-            return ctx->fail(ESI_ERR_CUDA, "cuTensorMapEncodeTiled failed for a state buffer");
         CKL(launch_step2<T>(flags, b, ctx->ns, ctx->st));
     } else {
         if ((flags & F_SMP) && a.tout >= 0)
             CKL(launch_sample_global<T>(a.smp, a.cur, ctx->sst, a.smp_out, a.tout, ctx->st));
-        CKL(launch_step3<T>(flags & ~F_SMP, a, ctx->ns, ctx->st));
+        CKL(launch_step3<T>(flags & ~F_SMP, b, ctx->ns, ctx->st));
     }
     return ESI_OK;
 }
@@ -1135,39 +1162,77 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
     CKL(launch_b2_maps<T>(ctx->pb2.as<T>(), ipb2, ns, ctx->g.nz, ctx->g.ny, ctx->g.nx, ctx->px,
                           T(lambda), eps, T(ctx->g.dx), ctx->src_pos.as<double>(), ctx->st));
     const int nzny = ctx->g.nz * ctx->g.ny;
-    // learned preconditioner: z = r / (lambda B^2) + up2(U(pack(r / (lambda B^2)))), flexible
-    // (Polak-Ribiere) beta = -alpha <z_{k+1}, A p_k> / <z_k, r_k>; falls back to the diagonal
-    // preconditioner (restarting the directions) when <z, r> <= 0 for any shot
+    // learned preconditioner, per shot: z = s + theta up2(U(pack(s))), s = r / (lambda B^2),
+    // with the flexible (Polak-Ribiere) beta = -alpha <z_{k+1}, A p_k> / <z_k, r_k>.  theta = 1
+    // while the network keeps <z, r> >= <s, r> / 2 (> 0); the first time it does not, the
+    // shot drops the network (theta = 0 from then on) and restarts its directions from the
+    // diagonal preconditioner (beta = 0), which it keeps to the end of the solve.
     const int ng = (nt + 15) / 16, hc = (ctx->g.nz + 1) / 2, wc = (ctx->g.nx + 1) / 2;
     const long long nimg = (long long)ns * ng, img_elems = (long long)hc * wc * 16;
-    double *za = nullptr;
+    // pc_dev: the four partial-dot arrays [4][ns][nblk_vec], their per-shot sums [4][ns]
+    // (<s, r>, <y, r>, <s, A p>, <y, A p>) and theta [ns]
+    std::vector<int> h_active(ns, 1), h_bad(ns, 0), iters(ns, 0);
+    double *pc_part = nullptr, *pc_dots = nullptr, *pc_theta = nullptr;
     std::vector<double> h_rho(ns), h_rhon(ns), h_za(ns), h_alpha(ns), h_beta(ns, 0.0);
+    std::vector<double> h_dots(4 * (size_t)ns), h_theta(ns, 1.0);
+    std::vector<char> h_restart(ns, 0);
     if (learned) {
         CK(ctx->pc_img.ensure((size_t)nimg * img_elems * 2));
         CK(ctx->pc_y.ensure((size_t)nimg * img_elems * 4));
-        CK(ctx->part3.ensure(sizeof(double) * (ns + (size_t)ns * nblk_vec)));
-        za = ctx->part3.as<double>();
+        CK(ctx->pc_dev.ensure(sizeof(double) * (4 * (size_t)ns * nblk_vec + 4 * (size_t)ns + ns)));
+        pc_part = ctx->pc_dev.as<double>();
+        pc_dots = pc_part + 4 * (size_t)ns * nblk_vec;
+        pc_theta = pc_dots + 4 * (size_t)ns;
     }
-    auto apply_learned = [&](const T *ap_prev, double *zr_out) -> esi_status {
+    // theta, <z, r> and <z, A p_prev> per active shot from the four sums on the host
+    auto pc_combine = [&](bool with_ap) {
+        for (int s = 0; s < ns; ++s) {
+            if (!h_active[s]) continue;
+            const double sr = h_dots[s], yr = h_dots[ns + s], sa = h_dots[2 * ns + s],
+                         ya = h_dots[3 * ns + s];
+            h_restart[s] = 0;
+            double th = h_theta[s];   // 0 once the shot has dropped the network
+            if (th > 0.0 && (!std::isfinite(yr) || (with_ap && !std::isfinite(ya)) ||
+                             sr + yr < 0.5 * sr)) {
+                th = 0.0;
+                h_restart[s] = 1;
+                ctx->pc_fallbacks++;
+            }
+            h_theta[s] = th;
+            h_rhon[s] = sr + th * yr;
+            h_za[s] = with_ap ? sa + th * ya : 0.0;
+        }
+    };
+    const long long pc_cells = (long long)ns * nt * ctx->N;   // fine space-time elements
+    auto apply_learned = [&](const T *ap_prev) -> esi_status {
         const float *rf = reinterpret_cast<const float *>(r);
+        cudaEvent_t pev = prof_mark(ctx);
         CKL(pcnet::pack_launch(rf, reinterpret_cast<const float *>(ipb2), ctx->pc_img.as<__nv_bfloat16>(),
                                ns, nt, ctx->g.nz, ctx->g.nx, ctx->px, ctx->sst, 1, 0, ctx->st));
+        // reads r, writes the 2 x 2-averaged BF16 image (1/8 of a float per element)
+        prof_close(ctx, pev, "pc_pack", 4.5, 1, pc_cells);
+        pev = prof_mark(ctx);
         for (long long i0 = 0; i0 < nimg; i0 += ctx->pc_batch) {
             const int nb = (int)std::min<long long>(ctx->pc_batch, nimg - i0);
             CK(pcnet_forward(ctx->pc, ctx->pc_img.as<__nv_bfloat16>() + i0 * img_elems, nb,
-                             ctx->pc_y.as<float>() + i0 * img_elems, ctx->st));
+                             ctx->pc_y.as<float>() + i0 * img_elems, ctx->st, true));
             ctx->launches += 13;
         }
-        double *pzr = ctx->part.as<double>(), *pza = za + ns;
+        // the network's own input and output streams (0.5 + 1 byte per element); its
+        // intermediate activations are not counted
+        prof_close(ctx, pev, "pc_net", 1.5, (nimg + ctx->pc_batch - 1) / ctx->pc_batch * 13, pc_cells);
+        pev = prof_mark(ctx);
         CKL(pcnet::pc_dots_launch(rf, reinterpret_cast<const float *>(ap_prev),
-                                  reinterpret_cast<const float *>(ipb2), ctx->pc_y.as<float>(), pzr,
-                                  pza, nblk_vec, ns, nt, ctx->g.nz, ctx->g.nx, ctx->px, ctx->sst,
-                                  active, ctx->st));
-        CKL(launch_reduce_partials(pzr, nblk_vec, ns, zr_out, ctx->st));
-        if (ap_prev) CKL(launch_reduce_partials(pza, nblk_vec, ns, za, ctx->st));
+                                  reinterpret_cast<const float *>(ipb2), ctx->pc_y.as<float>(),
+                                  pc_part, nblk_vec, ns, nt, ctx->g.nz, ctx->g.nx, ctx->px,
+                                  ctx->sst, active, ctx->st));
+        CKL(launch_reduce_partials(pc_part, nblk_vec, 4 * ns, pc_dots, ctx->st));
+        CK(cudaMemcpyAsync(h_dots.data(), pc_dots, sizeof(double) * 4 * ns, cudaMemcpyDeviceToHost,
+                           ctx->st));
+        // reads r, A p and the coarse correction (a quarter of a float per element)
+        prof_close(ctx, pev, "pc_dots", ap_prev ? 9.0 : 5.0, ap_prev ? 3 : 2, pc_cells);
         return ESI_OK;
     };
-    std::vector<int> h_active(ns, 1), h_bad(ns, 0), iters(ns, 0);
     CK(cudaMemsetAsync(bad, 0, sizeof(int) * ns, ctx->st));
     CK(cudaMemsetAsync(alpha, 0, sizeof(double) * ns, ctx->st));
     CK(cudaMemsetAsync(x, 0, (size_t)ns * ctx->N * nt * sizeof(T), ctx->st));
@@ -1181,17 +1246,15 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
     CKL(launch_reduce_partials(ctx->part.as<double>(), nblk_vec, ns, rr, ctx->st));
     CKL(launch_reduce_partials(rz_part ? rz_part : ctx->part.as<double>(), nblk_vec, ns, rho, ctx->st));
     CK(cudaMemsetAsync(active, 0xff, sizeof(int) * ns, ctx->st));  // nonzero: all shots
-    if (learned) {
-        e = apply_learned(nullptr, rho_new);
+    if (learned) {   // z_0, theta_0 and rho_0 = <z_0, r_0>
+        e = apply_learned(nullptr);
         if (e != ESI_OK) return e;
-        CK(cudaMemcpyAsync(h_rhon.data(), rho_new, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->st));
         CK(cudaStreamSynchronize(ctx->st));
-        for (int s = 0; s < ns; ++s)
-            if (!(h_rhon[s] > 0) || !std::isfinite(h_rhon[s])) learned = false;
-        if (learned)   // else rho keeps the diagonal preconditioner's <r, z>
-            CK(cudaMemcpyAsync(rho, rho_new, sizeof(double) * ns, cudaMemcpyDeviceToDevice, ctx->st));
-        else
-            ctx->pc_fallbacks++;
+        pc_combine(false);
+        h_rho = h_rhon;
+        CK(cudaMemcpyAsync(rho, h_rho.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, ctx->st));
+        CK(cudaMemcpyAsync(pc_theta, h_theta.data(), sizeof(double) * ns, cudaMemcpyHostToDevice,
+                           ctx->st));
     }
     std::vector<double> rr0(ns), rrn(ns);
     CK(cudaMemcpyAsync(rr0.data(), rr, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->st));
@@ -1201,15 +1264,20 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
         if (!(rr0[s] > 0)) h_active[s] = 0;  // b = 0: x = 0 is exact
     CK(cudaMemcpyAsync(active, h_active.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, ctx->st));
     double ms_mv = 0, ms_vec = 0, ms_pc = 0;
-    bool restart = false;
-    CK(ctx->part3.ensure(std::max(ctx->part3.n, sizeof(double) * (ns + (size_t)ns * nblk_vec + ns))));
-    double *zero_alpha = ctx->part3.as<double>() + ns + (size_t)ns * nblk_vec;
-    CK(cudaMemsetAsync(zero_alpha, 0, sizeof(double) * ns, ctx->st));
-    if (learned) za = ctx->part3.as<double>();
+    // phase split of each iteration, timed on the device: [ev0, ev1) the product, [ev1, ev3)
+    // the vector work, of which [ev2, ev3) the learned preconditioner
+    struct Events {
+        cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+        ~Events() {
+            for (auto x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } ev;
+    for (auto &x : ev.e) CK(cudaEventCreate(&x));
     int k;
     bool any_bad = false;
     for (k = 0; k < max_iter; ++k) {
-        const auto t0 = clk::now();
+        CK(cudaEventRecord(ev.e[0], ctx->st));
         ctx->prof_active = 0;
         for (int s = 0; s < ns; ++s) ctx->prof_active += h_active[s];
         // forward half of the product, fused with p = z + beta p (p0 = z0)
@@ -1220,13 +1288,13 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
         a.cg_r = r;
         a.cg_p = p;
         a.cg_beta = beta;
-        a.cg_first = k == 0 || restart;
-        restart = false;
+        a.cg_first = k == 0;
         a.cg_pc = pc;
         a.ipb2 = ipb2;
         a.eps = eps;
         if (learned) {
             a.pc_y = ctx->pc_y.as<float>();
+            a.pc_theta = pc_theta;
             a.pc_ng = ng;
             a.pc_hc = hc;
             a.pc_wc = wc;
@@ -1257,35 +1325,38 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
         if (e != ESI_OK) return e;
         CKL(launch_reduce_partials(ctx->part.as<double>(), nblk_step, ns, pap, ctx->st));
         CKL(launch_cg_alpha(rho, pap, alpha, bad, active, ns, ctx->st));
-        const auto t1 = clk::now();
-        cudaEvent_t ev = prof_mark(ctx);
+        CK(cudaEventRecord(ev.e[1], ctx->st));
+        cudaEvent_t pev = prof_mark(ctx);
         CKL(launch_cg_update<T>(x, r, p, ap, rows, ctx->g.nx, ctx->px, ns, alpha, active,
                                 ctx->part.as<double>(), learned ? nullptr : rz_part, nblk_vec,
                                 learned ? nullptr : ipb2, ctx->sst, nzny, ctx->st));
-        prof_close(ctx, ev, "cg_update", (6.0 + 0.0) * sizeof(T), 1,
+        prof_close(ctx, pev, "cg_update", (6.0 + 0.0) * sizeof(T), 1,
                    (long long)ctx->prof_active * ctx->N * nt);
         CKL(launch_reduce_partials(ctx->part.as<double>(), nblk_vec, ns, rr, ctx->st));
         if (learned) {
-            const auto tp = clk::now();
-            e = apply_learned(ap, rho_new);
+            CK(cudaEventRecord(ev.e[2], ctx->st));
+            e = apply_learned(ap);
             if (e != ESI_OK) return e;
-            CK(cudaMemcpyAsync(h_rhon.data(), rho_new, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->st));
-            CK(cudaMemcpyAsync(h_za.data(), za, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->st));
             CK(cudaMemcpyAsync(h_alpha.data(), alpha, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->st));
-            CK(cudaMemcpyAsync(h_rho.data(), rho, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->st));
-            CK(cudaStreamSynchronize(ctx->st));
-            ms_pc += std::chrono::duration<double, std::milli>(clk::now() - tp).count();
+            CK(cudaEventRecord(ev.e[3], ctx->st));
         } else {
             CKL(launch_reduce_partials(rz_part ? rz_part : ctx->part.as<double>(), nblk_vec, ns,
                                        rho_new, ctx->st));
         }
+        if (!learned) CK(cudaEventRecord(ev.e[3], ctx->st));
         CK(cudaMemcpyAsync(rrn.data(), rr, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->st));
         CK(cudaMemcpyAsync(h_bad.data(), bad, sizeof(int) * ns, cudaMemcpyDeviceToHost, ctx->st));
         CK(cudaStreamSynchronize(ctx->st));
         if ((e = check_dev_err(ctx)) != ESI_OK) return e;
-        const auto t2 = clk::now();
-        ms_mv += std::chrono::duration<double, std::milli>(t1 - t0).count();
-        ms_vec += std::chrono::duration<double, std::milli>(t2 - t1).count();
+        {
+            float m01 = 0, m13 = 0, m23 = 0;
+            CK(cudaEventElapsedTime(&m01, ev.e[0], ev.e[1]));
+            CK(cudaEventElapsedTime(&m13, ev.e[1], ev.e[3]));
+            if (learned) CK(cudaEventElapsedTime(&m23, ev.e[2], ev.e[3]));
+            ms_mv += m01;
+            ms_vec += m13 - m23;
+            ms_pc += m23;
+        }
         bool any = false;
         for (int s = 0; s < ns; ++s) {
             if (!h_active[s]) continue;
@@ -1305,25 +1376,15 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
         if (!any) break;
         CK(cudaMemcpyAsync(active, h_active.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, ctx->st));
         if (learned) {
-            bool ok = true;
-            for (int s = 0; s < ns; ++s)
-                if (h_active[s] && (!(h_rhon[s] > 0) || !std::isfinite(h_rhon[s]) || !std::isfinite(h_za[s])))
-                    ok = false;
-            if (ok) {
-                for (int s = 0; s < ns; ++s)
-                    h_beta[s] = h_active[s] ? -h_alpha[s] * h_za[s] / h_rho[s] : 0.0;
-                CK(cudaMemcpyAsync(beta, h_beta.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, ctx->st));
-                CK(cudaMemcpyAsync(rho, rho_new, sizeof(double) * ns, cudaMemcpyDeviceToDevice, ctx->st));
-            } else {
-                // not positive: restart with the diagonal preconditioner (p = z, beta = 0)
-                learned = false;
-                ctx->pc_fallbacks++;
-                restart = true;
-                CKL(launch_cg_update<T>(x, r, r, r, rows, ctx->g.nx, ctx->px, ns, zero_alpha, active,
-                                        ctx->part.as<double>(), rz_part, nblk_vec, ipb2, ctx->sst,
-                                        nzny, ctx->st));
-                CKL(launch_reduce_partials(rz_part, nblk_vec, ns, rho, ctx->st));
+            pc_combine(true);
+            for (int s = 0; s < ns; ++s) {
+                h_beta[s] = h_active[s] && !h_restart[s] ? -h_alpha[s] * h_za[s] / h_rho[s] : 0.0;
+                if (h_active[s]) h_rho[s] = h_rhon[s];
             }
+            CK(cudaMemcpyAsync(beta, h_beta.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, ctx->st));
+            CK(cudaMemcpyAsync(rho, h_rho.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, ctx->st));
+            CK(cudaMemcpyAsync(pc_theta, h_theta.data(), sizeof(double) * ns, cudaMemcpyHostToDevice,
+                               ctx->st));
         } else {
             CKL(launch_cg_beta(rho, rho_new, beta, active, ns, ctx->st));
         }
@@ -1476,7 +1537,7 @@ ESI_API esi_status esi_create(esi_ctx **out, const esi_grid *grid, const esi_geo
     } else {
         ctx->ntx = (g.nx + TX3 - 1) / TX3;
         ctx->nty = (g.ny + TY3 - 1) / TY3;
-        ctx->nzc = (g.nz + ZCH3_HOST - 1) / ZCH3_HOST;
+        ctx->nzc = (g.nz + ZCH3 - 1) / ZCH3;
         ctx->ntz = ctx->nzc;
         ctx->ntiles = ctx->ntx * ctx->nty * ctx->nzc;
     }

@@ -40,6 +40,8 @@ constexpr int PITCH = 32;           // x pitch multiple of the state / internal 
 // 3D kernel tile (xy plane, marching along z)
 constexpr int TX3 = 32, TY3 = 16;
 constexpr int SW3 = TX3 + 2 * HALO, SH3 = TY3 + 2 * HALO;
+constexpr int ZCH3 = 80;            // planes per block (z chunk)
+constexpr int RING3 = 8;            // staged planes (shared-memory ring of TMA boxes)
 
 // ----------------------------------------------------------------------------- feature flags
 enum : unsigned {
@@ -84,7 +86,10 @@ struct SmpList {
 // owned by the caller (extended sources, adjoint outputs) are dense: plane N = nz*ny*nx.
 template <typename T>
 struct StepArgs {
-    CUtensorMap tm;            // 2D kernel: TMA map of the input state, box (SW2, SH2, 1)
+    CUtensorMap tm;            // TMA map of the input state: 2D box (SW2, SH2, 1), 3D box
+                               // (SW3, SH3, 1, 1) (one tile with its halo)
+    CUtensorMap tm_old;        // 3D: the older state, box (TX3, TY3, 1, 1) (tile interior)
+    CUtensorMap tm_cc;         // 3D: c = v^2 dt^2 / dx^2, box (TX3, TY3, 1)
     int *dev_err;              // sticky device error word (bounded waits that gave up)
     int nz, ny, nx, px;        // grid and pitch (elements) of the state arrays
     long long sst;             // pitched plane (= shot stride of state arrays)
@@ -112,7 +117,8 @@ struct StepArgs {
     // per-shot maps [ns][sst] (pitched) of pen B^2 and 1 / (pen B^2), B = |x - x_s| + eps
     const T *pb2, *ipb2;
     // learned preconditioner: z = r * ipb2 + y[(s*ng + n/16)][iz/2][ix/2][n%16] (FP32)
-    const float *pc_y;
+    const float *pc_y;         // learned preconditioner: time-sample planes of its correction
+    const double *pc_theta;    // and its per-shot weight
     int pc_ng, pc_hc, pc_wc;
     // point injection at trace time tin
     InjList<T> inj;

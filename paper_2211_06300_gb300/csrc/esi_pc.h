@@ -38,14 +38,22 @@ constexpr long long param_count() {
     return n;
 }
 
+// activation map [n][H][W][C_] BF16, box (8 channels, 130 columns, 1 row, 1 image)
 cudaError_t make_act_map(CUtensorMap *tm, const void *base, int C_, int W, int H, int n);
+// conv epilogue options
+struct ConvEpi {
+    const float *oscale = nullptr;   // per-image output factor (applied after the activation)
+    const float *irms = nullptr;     // per-image input RMS: the accumulator is divided by it
+    int nchw = 0;                    // output planes [img][c][H][W] instead of channels-last
+};
 template <int CIN, int COUT, bool RELU, typename OUT>
 cudaError_t conv_launch(const void *in, const __nv_bfloat16 *wprep, const float *bias, OUT *out,
                         int nimg, int H, int W, int *dev_err, int nsm, cudaStream_t st,
-                        const float *oscale = nullptr);
-// rms[i] = root-mean-square of image i; xn = x / rms (BF16)
-cudaError_t normalize_launch(const __nv_bfloat16 *x, float *rms, __nv_bfloat16 *xn, int n,
-                             long long per, cudaStream_t st);
+                        const ConvEpi &epi = ConvEpi());
+// rms[i] = root-mean-square of image i (acc: n FP64 scratch sums); xn = x / rms (BF16)
+// unless xn is null
+cudaError_t normalize_launch(const __nv_bfloat16 *x, float *rms, double *acc, __nv_bfloat16 *xn,
+                             int n, long long per, cudaStream_t st);
 cudaError_t img_mul_launch(float *g, const float *s, int n, long long per, cudaStream_t st);
 cudaError_t wprep_launch(const float *W, __nv_bfloat16 *out, int cin, int cout, int flip,
                          cudaStream_t st);
@@ -68,9 +76,11 @@ cudaError_t cos_loss_launch(const __nv_bfloat16 *in, const float *y, const __nv_
                             double *dots, float *gy, long long per, int nimg, cudaStream_t st);
 cudaError_t adam_launch(float *p, const float *g, float *m, float *v, long long n, float lr, int t,
                         cudaStream_t st);
+// per-shot partial sums of <s, r>, <y, r>, <s, ap>, <y, ap> (s = r ipb2, y = the network's
+// time-sample planes upsampled 2 x 2) into part[4][ns][nblk]; ap may be null
 cudaError_t pc_dots_launch(const float *r, const float *ap, const float *ipb2, const float *y,
-                           double *part_zr, double *part_za, int nblk, int ns, int nt, int nz,
-                           int nx, int px, long long sst, const int *active, cudaStream_t st);
+                           double *part, int nblk, int ns, int nt, int nz, int nx, int px,
+                           long long sst, const int *active, cudaStream_t st);
 
 }  // namespace pcnet
 
@@ -81,8 +91,12 @@ void pcnet_destroy(PcNet *p);
 cudaError_t pcnet_set_params(PcNet *p, const float *params_dev, cudaStream_t st);
 cudaError_t pcnet_get_params(const PcNet *p, float *params_dev, cudaStream_t st);
 // y = rms(x) U(x / rms(x)) per image (positively homogeneous in x, as a preconditioner must
-// be): y[n][H1][W1][G] (FP32) for x[n][H1][W1][G] (BF16); n <= max_batch per call
-cudaError_t pcnet_forward(PcNet *p, const __nv_bfloat16 *x, int n, float *y, cudaStream_t st);
+// be): y[n][H1][W1][G] (FP32) for x[n][H1][W1][G] (BF16); n <= max_batch per call.  With
+// nchw the output is y[n][G][H1][W1] (time-sample planes); with keep_xn the normalised input
+// is materialised (BF16) for the weight gradient of the first layer, else the first layer
+// divides its accumulator by rms.
+cudaError_t pcnet_forward(PcNet *p, const __nv_bfloat16 *x, int n, float *y, cudaStream_t st,
+                          bool nchw = false, bool keep_xn = false);
 // loss = mean over images of 1 - cos^2(x + y, e); gradient of it into p's gradient buffer;
 // optional copy of the gradient to grad_out (FP32, parameter layout)
 cudaError_t pcnet_grad(PcNet *p, const __nv_bfloat16 *x, const __nv_bfloat16 *e, int n,

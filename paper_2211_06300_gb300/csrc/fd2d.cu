@@ -232,13 +232,14 @@ __global__ void __launch_bounds__(NT2, ESI_FD2_MINB) fd2_step_kernel(const __gri
                     const Vec<T> ib = ldv(a.ipb2 + (long long)s * a.sst + gi);
 #pragma unroll
                     for (int i = 0; i < VEC; ++i) pn.v[i] *= ib.v[i];
-                    if (a.pc_y) {   // + the learned coarse correction of this time sample
+                    if (a.pc_y) {   // + theta x the learned coarse correction of this time sample
+                        // (planes [s][pc_ng * 16][pc_hc][pc_wc])
                         const float *yr = a.pc_y +
-                            (((long long)s * a.pc_ng + a.n / 16) * a.pc_hc + gz / 2) * a.pc_wc * 16 +
-                            a.n % 16;
+                            (((long long)s * a.pc_ng * 16 + a.n) * a.pc_hc + gz / 2) * a.pc_wc;
+                        const T th = T(a.pc_theta[s]);
 #pragma unroll
                         for (int i = 0; i < VEC; ++i)
-                            if (gx0 + i < a.nx) pn.v[i] += T(yr[(long long)((gx0 + i) / 2) * 16]);
+                            if (gx0 + i < a.nx) pn.v[i] += th * T(yr[(gx0 + i) / 2]);
                     }
                 }
                 if (!a.cg_first) {

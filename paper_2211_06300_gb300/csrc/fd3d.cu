@@ -1,52 +1,228 @@
-// 3D propagation step with register marching along z (the slow axis).
+// 3D propagation step: TMA-staged xy planes, register marching along z (the slow axis).
 //
-// A block owns a 32 x 16 column tile of the xy plane and a chunk of ZCH3 planes.  Each
-// thread keeps the 9 values u(z-4 .. z+4) of its own column in registers; the plane z
-// is staged in shared memory with a 4-cell x/y halo for the in-plane neighbours.  So
-// every cell of the input state is read from global memory once per chunk by its owner
-// (plus the halo, mostly served by L2), the older state and c once, and the new state
-// written once.  Receiver sampling is done by a separate gather launch (trilinear
-// points straddle two planes); point injection walks a per-tile node list sorted by z.
+// A block owns a 32 x 16 column tile of the xy plane and a chunk of ZCH3 planes.  The
+// planes of its column tile, each with a 4-cell x/y halo, arrive by TMA (one 40 x 24 box per
+// plane, zero-filled outside the grid) in a ring of RING3 shared-memory slots, together with
+// the tile interior of the older state and of c.  One producer warp keeps the ring filled
+// (a slot is refilled once every consumer warp has released it on an mbarrier), so the
+// consumer warps never meet at a block-wide barrier while marching.  A consumer thread owns
+// one 16-byte row segment (4 FP32 or 2 FP64 cells) and keeps the 9 values u(z-4 .. z+4) of
+// those cells in registers, refilled from the ring.  So every cell of the input state
+// crosses from HBM once per chunk (plus the z halo of the chunk and the xy halo, mostly
+// served by L2), the older state and c once, and the new state is written once, with no
+// global-load latency on the marching path.  Receiver sampling is a separate gather launch
+// (trilinear points straddle two planes); point injection walks a per-tile node list sorted
+// by z.
 #include "esi_internal.h"
 
 namespace esi {
 
-constexpr int ZCH3 = 64;  // planes per block (z chunk)
-
 namespace {
 
-constexpr double W1 = 8.0 / 5.0, W2 = -1.0 / 5.0, W3 = 8.0 / 315.0, W4 = -1.0 / 560.0;
+// Fornberg (1988) 8th-order central weights of the second derivative, offsets 0..4; in 3D
+// the centre weight appears once per axis.
+constexpr double W0 = -205.0 / 72.0, W1 = 8.0 / 5.0, W2 = -1.0 / 5.0, W3 = 8.0 / 315.0,
+                 W4 = -1.0 / 560.0;
+
+template <typename T>
+struct alignas(16) Vec3 {
+    static constexpr int n = 16 / sizeof(T);
+    T v[n];
+};
+template <typename T>
+__device__ __forceinline__ Vec3<T> ldv3(const T *p) {
+    return *reinterpret_cast<const Vec3<T> *>(p);
+}
+template <typename T>
+__device__ __forceinline__ void stv3(T *p, const Vec3<T> &v) {
+    *reinterpret_cast<Vec3<T> *>(p) = v;
+}
+
+template <typename T>
+__host__ __device__ constexpr int consumers3() {   // one 16-byte row segment of the tile per consumer thread
+    return TX3 * TY3 / Vec3<T>::n;
+}
+template <typename T>
+__host__ __device__ constexpr int block3() {     // + one producer warp
+    return consumers3<T>() + 32;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+// 4D tiled TMA load (x, y, z, shot) of one plane box, completing on an mbarrier
+__device__ __forceinline__ void tma_load_plane(void *dst, const CUtensorMap *tm, int x, int y,
+                                               int z, int s, unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(tm)), "r"(x), "r"(y), "r"(z), "r"(s),
+        "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Poll the mbarrier phase with an iteration limit; false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned phase) {
+    for (long long i = 0; i < TMA_WAIT_LIMIT; ++i) {
+        unsigned done;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;"
+            " selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+template <typename T>
+struct Pair;
+template <>
+struct Pair<float> {
+    using type = float2;
+};
+template <>
+struct Pair<double> {
+    using type = double2;
+};
+
+// one ring slot: the halo box of u_n, then the interior boxes of u_{n-1} and c
+template <typename T>
+struct Slot3 {
+    T u[SH3][SW3];
+    T old[TY3][TX3];
+    T c[TY3][TX3];
+};
+static_assert(sizeof(Slot3<float>) % 128 == 0 && sizeof(Slot3<double>) % 128 == 0,
+              "ring slots must keep the 128-byte alignment of TMA destinations");
+
+// the marching step i holds planes i + 4 (its xy plane) .. i + 9 (the queue refill): six
+// slots, plus at least one being filled
+static_assert(RING3 >= 2 * HALO - 1, "the plane ring needs room for the live planes and one more");
+
+template <typename T>
+constexpr int ring_bytes() {
+    return RING3 * (int)sizeof(Slot3<T>) + 128;   // + slack for the 128-byte alignment
+}
 
 template <typename T, unsigned F>
-__global__ void __launch_bounds__(TX3 *TY3) fd3_step_kernel(const StepArgs<T> a, int nzc) {
-    __shared__ T pl[SH3][SW3];
-    __shared__ double red[TX3 * TY3 / 32];
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX3 + tx;
+__global__ void __launch_bounds__(block3<T>(), sizeof(T) == 4 ? 3 : 1) fd3_step_kernel(const __grid_constant__ StepArgs<T> a,
+                                                                  int nzc) {
+    using T2 = typename Pair<T>::type;
+    constexpr int VEC = Vec3<T>::n;        // cells per consumer thread
+    constexpr int NC = consumers3<T>();
+    constexpr int TPR = TX3 / VEC;         // consumer threads per tile row
+    extern __shared__ unsigned char smraw[];
+    // TMA destinations need 128-byte alignment: align the dynamic base at run time
+    Slot3<T> *ring = reinterpret_cast<Slot3<T> *>(smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u));
+    // full[k]: the planes of slot k have landed; empty[k]: every consumer warp is done with them
+    __shared__ __align__(8) unsigned long long full[RING3], empty[RING3];
+    __shared__ double red[NC / 32];
+    const int tid = threadIdx.x;
     const int s = blockIdx.z / nzc, zc = blockIdx.z - s * nzc;
     if (a.active && !a.active[s]) return;
     const int x0 = blockIdx.x * TX3, y0 = blockIdx.y * TY3;
-    const int gx = x0 + tx, gy = y0 + ty;
-    const bool colok = gx < a.nx && gy < a.ny;
     const int zb = zc * ZCH3, ze = min(a.nz, zb + ZCH3);
-    const long long plane = (long long)a.ny * a.px;
-    const T *cur = a.cur + (long long)s * a.sst;
-    T *po = a.po + (long long)s * a.sst;
-    const long long col = (long long)gy * a.px + gx;
-    const int tile = ((s * nzc + zc) * a.nty + blockIdx.y) * a.ntx + blockIdx.x;
+    const int nsteps = ze - zb;
+    const int J = nsteps + 2 * HALO;   // planes zb - 4 .. ze + 3 pass through the ring
+    constexpr unsigned BOXU = SH3 * SW3 * sizeof(T), BOXI = TY3 * TX3 * sizeof(T);
 
-    T q[9];
+    if (tid == 0) {
+        for (int k = 0; k < RING3; ++k) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[k])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[k])),
+                         "r"(NC / 32)
+                         : "memory");
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // plane j of the sequence is z = zb - 4 + j, in slot j % RING3; its n-th use of the slot
+    // (n = j / RING3) completes phase n of full[slot], its release phase n of empty[slot]
+    auto ready = [&](int j) { return mbar_wait_bounded(&full[j % RING3], (unsigned)(j / RING3) & 1u); };
+
+    if (tid >= NC) {
+        // ---- producer warp: one thread keeps the ring filled ahead of use
+        if (tid != NC) return;
+        bool ok = true;
+        int j = 0;
+        for (; j < J; ++j) {
+            if (j >= RING3 && !mbar_wait_bounded(&empty[j % RING3], (unsigned)(j / RING3 - 1) & 1u)) {
+                ok = false;   // a consumer warp stopped: issue nothing more
+                break;
+            }
+            unsigned long long *b = &full[j % RING3];
+            Slot3<T> &sl = ring[j % RING3];
+            const int z = zb - HALO + j;
+            const bool inner = j >= HALO && j < nsteps + HALO;   // a plane this block updates
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
+                         "r"(inner ? BOXU + 2 * BOXI : BOXU)
+                         : "memory");
+            // x0 - 4 and x0 are multiples of 4 elements (16 bytes); planes outside [0, nz) read zeros
+            tma_load_plane(&sl.u[0][0], &a.tm, x0 - HALO, y0 - HALO, z, s, b);
+            if (inner) {
+                tma_load_plane(&sl.old[0][0], &a.tm_old, x0, y0, z, s, b);
+                asm volatile(
+                    "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                    " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(&sl.c[0][0])),
+                    "l"(reinterpret_cast<unsigned long long>(&a.tm_cc)), "r"(x0), "r"(y0), "r"(z),
+                    "r"(smem_u32(b))
+                    : "memory");
+            }
+        }
+        if (!ok) {
+            atomicExch(a.dev_err, DEV_ERR_TMA_TIMEOUT);
+            // let the copies in flight land before the block's shared memory is released
+            for (int k = max(0, j - RING3); k < j; ++k) ready(k);
+        }
+        return;
+    }
+
+    // ---- consumer warps: one 16-byte row segment per thread, marching up the chunk
+    const int lane = tid & 31;
+    const int qx = tid % TPR, ry = tid / TPR;
+    const int lx = qx * VEC, gx0 = x0 + lx, gy = y0 + ry;
+    const bool rowok = gy < a.ny && gx0 < a.nx;   // px >= x0 + TX3: the segment is in the pitch
+    const long long plane = (long long)a.ny * a.px;
+    T *po = a.po + (long long)s * a.sst;
+    const long long col = (long long)gy * a.px + gx0;
+    const int tile = ((s * nzc + zc) * a.nty + blockIdx.y) * a.ntx + blockIdx.x;
+    auto release = [&](int j) {   // this warp is done with plane j
+        __syncwarp();
+        if (lane == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[j % RING3]))
+                         : "memory");
+    };
+    bool late = false;
+    T q[9][VEC];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        const int z = zb - HALO + k;
-        q[k] = (colok && z >= 0 && z < a.nz) ? cur[z * plane + col] : T(0);
+        late |= !ready(k);
+        const Vec3<T> c = ldv3(&ring[k % RING3].u[ry + HALO][lx + HALO]);
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) q[k][i] = c.v[i];
+        // planes zb - 4 .. zb - 1 serve only their centres: free their slots at once (the
+        // ring holds fewer than the 9 planes of the queue)
+        if (k < HALO) release(k);
     }
-    const T kxy = colok ? a.kx[gx] + a.ky[gy] : T(0);
+    T kxy[VEC];
+    bool xy_sponge = false;
+#pragma unroll
+    for (int i = 0; i < VEC; ++i) {
+        kxy[i] = (rowok && gx0 + i < a.nx) ? a.kx[gx0 + i] + a.ky[gy] : T(0);
+        xy_sponge |= kxy[i] != T(0);
+    }
     T xs = T(0), ys = T(0), zs = T(0);
     if constexpr ((F & (F_AP | F_SAD | F_CGP)) != 0) {
         xs = T(a.src_pos[3 * s + 0]);
         ys = T(a.src_pos[3 * s + 1]);
         zs = T(a.src_pos[3 * s + 2]);
     }
+    (void)xs;
+    (void)ys;
+    (void)zs;
     int ip = 0, ie = 0;
     if constexpr ((F & F_PT) != 0) {
         ip = a.inj.tile_ptr[tile];
@@ -55,114 +231,219 @@ __global__ void __launch_bounds__(TX3 *TY3) fd3_step_kernel(const StepArgs<T> a,
     T psum = T(0);
     const long long fbase = (long long)s * a.fst;    // caller dense fields
     const long long fb = (long long)s * a.fstp;      // internal pitched fields
-    const long long dcol = (long long)gy * a.nx + gx;
+    const long long dcol = (long long)gy * a.nx + gx0;
+    constexpr double WK[5] = {0.0, W1, W2, W3, W4};
 
-    for (int z = zb; z < ze; ++z) {
-        pl[ty + HALO][tx + HALO] = q[HALO];
-        for (int i = tid; i < SH3 * SW3; i += TX3 * TY3) {
-            const int ly = i / SW3, lx = i - ly * SW3;
-            if (ly >= HALO && ly < TY3 + HALO && lx >= HALO && lx < TX3 + HALO) continue;
-            const int hy = y0 - HALO + ly, hx = x0 - HALO + lx;
-            T v = T(0);
-            if (hy >= 0 && hy < a.ny && hx >= 0 && hx < a.nx)
-                v = cur[z * plane + (long long)hy * a.px + hx];
-            pl[ly][lx] = v;
-        }
-        __syncthreads();
-        if (colok) {
-            const int sy = ty + HALO, sx = tx + HALO;
-            const T u = q[HALO];
-            T L = T(W1) * ((pl[sy][sx - 1] - u) + (pl[sy][sx + 1] - u) + (pl[sy - 1][sx] - u) +
-                           (pl[sy + 1][sx] - u) + (q[3] - u) + (q[5] - u));
-            L += T(W2) * ((pl[sy][sx - 2] - u) + (pl[sy][sx + 2] - u) + (pl[sy - 2][sx] - u) +
-                          (pl[sy + 2][sx] - u) + (q[2] - u) + (q[6] - u));
-            L += T(W3) * ((pl[sy][sx - 3] - u) + (pl[sy][sx + 3] - u) + (pl[sy - 3][sx] - u) +
-                          (pl[sy + 3][sx] - u) + (q[1] - u) + (q[7] - u));
-            L += T(W4) * ((pl[sy][sx - 4] - u) + (pl[sy][sx + 4] - u) + (pl[sy - 4][sx] - u) +
-                          (pl[sy + 4][sx] - u) + (q[0] - u) + (q[8] - u));
-            const long long gi = z * plane + col;
-            const long long di = (long long)z * a.ny * a.nx + dcol;
-            T src = T(0);
-            if constexpr ((F & F_EXT) != 0) src += a.ext[fbase + (long long)a.n * a.N + di];
+    for (int i = 0; i < nsteps && !__any_sync(0xffffffffu, late); ++i) {
+        const int z = zb + i;
+        const long long gi = z * plane + col;
+        // the remaining per-cell global inputs first: their latency overlaps the wait
+        T ext[VEC];
+        Vec3<T> r_in, p_in, ipb, app;
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) ext[k] = r_in.v[k] = p_in.v[k] = ipb.v[k] = app.v[k] = T(0);
+        if (rowok) {
+            if constexpr ((F & F_EXT) != 0) {
+                const T *e = a.ext + fbase + (long long)a.n * a.N + (long long)z * a.ny * a.nx + dcol;
+#pragma unroll
+                for (int k = 0; k < VEC; ++k)
+                    if (gx0 + k < a.nx) ext[k] = e[k];
+            }
             if constexpr ((F & F_CGP) != 0) {
                 const long long vi = fb + (long long)a.n * a.sst + gi;
-                T pn = a.cg_r[vi];
-                if (a.cg_pc > T(0)) pn *= a.ipb2[(long long)s * a.sst + gi];   // z = r / (pen B^2)
-                if (!a.cg_first) pn += T(a.cg_beta[s]) * a.cg_p[vi];
-                a.cg_p[vi] = pn;
-                src += pn;
+                r_in = ldv3(a.cg_r + vi);
+                if (a.cg_pc > T(0)) ipb = ldv3(a.ipb2 + (long long)s * a.sst + gi);
+                if (!a.cg_first) p_in = ldv3(a.cg_p + vi);
             }
-            T S = L + a.dx2 * src;
+            if constexpr ((F & F_AP) != 0) app = ldv3(a.ap_p + fb + (long long)a.nout * a.sst + gi);
+        }
+        late |= !ready(i + HALO);
+        const Slot3<T> &sl = ring[(i + HALO) % RING3];
+        if (rowok) {
+            const int sy = ry + HALO;
+            // x neighbours: the shared row segment [lx, lx + VEC + 8)
+            T w[VEC + 2 * HALO];
+#pragma unroll
+            for (int c = 0; c < (VEC + 2 * HALO) / VEC; ++c) {
+                const Vec3<T> t = ldv3(&sl.u[sy][lx + c * VEC]);
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) w[c * VEC + k] = t.v[k];
+            }
+            // Laplacian sum: 3 w0 u + sum_k w_k (6 neighbours at distance k)
+            T L[VEC];
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) L[k] = T(3.0 * W0) * q[HALO][k];
+#pragma unroll
+            for (int d = 1; d <= HALO; ++d) {
+                const Vec3<T> up = ldv3(&sl.u[sy - d][lx + HALO]);
+                const Vec3<T> dn = ldv3(&sl.u[sy + d][lx + HALO]);
+#pragma unroll
+                for (int k = 0; k < VEC; ++k)
+                    L[k] += T(WK[d]) * (((w[k + HALO - d] + w[k + HALO + d]) + (up.v[k] + dn.v[k])) +
+                                        (q[HALO - d][k] + q[HALO + d][k]));
+            }
+            const Vec3<T> old = ldv3(&sl.old[ry][lx]);
+            const Vec3<T> cz = ldv3(&sl.c[ry][lx]);
+            T src[VEC], S[VEC];
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) src[k] = T(0);
+            if constexpr ((F & F_EXT) != 0) {
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) src[k] += ext[k];
+            }
+            if constexpr ((F & F_CGP) != 0) {
+                const long long vi = fb + (long long)a.n * a.sst + gi;
+                Vec3<T> pn = r_in;
+                if (a.cg_pc > T(0)) {   // z = r / (pen B^2)
+#pragma unroll
+                    for (int k = 0; k < VEC; ++k) pn.v[k] *= ipb.v[k];
+                }
+                if (!a.cg_first) {
+                    const T b = T(a.cg_beta[s]);
+#pragma unroll
+                    for (int k = 0; k < VEC; ++k) pn.v[k] += b * p_in.v[k];
+                }
+                stv3(a.cg_p + vi, pn);
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) src[k] += pn.v[k];
+            }
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) S[k] = L[k] + a.dx2 * src[k];
             if constexpr ((F & F_PT) != 0) {
                 // entries sorted by z: consume those of this plane
                 while (ip < ie) {
                     const int cell = a.inj.cell[ip];
-                    const int cz = cell / (TX3 * TY3);
-                    if (cz != z) break;
-                    const int rem = cell - cz * (TX3 * TY3);
-                    if (rem == ty * TX3 + tx) {
+                    const int cz3 = cell / (TX3 * TY3);
+                    if (cz3 != z) break;
+                    const int rem = cell - cz3 * (TX3 * TY3);
+                    const int cy = rem / TX3, cx = rem - cy * TX3;
+                    if (cy == ry && cx / VEC == qx) {
                         T sum = T(0);
                         for (int c = a.inj.cptr[ip]; c < a.inj.cptr[ip + 1]; ++c)
                             sum += a.inj.w[c] *
                                    a.inj_trace[a.inj.off0[c] + (long long)a.tin * a.inj.tstride[c]];
-                        S += sum;
+#pragma unroll
+                        for (int k = 0; k < VEC; ++k)
+                            if (k == cx - lx) S[k] += sum;
                     }
                     ++ip;
                 }
             }
-            const T kap = a.kz[z] + kxy;
-            const T al = T(1) / (T(1) + kap);
-            const T ga = (T(1) - kap) * al;
-            const T old = po[gi];
-            const T nw = u + ga * (u - old) + al * a.cc[gi] * S;
-            po[gi] = nw;
+            Vec3<T> nw;
+            const T kzz = a.kz[z];
+            if (xy_sponge || kzz != T(0)) {
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) {
+                    const T kap = kzz + kxy[k];
+                    const T al = T(1) / (T(1) + kap);
+                    const T ga = (T(1) - kap) * al;
+                    const T u = q[HALO][k];
+                    nw.v[k] = u + ga * (u - old.v[k]) + al * cz.v[k] * S[k];
+                }
+            } else {   // interior: alpha = gamma = 1
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) {
+                    const T u = q[HALO][k];
+                    nw.v[k] = u + (u - old.v[k]) + cz.v[k] * S[k];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < VEC; ++k)
+                if (gx0 + k >= a.nx) nw.v[k] = T(0);   // pad columns stay zero
+            stv3(po + gi, nw);
             if constexpr ((F & F_SAD) != 0) {
-                const T ex = T(gx) * a.dx - xs, ey = T(gy) * a.dx - ys, ez = T(z) * a.dx - zs;
-                const T B = sqrt(ex * ex + ey * ey + ez * ez) + a.eps;
-                a.grad[(long long)s * a.sst + gi] += B * B * src * S;
+                Vec3<T> gv = ldv3(a.grad + (long long)s * a.sst + gi);
+                const T ey = T(gy) * a.dx - ys, ez = T(z) * a.dx - zs;
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) {
+                    const T ex = T(gx0 + k) * a.dx - xs;
+                    const T B = sqrt(ex * ex + ey * ey + ez * ez) + a.eps;
+                    if (gx0 + k < a.nx) gv.v[k] += B * B * src[k] * S[k];
+                }
+                stv3(a.grad + (long long)s * a.sst + gi, gv);
             }
             if constexpr ((F & F_AP) != 0) {   // A p = S^T S p + pen B^2 p
                 const long long vi = fb + (long long)a.nout * a.sst + gi;
-                const T pv = a.ap_p[vi];
-                const T apv = nw + a.pb2[(long long)s * a.sst + gi] * pv;
-                a.ap[vi] = apv;
-                psum += pv * apv;
+                const Vec3<T> pb = ldv3(a.pb2 + (long long)s * a.sst + gi);
+                Vec3<T> apv;
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) {
+                    apv.v[k] = gx0 + k < a.nx ? nw.v[k] + pb.v[k] * app.v[k] : T(0);
+                    psum += app.v[k] * apv.v[k];
+                }
+                stv3(a.ap + vi, apv);
             }
-            if constexpr ((F & F_STW) != 0)
-                a.stash_w[((long long)a.slot_w * a.ns + s) * a.sst + gi] = S;
-            if constexpr ((F & F_GRD) != 0)
-                a.grad[(long long)s * a.sst + gi] +=
-                    nw * a.stash_r[((long long)a.slot_r * a.ns + s) * a.sst + gi];
-            if constexpr ((F & F_OUT) != 0)
-                a.fout[(long long)s * a.ofst + (long long)a.nout * a.oplane +
-                       ((long long)z * a.ny + gy) * a.opx + gx] = nw;
+            if constexpr ((F & F_STW) != 0) {
+                Vec3<T> sv;
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) sv.v[k] = gx0 + k < a.nx ? S[k] : T(0);
+                stv3(a.stash_w + ((long long)a.slot_w * a.ns + s) * a.sst + gi, sv);
+            }
+            if constexpr ((F & F_GRD) != 0) {
+                T *gp = a.grad + (long long)s * a.sst + gi;
+                Vec3<T> gv = ldv3(gp);
+                const Vec3<T> sr = ldv3(a.stash_r + ((long long)a.slot_r * a.ns + s) * a.sst + gi);
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) gv.v[k] += nw.v[k] * sr.v[k];
+                stv3(gp, gv);
+            }
+            if constexpr ((F & F_OUT) != 0) {
+                T *o = a.fout + (long long)s * a.ofst + (long long)a.nout * a.oplane +
+                       ((long long)z * a.ny + gy) * a.opx + gx0;
+                if (a.opx == a.px) {   // internal pitched target: the pads get their zeros
+                    stv3(o, nw);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < VEC; ++k)
+                        if (gx0 + k < a.nx) o[k] = nw.v[k];
+                }
+            }
             if constexpr ((F & F_DFT) != 0) {
                 for (int m = 0; m < a.nf; ++m) {
                     const T c = a.twid[(a.n * a.nf + m) * 2 + 0];
                     const T sn = a.twid[(a.n * a.nf + m) * 2 + 1];
-                    T *acc = a.dft + (((long long)s * a.nf + m) * a.sst + gi) * 2;
-                    acc[0] += nw * c;
-                    acc[1] += nw * sn;
+                    T2 *acc = reinterpret_cast<T2 *>(a.dft) + ((long long)s * a.nf + m) * a.sst + gi;
+                    // VEC complex accumulators = 32 bytes = two 16-byte vectors
+                    T2 v[VEC];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+                        reinterpret_cast<Vec3<T> *>(v)[h] = reinterpret_cast<const Vec3<T> *>(acc)[h];
+#pragma unroll
+                    for (int k = 0; k < VEC; ++k) {
+                        v[k].x += nw.v[k] * c;
+                        v[k].y += nw.v[k] * sn;
+                    }
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+                        reinterpret_cast<Vec3<T> *>(acc)[h] = reinterpret_cast<const Vec3<T> *>(v)[h];
                 }
             }
         } else if constexpr ((F & F_PT) != 0) {
             while (ip < ie && a.inj.cell[ip] / (TX3 * TY3) == z) ++ip;
         }
-        __syncthreads();
+        if (i + 1 < nsteps) {
+            // the queue moves one plane down; plane z + 5 comes from the ring
+            late |= !ready(i + 2 * HALO + 1);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) q[k] = q[k + 1];
-        const int zn = z + HALO + 1;
-        q[8] = (colok && zn < a.nz) ? cur[zn * plane + col] : T(0);
+            for (int k = 0; k < 8; ++k)
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) q[k][e] = q[k + 1][e];
+            const Vec3<T> c = ldv3(&ring[(i + 2 * HALO + 1) % RING3].u[ry + HALO][lx + HALO]);
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) q[8][e] = c.v[e];
+        }
+        release(i + HALO);   // plane z: its neighbours and centre were last read in this step
     }
+    if (late) atomicExch(a.dev_err, DEV_ERR_TMA_TIMEOUT);
     if constexpr ((F & F_AP) != 0) {
         T v = psum;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((tid & 31) == 0) red[tid >> 5] = double(v);
-        __syncthreads();
+        if (lane == 0) red[tid >> 5] = double(v);
+        asm volatile("bar.sync 1, %0;" ::"n"(NC) : "memory");   // consumer warps only
         if (tid == 0) {
             double t = 0.0;
-            for (int w = 0; w < TX3 * TY3 / 32; ++w) t += red[w];
+            for (int w = 0; w < NC / 32; ++w) t += red[w];
             const long long nblk = (long long)a.ntx * a.nty * nzc;
             a.dot_part[s * nblk + ((long long)zc * a.nty + blockIdx.y) * a.ntx + blockIdx.x] += t;
         }
@@ -172,8 +453,16 @@ __global__ void __launch_bounds__(TX3 *TY3) fd3_step_kernel(const StepArgs<T> a,
 template <typename T, unsigned F>
 cudaError_t go(const StepArgs<T> &a, int ns, cudaStream_t st) {
     const int nzc = (a.nz + ZCH3 - 1) / ZCH3;
-    dim3 grid(a.ntx, a.nty, ns * nzc), block(TX3, TY3);
-    fd3_step_kernel<T, F><<<grid, block, 0, st>>>(a, nzc);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(fd3_step_kernel<T, F>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             ring_bytes<T>());
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid(a.ntx, a.nty, ns * nzc);
+    fd3_step_kernel<T, F><<<grid, block3<T>(), ring_bytes<T>(), st>>>(a, nzc);
     return cudaGetLastError();
 }
 

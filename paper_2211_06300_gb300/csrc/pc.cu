@@ -19,6 +19,8 @@
 // 32 channels (below the tcgen05 minimum of 64 rows), runs on warp-level mma.sync.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "esi_internal.h"
 #include "esi_pc.h"
 
@@ -126,34 +128,52 @@ __device__ __forceinline__ void store_row<float>(float *dst, const float *v, int
 
 // y[img][h][w][co] = act(b[co] + sum_taps sum_ci x[img][h+dy-1][w+dx-1][ci] W[tap][ci][co])
 // wprep: [9][CIN/8][COUT][8] BF16 (the canonical K-major B operand per tap).
+//
+// A CTA owns a strip (one image, 128 columns, all H rows) at a time and marches down it: input
+// rows arrive by TMA in a ring of RROWS slots (each row once per strip), so output row y
+// takes its three taps' rows from slots y - 1, y, y + 1.  One thread waits for the rows,
+// issues the 9 x CIN/16 MMAs of row y into one of two TMEM accumulators and commits; the
+// four warps meanwhile drain row y - 1 from the other accumulator (bias, ReLU, scale,
+// store).  When row y - 1's MMAs are complete its oldest input slot is refilled, RROWS - 3
+// rows ahead of use.  Every wait is bounded; on a timeout the CTA records the error, lets
+// its copies and MMAs in flight finish and leaves.
+constexpr int RROWS = 6;
+
+template <int CIN, int COUT>
+struct ConvGeom {
+    static constexpr int NCH = CIN / 8;
+    static constexpr int RB = (PW * 16 + 127) / 128 * 128;   // one 8-channel row chunk (2176 B)
+    static constexpr int SLOT = NCH * RB;                      // one staged input row
+    static constexpr int RING = RROWS * SLOT;
+    static constexpr int WTAP = CIN * COUT * 2;                // one tap's weights
+    static constexpr int SMEM = (RING + 1023) / 1024 * 1024 + 9 * WTAP + 1024;
+    static constexpr int TCOLS = 2 * COUT <= 32 ? 32 : (2 * COUT <= 64 ? 64 : 128);
+};
+
 template <int CIN, int COUT, bool RELU, typename OUT>
 __global__ void __launch_bounds__(NTH) conv3x3_tc_kernel(const __grid_constant__ CUtensorMap in_map,
                                                          const __nv_bfloat16 *__restrict__ wprep,
                                                          const float *__restrict__ bias,
                                                          OUT *__restrict__ out, int nimg, int H,
-                                                         int W, int *dev_err,
-                                                         const float *__restrict__ oscale) {
-    constexpr int NCH = CIN / 8;
-    constexpr int BOX = 3 * PW * 16;                         // bytes of one TMA box (8 channels)
-    constexpr int CHUNK = (BOX + 127) / 128 * 128;           // 128-byte aligned box destinations
-    constexpr int PATCH = NCH * CHUNK;
-    constexpr int PATCH_AL = (PATCH + 1023) / 1024 * 1024;
-    constexpr int WTAP = CIN * COUT * 2;                     // bytes of one tap's weights
+                                                         int W, int *dev_err, ConvEpi epi) {
+    using Gm = ConvGeom<CIN, COUT>;
+    constexpr int NCH = Gm::NCH, RB = Gm::RB, SLOT = Gm::SLOT;
     constexpr unsigned IDESC = idesc_bf16(TM, COUT);
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // align the dynamic shared memory base at run time (TMA destinations need 128 bytes)
     unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    unsigned char *patch = smem;
-    unsigned char *wsm = smem + PATCH_AL;
-    __shared__ __align__(8) unsigned long long bar_load, bar_mma;
+    unsigned char *ring = smem;
+    unsigned char *wsm = smem + (Gm::RING + 1023) / 1024 * 1024;
+    __shared__ __align__(8) unsigned long long bar_full[RROWS], bar_mma[2];
     __shared__ unsigned tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    for (int i = tid; i < 9 * WTAP / 16; i += NTH)
+    for (int i = tid; i < 9 * Gm::WTAP / 16; i += NTH)
         reinterpret_cast<uint4 *>(wsm)[i] = reinterpret_cast<const uint4 *>(wprep)[i];
     if (tid == 0) {
-        mbar_init(&bar_load);
-        mbar_init(&bar_mma);
+        for (int k = 0; k < RROWS; ++k) mbar_init(&bar_full[k]);
+        mbar_init(&bar_mma[0]);
+        mbar_init(&bar_mma[1]);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // the weights were written through the generic proxy; the tensor core reads them
@@ -161,8 +181,9 @@ __global__ void __launch_bounds__(NTH) conv3x3_tc_kernel(const __grid_constant__
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(
-                         smem_u32(&tmem_base))
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "n"(Gm::TCOLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -171,85 +192,138 @@ __global__ void __launch_bounds__(NTH) conv3x3_tc_kernel(const __grid_constant__
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = tmem_base;
     const int tiles_x = (W + TM - 1) / TM;
-    const long long ntiles = (long long)nimg * H * tiles_x;
-    unsigned phase = 0;
-    int failed = 0;   // 1: load wait gave up, 2: MMA wait gave up
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int tx = int(t % tiles_x);
-        const long long rr = t / tiles_x;
-        const int y = int(rr % H), img = int(rr / H);
+    const long long nstrips = (long long)nimg * tiles_x;
+    const int nin = H + 2;            // input rows -1 .. H of a strip
+    unsigned seq_in = 0;              // input rows staged by this CTA before the current strip
+    unsigned seq_out = 0;             // output rows computed before the current strip
+    int issued = 0;                   // input rows of the current strip issued so far
+    int mma_open = -1;                // output row whose MMAs may still be in flight
+    bool late = false;
+    // input row j of the strip: slot (seq_in + j) % RROWS, completed phase parity
+    auto slot_of = [&](int j) { return (seq_in + (unsigned)j) % RROWS; };
+    auto par_in = [&](int j) { return ((seq_in + (unsigned)j) / RROWS) & 1u; };
+    for (long long st = blockIdx.x; st < nstrips; st += gridDim.x) {
+        const int tx = int(st % tiles_x), img = int(st / tiles_x);
         const int x0 = tx * TM;
-        if (tid == 0) {
+        auto issue = [&](int j) {   // thread 0: stage input row j - 1
+            const unsigned k = slot_of(j);
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
-                             smem_u32(&bar_load)),
-                         "r"((unsigned)(NCH * BOX))
+                             smem_u32(&bar_full[k])),
+                         "r"((unsigned)(NCH * PW * 16))
                          : "memory");
 #pragma unroll
             for (int c = 0; c < NCH; ++c)
-                tma_load_4d(patch + c * CHUNK, &in_map, 8 * c, x0 - 1, y - 1, img, &bar_load);
+                tma_load_4d(ring + k * SLOT + c * RB, &in_map, 8 * c, x0 - 1, j - 1, img,
+                            &bar_full[k]);
+        };
+        issued = min(nin, RROWS);
+        if (tid == 0)
+            for (int j = 0; j < issued; ++j) issue(j);
+        const float sc = epi.oscale ? epi.oscale[img] : 1.0f;   // per-image output factor
+        float isc = 1.0f;                                        // per-image input factor
+        if (epi.irms) {
+            const float r = epi.irms[img];
+            isc = r > 0.0f ? 1.0f / r : 0.0f;
         }
-        if (__syncthreads_or(!mbar_wait(&bar_load, phase))) {
-            failed = 1;
-            break;
-        }
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const unsigned pa = smem_u32(patch), wb = smem_u32(wsm);
+        auto epilogue = [&](int y, unsigned o) {
+            float v[COUT];
+            tmem_ld<COUT>(tmem + ((unsigned)(warp * 32) << 16) + (o & 1u) * COUT, v);
+            const int px = x0 + warp * 32 + lane;
+            if (px < W) {
 #pragma unroll
-            for (int tap = 0; tap < 9; ++tap) {
-                const int dy = tap / 3, dx = tap % 3;
+                for (int c = 0; c < COUT; ++c) {
+                    float a = v[c] * isc + (bias ? bias[c] : 0.0f);
+                    v[c] = sc * (RELU ? fmaxf(a, 0.0f) : a);
+                }
+                if (epi.nchw) {   // planes [img][c][H][W]: coalesced along px per channel
+                    OUT *o0 = out + ((long long)img * COUT * H + y) * W + px;
 #pragma unroll
-                for (int ks = 0; ks < CIN / 16; ++ks) {
-                    const unsigned long long da =
-                        sdesc(pa + ks * 2 * CHUNK + (dy * PW + dx) * 16, CHUNK, 128);
-                    const unsigned long long db =
-                        sdesc(wb + tap * WTAP + ks * 2 * COUT * 16, COUT * 16, 128);
-                    const unsigned acc = (tap | ks) ? 1u : 0u;
-                    asm volatile(
-                        "{ .reg .pred p; setp.ne.u32 p, %4, 0;"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(tmem),
-                        "l"(da), "l"(db), "r"(IDESC), "r"(acc)
-                        : "memory");
+                    for (int c = 0; c < COUT; ++c) o0[(long long)c * H * W] = OUT(v[c]);
+                } else {
+                    store_row<OUT>(out + (((long long)img * H + y) * W + px) * COUT, v, COUT);
                 }
             }
-            asm volatile(
-                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    smem_u32(&bar_mma))
-                : "memory");
-        }
-        if (__syncthreads_or(!mbar_wait(&bar_mma, phase))) {
-            failed = 2;
-            break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        float v[COUT];
-        tmem_ld<COUT>(tmem + ((unsigned)(warp * 32) << 16), v);
-        const int px = x0 + warp * 32 + lane;
-        if (px < W) {
-            const float sc = oscale ? oscale[img] : 1.0f;   // per-image output scale
+        };
+        for (int y = 0; y < H; ++y) {
+            const unsigned o = seq_out + (unsigned)y;
+            if (tid == 0) {
+                bool ok = true;
 #pragma unroll
-            for (int c = 0; c < COUT; ++c) {
-                float a = v[c] + (bias ? bias[c] : 0.0f);
-                v[c] = sc * (RELU ? fmaxf(a, 0.0f) : a);
+                for (int d = 0; d < 3; ++d) ok &= mbar_wait(&bar_full[slot_of(y + d)], par_in(y + d));
+                late |= !ok;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned wb = smem_u32(wsm), acc_addr = tmem + (o & 1u) * COUT;
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int dy = tap / 3, dx = tap % 3;
+                    const unsigned pa = smem_u32(ring + slot_of(y + dy) * SLOT);
+#pragma unroll
+                    for (int ks = 0; ks < CIN / 16; ++ks) {
+                        const unsigned long long da = sdesc(pa + ks * 2 * RB + dx * 16, RB, 128);
+                        const unsigned long long db =
+                            sdesc(wb + tap * Gm::WTAP + ks * 2 * COUT * 16, COUT * 16, 128);
+                        const unsigned acc = (tap | ks) ? 1u : 0u;
+                        asm volatile(
+                            "{ .reg .pred p; setp.ne.u32 p, %4, 0;"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(
+                                acc_addr),
+                            "l"(da), "l"(db), "r"(IDESC), "r"(acc)
+                            : "memory");
+                    }
+                }
+                asm volatile(
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        smem_u32(&bar_mma[o & 1u]))
+                    : "memory");
             }
-            store_row<OUT>(out + (((long long)img * H + y) * W + px) * COUT, v, COUT);
+            mma_open = y;
+            if (y >= 1) {
+                // row y - 1: its MMAs are complete once its commit arrives
+                late |= !mbar_wait(&bar_mma[(o - 1) & 1u], ((o - 1) >> 1) & 1u);
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                epilogue(y - 1, o - 1);
+                // input row y - 2 (sequence j = y - 1) had its last reader in row y - 1
+                if (tid == 0)
+                    while (issued < nin && issued <= y - 1 + RROWS) issue(issued++);
+                else
+                    issued = min(nin, max(issued, y + RROWS));
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            if (__syncthreads_or(late)) goto timeout;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        }
+        {
+            const unsigned o = seq_out + (unsigned)(H - 1);
+            late |= !mbar_wait(&bar_mma[o & 1u], (o >> 1) & 1u);
+            mma_open = -1;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            epilogue(H - 1, o);
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        phase ^= 1u;
+        if (__syncthreads_or(late)) goto timeout;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        seq_in += (unsigned)nin;
+        seq_out += (unsigned)H;
     }
-    if (failed) {
-        // let the copy or the MMAs in flight finish before the TMEM and shared memory go
-        if (tid == 0) {
-            atomicExch(dev_err, DEV_ERR_TMA_TIMEOUT);
-            mbar_wait(failed == 1 ? &bar_load : &bar_mma, phase);
+    goto done;
+timeout:
+    // let the copies and the MMAs in flight finish before the TMEM and shared memory go
+    if (tid == 0) {
+        atomicExch(dev_err, DEV_ERR_TMA_TIMEOUT);
+        for (int j = max(0, issued - RROWS); j < issued; ++j) mbar_wait(&bar_full[slot_of(j)], par_in(j));
+        if (mma_open >= 0) {
+            const unsigned o = seq_out + (unsigned)mma_open;
+            mbar_wait(&bar_mma[o & 1u], (o >> 1) & 1u);
         }
-        __syncthreads();
     }
+    __syncthreads();
+done:
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "n"(Gm::TCOLS)
+                     : "memory");
 }
 
 // ----------------------------------------------------------------------------- weights
@@ -270,38 +344,61 @@ __global__ void wprep_kernel(const float *W, __nv_bfloat16 *out, int cin, int co
 }
 
 // ----------------------------------------------------------------------------- data movement
-// residual -> network input: img[(s*ng + g)][hc][wc][c] = 1/4 sum_{2x2} r[s][16g+c] * ipb2[s]
+// residual -> network input: img[(s*ng + g)][hc][wc][c] = 1/4 sum_{2x2} r[s][16g+c] * ipb2[s].
+// A block takes whole output rows (s, g, zc); its threads run along the row.
 __global__ void pack_kernel(const float *r, const float *ipb2, __nv_bfloat16 *img, int ns, int nt,
                             int ng, int nz, int nx, int px, long long sst, int hc, int wc,
                             int scale_by_map, int dense) {
-    const long long total = (long long)ns * ng * hc * wc;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int x = int(i % wc);
-        const long long r1 = i / wc;
-        const int z = int(r1 % hc);
-        const long long ig = r1 / hc;
-        const int g = int(ig % ng), s = int(ig / ng);
-        float v[G];
+    const int nrow = ns * ng * hc;
+    const long long plane = dense ? (long long)nz * nx : sst;
+    const int rstride = dense ? nx : px;
+    for (int rw = blockIdx.x; rw < nrow; rw += gridDim.x) {
+        const int zc = rw % hc, ig = rw / hc;
+        const int g = ig % ng, s = ig / ng;
+        const float *rs = r + (long long)s * nt * plane;
+        __nv_bfloat16 *orow = img + ((long long)ig * hc + zc) * wc * G;
+        for (int xc = threadIdx.x; xc < wc; xc += blockDim.x) {
+            float v[G];
 #pragma unroll
-        for (int c = 0; c < G; ++c) v[c] = 0.0f;
-        for (int a = 0; a < 2; ++a)
-            for (int b = 0; b < 2; ++b) {
-                const int iz = 2 * z + a, ix = 2 * x + b;
-                if (iz >= nz || ix >= nx) continue;
-                const long long cell = dense ? (long long)iz * nx + ix : (long long)iz * px + ix;
-                const long long plane = dense ? (long long)nz * nx : sst;
-                const float m = scale_by_map ? ipb2[(long long)s * sst + (long long)iz * px + ix] : 1.0f;
+            for (int c = 0; c < G; ++c) v[c] = 0.0f;
 #pragma unroll
-                for (int c = 0; c < G; ++c) {
-                    const int t = G * g + c;
-                    if (t < nt) v[c] += r[((long long)s * nt + t) * plane + cell] * m;
+            for (int a = 0; a < 2; ++a) {
+                const int iz = 2 * zc + a;
+                if (iz >= nz) continue;
+                if (!dense) {
+                    // pitched rows: the two cells are one aligned float2; the second lies in
+                    // the pad past nx (never read into the sum) when nx is odd
+                    const long long cell = (long long)iz * px + 2 * xc;
+                    const bool two = 2 * xc + 1 < nx;
+                    float2 m = make_float2(1.0f, 1.0f);
+                    if (scale_by_map) m = *reinterpret_cast<const float2 *>(ipb2 + (long long)s * sst + cell);
+#pragma unroll
+                    for (int c = 0; c < G; ++c) {
+                        const int t = G * g + c;
+                        if (t < nt) {
+                            const float2 rv = *reinterpret_cast<const float2 *>(rs + (long long)t * plane + cell);
+                            v[c] += rv.x * m.x + (two ? rv.y * m.y : 0.0f);
+                        }
+                    }
+                    continue;
+                }
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const int ix = 2 * xc + b;
+                    if (ix >= nx) continue;
+                    const long long cell = (long long)iz * rstride + ix;
+                    const float m = scale_by_map ? ipb2[(long long)s * sst + (long long)iz * px + ix] : 1.0f;
+#pragma unroll
+                    for (int c = 0; c < G; ++c) {
+                        const int t = G * g + c;
+                        if (t < nt) v[c] += rs[(long long)t * plane + cell] * m;
+                    }
                 }
             }
-        float o[G];
 #pragma unroll
-        for (int c = 0; c < G; ++c) o[c] = 0.25f * v[c];
-        store_row<__nv_bfloat16>(img + i * G, o, G);
+            for (int c = 0; c < G; ++c) v[c] *= 0.25f;
+            store_row<__nv_bfloat16>(orow + (long long)xc * G, v, G);
+        }
     }
 }
 
@@ -364,24 +461,38 @@ __global__ void upadd_kernel(const __nv_bfloat16 *coarse, const __nv_bfloat16 *s
 }
 
 // per-image root-mean-square of BF16 images [n][per]; rms[img] (FP32)
-__global__ void img_rms_kernel(const __nv_bfloat16 *x, float *rms, long long per) {
-    const int img = blockIdx.x;
-    double s = 0.0;
-    for (long long i = threadIdx.x; i < per; i += blockDim.x) {
-        const double v = __bfloat162float(x[(long long)img * per + i]);
-        s += v * v;
+// per-image sum of squares: blocks (chunk, image), 8 BF16 values per load, FP32 within a
+// thread, FP64 across threads and blocks
+__global__ void img_sumsq_kernel(const __nv_bfloat16 *x, double *acc, long long per) {
+    const int img = blockIdx.y;
+    const long long n8 = per / 8;   // per is a multiple of G = 16
+    const uint4 *v = reinterpret_cast<const uint4 *>(x + (long long)img * per);
+    float s = 0.0f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n8;
+         i += (long long)gridDim.x * blockDim.x) {
+        const uint4 q = v[i];
+        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&q);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 f = __bfloat1622float2(h[k]);
+            s += f.x * f.x + f.y * f.y;
+        }
     }
     __shared__ double red[256];
-    red[threadIdx.x] = s;
+    red[threadIdx.x] = double(s);
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
         if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) rms[img] = float(sqrt(red[0] / double(per)));
+    if (threadIdx.x == 0) atomicAdd(acc + img, red[0]);
 }
 
-// xn = x / rms[img] (0 where rms = 0), BF16 out
+__global__ void img_rms_kernel(const double *acc, float *rms, int n, long long per) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) rms[i] = float(sqrt(acc[i] / double(per)));
+}
+
 __global__ void img_scale_kernel(const __nv_bfloat16 *x, const float *rms, __nv_bfloat16 *xn,
                                  long long per, long long total) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -622,50 +733,69 @@ __global__ void adam_kernel(float *p, const float *g, float *m, float *v, long l
     }
 }
 
-// z = r * ipb2 + up2(y)[time sample]: the preconditioned residual, evaluated on the fly
-__device__ __forceinline__ float z_of(const float *r, const float *ipb2, const float *y,
-                                      int s, int t, int iz, int ix, int nt, int ng, int px,
-                                      long long sst, int hc, int wc) {
-    const long long cell = (long long)iz * px + ix;
-    float z = r[((long long)s * nt + t) * sst + cell] * ipb2[(long long)s * sst + cell];
-    const long long yi = ((((long long)s * ng + t / G) * hc + iz / 2) * wc + ix / 2) * G + (t % G);
-    return z + y[yi];
-}
 
-// per-shot <z, r> and <z, a> (a = A p of the previous iteration) for the flexible CG
+// per-shot <s, r>, <y, r>, <s, a>, <y, a> for the flexible CG (a = A p of the previous
+// iteration, s = r ipb2, y = up2 of the network's coarse correction), into
+// part[q][shot][block], q in that order.  A block takes whole rows (t, iz) of one shot, its
+// threads 4 cells (16 bytes) of the row each; a thread's running totals are compensated FP32
+// sums, the block's FP64.
 __global__ void pc_dots_kernel(const float *r, const float *ap, const float *ipb2,
-                               const float *y, double *part_zr, double *part_za, int nt,
-                               int ng, int nz, int nx, int px, long long sst, int hc, int wc,
-                               const int *active) {
-    const int s = blockIdx.y;
+                               const float *y, double *part, int nt, int ng, int nz, int nx,
+                               int px, long long sst, int hc, int wc, const int *active) {
+    const int s = blockIdx.y, ns = gridDim.y;
     if (active && !active[s]) return;
-    const long long rows = (long long)nt * nz;
-    double zr = 0.0, za = 0.0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < rows * nx;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long row = i / nx;
-        const int ix = int(i - row * nx);
-        const int t = int(row / nz), iz = int(row % nz);
-        const float z = z_of(r, ipb2, y, s, t, iz, ix, nt, ng, px, sst, hc, wc);
-        const long long k = ((long long)s * nt + t) * sst + (long long)iz * px + ix;
-        zr += double(z) * double(r[k]);
-        if (ap) za += double(z) * double(ap[k]);
+    const int rows = nt * nz, nq = (nx + 3) / 4;
+    // compensated (Kahan) FP32 sums per thread: FP64 arithmetic is scarce on this part
+    float sum[4] = {0.0f, 0.0f, 0.0f, 0.0f}, comp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    auto kadd = [&](int q, float v) {
+        const float yv = v - comp[q];
+        const float t = sum[q] + yv;
+        comp[q] = (t - sum[q]) - yv;
+        sum[q] = t;
+    };
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int t = row / nz, iz = row - t * nz;
+        const long long off = ((long long)s * nt + t) * sst + (long long)iz * px;
+        const float *rr = r + off;
+        const float *aa = ap ? ap + off : nullptr;
+        const float *ib = ipb2 + (long long)s * sst + (long long)iz * px;
+        // y: time-sample planes [s][ng * G][hc][wc]
+        const float *yr = y + (((long long)s * ng * G + t) * hc + iz / 2) * wc;
+        for (int c = threadIdx.x; c < nq; c += blockDim.x) {
+            const int x = 4 * c;
+            const float4 r4 = *reinterpret_cast<const float4 *>(rr + x);
+            const float4 b4 = *reinterpret_cast<const float4 *>(ib + x);
+            const float4 a4 = aa ? *reinterpret_cast<const float4 *>(aa + x) : make_float4(0, 0, 0, 0);
+            const float y0 = yr[2 * c], y1 = x + 2 < nx ? yr[2 * c + 1] : 0.0f;
+            const float rv[4] = {r4.x, r4.y, r4.z, r4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
+            const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+            float f[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (x + k >= nx) break;
+                const float sv = rv[k] * bv[k], yv = k < 2 ? y0 : y1;
+                f[0] += sv * rv[k];
+                f[1] += yv * rv[k];
+                f[2] += sv * av[k];
+                f[3] += yv * av[k];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) kadd(q, f[q]);
+        }
     }
-    __shared__ double red[2][256];
-    red[0][threadIdx.x] = zr;
-    red[1][threadIdx.x] = za;
+    __shared__ double red[4][256];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) red[q][threadIdx.x] = double(sum[q]) - double(comp[q]);
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
         if (threadIdx.x < o) {
-            red[0][threadIdx.x] += red[0][threadIdx.x + o];
-            red[1][threadIdx.x] += red[1][threadIdx.x + o];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + o];
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        part_zr[(long long)s * gridDim.x + blockIdx.x] = red[0][0];
-        part_za[(long long)s * gridDim.x + blockIdx.x] = red[1][0];
-    }
+    if (threadIdx.x < 4)
+        part[((long long)threadIdx.x * ns + s) * gridDim.x + blockIdx.x] = red[threadIdx.x][0];
 }
 
 inline int grid_for(long long n, int cap = 4096) {
@@ -682,7 +812,7 @@ cudaError_t make_act_map(CUtensorMap *tm, const void *base, int C_, int W, int H
     const cuuint64_t dims[4] = {(cuuint64_t)C_, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)n};
     const cuuint64_t strides[3] = {(cuuint64_t)C_ * 2, (cuuint64_t)W * C_ * 2,
                                    (cuuint64_t)H * W * C_ * 2};
-    const cuuint32_t box[4] = {8, (cuuint32_t)PW, 3, 1};
+    const cuuint32_t box[4] = {8, (cuuint32_t)PW, 1, 1};
     const cuuint32_t es[4] = {1, 1, 1, 1};
     CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), dims, strides,
                      box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -693,30 +823,43 @@ cudaError_t make_act_map(CUtensorMap *tm, const void *base, int C_, int W, int H
 template <int CIN, int COUT, bool RELU, typename OUT>
 cudaError_t conv_launch(const void *in, const __nv_bfloat16 *wprep, const float *bias, OUT *out,
                         int nimg, int H, int W, int *dev_err, int nsm, cudaStream_t st,
-                        const float *oscale) {
+                        const ConvEpi &epi) {
+    using Gm = ConvGeom<CIN, COUT>;
     CUtensorMap tm;
     cudaError_t e = make_act_map(&tm, in, CIN, W, H, nimg);
     if (e != cudaSuccess) return e;
-    constexpr int CHUNK = (3 * PW * 16 + 127) / 128 * 128;
-    constexpr int PATCH = (CIN / 8) * CHUNK;
-    constexpr int SMEM = (PATCH + 1023) / 1024 * 1024 + 9 * CIN * COUT * 2 + 1024;  // + alignment slack
     auto kern = conv3x3_tc_kernel<CIN, COUT, RELU, OUT>;
-    static bool attr = false;
-    if (!attr) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    static int per_sm = 0;
+    if (!per_sm) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Gm::SMEM);
         if (e != cudaSuccess) return e;
-        attr = true;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        // resident CTAs per SM from the shared memory, register and TMEM budgets (a CTA
+        // beyond them only waits for its turn: strips are independent)
+        int dev = 0, smem_sm = 0, rsv = 0, regs_sm = 0;
+        cudaFuncAttributes fa;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess ||
+            (e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess)
+            return e;
+        const int by_smem = smem_sm / (Gm::SMEM + (int)fa.sharedSizeBytes + rsv);
+        const int by_regs = regs_sm / (NTH * std::max(fa.numRegs, 1));
+        per_sm = std::max(1, std::min({by_smem, by_regs, 512 / Gm::TCOLS}));
     }
-    const long long tiles = (long long)nimg * H * ((W + TM - 1) / TM);
-    const int grid = (int)std::min<long long>(tiles, (long long)nsm * 4);
-    kern<<<grid, NTH, SMEM, st>>>(tm, wprep, bias, out, nimg, H, W, dev_err, oscale);
+    const long long strips = (long long)nimg * ((W + TM - 1) / TM);
+    const int grid = (int)std::min<long long>(strips, (long long)nsm * per_sm);
+    kern<<<grid, NTH, Gm::SMEM, st>>>(tm, wprep, bias, out, nimg, H, W, dev_err, epi);
     return cudaGetLastError();
 }
 
 #define CONV_INST(CI, CO, R, O)                                                                 \
     template cudaError_t conv_launch<CI, CO, R, O>(const void *, const __nv_bfloat16 *,        \
                                                    const float *, O *, int, int, int, int *,   \
-                                                   int, cudaStream_t, const float *);
+                                                   int, cudaStream_t, const ConvEpi &);
 CONV_INST(16, 32, true, __nv_bfloat16)
 CONV_INST(32, 32, true, __nv_bfloat16)
 CONV_INST(32, 16, false, float)
@@ -724,11 +867,15 @@ CONV_INST(16, 32, false, float)
 CONV_INST(32, 32, false, float)
 #undef CONV_INST
 
-cudaError_t normalize_launch(const __nv_bfloat16 *x, float *rms, __nv_bfloat16 *xn, int n,
-                             long long per, cudaStream_t st) {
-    img_rms_kernel<<<n, 256, 0, st>>>(x, rms, per);
-    cudaError_t e = cudaGetLastError();
+cudaError_t normalize_launch(const __nv_bfloat16 *x, float *rms, double *acc, __nv_bfloat16 *xn,
+                             int n, long long per, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double) * n, st);
     if (e != cudaSuccess) return e;
+    const int chunks = (int)std::max<long long>(1, std::min<long long>(32, per / 8 / 256 / 4));
+    img_sumsq_kernel<<<dim3(chunks, n), 256, 0, st>>>(x, acc, per);
+    img_rms_kernel<<<(n + 255) / 256, 256, 0, st>>>(acc, rms, n, per);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || !xn) return e;
     img_scale_kernel<<<grid_for((long long)n * per), 256, 0, st>>>(x, rms, xn, per, (long long)n * per);
     return cudaGetLastError();
 }
@@ -748,8 +895,9 @@ cudaError_t pack_launch(const float *r, const float *ipb2, __nv_bfloat16 *img, i
                         int nz, int nx, int px, long long sst, int scale_by_map, int dense,
                         cudaStream_t st) {
     const int ng = (nt + G - 1) / G, hc = (nz + 1) / 2, wc = (nx + 1) / 2;
-    pack_kernel<<<grid_for((long long)ns * ng * hc * wc), 256, 0, st>>>(
-        r, ipb2, img, ns, nt, ng, nz, nx, px, sst, hc, wc, scale_by_map, dense);
+    const int nrow = ns * ng * hc;
+    pack_kernel<<<std::min(nrow, 4096), 256, 0, st>>>(r, ipb2, img, ns, nt, ng, nz, nx, px, sst,
+                                                         hc, wc, scale_by_map, dense);
     return cudaGetLastError();
 }
 
@@ -823,12 +971,11 @@ cudaError_t adam_launch(float *p, const float *g, float *m, float *v, long long 
 }
 
 cudaError_t pc_dots_launch(const float *r, const float *ap, const float *ipb2,
-                           const float *y, double *part_zr, double *part_za, int nblk,
-                           int ns, int nt, int nz, int nx, int px, long long sst,
-                           const int *active, cudaStream_t st) {
+                           const float *y, double *part, int nblk, int ns, int nt, int nz, int nx,
+                           int px, long long sst, const int *active, cudaStream_t st) {
     const int ng = (nt + G - 1) / G;
-    pc_dots_kernel<<<dim3(nblk, ns), 256, 0, st>>>(r, ap, ipb2, y, part_zr, part_za, nt, ng, nz, nx,
-                                                   px, sst, (nz + 1) / 2, (nx + 1) / 2, active);
+    pc_dots_kernel<<<dim3(nblk, ns), 256, 0, st>>>(r, ap, ipb2, y, part, nt, ng, nz, nx, px, sst,
+                                                   (nz + 1) / 2, (nx + 1) / 2, active);
     return cudaGetLastError();
 }
 

@@ -44,6 +44,7 @@ struct PcNet {
     // gradients (FP32) and BF16 staging
     Buf gy, gL1, gD2, gL2, gD3, gL3, gBT, gP3, gP2, gP1, gbf, dwpart, yscratch, dots;
     Buf xn, rms;    // normalised input images and their per-image scale
+    Buf rms_acc;    // per-image FP64 sums of squares
     Buf dev_err;
     bool weights_ready = false;
 };
@@ -113,7 +114,8 @@ PcNet *pcnet_create(int H1, int W1, int max_batch, cudaStream_t st, std::string 
         (e = act(p->bt, 3, C)) || (e = act(p->u3, 2, C)) || (e = act(p->d3, 2, C)) ||
         (e = act(p->u2, 1, C)) || (e = act(p->d2, 1, C)) || (e = act(p->u1, 0, C)) ||
         (e = p->dev_err.ensure(sizeof(int))) || (e = p->dots.ensure(sizeof(double) * 3 * n)) ||
-        (e = act(p->xn, 0, G)) || (e = p->rms.ensure(sizeof(float) * n))) {
+        (e = act(p->xn, 0, G)) || (e = p->rms.ensure(sizeof(float) * n)) ||
+        (e = p->rms_acc.ensure(sizeof(double) * n))) {
         *err = std::string("preconditioner allocation: ") + cudaGetErrorString(e);
         delete p;
         return nullptr;
@@ -141,16 +143,22 @@ cudaError_t pcnet_get_params(const PcNet *p, float *dst, cudaStream_t st) {
     return cudaMemcpyAsync(dst, p->params.p, (size_t)param_count() * 4, cudaMemcpyDeviceToDevice, st);
 }
 
-cudaError_t pcnet_forward(PcNet *p, const __nv_bfloat16 *x, int n, float *y, cudaStream_t st) {
+cudaError_t pcnet_forward(PcNet *p, const __nv_bfloat16 *x, int n, float *y, cudaStream_t st,
+                          bool nchw, bool keep_xn) {
     if (n > p->max_batch || n < 1) return cudaErrorInvalidValue;
     if (!p->weights_ready) RET(prep_weights(p, st));
     const int *H = p->H, *W = p->W;
     int *de = p->dev_err.as<int>();
     auto wf = [&](int l) { return p->wf.as<__nv_bfloat16>() + p->wf_off[l]; };
     using bf = __nv_bfloat16;
-    RET(normalize_launch(x, p->rms.as<float>(), p->xn.as<bf>(), n, (long long)H[0] * W[0] * G, st));
-    x = p->xn.as<bf>();
-    RET((conv_launch<G, C, true, bf>(x, wf(0), bias_of(p, 0), p->e1.as<bf>(), n, H[0], W[0], de, p->nsm, st)));
+    RET(normalize_launch(x, p->rms.as<float>(), p->rms_acc.as<double>(), keep_xn ? p->xn.as<bf>() : nullptr, n,
+                         (long long)H[0] * W[0] * G, st));
+    ConvEpi e0;
+    if (keep_xn)
+        x = p->xn.as<bf>();
+    else
+        e0.irms = p->rms.as<float>();   // conv(x / rms) = conv(x) / rms before the bias
+    RET((conv_launch<G, C, true, bf>(x, wf(0), bias_of(p, 0), p->e1.as<bf>(), n, H[0], W[0], de, p->nsm, st, e0)));
     RET(pool_launch(p->e1.as<bf>(), p->p1.as<bf>(), n, H[0], W[0], st));
     RET((conv_launch<C, C, true, bf>(p->p1.p, wf(1), bias_of(p, 1), p->e2.as<bf>(), n, H[1], W[1], de, p->nsm, st)));
     RET(pool_launch(p->e2.as<bf>(), p->p2.as<bf>(), n, H[1], W[1], st));
@@ -162,8 +170,10 @@ cudaError_t pcnet_forward(PcNet *p, const __nv_bfloat16 *x, int n, float *y, cud
     RET(upadd_launch(p->d3.as<bf>(), p->e2.as<bf>(), p->u2.as<bf>(), n, H[1], W[1], st));
     RET((conv_launch<C, C, true, bf>(p->u2.p, wf(5), bias_of(p, 5), p->d2.as<bf>(), n, H[1], W[1], de, p->nsm, st)));
     RET(upadd_launch(p->d2.as<bf>(), p->e1.as<bf>(), p->u1.as<bf>(), n, H[0], W[0], st));
-    RET((conv_launch<C, G, false, float>(p->u1.p, wf(6), bias_of(p, 6), y, n, H[0], W[0], de, p->nsm, st,
-                                         p->rms.as<float>())));
+    ConvEpi e6;
+    e6.oscale = p->rms.as<float>();
+    e6.nchw = nchw ? 1 : 0;
+    RET((conv_launch<C, G, false, float>(p->u1.p, wf(6), bias_of(p, 6), y, n, H[0], W[0], de, p->nsm, st, e6)));
     return cudaSuccess;
 }
 
@@ -188,7 +198,7 @@ cudaError_t pcnet_grad(PcNet *p, const __nv_bfloat16 *x, const __nv_bfloat16 *e,
     const int nblk = 2 * p->nsm;
     RET(p->dwpart.ensure((size_t)9 * nblk * C * C * 4));
     float *y = p->yscratch.as<float>();
-    RET(pcnet_forward(p, x, n, y, st));
+    RET(pcnet_forward(p, x, n, y, st, false, true));
     RET(cos_loss_launch(x, y, e, p->dots.as<double>(), p->gy.as<float>(), (long long)H[0] * W[0] * G, n, st));
     // y = rms * U(xn): the network's output gradient carries the per-image scale
     RET(img_mul_launch(p->gy.as<float>(), p->rms.as<float>(), n, (long long)H[0] * W[0] * G, st));

@@ -156,13 +156,16 @@ def main():
     ap.add_argument("--per-iter", type=int, default=80)
     ap.add_argument("--epochs", type=int, default=6)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--iters", default="1,2,3,5,8",
+                    help="diagonal-PCG iteration counts whose residual / error pairs are taken")
     ap.add_argument("--eval", action="store_true")
     args = ap.parse_args()
     dev = torch.device("cuda")
     Xs, Es, meta = [], [], []
     t0 = time.perf_counter()
     for s in TRAIN_SEEDS:
-        X, E, m = make_pairs(s, args.nt, args.ns, per_iter=args.per_iter, device=dev)
+        X, E, m = make_pairs(s, args.nt, args.ns, iters=tuple(int(k) for k in args.iters.split(",")),
+                             per_iter=args.per_iter, device=dev)
         Xs.append(X)
         Es.append(E)
         meta.append(m)
