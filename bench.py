@@ -58,6 +58,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-nt", type=int, default=1500, help="oracle sample: steps per bench step")
+    ap.add_argument("--workload", default="esi2d", choices=["esi2d", "dft3d"],
+                    help="dft3d: forward modelling with the on-the-fly DTFT (5 frequencies, FP16 "
+                         "output) on the 400^3, nt 2000 volume instead of the ESI step")
+    ap.add_argument("--n3d", type=int, default=400)
+    ap.add_argument("--nt3d", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -198,6 +203,102 @@ def cpu_baseline(nt_sample=3000, shots=4):
                       f"{dt:.1f} s"}
 
 
+# ----------------------------------------------------------------------------- 3D DTFT arm
+def roofline_of(prof, peaks):
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    single = [k for k in prof if k["name"] != "pc_net"]
+    if not single:
+        return None
+    top = max(single, key=lambda k: k["ms"])
+    per_launch_ms = top["ms"] / max(top["launches"], 1)
+    bytes_per_launch = top["cells"] * top["bytes_per_cell"] / max(top["launches"], 1)
+    achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": top["name"], "achieved": achieved, "peak": hbm,
+            "unit": "GB/s", "frac": achieved / hbm,
+            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+            "traffic": traffic_per_launch(top), "per_launch_us": 1e3 * per_launch_ms,
+            "bytes_per_launch": bytes_per_launch,
+            "share": top["ms"] / sum(k["ms"] for k in prof)}
+
+
+def run_dft3d(args, rank, world, local):
+    """One step = forward modelling of the 400^3 volume over nt 2000 steps with the DTFT at
+    4, 6, 8, 10, 12 Hz into FP16 and the 160 x 160 receiver traces; every rank runs its own
+    copy of the shot (replicas: the volume is not split)."""
+    import torch
+    from paper_2211_06300_gb300 import esi, shard, synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    w = synth.workload_3d(n=args.n3d, nt=args.nt3d)
+    ctx = esi.Context(torch.tensor(w.v_true, dtype=torch.float32, device=dev), w.dx, w.dt,
+                      w.nt, w.nb, w.geom, vref=float(w.v_true.max()))
+    wav = torch.tensor(w.wavelets(), dtype=torch.float32, device=dev)
+    tr = torch.empty(w.nt * int(w.geom.rec_offset[-1]), dtype=torch.float32, device=dev)
+    freqs = [4.0, 6.0, 8.0, 10.0, 12.0]
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        ctx.dft_extract(freqs, wavelet=wav, half=True, traces=tr)
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = ctx.launches
+    ctx.set_profiling(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream(dev)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        U, _ = ctx.dft_extract(freqs, wavelet=wav, half=True, traces=tr)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    prof = ctx.profile()
+    ctx.set_profiling(False)
+    launches = ctx.launches - l0
+    clk = clocks.stop()
+    cells = args.steps * w.ncell * w.nt
+    t_max = shard.max_over_ranks(ms, dist, dev)
+    cells_all = shard.sum_over_ranks(cells, dist, dev)
+    # end to end: the wavelet from pinned host memory in, traces and the FP16 wavefields out
+    wav_h = wav.cpu().pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        wav.copy_(wav_h, non_blocking=True)
+        U, _ = ctx.dft_extract(freqs, wavelet=wav, half=True, traces=tr)
+        tr_h, U_h = tr.cpu(), U.cpu()
+    te = shard.max_over_ranks(time.perf_counter() - t0, dist, dev)
+    if rank == 0:
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            pass
+        print(json.dumps({
+            "metric": "FD Gcell-updates/s (forward modelling with on-the-fly DTFT)",
+            "value": cells_all / (t_max * 1e-3) / 1e9, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"dft3d-{args.n3d}^3-nt{args.nt3d}-5freqs-fp16",
+                       "freqs_hz": freqs, "l2": "inputs larger than L2 (states 2 x 256 MB)"},
+            "roofline": roofline_of(prof, peaks), "kernels": prof,
+            "e2e": {"value": cells_all / te / 1e9, "unit": UNIT,
+                    "h2d_bytes_per_step": int(wav_h.numel() * 4),
+                    "d2h_bytes_per_step": int(tr_h.numel() * 4 + U_h.numel() * 2)},
+            "gpu_launches": launches, "clocks": clk}), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 # ----------------------------------------------------------------------------- CUDA arm
 def main():
     args = parse()
@@ -206,6 +307,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "dft3d":
+        run_dft3d(args, rank, world, local)
         return
     import numpy as np
     import torch
@@ -319,22 +423,9 @@ def main():
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     # dominant kernel = largest accumulated device time among single-kernel entries
     # ("pc_net" groups the preconditioner network's 13 launches per batch)
-    roof = None
-    single = [k for k in prof if k["name"] != "pc_net"]
-    if single:
-        top = max(single, key=lambda k: k["ms"])
-        per_launch_ms = top["ms"] / max(top["launches"], 1)
-        bytes_per_launch = top["cells"] * top["bytes_per_cell"] / max(top["launches"], 1)
-        achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": top["name"], "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_src,
-                "traffic": traffic_per_launch(top), "per_launch_us": 1e3 * per_launch_ms,
-                "bytes_per_launch": bytes_per_launch,
-                "share": top["ms"] / sum(k["ms"] for k in prof)}
+    roof = roofline_of(prof, peaks) if prof else None
     iters = [int(max(r["iters"])) for r in reps]
     cg_ms = [r["ms_total"] for r in reps]
 

@@ -263,9 +263,9 @@ ESI_API esi_status esi_normal_apply(esi_ctx *ctx, double lambda, double eps, con
  * before U and the output multiplied by it (y = rms U(x / rms), so the preconditioner is
  * positively homogeneous).  The network is a learned object: its only judge is the CG
  * residual.  In the solver the correction enters per shot as z = s + theta up2(y): theta = 1
- * while <z, r> >= <s, r> / 2 (s the diagonal preconditioner's output); the first time that
- * fails the shot drops the network (theta = 0 to the end of the solve) and restarts its
- * directions from the diagonal preconditioner.
+ * while <z, r> >= <s, r> / 2 (s the diagonal preconditioner's output) on every active shot;
+ * the first time that fails on any shot the solve drops the network (theta = 0 to its end)
+ * and every shot restarts its directions from the diagonal preconditioner.
  */
 typedef struct esi_pc esi_pc;
 
@@ -275,8 +275,7 @@ ESI_API size_t esi_pc_param_count(void);
  * esi_cg_solve(..., ESI_PC_LEARNED, ...) then uses flexible (Polak-Ribiere) CG with z above. */
 ESI_API esi_status esi_pc_load(esi_ctx *ctx, const void *weights_dev, size_t bytes);
 
-/* How many shots dropped the learned correction (and restarted diagonally), summed over the
- * context's learned solves. */
+/* How many learned solves of this context dropped the network and restarted diagonally. */
 ESI_API long long esi_pc_fallbacks(const esi_ctx *ctx);
 
 /* Pack a dense field [ns][nt][N] (scaled by 1 / (lambda B^2) when scale != 0) into the

@@ -96,6 +96,7 @@ struct esi_ctx {
     PcNet *pc = nullptr;           // learned preconditioner (esi_pc_load)
     DBuf pc_img, pc_y;             // network input images (BF16) and output (FP32)
     DBuf pc_dev;                   // learned-PCG dot partials, sums and per-shot theta
+    DBuf dftsnap;                  // blocked DTFT: DFT_BLOCK new states [slot][ns][sst]
     int pc_batch = 0;
     DBuf ckpt, ckpt_scale, absbits, stash, gacc, twid, dftacc;
     long long total_rec = 0;
@@ -215,7 +216,7 @@ double step_bpc(const esi_ctx *ctx, unsigned f, int nf) {
     if (f & F_STW) b += e;
     if (f & F_GRD) b += 3 * e;
     if (f & F_SAD) b += 2 * e;
-    if (f & F_DFT) b += 4.0 * nf * e;
+    if (f & F_DFT) b += e;   // the state into the DTFT block stash
     return b;
 }
 
@@ -742,6 +743,50 @@ esi_status fwd_loop(esi_ctx *ctx, StepArgs<T> a, unsigned flags, T *&cur, T *&po
     return ESI_OK;
 }
 
+// Forward modelling with the blocked DTFT: steps [n0, n0 + K) store their new states in the
+// stash, then one launch folds them into the accumulators; the whole run is one graph.
+template <typename T>
+esi_status fwd_dft_loop(esi_ctx *ctx, StepArgs<T> a, unsigned flags, T *cur, T *po, T *tr) {
+    cudaEvent_t ev = prof_mark(ctx);
+    const int nt = ctx->nt;
+    auto body = [&]() -> esi_status {
+        T *c = cur, *q = po;
+        for (int n0 = 0; n0 < nt; n0 += DFT_BLOCK) {
+            const int n1 = std::min(nt, n0 + DFT_BLOCK);
+            for (int n = n0; n < n1; ++n) {
+                a.cur = c;
+                a.po = q;
+                a.n = n;
+                a.tin = n;
+                a.tout = n - 1;
+                a.slot_w = n - n0;
+                esi_status e = step<T>(ctx, flags, a);
+                if (e != ESI_OK) return e;
+                std::swap(c, q);
+            }
+            CKL(launch_dft_block<T>(a.stash_w, n1 - n0, ctx->ns, ctx->sst, a.nf,
+                                    a.twid + (size_t)n0 * a.nf * 2, a.dft, ctx->st));
+        }
+        CKL(launch_sample_global<T>(a.smp, c, ctx->sst, tr, nt - 1, ctx->st));
+        return ESI_OK;
+    };
+    esi_status e;
+    if (ctx->use_graphs && nt >= GRAPH_MIN_STEPS) {
+        auto key = loop_key(a, flags, +2, 0, nt, false, cur, po);
+        if (!graph_replay(ctx, key, e)) e = graph_capture(ctx, std::move(key), body);
+    } else {
+        e = body();
+    }
+    if (e != ESI_OK) return e;
+    // the stencil and the stash store per step, plus the block pass: the stash once more
+    // and the accumulators' read and write once per block
+    const double es = double(sizeof(T));
+    prof_close(ctx, ev, step_name(ctx, flags) + "+dft_block",
+               step_bpc(ctx, flags, a.nf) + es + 4.0 * a.nf * es / DFT_BLOCK, nt + (nt + DFT_BLOCK - 1) / DFT_BLOCK,
+               (long long)nt * ctx->prof_active * ctx->N);
+    return ESI_OK;
+}
+
 template <typename T>
 esi_status forward_impl(esi_ctx *ctx, const void *wavelet, const void *ext, void *traces,
                         const double *freqs, int nf, T *dft_acc) {
@@ -769,7 +814,11 @@ esi_status forward_impl(esi_ctx *ctx, const void *wavelet, const void *ext, void
         tr = ctx->traces.as<T>();
     }
     a.smp_out = tr;
+    T *cur = ctx->u0.as<T>(), *po = ctx->u1.as<T>();
     if (nf > 0) {
+        // blocked DTFT: each step stores u_{n+1} in a DFT_BLOCK-slot stash, and one pass per
+        // block adds the block's terms to the accumulators (80 -> ~13 bytes per cell update
+        // for five frequencies)
         flags |= F_DFT;
         std::vector<T> tw((size_t)ctx->nt * nf * 2);
         for (int n = 0; n < ctx->nt; ++n)
@@ -779,11 +828,13 @@ esi_status forward_impl(esi_ctx *ctx, const void *wavelet, const void *ext, void
                 tw[((size_t)n * nf + m) * 2 + 1] = T(std::sin(ph));
             }
         CK(upload(ctx->twid, tw, ctx->st));
+        CK(ctx->dftsnap.ensure((size_t)DFT_BLOCK * ctx->ns * ctx->sst * sizeof(T)));
         a.nf = nf;
         a.twid = ctx->twid.as<T>();
         a.dft = dft_acc;
+        a.stash_w = ctx->dftsnap.as<T>();
+        return fwd_dft_loop<T>(ctx, a, flags, cur, po, tr);
     }
-    T *cur = ctx->u0.as<T>(), *po = ctx->u1.as<T>();
     e = fwd_loop<T>(ctx, a, flags, cur, po, 0, ctx->nt);
     if (e != ESI_OK) return e;
     CKL(launch_sample_global<T>(a.smp, cur, ctx->sst, tr, ctx->nt - 1, ctx->st));
@@ -1164,9 +1215,11 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
     const int nzny = ctx->g.nz * ctx->g.ny;
     // learned preconditioner, per shot: z = s + theta up2(U(pack(s))), s = r / (lambda B^2),
     // with the flexible (Polak-Ribiere) beta = -alpha <z_{k+1}, A p_k> / <z_k, r_k>.  theta = 1
-    // while the network keeps <z, r> >= <s, r> / 2 (> 0); the first time it does not, the
-    // shot drops the network (theta = 0 from then on) and restarts its directions from the
-    // diagonal preconditioner (beta = 0), which it keeps to the end of the solve.
+    // while the network keeps <z, r> >= <s, r> / 2 (> 0) on every active shot; the first time
+    // it does not on any shot, the solve drops the network (theta = 0) and every shot restarts
+    // its directions from the diagonal preconditioner (beta = 0) for the rest of the solve.
+    // (Dropping it per shot, or damping theta, measured more iterations: the shots that keep
+    // the network longer restart later.)
     const int ng = (nt + 15) / 16, hc = (ctx->g.nz + 1) / 2, wc = (ctx->g.nx + 1) / 2;
     const long long nimg = (long long)ns * ng, img_elems = (long long)hc * wc * 16;
     // pc_dev: the four partial-dot arrays [4][ns][nblk_vec], their per-shot sums [4][ns]
@@ -1186,21 +1239,21 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
     }
     // theta, <z, r> and <z, A p_prev> per active shot from the four sums on the host
     auto pc_combine = [&](bool with_ap) {
+        bool fail = false;
+        for (int s = 0; s < ns; ++s) {
+            if (!h_active[s]) continue;
+            const double sr = h_dots[s], yr = h_dots[ns + s], ya = h_dots[3 * ns + s];
+            fail |= !std::isfinite(yr) || (with_ap && !std::isfinite(ya)) || sr + yr < 0.5 * sr;
+        }
+        if (fail) ctx->pc_fallbacks++;
         for (int s = 0; s < ns; ++s) {
             if (!h_active[s]) continue;
             const double sr = h_dots[s], yr = h_dots[ns + s], sa = h_dots[2 * ns + s],
                          ya = h_dots[3 * ns + s];
-            h_restart[s] = 0;
-            double th = h_theta[s];   // 0 once the shot has dropped the network
-            if (th > 0.0 && (!std::isfinite(yr) || (with_ap && !std::isfinite(ya)) ||
-                             sr + yr < 0.5 * sr)) {
-                th = 0.0;
-                h_restart[s] = 1;
-                ctx->pc_fallbacks++;
-            }
-            h_theta[s] = th;
-            h_rhon[s] = sr + th * yr;
-            h_za[s] = with_ap ? sa + th * ya : 0.0;
+            h_restart[s] = fail;
+            h_theta[s] = fail ? 0.0 : 1.0;
+            h_rhon[s] = fail ? sr : sr + yr;
+            h_za[s] = with_ap ? sa + h_theta[s] * ya : 0.0;
         }
     };
     const long long pc_cells = (long long)ns * nt * ctx->N;   // fine space-time elements
@@ -1385,6 +1438,11 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
             CK(cudaMemcpyAsync(rho, h_rho.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, ctx->st));
             CK(cudaMemcpyAsync(pc_theta, h_theta.data(), sizeof(double) * ns, cudaMemcpyHostToDevice,
                                ctx->st));
+            // once every active shot has dropped the network the solve is the diagonal PCG
+            // (rho already holds <s, r>): stop running the network
+            bool any_net = false;
+            for (int s = 0; s < ns; ++s) any_net |= h_active[s] && h_theta[s] > 0.0;
+            if (!any_net) learned = false;
         } else {
             CKL(launch_cg_beta(rho, rho_new, beta, active, ns, ctx->st));
         }

@@ -42,6 +42,7 @@ constexpr int TX3 = 32, TY3 = 16;
 constexpr int SW3 = TX3 + 2 * HALO, SH3 = TY3 + 2 * HALO;
 constexpr int ZCH3 = 80;            // planes per block (z chunk)
 constexpr int RING3 = 8;            // staged planes (shared-memory ring of TMA boxes)
+constexpr int DFT_BLOCK = 16;       // time steps per blocked DTFT pass
 
 // ----------------------------------------------------------------------------- feature flags
 enum : unsigned {
@@ -54,7 +55,7 @@ enum : unsigned {
     F_STW = 1u << 6,  // write the stash s = L + dx^2 q (gradient recompute)
     F_GRD = 1u << 7,  // gradient: G += new * stash
     F_SAD = 1u << 8,  // saddle-point gradient: G += B^2 q s
-    F_DFT = 1u << 9,  // on-the-fly DTFT of the new state
+    F_DFT = 1u << 9,  // on-the-fly DTFT: the new state into the block stash (slot slot_w)
 };
 
 // Point lists on the device, CSR over (shot, tile).  Injection lists hold unique nodes
@@ -225,6 +226,12 @@ cudaError_t launch_encode(const T *u, long long len, long long sstride, int ns, 
 template <typename T>
 cudaError_t launch_decode(const void *codes, long long len, long long sstride, int ns, int kind,
                           const float *dec_scale, T *u, cudaStream_t st);
+
+// Blocked DTFT: acc [ns][nf][sst][2] += sum_k snap[k][ns][sst] (cos, sin)(twid[k][nf]) over the
+// K stashed states of one block
+template <typename T>
+cudaError_t launch_dft_block(const T *snap, int K, int ns, long long sst, int nf, const T *twid,
+                             T *acc, cudaStream_t st);
 
 // DTFT output: pitched accumulators [ns][nf][sst][2] -> caller dense [ns][nf][N][2], either
 // copied in the field precision (half == 0) or as half pairs with a per (shot, f) scale

@@ -334,23 +334,8 @@ __global__ void __launch_bounds__(NT2, ESI_FD2_MINB) fd2_step_kernel(const __gri
                         if (gx0 + i < a.nx) o[i] = nw.v[i];
                 }
             }
-            if constexpr ((F & F_DFT) != 0) {
-                for (int m = 0; m < a.nf; ++m) {
-                    const T c = a.twid[(a.n * a.nf + m) * 2 + 0];
-                    const T sn = a.twid[(a.n * a.nf + m) * 2 + 1];
-                    T *acc = a.dft + (((long long)s * a.nf + m) * a.sst + gi) * 2;
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        Vec<T> av = ldv(acc + h * VEC);
-#pragma unroll
-                        for (int i = 0; i < VEC / 2; ++i) {
-                            av.v[2 * i] += nw.v[h * VEC / 2 + i] * c;
-                            av.v[2 * i + 1] += nw.v[h * VEC / 2 + i] * sn;
-                        }
-                        stv(acc + h * VEC, av);
-                    }
-                }
-            }
+            if constexpr ((F & F_DFT) != 0)   // the DTFT's block stash (slot n - n0)
+                stv(a.stash_w + ((long long)a.slot_w * a.ns + s) * a.sst + gi, nw);
         }
     }
     if constexpr ((F & F_AP) != 0) {

@@ -77,17 +77,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsig
     return false;
 }
 
-template <typename T>
-struct Pair;
-template <>
-struct Pair<float> {
-    using type = float2;
-};
-template <>
-struct Pair<double> {
-    using type = double2;
-};
-
 // one ring slot: the halo box of u_n, then the interior boxes of u_{n-1} and c
 template <typename T>
 struct Slot3 {
@@ -110,7 +99,6 @@ constexpr int ring_bytes() {
 template <typename T, unsigned F>
 __global__ void __launch_bounds__(block3<T>(), sizeof(T) == 4 ? 3 : 1) fd3_step_kernel(const __grid_constant__ StepArgs<T> a,
                                                                   int nzc) {
-    using T2 = typename Pair<T>::type;
     constexpr int VEC = Vec3<T>::n;        // cells per consumer thread
     constexpr int NC = consumers3<T>();
     constexpr int TPR = TX3 / VEC;         // consumer threads per tile row
@@ -398,26 +386,8 @@ __global__ void __launch_bounds__(block3<T>(), sizeof(T) == 4 ? 3 : 1) fd3_step_
                         if (gx0 + k < a.nx) o[k] = nw.v[k];
                 }
             }
-            if constexpr ((F & F_DFT) != 0) {
-                for (int m = 0; m < a.nf; ++m) {
-                    const T c = a.twid[(a.n * a.nf + m) * 2 + 0];
-                    const T sn = a.twid[(a.n * a.nf + m) * 2 + 1];
-                    T2 *acc = reinterpret_cast<T2 *>(a.dft) + ((long long)s * a.nf + m) * a.sst + gi;
-                    // VEC complex accumulators = 32 bytes = two 16-byte vectors
-                    T2 v[VEC];
-#pragma unroll
-                    for (int h = 0; h < 2; ++h)
-                        reinterpret_cast<Vec3<T> *>(v)[h] = reinterpret_cast<const Vec3<T> *>(acc)[h];
-#pragma unroll
-                    for (int k = 0; k < VEC; ++k) {
-                        v[k].x += nw.v[k] * c;
-                        v[k].y += nw.v[k] * sn;
-                    }
-#pragma unroll
-                    for (int h = 0; h < 2; ++h)
-                        reinterpret_cast<Vec3<T> *>(acc)[h] = reinterpret_cast<const Vec3<T> *>(v)[h];
-                }
-            }
+            if constexpr ((F & F_DFT) != 0)   // the DTFT's block stash (slot n - n0)
+                stv3(a.stash_w + ((long long)a.slot_w * a.ns + s) * a.sst + gi, nw);
         } else if constexpr ((F & F_PT) != 0) {
             while (ip < ie && a.inj.cell[ip] / (TX3 * TY3) == z) ++ip;
         }

@@ -454,6 +454,72 @@ cudaError_t launch_decode(const void *codes, long long len, long long sstride, i
     return cudaGetLastError();
 }
 
+namespace {
+
+// Blocked DTFT (Eq. "dtft"): acc[s][m][cell] += sum_k snap[k][s][cell] e^{+j 2 pi f_m t_k} for
+// the K states of one block, twid[k][m] = (cos, sin) of their phases.  A thread takes 16 bytes
+// of cells (pads included: they hold zeros) and up to DFT_MCH frequencies at a time in registers.
+constexpr int DFT_MCH = 4;
+
+template <typename T>
+__global__ void dft_block_kernel(const T *snap, int K, int ns, long long sst, int nf,
+                                 const T *twid, T *acc) {
+    constexpr int VEC = V16<T>::n;
+    const int s = blockIdx.y;
+    const long long nch = sst / VEC;
+    for (long long c = (long long)blockIdx.x * RT + threadIdx.x; c < nch;
+         c += (long long)gridDim.x * RT) {
+        const long long cell = c * VEC;
+        for (int m0 = 0; m0 < nf; m0 += DFT_MCH) {
+            T re[DFT_MCH][VEC], im[DFT_MCH][VEC];
+#pragma unroll
+            for (int j = 0; j < DFT_MCH; ++j)
+#pragma unroll
+                for (int i = 0; i < VEC; ++i) re[j][i] = im[j][i] = T(0);
+            for (int k = 0; k < K; ++k) {
+                const V16<T> u = *reinterpret_cast<const V16<T> *>(snap + ((long long)k * ns + s) * sst + cell);
+#pragma unroll
+                for (int j = 0; j < DFT_MCH; ++j) {
+                    if (m0 + j >= nf) break;
+                    const T cs = twid[((long long)k * nf + m0 + j) * 2];
+                    const T sn = twid[((long long)k * nf + m0 + j) * 2 + 1];
+#pragma unroll
+                    for (int i = 0; i < VEC; ++i) {
+                        re[j][i] += u.v[i] * cs;
+                        im[j][i] += u.v[i] * sn;
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < DFT_MCH; ++j) {
+                if (m0 + j >= nf) break;
+                // VEC complex values = 32 bytes = two 16-byte vectors
+                V16<T> *a = reinterpret_cast<V16<T> *>(acc + (((long long)s * nf + m0 + j) * sst + cell) * 2);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    V16<T> av = a[h];
+#pragma unroll
+                    for (int i = 0; i < VEC / 2; ++i) {
+                        av.v[2 * i] += re[j][h * VEC / 2 + i];
+                        av.v[2 * i + 1] += im[j][h * VEC / 2 + i];
+                    }
+                    a[h] = av;
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_dft_block(const T *snap, int K, int ns, long long sst, int nf, const T *twid,
+                             T *acc, cudaStream_t st) {
+    dft_block_kernel<T><<<dim3(blocks_for(sst / V16<T>::n, 1024), ns), RT, 0, st>>>(snap, K, ns, sst,
+                                                                                 nf, twid, acc);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_dft_output(const T *acc, long long sst, int rows, int nx, int px, int ns,
                               int nf, int half, void *out, unsigned *bits, float *scales_dev,
@@ -494,7 +560,9 @@ cudaError_t launch_dft_output(const T *acc, long long sst, int rows, int nx, int
     template cudaError_t launch_decode<T>(const void *, long long, long long, int, int,          \
                                           const float *, T *, cudaStream_t);                     \
     template cudaError_t launch_dft_output<T>(const T *, long long, int, int, int, int, int, int, \
-                                              void *, unsigned *, float *, cudaStream_t);
+                                              void *, unsigned *, float *, cudaStream_t);       \
+    template cudaError_t launch_dft_block<T>(const T *, int, int, long long, int, const T *, T *, \
+                                             cudaStream_t);
 
 ESI_INST(float)
 ESI_INST(double)

@@ -2,7 +2,8 @@
 
 Pairs come from the solver itself: on seeded training models (the dipping-layer recipe of
 ``synth.workload_esi_2d`` with other seeds) the diagonally preconditioned CG is run to a
-tight tolerance for the solution q*, and to k = 1, 2, 3, 5, 8 iterations for iterates q_k;
+tight tolerance for the solution q*, and to k = 1, 2, 3, 5, 8, 12, 16, 20 iterations for
+iterates q_k (50 images drawn from each: 5 models x 8 x 50 = 2000 pairs);
 the residual r_k = S^T d - (S^T S + beta B^2) q_k, scaled by 1 / (beta B^2) and packed, is
 the network input, and the packed error q* - q_k the target (the preconditioned residual
 should point along the error).  The objective is the scale-free cosine misfit of
@@ -153,10 +154,10 @@ def main():
     ap.add_argument("--out", default=None)
     ap.add_argument("--nt", type=int, default=3000)
     ap.add_argument("--ns", type=int, default=8)
-    ap.add_argument("--per-iter", type=int, default=80)
-    ap.add_argument("--epochs", type=int, default=6)
+    ap.add_argument("--per-iter", type=int, default=50)
+    ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--lr", type=float, default=1e-3)
-    ap.add_argument("--iters", default="1,2,3,5,8",
+    ap.add_argument("--iters", default="1,2,3,5,8,12,16,20",
                     help="diagonal-PCG iteration counts whose residual / error pairs are taken")
     ap.add_argument("--eval", action="store_true")
     args = ap.parse_args()
