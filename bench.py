@@ -72,9 +72,15 @@ def workload_name(ns, nt):
 
 # ----------------------------------------------------------------------------- DRAM traffic
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per cell update of a step-kernel variant,
-# from the capture summarised in profiles/ (16 shots of 801 x 241), valid only for the
+# from the capture summarised in profiles/fd2_step_801x241_16shots.md (16 shots of 801 x 241,
+# one launch = 3,088,656 cell updates), valid only for the
 # kernel sources it was taken on: the SHA-256 of fd2d.cu and esi_internal.h at capture time.
-MEASURED_TRAFFIC = {}
+_SHA = "a3f13c11fae45243f13514923dd571846149fe34416508ab05ec6fa67b9a66f3"
+MEASURED_TRAFFIC = {
+    "fd2_step[PT|AP]": ((52.540672e6 + 0.893696e6) / 3088656, _SHA),
+    "fd2_step[CGP|SMP]": ((69.079040e6 + 1.337600e6) / 3088656, _SHA),
+    "fd2_step[EXT|SAD]": ((51.681280e6 + 0.226304e6) / 3088656, _SHA),
+}
 TRAFFIC_SOURCES = ("paper_2211_06300_gb300/csrc/fd2d.cu", "paper_2211_06300_gb300/csrc/esi_internal.h")
 
 
@@ -183,9 +189,9 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
-def cpu_baseline(nt_sample=3000, shots=4):
+def cpu_baseline(nt_sample=3000, shots=8):
     """The oracle as it stands on the host cores: `shots` shots of the same workload, one
-    forward + one adjoint modelling each over nt_sample steps (about 10-20 s)."""
+    forward + one adjoint modelling each over nt_sample steps (about 15 s on 16 cores)."""
     import oracle
     from paper_2211_06300_gb300 import synth
     w = synth.workload_esi_2d(nt=nt_sample, ns=shots)
