@@ -58,9 +58,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-nt", type=int, default=1500, help="oracle sample: steps per bench step")
-    ap.add_argument("--workload", default="esi2d", choices=["esi2d", "dft3d"],
+    ap.add_argument("--workload", default="esi2d", choices=["esi2d", "dft3d", "wri2d"],
                     help="dft3d: forward modelling with the on-the-fly DTFT (5 frequencies, FP16 "
-                         "output) on the 400^3, nt 2000 volume instead of the ESI step")
+                         "output) on the 400^3, nt 2000 volume instead of the ESI step; wri2d: "
+                         "the WRI solve (B = I) and its gradient on the ESI step's workload")
+    ap.add_argument("--wri-factor", type=float, default=1e-2,
+                    help="WRI penalty: beta = factor * lambda_max(S^T S)")
     ap.add_argument("--n3d", type=int, default=400)
     ap.add_argument("--nt3d", type=int, default=2000)
     return ap.parse_args()
@@ -305,6 +308,121 @@ def run_dft3d(args, rank, world, local):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------- WRI arm
+def run_wri2d(args, rank, world, local):
+    """One step = WRI on the 801 x 241, nt 3000, 16-shot workload: the data residual of the
+    point sources, CG on (S^T S + beta I) q = S^T (d - S f) to 1e-3 (the CG section's
+    "B = I with a different right hand side"), and the saddle-point gradient with
+    u = A^{-1}(f + q), lambda = beta q.  Shots are sharded over ranks as in the ESI step."""
+    import numpy as np
+    import torch
+    from paper_2211_06300_gb300 import esi, pc_train, shard, synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    ns, nt = args.ns, args.nt
+    wl = synth.workload_esi_2d(nt=nt, ns=ns * world)
+    geom = wl.geom.select(range(*shard.shot_range(ns * world, rank, world)))
+    vref = float(wl.v_true.max())
+    f32 = torch.float32
+    v0 = torch.tensor(wl.v_start, dtype=f32, device=dev)
+    wav = torch.tensor(wl.wavelets()[rank * ns:(rank + 1) * ns], dtype=f32, device=dev).contiguous()
+    ct = esi.Context(torch.tensor(wl.v_true, dtype=f32, device=dev), wl.dx, wl.dt, nt, wl.nb,
+                     geom, vref=vref)
+    dobs = ct.forward(wavelet=wav)
+    ct.close()
+    ctx = esi.Context(v0, wl.dx, wl.dt, nt, wl.nb, geom, vref=vref)
+    c1 = esi.Context(v0, wl.dx, wl.dt, nt, wl.nb, geom.select([0]), vref=vref)
+    # beta = factor * lambda_max(S^T S): pc_train.penalty divides by (max B)^2, undone here
+    nz, nx = wl.shape
+    far = max(math.hypot(x, z) for x in (0.0, (nx - 1) * wl.dx) for z in (0.0, (nz - 1) * wl.dx))
+    beta = pc_train.penalty(c1, wl.shape, wl.dx, nt, dev, factor=args.wri_factor) * (far + wl.dx) ** 2
+    c1.close()
+    q = ctx.empty_field()
+    N = wl.ncell
+
+    def step():
+        ctx.set_velocity(v0)
+        _, rep = ctx.cg_solve(dobs, lam=beta, tol=args.tol, max_iter=args.max_iter, out=q,
+                              wri_wavelet=wav)
+        g, _ = ctx.gradient(wavelet=wav, ext=q, mode="wri", beta=beta, param="v")
+        props = sum(1 + 1 + 2 * int(k) + 1 for k in rep["iters"])   # S f, b, products, gradient
+        return g, rep, props * N * nt
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = ctx.launches
+    ctx.set_profiling(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream(dev)
+    barrier()
+    e0.record(stream)
+    cells, reps = 0, []
+    for _ in range(args.steps):
+        _, rep, c = step()
+        cells += c
+        reps.append(rep)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    prof = ctx.profile()
+    ctx.set_profiling(False)
+    launches = ctx.launches - l0
+    clk = clocks.stop()
+    t_max = shard.max_over_ranks(ms, dist, dev)
+    cells_all = shard.sum_over_ranks(cells, dist, dev)
+    d_host = dobs.cpu().pin_memory()
+    d_dev = torch.empty_like(dobs)
+    barrier()
+    t0 = time.perf_counter()
+    ce = 0
+    for _ in range(args.steps):
+        d_dev.copy_(d_host, non_blocking=True)
+        ctx.set_velocity(v0)
+        _, rep = ctx.cg_solve(d_dev, lam=beta, tol=args.tol, max_iter=args.max_iter, out=q,
+                              wri_wavelet=wav)
+        g, _ = ctx.gradient(wavelet=wav, ext=q, mode="wri", beta=beta, param="v")
+        g_host = g.cpu()
+        ce += sum(3 + 2 * int(k) for k in rep["iters"]) * N * nt
+    te = shard.max_over_ranks(time.perf_counter() - t0, dist, dev)
+    ce = shard.sum_over_ranks(ce, dist, dev)
+    if rank == 0:
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            pass
+        print(json.dumps({
+            "metric": "FD Gcell-updates/s fwd+adj; WRI CG time to 1e-3 residual",
+            "value": cells_all / (t_max * 1e-3) / 1e9, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "wri2d-801x241-nt%d-%dshots-fp32" % (nt, ns), "beta": beta,
+                       "wri_factor": args.wri_factor, "tol": args.tol,
+                       "l2": "inputs larger than L2 (CG vectors 4 x 37 GB per GPU)"},
+            "cg": {"iters_max_per_step": [int(max(r["iters"])) for r in reps],
+                   "time_to_tol_ms": [r["ms_total"] for r in reps],
+                   "converged": [bool(r["converged"]) for r in reps]},
+            "roofline": roofline_of(prof, peaks), "kernels": prof,
+            "e2e": {"value": ce / te / 1e9, "unit": UNIT,
+                    "h2d_bytes_per_step": int(d_host.numel() * d_host.element_size()),
+                    "d2h_bytes_per_step": int(g_host.numel() * g_host.element_size())},
+            "gpu_launches": launches, "clocks": clk}), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 # ----------------------------------------------------------------------------- CUDA arm
 def main():
     args = parse()
@@ -316,6 +434,9 @@ def main():
         return
     if args.workload == "dft3d":
         run_dft3d(args, rank, world, local)
+        return
+    if args.workload == "wri2d":
+        run_wri2d(args, rank, world, local)
         return
     import numpy as np
     import torch

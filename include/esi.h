@@ -152,7 +152,8 @@ ESI_API esi_status esi_adjoint(esi_ctx *ctx, const void *traces_dev, void *ext_o
 
 typedef enum esi_grad_mode {
     ESI_GRAD_ADJOINT_STATE = 0,  /* back-propagate a data residual (Eq. "gradient") */
-    ESI_GRAD_SADDLE_POINT = 1    /* Algorithm 2: lambda = beta B^H B q, no adjoint run */
+    ESI_GRAD_SADDLE_POINT = 1,   /* Algorithm 2: lambda = beta B^H B q, no adjoint run */
+    ESI_GRAD_WRI_SADDLE = 2      /* WRI (Eq. "gradient2"): u = A^{-1}(f + q), lambda = beta q */
 } esi_grad_mode;
 
 typedef enum esi_param { ESI_PARAM_C = 0, ESI_PARAM_V = 1, ESI_PARAM_M = 2 } esi_param;
@@ -181,6 +182,9 @@ typedef struct esi_grad_opts {
  *   ckpt_every steps from stored (optionally compressed) checkpoints.
  * Saddle-point mode (Algorithm 2): ext_src is the ESI solution q, the
  *   adjoint field is lambda = beta B^H B q with B = ||x - x_s|| + eps; one forward run.
+ * WRI saddle mode (Eq. "newadj2", "gradient2"): ext_src is the WRI solution q and
+ *   wavelet_dev the point sources f; u = A^{-1}(f + q), lambda = beta q (B = I); one
+ *   forward run.
  *   grad_dev    : device [N], written (sum over all shots) in the chosen parameter
  *   misfit      : host double, written in adjoint-state mode with dobs (may be NULL)
  */
@@ -238,6 +242,21 @@ typedef struct esi_cg_report {
 ESI_API esi_status esi_cg_solve(esi_ctx *ctx, double lambda, double tol, int max_iter,
                                 const void *dobs_dev, void *q_out_dev, int precond, double eps,
                                 esi_cg_report *report);
+
+/*
+ * esi_wri_solve -- WRI by the same CG (the CG section: "B = I with a different right hand
+ * side"; Eq. "normalwri"):
+ *   (S^T S + lambda I) q = S^T (d - S f),
+ * f the point sources (wavelet_dev [ns][nt], as in esi_forward) and d the observed traces.
+ * One forward modelling with f gives the data residual d - S f (kept in context scratch);
+ * then Algorithm 1 exactly as in esi_cg_solve (no preconditioner: with B = I the diagonal
+ * one is a constant).  The wavefield is u = A^{-1}(f + q); the WRI gradient is
+ * esi_gradient in ESI_GRAD_WRI_SADDLE mode.  q_out_dev: device [ns][nt][N].  Errors and
+ * report as esi_cg_solve.
+ */
+ESI_API esi_status esi_wri_solve(esi_ctx *ctx, double lambda, double tol, int max_iter,
+                                 const void *wavelet_dev, const void *dobs_dev, void *q_out_dev,
+                                 esi_cg_report *report);
 
 /*
  * esi_normal_apply -- the ESI normal operator (Eq. "normalewi"; the matrix-vector product

@@ -387,6 +387,72 @@ class Oracle:
             rz = rz_new
         return {"x": x, "rel_res": np.asarray(hist), "iters": k + 1}
 
+    # ---------------------------------------------------------------- WRI (B = I)
+    # The CG section notes that the same CG serves WRI "by simply choosing B = I with a
+    # different right hand side": Eq. "normalwri", (S^H S + beta I) q = S^H (d - S f), with
+    # u = A^{-1}(f + q) (Eq. "newq") and the gradient beta <A u - f, dA/dm u> = <lambda,
+    # dA/dm u>, lambda = beta q (Eq. "newadj2", "gradient2").
+    def wri_rhs(self, sh: Shot, d: np.ndarray, wavelet: np.ndarray) -> np.ndarray:
+        """b = S^T (d - S f): the data residual of the point sources, back-propagated."""
+        Sf = self.forward(sh, wavelet=wavelet)["traces"]
+        return self.ST(sh, np.asarray(d, dtype=np.float64).reshape(self.nt, sh.nr) - Sf)
+
+    def wri_matvec(self, sh: Shot, p: np.ndarray, beta: float) -> np.ndarray:
+        """(S^T S + beta I) p."""
+        p = np.asarray(p, dtype=np.float64).reshape(self.nt, self.N)
+        return self.ST(sh, self.S(sh, p)) + beta * p
+
+    def wri_cg(self, sh: Shot, d: np.ndarray, wavelet: np.ndarray, beta: float, tol: float,
+               n_cg: int) -> Dict:
+        """Algorithm 1 on the WRI system, verbatim as in cg()."""
+        b = self.wri_rhs(sh, d, wavelet)
+        x = np.zeros_like(b)
+        r = b.copy()
+        p = r.copy()
+        rr = float(np.sum(r * r))
+        r0 = math.sqrt(rr)
+        hist = []
+        k = 0
+        for k in range(n_cg):
+            Ap = self.wri_matvec(sh, p, beta)
+            alpha = rr / float(np.sum(p * Ap))
+            x = x + alpha * p
+            r = r - alpha * Ap
+            rr_new = float(np.sum(r * r))
+            hist.append(math.sqrt(rr_new) / r0 if r0 > 0 else 0.0)
+            if math.sqrt(rr_new) < tol * r0 or k == n_cg - 1:
+                break
+            p = r + (rr_new / rr) * p
+            rr = rr_new
+        return {"x": x, "rel_res": np.asarray(hist), "iters": k + 1, "b": b}
+
+    def wri_objective(self, sh: Shot, q: np.ndarray, d: np.ndarray, wavelet: np.ndarray,
+                      beta: float) -> float:
+        """J_WRI = 1/2 ||R u - d||^2 + beta/2 ||q||^2 with u = A^{-1}(f + q) (Eq. "wrimisfit")."""
+        tr = self.forward(sh, wavelet=wavelet, q_ext=q)["traces"]
+        e = tr - np.asarray(d, dtype=np.float64).reshape(self.nt, sh.nr)
+        return 0.5 * float(np.sum(e * e)) + 0.5 * beta * float(np.sum(np.asarray(q) ** 2))
+
+    def wri_gradient(self, sh: Shot, q: np.ndarray, wavelet: np.ndarray, beta: float,
+                     param: str = "c") -> np.ndarray:
+        """The WRI saddle-point gradient: u = A^{-1}(f + q), lambda = beta q.  With the discrete
+        adjoint convention (S^T e)_n = c mu_{n+1}, the adjoint field of the residual at the
+        solution is mu_{n+1} = -beta q_n / c; g_c = sum_n mu_{n+1} (Lap u_n + f_n + q_n)."""
+        fw = self.forward(sh, wavelet=wavelet, q_ext=q, want_s=True)
+        qq = np.asarray(q, dtype=np.float64).reshape(self.nt, self.N)
+        mu = -beta * qq / self.c[None, :]
+        return self.to_param(np.sum(mu * fw["s"], axis=0), param)
+
+    def assemble_S(self, sh: Shot) -> np.ndarray:
+        """Dense data operator S (columns S e_j over space-time; tiny sizes only)."""
+        n = self.nt * self.N
+        M = np.empty((self.nt * sh.nr, n))
+        for j in range(n):
+            ej = np.zeros(n)
+            ej[j] = 1.0
+            M[:, j] = self.S(sh, ej.reshape(self.nt, self.N)).ravel()
+        return M
+
     def assemble_normal(self, sh: Shot, beta: float, eps: Optional[float] = None) -> np.ndarray:
         """Dense normal matrix, column j = A e_j (tiny sizes only)."""
         n = self.nt * self.N

@@ -97,6 +97,7 @@ struct esi_ctx {
     DBuf pc_img, pc_y;             // network input images (BF16) and output (FP32)
     DBuf pc_dev;                   // learned-PCG dot partials, sums and per-shot theta
     DBuf dftsnap;                  // blocked DTFT: DFT_BLOCK new states [slot][ns][sst]
+    DBuf wri_res;                  // WRI: data residual d - S f [traces]
     int pc_batch = 0;
     DBuf ckpt, ckpt_scale, absbits, stash, gacc, twid, dftacc;
     long long total_rec = 0;
@@ -1033,16 +1034,25 @@ esi_status gradient_impl(esi_ctx *ctx, const void *wavelet, const void *ext, con
     CK(cudaMemsetAsync(ctx->gacc.p, 0, (size_t)ns * ctx->sst * sizeof(T), ctx->st));
     const T eps = T(o->eps > 0 ? o->eps : ctx->g.dx);
     double extra = 1.0;
-    if (o->mode == ESI_GRAD_SADDLE_POINT) {
+    if (o->mode == ESI_GRAD_SADDLE_POINT || o->mode == ESI_GRAD_WRI_SADDLE) {
         if (!ext) return ctx->fail(ESI_ERR_ARG, "saddle-point gradient needs the extended source q");
+        const bool wri = o->mode == ESI_GRAD_WRI_SADDLE;
+        if (wri && !wavelet) return ctx->fail(ESI_ERR_ARG, "the WRI gradient needs the point sources f");
         CK(cudaMemsetAsync(ctx->u0.p, 0, ctx->u0.n, ctx->st));
         CK(cudaMemsetAsync(ctx->u1.p, 0, ctx->u1.n, ctx->st));
         StepArgs<T> a = base_args<T>(ctx);
         a.ext = reinterpret_cast<const T *>(ext);
         a.grad = ctx->gacc.as<T>();
         a.eps = eps;
+        unsigned flags = F_EXT | F_SAD;
+        if (wri) {   // u = A^{-1}(f + q), adjoint field beta q (B = I)
+            flags |= F_PT;
+            a.unit_b = 1;
+            a.inj = inj_view<T>(ctx->inj_src);
+            a.inj_trace = reinterpret_cast<const T *>(wavelet);
+        }
         T *cur = ctx->u0.as<T>(), *po = ctx->u1.as<T>();
-        e = fwd_loop<T>(ctx, a, F_EXT | F_SAD, cur, po, 0, nt);
+        e = fwd_loop<T>(ctx, a, flags, cur, po, 0, nt);
         if (e != ESI_OK) return e;
         extra = -o->beta;
     } else {
@@ -1124,7 +1134,7 @@ esi_status gradient_impl(esi_ctx *ctx, const void *wavelet, const void *ext, con
     CKL(launch_grad_finalize<T>(ctx->gacc.as<T>(), ns, ctx->sst, ctx->cc.as<T>(), ctx->g.nz,
                                 ctx->g.ny, ctx->g.nx, ctx->px, ctx->dt, ctx->g.dx, extra, o->param,
                                 reinterpret_cast<T *>(grad), ctx->st));
-    if (misfit && !adj && o->mode != ESI_GRAD_SADDLE_POINT) return check_dev_err(ctx);
+    if (misfit && !adj && o->mode == ESI_GRAD_ADJOINT_STATE) return check_dev_err(ctx);
     return ESI_OK;
 }
 
@@ -1164,9 +1174,14 @@ esi_status dft_impl(esi_ctx *ctx, const void *wavelet, const void *ext, const do
 // rho; p = z + beta p, where z = r (no preconditioner, Algorithm 1 as printed) or
 // z = r / (lambda B^2) (diagonal preconditioner) and rho = <r, z>.  The work vectors r, p,
 // A p live in the internal pitched layout; x is the caller's dense q_out.
+// WRI (the CG section's "B = I with a different right hand side", Eq. "normalwri"): with
+// wri_wavelet the annihilator is the identity and the right-hand side is S^T (d - S f), f the
+// point sources; the rest of Algorithm 1 is unchanged.
 template <typename T>
 esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const void *dobs,
-                   void *q_out, int precond, double eps_in, esi_cg_report *rep) {
+                   void *q_out, int precond, double eps_in, esi_cg_report *rep,
+                   const void *wri_wavelet = nullptr) {
+    const int unit_b = wri_wavelet != nullptr;
     using clk = std::chrono::steady_clock;
     const auto t_start = clk::now();
     const int ns = ctx->ns, nt = ctx->nt;
@@ -1175,6 +1190,8 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
     bool learned = precond == ESI_PC_LEARNED;
     if (precond != ESI_PC_NONE && precond != ESI_PC_DIAG && !learned)
         return ctx->fail(ESI_ERR_ARG, "unknown preconditioner");
+    if (learned && unit_b)
+        return ctx->fail(ESI_ERR_UNSUPPORTED, "the learned preconditioner serves the ESI system");
     if (learned && (!ctx->pc || sizeof(T) != 4 || ctx->g.ndim != 2))
         return ctx->fail(ESI_ERR_UNSUPPORTED,
                          "the learned preconditioner needs esi_pc_load on a 2D FP32 context");
@@ -1188,7 +1205,9 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
     CK(ctx->cg_p.ensure(vb));
     CK(ctx->cg_ap.ensure(vb));
     CK(ctx->traces.ensure(std::max<size_t>((size_t)ctx->total_rec * nt * sizeof(T), 16)));
-    const int nblk_step = ctx->g.ndim == 2 ? ctx->ntx * ctx->ntz : ctx->ntx * ctx->nty * ctx->nzc;
+    // <p, A p> partials of the adjoint half: one per warp of a 2D tile, one per 3D block
+    const int nblk_step = ctx->g.ndim == 2 ? ctx->ntx * ctx->ntz * (NT2 / 32)
+                                            : ctx->ntx * ctx->nty * ctx->nzc;
     const int nblk_vec = 1216;  // 8 x 152 SMs
     const size_t npart = (size_t)ns * std::max(nblk_step, nblk_vec);
     CK(ctx->part.ensure(sizeof(double) * npart));
@@ -1211,7 +1230,7 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
         ipb2 = ctx->ipb2.as<T>();
     }
     CKL(launch_b2_maps<T>(ctx->pb2.as<T>(), ipb2, ns, ctx->g.nz, ctx->g.ny, ctx->g.nx, ctx->px,
-                          T(lambda), eps, T(ctx->g.dx), ctx->src_pos.as<double>(), ctx->st));
+                          T(lambda), eps, T(ctx->g.dx), ctx->src_pos.as<double>(), unit_b, ctx->st));
     const int nzny = ctx->g.nz * ctx->g.ny;
     // learned preconditioner, per shot: z = s + theta up2(U(pack(s))), s = r / (lambda B^2),
     // with the flexible (Polak-Ribiere) beta = -alpha <z_{k+1}, A p_k> / <z_k, r_k>.  theta = 1
@@ -1225,6 +1244,7 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
     // pc_dev: the four partial-dot arrays [4][ns][nblk_vec], their per-shot sums [4][ns]
     // (<s, r>, <y, r>, <s, A p>, <y, A p>) and theta [ns]
     std::vector<int> h_active(ns, 1), h_bad(ns, 0), iters(ns, 0);
+    std::vector<char> h_conv(ns, 0);
     double *pc_part = nullptr, *pc_dots = nullptr, *pc_theta = nullptr;
     std::vector<double> h_rho(ns), h_rhon(ns), h_za(ns), h_alpha(ns), h_beta(ns, 0.0);
     std::vector<double> h_dots(4 * (size_t)ns), h_theta(ns, 1.0);
@@ -1289,6 +1309,15 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
     CK(cudaMemsetAsync(bad, 0, sizeof(int) * ns, ctx->st));
     CK(cudaMemsetAsync(alpha, 0, sizeof(double) * ns, ctx->st));
     CK(cudaMemsetAsync(x, 0, (size_t)ns * ctx->N * nt * sizeof(T), ctx->st));
+    if (unit_b) {
+        // WRI: the data residual d - S f of the point sources replaces d
+        const long long tl = (long long)ctx->total_rec * nt;
+        CK(ctx->wri_res.ensure(std::max<size_t>((size_t)tl * sizeof(T), 16)));
+        e = forward_impl<T>(ctx, wri_wavelet, nullptr, ctx->wri_res.p, nullptr, 0, nullptr);
+        if (e != ESI_OK) return e;
+        CKL(launch_sub_from<T>(ctx->wri_res.as<T>(), reinterpret_cast<const T *>(dobs), tl, ctx->st));
+        dobs = ctx->wri_res.p;
+    }
     // b = S^T d, written straight into r (x0 = 0, r0 = b)
     e = adjoint_impl<T>(ctx, dobs, r, nullptr, true);
     if (e != ESI_OK) return e;
@@ -1421,7 +1450,9 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
             iters[s] = k + 1;
             const double rel = std::sqrt(rrn[s] / rr0[s]);
             if (rep && rep->rel_res && k < hist_cap) rep->rel_res[(size_t)s * hist_cap + k] = rel;
-            if (std::sqrt(rrn[s]) < tol * std::sqrt(rr0[s]) || k == max_iter - 1)
+            const bool met = std::sqrt(rrn[s]) < tol * std::sqrt(rr0[s]);
+            h_conv[s] = met;
+            if (met || k == max_iter - 1)
                 h_active[s] = 0;  // exit loop for this shot (Algorithm 1's stopping test)
             else
                 any = true;
@@ -1447,9 +1478,10 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
             CKL(launch_cg_beta(rho, rho_new, beta, active, ns, ctx->st));
         }
     }
+    // judged on each shot's own last residual (the device partials of frozen shots are reused)
     bool conv = true;
     for (int s = 0; s < ns; ++s)
-        if (rr0[s] > 0 && !(iters[s] > 0 && std::sqrt(rrn[s]) < tol * std::sqrt(rr0[s]))) conv = false;
+        if (rr0[s] > 0 && !(iters[s] > 0 && h_conv[s])) conv = false;
     if (rep) {
         int mx = 0;
         for (int s = 0; s < ns; ++s) {
@@ -1690,6 +1722,20 @@ ESI_API esi_status esi_dft_extract(esi_ctx *ctx, const void *wavelet_dev, const 
                                  scales_host, traces_dev);
 }
 
+ESI_API esi_status esi_wri_solve(esi_ctx *ctx, double lambda, double tol, int max_iter,
+                                 const void *wavelet_dev, const void *dobs_dev, void *q_out_dev,
+                                 esi_cg_report *report) {
+    if (!ctx) return ESI_ERR_ARG;
+    if (!wavelet_dev || !dobs_dev || !q_out_dev || !(lambda >= 0) || !(tol >= 0))
+        return ctx->fail(ESI_ERR_ARG, "bad WRI arguments");
+    ctx->err.clear();
+    return ctx->g.dtype == ESI_F64
+               ? cg_impl<double>(ctx, lambda, tol, max_iter, dobs_dev, q_out_dev, ESI_PC_NONE, 0.0,
+                                 report, wavelet_dev)
+               : cg_impl<float>(ctx, lambda, tol, max_iter, dobs_dev, q_out_dev, ESI_PC_NONE, 0.0,
+                                report, wavelet_dev);
+}
+
 ESI_API esi_status esi_cg_solve(esi_ctx *ctx, double lambda, double tol, int max_iter,
                                 const void *dobs_dev, void *q_out_dev, int precond, double eps,
                                 esi_cg_report *report) {
@@ -1761,7 +1807,7 @@ ESI_API esi_status esi_pc_pack(esi_ctx *ctx, const void *field_dev, double lambd
         CKL(launch_b2_maps<float>(ctx->pb2.as<float>(), ctx->ipb2.as<float>(), ctx->ns, ctx->g.nz,
                                   ctx->g.ny, ctx->g.nx, ctx->px, float(lambda),
                                   float(eps > 0 ? eps : ctx->g.dx), float(ctx->g.dx),
-                                  ctx->src_pos.as<double>(), ctx->st));
+                                  ctx->src_pos.as<double>(), 0, ctx->st));
         ipb2 = ctx->ipb2.as<float>();
     }
     CKL(pcnet::pack_launch(reinterpret_cast<const float *>(field_dev), ipb2,

@@ -30,7 +30,10 @@ namespace esi {
 // ----------------------------------------------------------------------------- tiling
 constexpr int HALO = 4;             // stencil radius (8th order)
 constexpr int TX2 = 64;             // tile width (x) of the 2D step kernel
-constexpr int TZ2 = 32;             // tile height (z)
+#ifndef ESI_TZ2
+#define ESI_TZ2 32
+#endif
+constexpr int TZ2 = ESI_TZ2;        // tile height (z)
 constexpr int NT2 = 256;            // threads per block of the 2D step kernel
 constexpr int SW2 = TX2 + 2 * HALO; // shared tile width incl. halo (72: 16-byte rows)
 constexpr int SH2 = TZ2 + 2 * HALO; // shared tile height incl. halo
@@ -139,6 +142,7 @@ struct StepArgs {
     T pen;                     // penalty beta
     const double *src_pos;     // [ns][3] source (x, y, z) metres
     T eps, dx;
+    int unit_b;                // F_SAD: the annihilator is the identity (WRI), not ||x - x_s|| + eps
     // stash [slot][ns][sst] pitched; write slot sw, read slot sr
     T *stash_w;
     const T *stash_r;
@@ -189,10 +193,14 @@ cudaError_t launch_cg_update(T *x, T *r, const T *p, const T *ap, long long rows
                              double *part2, int nblk, const T *ipb2, long long sst, int nzny,
                              cudaStream_t st);
 
-// per-shot maps pb2 = pen B^2 and ipb2 = 1 / pb2 over the pitched plane (pad cells 0)
+// per-shot maps pb2 = pen B^2 and ipb2 = 1 / pb2 over the pitched plane (pad cells 0); with
+// unit_b the annihilator is the identity (WRI: pb2 = pen)
 template <typename T>
 cudaError_t launch_b2_maps(T *pb2, T *ipb2, int ns, int nz, int ny, int nx, int px, T pen, T eps,
-                           T dx, const double *src_pos, cudaStream_t st);
+                           T dx, const double *src_pos, int unit_b, cudaStream_t st);
+// y = x - y over len elements
+template <typename T>
+cudaError_t launch_sub_from(T *y, const T *x, long long len, cudaStream_t st);
 // alpha = rr / pAp ; flags breakdown
 cudaError_t launch_cg_alpha(const double *rr, const double *pap, double *alpha, int *bad,
                             const int *active, int ns, cudaStream_t st);

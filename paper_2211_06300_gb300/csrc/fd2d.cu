@@ -87,7 +87,6 @@ __global__ void __launch_bounds__(NT2, ESI_FD2_MINB) fd2_step_kernel(const __gri
     __shared__ __align__(128) T tl[SH2][SW2];
     __shared__ __align__(8) unsigned long long bar;
     __shared__ __align__(16) T qpt[(F & F_PT) ? TZ2 * TX2 : VEC];
-    __shared__ double red[NT2 / 32];
     const int tid = threadIdx.x;
     const int s = blockIdx.z;
     if (a.active && !a.active[s]) return;
@@ -289,7 +288,7 @@ __global__ void __launch_bounds__(NT2, ESI_FD2_MINB) fd2_step_kernel(const __gri
 #pragma unroll
                 for (int i = 0; i < VEC; ++i) {
                     const T ex = T(gx0 + i) * a.dx - xs;
-                    const T B = sqrt(ex * ex + ez * ez) + a.eps;
+                    const T B = a.unit_b ? T(1) : sqrt(ex * ex + ez * ez) + a.eps;
                     B2[i] = B * B;
                 }
                 {
@@ -339,17 +338,14 @@ __global__ void __launch_bounds__(NT2, ESI_FD2_MINB) fd2_step_kernel(const __gri
         }
     }
     if constexpr ((F & F_AP) != 0) {
+        // one partial per warp (deterministic, and no block-wide wait at the end):
+        // dot_part[shot][tile][warp], accumulated over the time steps
         T v = psum;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((tid & 31) == 0) red[tid >> 5] = double(v);
-        __syncthreads();
-        if (tid == 0) {
-            double t = 0.0;
-#pragma unroll
-            for (int k = 0; k < NT2 / 32; ++k) t += red[k];
-            a.dot_part[(long long)s * (a.ntx * a.ntz) + blockIdx.y * a.ntx + blockIdx.x] += t;
-        }
+        if ((tid & 31) == 0)
+            a.dot_part[((long long)s * (a.ntx * a.ntz) + blockIdx.y * a.ntx + blockIdx.x) *
+                           (NT2 / 32) + (tid >> 5)] += double(v);
     }
 }
 
@@ -397,6 +393,7 @@ cudaError_t launch_step2(unsigned flags, const StepArgs<T> &a, int ns, cudaStrea
         ESI_CASE(F_EXT | F_PT | F_STW)
         // saddle-point gradient
         ESI_CASE(F_EXT | F_SAD)
+        ESI_CASE(F_EXT | F_PT | F_SAD)   // WRI: u = A^{-1}(f + q)
         // adjoint modelling
         ESI_CASE(F_PT)
         ESI_CASE(F_PT | F_OUT)

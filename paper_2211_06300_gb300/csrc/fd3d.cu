@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(block3<T>(), sizeof(T) == 4 ? 3 : 1) fd3_step_
 #pragma unroll
                 for (int k = 0; k < VEC; ++k) {
                     const T ex = T(gx0 + k) * a.dx - xs;
-                    const T B = sqrt(ex * ex + ey * ey + ez * ez) + a.eps;
+                    const T B = a.unit_b ? T(1) : sqrt(ex * ex + ey * ey + ez * ez) + a.eps;
                     if (gx0 + k < a.nx) gv.v[k] += B * B * src[k] * S[k];
                 }
                 stv3(a.grad + (long long)s * a.sst + gi, gv);
@@ -456,6 +456,7 @@ cudaError_t launch_step3(unsigned flags, const StepArgs<T> &a, int ns, cudaStrea
         ESI_CASE(F_EXT | F_STW)
         ESI_CASE(F_EXT | F_PT | F_STW)
         ESI_CASE(F_EXT | F_SAD)
+        ESI_CASE(F_EXT | F_PT | F_SAD)   // WRI: u = A^{-1}(f + q)
         ESI_CASE(F_PT | F_OUT)
         ESI_CASE(F_PT | F_AP)
         ESI_CASE(F_PT | F_GRD)

@@ -345,10 +345,12 @@ __global__ void wprep_kernel(const float *W, __nv_bfloat16 *out, int cin, int co
 
 // ----------------------------------------------------------------------------- data movement
 // residual -> network input: img[(s*ng + g)][hc][wc][c] = 1/4 sum_{2x2} r[s][16g+c] * ipb2[s].
-// A block takes whole output rows (s, g, zc); its threads run along the row.
-__global__ void pack_kernel(const float *r, const float *ipb2, __nv_bfloat16 *img, int ns, int nt,
-                            int ng, int nz, int nx, int px, long long sst, int hc, int wc,
-                            int scale_by_map, int dense) {
+// A block takes whole output rows (s, g, zc); its threads run along the row, each producing
+// one pixel's 16 channels in two halves of 8 (few live registers, many loads in flight).
+__global__ void __launch_bounds__(256, 4) pack_kernel(const float *r, const float *ipb2,
+                                                      __nv_bfloat16 *img, int ns, int nt, int ng,
+                                                      int nz, int nx, int px, long long sst,
+                                                      int hc, int wc, int scale_by_map, int dense) {
     const int nrow = ns * ng * hc;
     const long long plane = dense ? (long long)nz * nx : sst;
     const int rstride = dense ? nx : px;
@@ -358,46 +360,43 @@ __global__ void pack_kernel(const float *r, const float *ipb2, __nv_bfloat16 *im
         const float *rs = r + (long long)s * nt * plane;
         __nv_bfloat16 *orow = img + ((long long)ig * hc + zc) * wc * G;
         for (int xc = threadIdx.x; xc < wc; xc += blockDim.x) {
-            float v[G];
+            // the 2 x 2 cells: rows iz0, iz0 + 1 (if inside), columns ix0, ix0 + 1 (if inside)
+            const int iz0 = 2 * zc, ix0 = 2 * xc;
+            const bool row2 = iz0 + 1 < nz, col2 = ix0 + 1 < nx;
+            float m[2][2] = {{1.0f, 1.0f}, {1.0f, 1.0f}};
+            if (scale_by_map) {
 #pragma unroll
-            for (int c = 0; c < G; ++c) v[c] = 0.0f;
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                const int iz = 2 * zc + a;
-                if (iz >= nz) continue;
-                if (!dense) {
-                    // pitched rows: the two cells are one aligned float2; the second lies in
-                    // the pad past nx (never read into the sum) when nx is odd
-                    const long long cell = (long long)iz * px + 2 * xc;
-                    const bool two = 2 * xc + 1 < nx;
-                    float2 m = make_float2(1.0f, 1.0f);
-                    if (scale_by_map) m = *reinterpret_cast<const float2 *>(ipb2 + (long long)s * sst + cell);
-#pragma unroll
-                    for (int c = 0; c < G; ++c) {
-                        const int t = G * g + c;
-                        if (t < nt) {
-                            const float2 rv = *reinterpret_cast<const float2 *>(rs + (long long)t * plane + cell);
-                            v[c] += rv.x * m.x + (two ? rv.y * m.y : 0.0f);
-                        }
-                    }
-                    continue;
-                }
-#pragma unroll
-                for (int b = 0; b < 2; ++b) {
-                    const int ix = 2 * xc + b;
-                    if (ix >= nx) continue;
-                    const long long cell = (long long)iz * rstride + ix;
-                    const float m = scale_by_map ? ipb2[(long long)s * sst + (long long)iz * px + ix] : 1.0f;
-#pragma unroll
-                    for (int c = 0; c < G; ++c) {
-                        const int t = G * g + c;
-                        if (t < nt) v[c] += rs[(long long)t * plane + cell] * m;
-                    }
+                for (int a = 0; a < 2; ++a) {
+                    if (a == 1 && !row2) break;
+                    const float *ib = ipb2 + (long long)s * sst + (long long)(iz0 + a) * px + ix0;
+                    m[a][0] = ib[0];
+                    m[a][1] = col2 ? ib[1] : 0.0f;
                 }
             }
+            if (!col2) m[0][1] = m[1][1] = 0.0f;
+            if (!row2) m[1][0] = m[1][1] = 0.0f;
 #pragma unroll
-            for (int c = 0; c < G; ++c) v[c] *= 0.25f;
-            store_row<__nv_bfloat16>(orow + (long long)xc * G, v, G);
+            for (int h = 0; h < 2; ++h) {
+                float v[G / 2];
+#pragma unroll
+                for (int c = 0; c < G / 2; ++c) {
+                    const int t = G * g + (G / 2) * h + c;
+                    float acc = 0.0f;
+                    if (t < nt) {
+                        const float *rt = rs + (long long)t * plane + (long long)iz0 * rstride + ix0;
+#pragma unroll
+                        for (int a = 0; a < 2; ++a) {
+                            const float *rr = rt + (long long)a * rstride;
+                            const bool in = a == 0 || row2;
+                            const float r0 = in ? rr[0] : 0.0f;
+                            const float r1 = in && col2 ? rr[1] : 0.0f;
+                            acc += r0 * m[a][0] + r1 * m[a][1];
+                        }
+                    }
+                    v[c] = 0.25f * acc;
+                }
+                store_row<__nv_bfloat16>(orow + (long long)xc * G + (G / 2) * h, v, G / 2);
+            }
         }
     }
 }

@@ -176,6 +176,13 @@ __global__ void cg_beta_kernel(double *rr_old, const double *rr_new, double *bet
 }
 
 template <typename T>
+__global__ void sub_from_kernel(T *y, const T *x, long long len) {
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < len;
+         i += (long long)gridDim.x * RT)
+        y[i] = x[i] - y[i];
+}
+
+template <typename T>
 __global__ void residual_kernel(T *d, const T *dobs, long long len, double *part) {
     double acc = 0.0;
     for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < len;
@@ -360,7 +367,7 @@ __global__ void add_b2p_kernel(T *out, const T *p, int nt, int nz, int ny, int n
 
 template <typename T>
 __global__ void b2_maps_kernel(T *pb2, T *ipb2, int nz, int ny, int nx, int px, T pen, T eps,
-                               T dx, const double *src_pos) {
+                               T dx, const double *src_pos, int unit_b) {
     const int s = blockIdx.y;
     const long long plane = (long long)nz * ny * px;
     const double xs = src_pos[3 * s], ys = src_pos[3 * s + 1], zs = src_pos[3 * s + 2];
@@ -373,7 +380,7 @@ __global__ void b2_maps_kernel(T *pb2, T *ipb2, int nz, int ny, int nx, int px, 
         if (x < nx) {
             const double ex = x * double(dx) - xs, ez = iz * double(dx) - zs;
             const double ey = ny > 1 ? iy * double(dx) - ys : 0.0;
-            const double B = std::sqrt(ex * ex + ey * ey + ez * ez) + double(eps);
+            const double B = unit_b ? 1.0 : std::sqrt(ex * ex + ey * ey + ez * ez) + double(eps);
             v = T(double(pen) * B * B);
             iv = T(1.0 / (double(pen) * B * B));
         }
@@ -393,10 +400,10 @@ cudaError_t launch_add_b2p(T *out, const T *p, int ns, int nt, int nz, int ny, i
 
 template <typename T>
 cudaError_t launch_b2_maps(T *pb2, T *ipb2, int ns, int nz, int ny, int nx, int px, T pen, T eps,
-                           T dx, const double *src_pos, cudaStream_t st) {
+                           T dx, const double *src_pos, int unit_b, cudaStream_t st) {
     const long long plane = (long long)nz * ny * px;
     b2_maps_kernel<T><<<dim3(blocks_for(plane, 2048), ns), RT, 0, st>>>(pb2, ipb2, nz, ny, nx, px,
-                                                                        pen, eps, dx, src_pos);
+                                                                        pen, eps, dx, src_pos, unit_b);
     return cudaGetLastError();
 }
 
@@ -409,6 +416,12 @@ cudaError_t launch_cg_alpha(const double *rr, const double *pap, double *alpha, 
 cudaError_t launch_cg_beta(double *rr_old, const double *rr_new, double *beta,
                            const int *active, int ns, cudaStream_t st) {
     cg_beta_kernel<<<(ns + 127) / 128, 128, 0, st>>>(rr_old, rr_new, beta, active, ns);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_sub_from(T *y, const T *x, long long len, cudaStream_t st) {
+    sub_from_kernel<T><<<blocks_for(len, 4096), RT, 0, st>>>(y, x, len);
     return cudaGetLastError();
 }
 
@@ -545,7 +558,8 @@ cudaError_t launch_dft_output(const T *acc, long long sst, int rows, int nx, int
                                              double *, int, const T *, long long, int,           \
                                              cudaStream_t);                                      \
     template cudaError_t launch_b2_maps<T>(T *, T *, int, int, int, int, int, T, T, T,           \
-                                           const double *, cudaStream_t);                        \
+                                           const double *, int, cudaStream_t);                   \
+    template cudaError_t launch_sub_from<T>(T *, const T *, long long, cudaStream_t);            \
     template cudaError_t launch_add_b2p<T>(T *, const T *, int, int, int, int, int, T, T, T,     \
                                            const double *, cudaStream_t);                        \
     template cudaError_t launch_residual<T>(T *, const T *, long long, double *, int,            \

@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(HERE, "libesi.so")
 ESI_OK, ESI_ERR_ARG, ESI_ERR_CFL, ESI_ERR_OOM, ESI_ERR_CUDA = 0, 1, 2, 3, 4
 ESI_ERR_BREAKDOWN, ESI_ERR_TIMEOUT, ESI_ERR_NOT_CONVERGED, ESI_ERR_UNSUPPORTED = 5, 6, 7, 8
 ESI_F32, ESI_F64 = 0, 1
-GRAD_ADJOINT_STATE, GRAD_SADDLE_POINT = 0, 1
+GRAD_ADJOINT_STATE, GRAD_SADDLE_POINT, GRAD_WRI_SADDLE = 0, 1, 2
+GRAD_MODES = {"adjoint": GRAD_ADJOINT_STATE, "saddle": GRAD_SADDLE_POINT, "wri": GRAD_WRI_SADDLE}
 PARAMS = {"c": 0, "v": 1, "m": 2}
 CKPT = {"f32": 0, "f16": 1, "bf16": 2}
 DFT_C64, DFT_C32_HALF = 0, 1
@@ -31,7 +32,7 @@ EXPORTS = ["esi_create", "esi_destroy", "esi_set_stream", "esi_set_velocity", "e
            "esi_get_profile", "esi_forward_noalloc", "esi_normal_apply", "esi_pc_param_count",
            "esi_pc_fallbacks", "esi_pc_pack", "esi_pc_create", "esi_pc_destroy",
            "esi_pc_last_error", "esi_pc_set_params", "esi_pc_get_params", "esi_pc_apply",
-           "esi_pc_grad", "esi_pc_train_step"]
+           "esi_pc_grad", "esi_pc_train_step", "esi_wri_solve"]
 
 
 class EsiGrid(ctypes.Structure):
@@ -100,6 +101,7 @@ def load_library(require_gpu: bool = True) -> ctypes.CDLL:
     L.esi_dft_extract.argtypes = [vp, vp, vp, ctypes.POINTER(d), i, vp, i,
                                   ctypes.POINTER(ctypes.c_float), vp]
     L.esi_cg_solve.argtypes = [vp, d, d, i, vp, vp, i, d, ctypes.POINTER(EsiCgReport)]
+    L.esi_wri_solve.argtypes = [vp, d, d, i, vp, vp, vp, ctypes.POINTER(EsiCgReport)]
     L.esi_pc_load.argtypes = [vp, vp, ctypes.c_size_t]
     L.esi_normal_apply.argtypes = [vp, d, d, vp, vp]
     L.esi_pc_param_count.argtypes = []
@@ -132,7 +134,7 @@ def load_library(require_gpu: bool = True) -> ctypes.CDLL:
                  "esi_pc_set_params", "esi_pc_get_params", "esi_pc_apply", "esi_pc_grad",
                  "esi_pc_train_step",
                  "esi_adjoint", "esi_gradient", "esi_dft_extract", "esi_cg_solve",
-                 "esi_pc_load"):
+                 "esi_pc_load", "esi_wri_solve"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -311,7 +313,7 @@ class Context:
                  param: str = "v", ckpt_every: int = 20, ckpt: str = "f32", beta: float = 0.0,
                  eps: float = 0.0, out=None):
         o = EsiGradOpts()
-        o.mode = GRAD_SADDLE_POINT if mode == "saddle" else GRAD_ADJOINT_STATE
+        o.mode = GRAD_MODES[mode]
         o.param = PARAMS[param]
         o.ckpt_every = int(ckpt_every)
         o.ckpt_kind = CKPT[ckpt]
@@ -343,7 +345,9 @@ class Context:
         return out, (scales.reshape(self.ns, nf) if scales is not None else None)
 
     def cg_solve(self, dobs, lam: float, tol: float, max_iter: int, precond: str = "none",
-                 eps: float = 0.0, out=None, hist: int = 0):
+                 eps: float = 0.0, out=None, hist: int = 0, wri_wavelet=None):
+        """ESI normal equation by Algorithm 1; with wri_wavelet (the point sources f) the WRI
+        system (S^T S + lam I) q = S^T (d - S f) instead (esi_wri_solve)."""
         q = self.empty_field() if out is None else out
         rep = EsiCgReport()
         hist = max(int(hist), int(max_iter))
@@ -352,10 +356,14 @@ class Context:
         rep.max_hist = hist
         rep.iters = its.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
         rep.rel_res = rel.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        st = self._check(self.L.esi_cg_solve(self.h, float(lam), float(tol), int(max_iter),
-                                             _ptr(dobs), _ptr(q), PC[precond], float(eps),
-                                             ctypes.byref(rep)),
-                         allow=(ESI_OK, ESI_ERR_NOT_CONVERGED))
+        if wri_wavelet is not None:
+            call = self.L.esi_wri_solve(self.h, float(lam), float(tol), int(max_iter),
+                                        _ptr(wri_wavelet), _ptr(dobs), _ptr(q), ctypes.byref(rep))
+        else:
+            call = self.L.esi_cg_solve(self.h, float(lam), float(tol), int(max_iter),
+                                       _ptr(dobs), _ptr(q), PC[precond], float(eps),
+                                       ctypes.byref(rep))
+        st = self._check(call, allow=(ESI_OK, ESI_ERR_NOT_CONVERGED))
         report = {"iters": its.copy(), "rel_res": [rel[s, :its[s]].copy() for s in range(self.ns)],
                   "converged": bool(rep.converged), "iters_max": int(rep.iters_max),
                   "ms_matvec": rep.ms_matvec, "ms_vector": rep.ms_vector,

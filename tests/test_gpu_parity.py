@@ -316,3 +316,36 @@ def test_diag_pcg_matches_oracle(prec):
             tol_hist, s
     q, rep = ctx.cg_solve(_dev(d, prec), lam=lam, tol=1e-3, max_iter=60, precond="diag")
     assert rep["converged"] and max(rep["iters"]) < 60
+
+
+# ----------------------------------------------------------------------------- WRI (B = I)
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_wri_cg_and_gradient_match_oracle(prec):
+    """WRI through the same CG (the CG section's "B = I with a different right hand side"):
+    iterates of (S^T S + beta I) q = S^T (d - S f) and the saddle-point gradient with
+    u = A^{-1}(f + q), lambda = beta q, against the oracle, several shots with ragged tiles."""
+    v, geom, p = _ragged_case(nt=80)
+    nt = p["nt"]
+    o, shots = _orc(v, geom, p, vref=float(v.max()))
+    wav = np.stack([synth.ricker(nt, p["dt"], 25.0)] * geom.ns)
+    # observed data with an O(1) residual against S f (data close to S f would leave the
+    # right-hand side S^T (d - S f) as a cancellation-dominated difference)
+    Sf = np.concatenate([o.forward(sh, wavelet=wav[s])["traces"].ravel()
+                         for s, sh in enumerate(shots)])
+    d = Sf + synth.normal(42, Sf.shape) * np.abs(Sf).max()
+    lam, nmax = 0.05, 5
+    ctx = _ctx(v, geom, p, prec, vref=float(v.max()))
+    q, rep = ctx.cg_solve(_dev(d, prec), lam=lam, tol=0.0, max_iter=nmax,
+                          wri_wavelet=_dev(wav, prec))
+    tol = {"f64": 1e-12, "f32": 1e-4}[prec]
+    for s, sh in enumerate(shots):
+        o0, o1 = geom.rec_offset[s], geom.rec_offset[s + 1]
+        ref = o.wri_cg(sh, d[nt * o0:nt * o1].reshape(nt, -1), wav[s], lam, 0.0, nmax)
+        assert rep["iters"][s] == ref["iters"] == nmax, s
+        assert np.allclose(rep["rel_res"][s], ref["rel_res"], rtol=10 * tol, atol=0), s
+        assert oracle.rel_l2(q[s].reshape(nt, -1).double().cpu().numpy(), ref["x"]) <= tol, s
+    g, _ = ctx.gradient(wavelet=_dev(wav, prec), ext=q, mode="wri", beta=lam, param="v")
+    qh = q.double().cpu().numpy()
+    g_ref = sum(o.wri_gradient(sh, qh[s].reshape(nt, -1), wav[s], lam, param="v")
+                for s, sh in enumerate(shots))
+    assert oracle.rel_l2(g.double().cpu().numpy().ravel(), g_ref) <= tol

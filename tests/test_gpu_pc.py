@@ -122,3 +122,28 @@ def test_cg_with_learned_preconditioner_reaches_the_true_residual():
         qs = q[s].reshape(nt, -1).double().cpu().numpy()
         r = b - o.normal_matvec(sh, qs, lam)
         assert np.linalg.norm(r) / np.linalg.norm(b) < 2e-3, s
+
+
+def test_pack_matches_oracle_with_ragged_edges_and_time_padding():
+    """esi_pc_pack: r / (lambda B^2), 16-sample time groups (zero-padded past nt), 2 x 2
+    averages with zero fill at odd edges, BF16 - against the oracle's pack."""
+    from paper_2211_06300_gb300 import esi
+    shape, dx, dt, nt, nb = (23, 37), 10.0, 1e-3, 40, 4     # odd nz, nx; nt = 2.5 groups
+    v = synth.dipping_layers(shape, dx, 3, nlayers=3, vmin=1500, vmax=2500, nanom=1, sigma=30.0)
+    geom = synth.surface_line(2, [105.0, 262.5], 25.0, [np.arange(5.0, 360.0, 10.0)] * 2, 25.0)
+    ctx = esi.Context(torch.tensor(v, dtype=torch.float32, device="cuda"), dx, dt, nt, nb, geom)
+    rng = np.random.default_rng(13)
+    field = rng.standard_normal((2, nt) + shape)
+    lam = 3e-4
+    img = ctx.pc_pack(torch.tensor(field, dtype=torch.float32, device="cuda"), lam=lam,
+                      scale=True).double().cpu().numpy()
+    o = oracle.Oracle(v, dx, dt, nt, nb)
+    ng = (nt + cnn.G - 1) // cnn.G
+    for s in range(2):
+        B = o.annihilator(geom.src_xyz[s]).reshape(shape)
+        sc = np.zeros((ng * cnn.G,) + shape)
+        sc[:nt] = field[s] / (lam * B * B)[None]
+        ref = _bf16(cnn.pack(sc))
+        got = img[s * ng:(s + 1) * ng]
+        assert got.shape == ref.shape
+        assert oracle.rel_l2(got, ref) < 4e-3, s
