@@ -12,8 +12,9 @@ The metric is FD cell-updates per second over every forward and adjoint propagat
 the step (Gcell/s).  Beside it, outside the timed steps: the CG time to 1e-3 of the same
 system with each preconditioner -- none (plain Algorithm 1, capped at --plain-iter
 iterations; the residual it reaches is given when the cap comes first), the diagonal
-z = r / (beta B^2), and the learned network (when its weights are present) -- with the
-device time split into the product, the vector updates and the preconditioner.
+z = r / (beta B^2), and the learned network (when its weights are present) -- and in its
+data-space form, with the device time split into the product, the vector updates and the
+preconditioner.
 
 Multi-GPU: shots are independent systems, so each rank solves its own 16 shots (weak
 scaling) with no collective on the data path; ranks meet only at the timing barriers.
@@ -557,11 +558,29 @@ def main():
     cg_ms = [r["ms_total"] for r in reps]
 
     # CG alone on the same system with each preconditioner (untimed by the steps above)
-    def cg_only(pc, cap):
+    # the true residual ||S^T d - (S^T S + beta B^2) q|| / ||S^T d|| of each solution, on the
+    # first and last shot (a two-shot context keeps the extra memory to a few GB)
+    sel = [0, ns - 1]
+    ctx2 = esi.Context(v0, wl.dx, wl.dt, nt, wl.nb, geom.select(sel), vref=vref)
+    d2 = torch.cat([ctx.traces_of(dobs, s).reshape(-1) for s in sel]).contiguous()
+    b_rhs, _ = ctx2.adjoint(d2)
+
+    def true_rel_res():
+        q2 = q[sel].contiguous()
+        res = ctx2.normal_apply(q2, beta)
+        torch.sub(b_rhs, res, out=res)
+        num = res.reshape(len(sel), -1).norm(dim=1)
+        den = b_rhs.reshape(len(sel), -1).norm(dim=1)
+        del res, q2
+        return float((num / den).max())
+
+    def cg_only(pc, cap, data_space=False):
         torch.cuda.synchronize()
         ctx.set_velocity(v0)
-        _, r = ctx.cg_solve(dobs, lam=beta, tol=args.tol, max_iter=cap, out=q, precond=pc)
+        _, r = ctx.cg_solve(dobs, lam=beta, tol=args.tol, max_iter=cap, out=q, precond=pc,
+                            data_space=data_space)
         return {"iters_max": int(max(r["iters"])), "time_ms": r["ms_total"],
+                "true_rel_res_first_last_shot": true_rel_res(),
                 "reached_tol": bool(r["converged"]),
                 "rel_res_max_over_shots": float(max(x[-1] for x in r["rel_res"] if x.size)),
                 "device_ms": {"product": r["ms_matvec"], "vector": r["ms_vector"],
@@ -570,9 +589,19 @@ def main():
     if args.plain_iter > 0:
         compare["none"] = cg_only("none", args.plain_iter)
     compare["diag"] = cg_only("diag", args.max_iter)
+    # the same ESI system in data space (section "Switching from the wavefield to data space");
+    # its stopping test is on the data-space residual, so it is also run to tol / 10 to
+    # compare at a matching true residual
+    compare["data_space"] = cg_only("none", args.max_iter, data_space=True)
+    tol0 = args.tol
+    args.tol = tol0 / 10
+    compare["data_space_tol_div10"] = cg_only("none", args.max_iter, data_space=True)
+    args.tol = tol0
     if have_pc:
         compare["learned"] = cg_only("learned", args.max_iter)
         compare["learned"]["fallbacks"] = ctx.pc_fallbacks
+    del b_rhs
+    ctx2.close()
     cb = None
     if not args.no_cpu_baseline and world == 1:
         try:

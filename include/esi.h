@@ -244,6 +244,23 @@ ESI_API esi_status esi_cg_solve(esi_ctx *ctx, double lambda, double tol, int max
                                 esi_cg_report *report);
 
 /*
+ * esi_dscg_solve -- the ESI normal equation solved in data space (the section "Switching
+ * from the wavefield to data space"; Eq. "wd", "q"): Algorithm 1 on
+ *   (I + K) w = K d,   K = S (lambda B^2)^{-1} S^T,   B = ||x - x_s|| + eps,
+ * for the synthetic data w, then q = (lambda B^2)^{-1} S^T (d - w).  Each product K p is
+ * one adjoint modelling of p, whose space-time field is kept in context scratch (one
+ * pitched [ns][nt][N] vector), and one forward modelling with that field times
+ * 1/(lambda B^2) as the extended source; the CG vectors are traces-layout data vectors.
+ * Per shot, stopping and frozen shots as in esi_cg_solve (the residual is the data-space
+ * one).  q_out_dev: device [ns][nt][N]; w_out_dev: device traces layout (may be NULL).
+ * Errors and report as esi_cg_solve (ms_matvec: the products, ms_vector: the data-space
+ * vector work).
+ */
+ESI_API esi_status esi_dscg_solve(esi_ctx *ctx, double lambda, double tol, int max_iter,
+                                  const void *dobs_dev, void *q_out_dev, void *w_out_dev,
+                                  double eps, esi_cg_report *report);
+
+/*
  * esi_wri_solve -- WRI by the same CG (the CG section: "B = I with a different right hand
  * side"; Eq. "normalwri"):
  *   (S^T S + lambda I) q = S^T (d - S f),

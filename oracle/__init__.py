@@ -443,6 +443,44 @@ class Oracle:
         mu = -beta * qq / self.c[None, :]
         return self.to_param(np.sum(mu * fw["s"], axis=0), param)
 
+    # ---------------------------------------------------------------- data-space CG
+    # The section "Switching from the wavefield to data space": with w := R u the synthetic
+    # data, Eq. "wd" reads (I + S (beta B^H B)^{-1} S^H) w = S (beta B^H B)^{-1} S^H d, an
+    # SPD system in data space (nr x nt unknowns per shot) solved by CG; then Eq. "q" gives
+    # q = (beta B^H B)^{-1} S^H (d - w).
+    def ds_K(self, sh: Shot, e: np.ndarray, beta: float, eps: Optional[float] = None) -> np.ndarray:
+        """K e = S (beta B^2)^{-1} S^T e: adjoint modelling of e, scaling, forward modelling."""
+        B = self.annihilator(sh.src_xyz, eps)
+        lam = self.ST(sh, np.asarray(e, dtype=np.float64).reshape(self.nt, sh.nr))
+        return self.S(sh, lam / (beta * B * B)[None, :])
+
+    def ds_cg(self, sh: Shot, d: np.ndarray, beta: float, tol: float, n_cg: int,
+              eps: Optional[float] = None) -> Dict:
+        """Algorithm 1 on (I + K) w = K d, then q = (beta B^2)^{-1} S^T (d - w)."""
+        d = np.asarray(d, dtype=np.float64).reshape(self.nt, sh.nr)
+        b = self.ds_K(sh, d, beta, eps)
+        x = np.zeros_like(b)
+        r = b.copy()
+        p = r.copy()
+        rr = float(np.sum(r * r))
+        r0 = math.sqrt(rr)
+        hist = []
+        k = 0
+        for k in range(n_cg):
+            Ap = p + self.ds_K(sh, p, beta, eps)
+            alpha = rr / float(np.sum(p * Ap))
+            x = x + alpha * p
+            r = r - alpha * Ap
+            rr_new = float(np.sum(r * r))
+            hist.append(math.sqrt(rr_new) / r0 if r0 > 0 else 0.0)
+            if math.sqrt(rr_new) < tol * r0 or k == n_cg - 1:
+                break
+            p = r + (rr_new / rr) * p
+            rr = rr_new
+        B = self.annihilator(sh.src_xyz, eps)
+        q = self.ST(sh, d - x) / (beta * B * B)[None, :]
+        return {"w": x, "q": q, "rel_res": np.asarray(hist), "iters": k + 1, "b": b}
+
     def assemble_S(self, sh: Shot) -> np.ndarray:
         """Dense data operator S (columns S e_j over space-time; tiny sizes only)."""
         n = self.nt * self.N

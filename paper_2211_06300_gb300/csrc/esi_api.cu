@@ -98,6 +98,7 @@ struct esi_ctx {
     DBuf pc_dev;                   // learned-PCG dot partials, sums and per-shot theta
     DBuf dftsnap;                  // blocked DTFT: DFT_BLOCK new states [slot][ns][sst]
     DBuf wri_res;                  // WRI: data residual d - S f [traces]
+    DBuf dsv, dseg;                // data-space CG: 5 data vectors; shot segments
     int pc_batch = 0;
     DBuf ckpt, ckpt_scale, absbits, stash, gacc, twid, dftacc;
     long long total_rec = 0;
@@ -130,6 +131,11 @@ struct esi_ctx {
     std::vector<GraphEntry> graphs;
     cudaStream_t cap = nullptr;
     bool use_graphs = true;
+    // 2D CG product halves by the persistent TMA-fed kernel (fd2cg.cu): off by default -- with
+    // 52 KB stages two blocks fit per SM and keep one tile in flight each, which measured
+    // slower than the one-tile-per-block kernel (18.3 / 19.7 us against 14.1 / 17.2 us per
+    // step of 16 shots of 801 x 241); ESI_TMA_CG=1 selects it
+    bool tma_cg = false;
     unsigned long long graph_clock = 0;
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> evpool;
@@ -437,7 +443,10 @@ namespace {
 //   kind 0, a state buffer with the halo box: 2D [ns][nz][px] as dims (nx, nz, ns), box
 //     (SW2, SH2, 1); 3D [ns][nz][ny][px] as dims (nx, ny, nz, ns), box (SW3, SH3, 1, 1);
 //   kind 1, a 3D state buffer with the tile-interior box (TX3, TY3, 1, 1);
-//   kind 2, the 3D array c [nz][ny][px] as dims (nx, ny, nz), box (TX3, TY3, 1).
+//   kind 2, the 3D array c [nz][ny][px] as dims (nx, ny, nz), box (TX3, TY3, 1);
+//   2D tile-interior boxes (TX2, TZ2) of the CG-product streams: kind 3, a per-shot array
+//   [ns][nz][px] (states, lambda B^2 maps); kind 4, c [nz][px]; kind 5, a space-time vector
+//   [ns][nt][nz][px] as dims (nx, nz, nt, ns).
 bool state_map(esi_ctx *ctx, const void *base, CUtensorMap *out, int kind = 0) {
     for (auto &m : ctx->tmaps)
         if (m.base == base && m.kind == kind) {
@@ -453,11 +462,21 @@ bool state_map(esi_ctx *ctx, const void *base, CUtensorMap *out, int kind = 0) {
     cuuint64_t str[3];
     cuuint32_t box[4];
     cuuint32_t rank;
-    if (ctx->g.ndim == 2) {
+    if (ctx->g.ndim == 2 && kind == 4) {
+        rank = 2;
+        dims[0] = nx, dims[1] = nz;
+        str[0] = row;
+        box[0] = TX2, box[1] = TZ2;
+    } else if (ctx->g.ndim == 2 && kind == 5) {
+        rank = 4;
+        dims[0] = nx, dims[1] = nz, dims[2] = (cuuint64_t)ctx->nt, dims[3] = ns;
+        str[0] = row, str[1] = shot, str[2] = shot * (cuuint64_t)ctx->nt;
+        box[0] = TX2, box[1] = TZ2, box[2] = 1, box[3] = 1;
+    } else if (ctx->g.ndim == 2) {
         rank = 3;
         dims[0] = nx, dims[1] = nz, dims[2] = ns;
         str[0] = row, str[1] = shot;
-        box[0] = SW2, box[1] = SH2, box[2] = 1;
+        box[0] = kind == 3 ? TX2 : SW2, box[1] = kind == 3 ? TZ2 : SH2, box[2] = 1;
     } else if (kind == 2) {
         rank = 3;
         dims[0] = nx, dims[1] = ny, dims[2] = nz;
@@ -515,7 +534,21 @@ esi_status step(esi_ctx *ctx, unsigned flags, const StepArgs<T> &a) {
     if (!state_map(ctx, a.cur, &b.tm) ||
         (ctx->g.ndim == 3 && (!state_map(ctx, a.po, &b.tm_old, 1) || !state_map(ctx, a.cc, &b.tm_cc, 2))))
         return ctx->fail(ESI_ERR_CUDA, "cuTensorMapEncodeTiled failed for a state buffer");
-    if (ctx->g.ndim == 2) {
+    if (ctx->g.ndim == 2 && ctx->tma_cg &&
+        (flags == (F_CGP | F_SMP) || flags == (F_PT | F_AP))) {
+        // the CG product halves: every stream by TMA (tile-interior boxes)
+        const bool fwd = flags == (F_CGP | F_SMP);
+        bool ok = state_map(ctx, a.po, &b.tm_old, 3) && state_map(ctx, a.cc, &b.tm_cc, 4);
+        if (fwd) {
+            ok = ok && state_map(ctx, a.cg_r, &b.tm_a, 5) &&
+                 (a.cg_first || state_map(ctx, a.cg_p, &b.tm_c, 5)) &&
+                 (!(a.cg_pc > T(0)) || state_map(ctx, a.ipb2, &b.tm_b, 3));
+        } else {
+            ok = ok && state_map(ctx, a.ap_p, &b.tm_a, 5) && state_map(ctx, a.pb2, &b.tm_b, 3);
+        }
+        if (!ok) return ctx->fail(ESI_ERR_CUDA, "cuTensorMapEncodeTiled failed for a CG stream");
+        CKL(launch_step2_cg<T>(flags, b, ctx->ns, ctx->st));
+    } else if (ctx->g.ndim == 2) {
         CKL(launch_step2<T>(flags, b, ctx->ns, ctx->st));
     } else {
         if ((flags & F_SMP) && a.tout >= 0)
@@ -952,13 +985,14 @@ esi_status adj_loop(esi_ctx *ctx, StepArgs<T> a, unsigned flags, T *&cur, T *&po
 
 template <typename T>
 esi_status adjoint_impl(esi_ctx *ctx, const void *traces, void *ext_out, void *wav_out,
-                        bool pitched_out = false) {
+                        bool pitched_out = false, const int *active = nullptr) {
     ctx->prof_active = ctx->ns;
     esi_status e = ensure_states<T>(ctx, true);
     if (e != ESI_OK) return e;
     CK(cudaMemsetAsync(ctx->a0.p, 0, ctx->a0.n, ctx->st));
     CK(cudaMemsetAsync(ctx->a1.p, 0, ctx->a1.n, ctx->st));
     StepArgs<T> a = base_args<T>(ctx);
+    a.active = active;
     unsigned flags = F_PT;
     a.inj = inj_view<T>(ctx->inj_rec);
     a.inj_trace = reinterpret_cast<const T *>(traces);
@@ -1499,6 +1533,179 @@ esi_status cg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const 
     return conv ? ESI_OK : ESI_ERR_NOT_CONVERGED;
 }
 
+// ------------------------------------------------------------------ data-space CG
+// The section "Switching from the wavefield to data space": Algorithm 1 on Eq. "wd",
+//   (I + K) w = K d,   K = S (lambda B^2)^{-1} S^T,
+// for the synthetic data w (traces layout), then Eq. "q": q = (lambda B^2)^{-1} S^T (d - w).
+// K e is one adjoint modelling of e (its space-time field kept in a pitched context buffer)
+// and one forward modelling with that field times 1/(lambda B^2) as the extended source
+// (the CG forward-half kernel with p = z = r / (lambda B^2), sampling at the receivers).
+// The CG vectors are data vectors: per iteration no pass over space-time vectors remains
+// besides the product's own field.  The nonzero spectrum of I + K is that of the diagonally
+// preconditioned wavefield system, so the iteration counts match the diagonal PCG.
+template <typename T>
+esi_status dscg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const void *dobs,
+                     void *q_out, void *w_out, double eps_in, esi_cg_report *rep) {
+    using clk = std::chrono::steady_clock;
+    const auto t_start = clk::now();
+    const int ns = ctx->ns, nt = ctx->nt;
+    if (!(lambda > 0)) return ctx->fail(ESI_ERR_ARG, "the data-space form needs lambda > 0");
+    if (max_iter < 1) return ctx->fail(ESI_ERR_ARG, "max_iter must be >= 1");
+    esi_status e = ensure_states<T>(ctx, true);
+    if (e != ESI_OK) return e;
+    const long long plen = ctx->sst * nt;
+    const long long dl = (long long)ctx->total_rec * nt;      // data vector length
+    CK(ctx->cg_r.ensure((size_t)ns * plen * sizeof(T)));       // the adjoint field S^T e
+    CK(ctx->cg_p.ensure((size_t)ns * plen * sizeof(T)));       // the scaled source (written)
+    CK(ctx->dsv.ensure((size_t)5 * std::max<long long>(dl, 4) * sizeof(T)));
+    T *F = ctx->cg_r.as<T>(), *Fs = ctx->cg_p.as<T>();
+    T *x = ctx->dsv.as<T>(), *r = x + dl, *p = r + dl, *kp = p + dl, *db = kp + dl;
+    const T eps = T(eps_in > 0 ? eps_in : ctx->g.dx);
+    CK(ctx->pb2.ensure((size_t)ns * ctx->sst * sizeof(T)));
+    CK(ctx->ipb2.ensure((size_t)ns * ctx->sst * sizeof(T)));
+    T *ipb2 = ctx->ipb2.as<T>();
+    CKL(launch_b2_maps<T>(ctx->pb2.as<T>(), ipb2, ns, ctx->g.nz, ctx->g.ny, ctx->g.nx, ctx->px,
+                          T(lambda), eps, T(ctx->g.dx), ctx->src_pos.as<double>(), 0, ctx->st));
+    // shot segments of the data vectors
+    std::vector<long long> seg(ns + 1);
+    for (int s = 0; s <= ns; ++s) seg[s] = ctx->rec_off[s] * (long long)nt;
+    CK(upload(ctx->dseg, seg, ctx->st));
+    const long long *dseg = ctx->dseg.as<long long>();
+    const int nb = DVEC_NBLK;
+    CK(ctx->part.ensure(sizeof(double) * (size_t)ns * nb));
+    // device scalars: rr[ns] pap[ns] alpha[ns] beta[ns] rrn[ns] | active[ns] bad[ns]
+    CK(ctx->scal.ensure(sizeof(double) * 5 * ns + sizeof(int) * 2 * ns));
+    double *rr = ctx->scal.as<double>(), *pap = rr + ns, *alpha = pap + ns, *beta = alpha + ns,
+           *rrn = beta + ns;
+    int *active = reinterpret_cast<int *>(rrn + ns), *bad = active + ns;
+    CK(cudaMemsetAsync(active, 0xff, sizeof(int) * ns, ctx->st));
+    CK(cudaMemsetAsync(bad, 0, sizeof(int) * ns, ctx->st));
+    // out = K e for the active shots
+    auto apply_K = [&](const T *ein, T *out) -> esi_status {
+        esi_status st = adjoint_impl<T>(ctx, ein, F, nullptr, true, active);
+        if (st != ESI_OK) return st;
+        CK(cudaMemsetAsync(ctx->u0.p, 0, ctx->u0.n, ctx->st));
+        CK(cudaMemsetAsync(ctx->u1.p, 0, ctx->u1.n, ctx->st));
+        StepArgs<T> a = base_args<T>(ctx);
+        a.active = active;
+        a.cg_r = F;
+        a.cg_p = Fs;
+        a.cg_beta = beta;
+        a.cg_first = 1;           // p = z = F / (lambda B^2)
+        a.cg_pc = T(lambda);
+        a.ipb2 = ipb2;
+        a.eps = eps;
+        a.smp = smp_view<T>(ctx->smp_rec);
+        a.smp_out = out;
+        T *cur = ctx->u0.as<T>(), *po = ctx->u1.as<T>();
+        st = fwd_loop<T>(ctx, a, F_CGP | F_SMP, cur, po, 0, nt);
+        if (st != ESI_OK) return st;
+        CKL(launch_sample_global<T>(a.smp, cur, ctx->sst, out, nt - 1, ctx->st));
+        return ESI_OK;
+    };
+    // right-hand side K d; x0 = 0, r0 = p0 = K d
+    e = apply_K(reinterpret_cast<const T *>(dobs), db);
+    if (e != ESI_OK) return e;
+    CK(cudaMemsetAsync(x, 0, dl * sizeof(T), ctx->st));
+    CK(cudaMemcpyAsync(r, db, dl * sizeof(T), cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaMemcpyAsync(p, db, dl * sizeof(T), cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaMemsetAsync(alpha, 0, sizeof(double) * ns, ctx->st));
+    CKL(launch_dvec_update<T>(x, r, p, p, dseg, alpha, nullptr, ctx->part.as<double>(), ns, ctx->st));
+    CKL(launch_reduce_partials(ctx->part.as<double>(), nb, ns, rr, ctx->st));
+    std::vector<double> rr0(ns), h_rrn(ns);
+    std::vector<int> h_active(ns, 1), h_bad(ns, 0), iters(ns, 0);
+    std::vector<char> h_conv(ns, 0);
+    CK(cudaMemcpyAsync(rr0.data(), rr, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    for (int s = 0; s < ns; ++s)
+        if (!(rr0[s] > 0)) h_active[s] = 0;
+    CK(cudaMemcpyAsync(active, h_active.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, ctx->st));
+    const int hist_cap = rep ? rep->max_hist : 0;
+    double ms_mv = 0, ms_vec = 0;
+    struct Events {
+        cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+        ~Events() {
+            for (auto z : e)
+                if (z) cudaEventDestroy(z);
+        }
+    } ev;
+    for (auto &z : ev.e) CK(cudaEventCreate(&z));
+    bool any_bad = false;
+    for (int k = 0; k < max_iter; ++k) {
+        ctx->prof_active = 0;
+        for (int s = 0; s < ns; ++s) ctx->prof_active += h_active[s];
+        CK(cudaEventRecord(ev.e[0], ctx->st));
+        e = apply_K(p, kp);                                      // kp = K p
+        if (e != ESI_OK) return e;
+        CK(cudaEventRecord(ev.e[1], ctx->st));
+        CKL(launch_dvec_ident_dot<T>(kp, p, dseg, active, ctx->part.as<double>(), ns, ctx->st));
+        CKL(launch_reduce_partials(ctx->part.as<double>(), nb, ns, pap, ctx->st));
+        CKL(launch_cg_alpha(rr, pap, alpha, bad, active, ns, ctx->st));
+        CKL(launch_dvec_update<T>(x, r, p, kp, dseg, alpha, active, ctx->part.as<double>(), ns, ctx->st));
+        CKL(launch_reduce_partials(ctx->part.as<double>(), nb, ns, rrn, ctx->st));
+        CK(cudaEventRecord(ev.e[2], ctx->st));
+        CK(cudaMemcpyAsync(h_rrn.data(), rrn, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaMemcpyAsync(h_bad.data(), bad, sizeof(int) * ns, cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        if ((e = check_dev_err(ctx)) != ESI_OK) return e;
+        float m01 = 0, m12 = 0;
+        CK(cudaEventElapsedTime(&m01, ev.e[0], ev.e[1]));
+        CK(cudaEventElapsedTime(&m12, ev.e[1], ev.e[2]));
+        ms_mv += m01;
+        ms_vec += m12;
+        bool any = false;
+        for (int s = 0; s < ns; ++s) {
+            if (!h_active[s]) continue;
+            if (h_bad[s]) {
+                any_bad = true;
+                h_active[s] = 0;
+                continue;
+            }
+            iters[s] = k + 1;
+            if (rep && rep->rel_res && k < hist_cap)
+                rep->rel_res[(size_t)s * hist_cap + k] = std::sqrt(h_rrn[s] / rr0[s]);
+            const bool met = std::sqrt(h_rrn[s]) < tol * std::sqrt(rr0[s]);
+            h_conv[s] = met;
+            if (met || k == max_iter - 1)
+                h_active[s] = 0;   // Algorithm 1's stopping test, per shot
+            else
+                any = true;
+        }
+        if (!any) break;
+        CK(cudaMemcpyAsync(active, h_active.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, ctx->st));
+        CKL(launch_cg_beta(rr, rrn, beta, active, ns, ctx->st));
+        CKL(launch_dvec_xpby<T>(p, r, dseg, beta, active, ns, ctx->st));
+    }
+    // q = (lambda B^2)^{-1} S^T (d - w), every shot
+    CK(cudaMemsetAsync(active, 0xff, sizeof(int) * ns, ctx->st));
+    CK(cudaMemcpyAsync(r, x, dl * sizeof(T), cudaMemcpyDeviceToDevice, ctx->st));
+    CKL(launch_sub_from<T>(r, reinterpret_cast<const T *>(dobs), dl, ctx->st));
+    e = adjoint_impl<T>(ctx, r, F, nullptr, true);
+    if (e != ESI_OK) return e;
+    CKL(launch_scale_to_dense<T>(reinterpret_cast<T *>(q_out), F, ipb2, ns, nt,
+                                 ctx->g.nz * ctx->g.ny, ctx->g.nx, ctx->px, ctx->sst, ctx->st));
+    if (w_out)
+        CK(cudaMemcpyAsync(w_out, x, dl * sizeof(T), cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    bool conv = true;
+    int mx = 0;
+    for (int s = 0; s < ns; ++s) {
+        if (rr0[s] > 0 && !(iters[s] > 0 && h_conv[s])) conv = false;
+        mx = std::max(mx, iters[s]);
+    }
+    if (rep) {
+        for (int s = 0; s < ns && rep->iters; ++s) rep->iters[s] = iters[s];
+        rep->iters_max = mx;
+        rep->converged = conv ? 1 : 0;
+        rep->ms_matvec = ms_mv;
+        rep->ms_vector = ms_vec;
+        rep->ms_precond = 0;
+        rep->ms_total = std::chrono::duration<double, std::milli>(clk::now() - t_start).count();
+    }
+    if (any_bad) return ctx->fail(ESI_ERR_BREAKDOWN, "CG breakdown: p^T (I + K) p <= 0 or non-finite");
+    return conv ? ESI_OK : ESI_ERR_NOT_CONVERGED;
+}
+
 template <typename T>
 esi_status create_impl(esi_ctx *ctx, const void *vel) {
     CK(ctx->dev_err.ensure(sizeof(int)));
@@ -1632,6 +1839,7 @@ ESI_API esi_status esi_create(esi_ctx **out, const esi_grid *grid, const esi_geo
         ctx->ntiles = ctx->ntx * ctx->nty * ctx->nzc;
     }
     if (const char *ev = std::getenv("ESI_NO_GRAPHS")) ctx->use_graphs = ev[0] == '0';
+    if (const char *ev = std::getenv("ESI_TMA_CG")) ctx->tma_cg = ev[0] == '1';
     esi_ctx *c = ctx.get();
     {
         esi_ctx *ctx = c;  // for CK
@@ -1720,6 +1928,20 @@ ESI_API esi_status esi_dft_extract(esi_ctx *ctx, const void *wavelet_dev, const 
                                   scales_host, traces_dev)
                : dft_impl<float>(ctx, wavelet_dev, ext_src_dev, freqs_hz, nf, out_dev, out_kind,
                                  scales_host, traces_dev);
+}
+
+ESI_API esi_status esi_dscg_solve(esi_ctx *ctx, double lambda, double tol, int max_iter,
+                                  const void *dobs_dev, void *q_out_dev, void *w_out_dev,
+                                  double eps, esi_cg_report *report) {
+    if (!ctx) return ESI_ERR_ARG;
+    if (!dobs_dev || !q_out_dev || !(lambda > 0) || !(tol >= 0))
+        return ctx->fail(ESI_ERR_ARG, "bad data-space CG arguments");
+    ctx->err.clear();
+    return ctx->g.dtype == ESI_F64
+               ? dscg_impl<double>(ctx, lambda, tol, max_iter, dobs_dev, q_out_dev, w_out_dev, eps,
+                                   report)
+               : dscg_impl<float>(ctx, lambda, tol, max_iter, dobs_dev, q_out_dev, w_out_dev, eps,
+                                  report);
 }
 
 ESI_API esi_status esi_wri_solve(esi_ctx *ctx, double lambda, double tol, int max_iter,

@@ -92,8 +92,9 @@ template <typename T>
 struct StepArgs {
     CUtensorMap tm;            // TMA map of the input state: 2D box (SW2, SH2, 1), 3D box
                                // (SW3, SH3, 1, 1) (one tile with its halo)
-    CUtensorMap tm_old;        // 3D: the older state, box (TX3, TY3, 1, 1) (tile interior)
-    CUtensorMap tm_cc;         // 3D: c = v^2 dt^2 / dx^2, box (TX3, TY3, 1)
+    CUtensorMap tm_old;        // the older state, tile-interior box (3D; 2D CG product)
+    CUtensorMap tm_cc;         // c = v^2 dt^2 / dx^2, tile-interior box (3D; 2D CG product)
+    CUtensorMap tm_a, tm_b, tm_c;   // 2D CG product: its space-time / per-shot streams
     int *dev_err;              // sticky device error word (bounded waits that gave up)
     int nz, ny, nx, px;        // grid and pitch (elements) of the state arrays
     long long sst;             // pitched plane (= shot stride of state arrays)
@@ -166,6 +167,10 @@ template <typename T>
 cudaError_t launch_step2(unsigned flags, const StepArgs<T> &a, int ns, cudaStream_t st);
 template <typename T>
 cudaError_t launch_step3(unsigned flags, const StepArgs<T> &a, int ns, cudaStream_t st);
+// the two CG-product variants of the 2D step (F_CGP | F_SMP, F_PT | F_AP), persistent and
+// TMA-fed (the StepArgs carry the tile-interior maps of every stream)
+template <typename T>
+cudaError_t launch_step2_cg(unsigned flags, const StepArgs<T> &a, int ns, cudaStream_t st);
 
 // sample a whole state (global memory) for every receiver of a list at time tout
 template <typename T>
@@ -201,6 +206,23 @@ cudaError_t launch_b2_maps(T *pb2, T *ipb2, int ns, int nz, int ny, int nx, int 
 // y = x - y over len elements
 template <typename T>
 cudaError_t launch_sub_from(T *y, const T *x, long long len, cudaStream_t st);
+// data-space CG vectors (traces layout; shot s owns [seg[s], seg[s+1])), partials [ns][64]:
+// ap = p + kp in place over kp with <p, ap>; x += alpha p, r -= alpha ap with ||r||^2; p = r + beta p
+constexpr int DVEC_NBLK = 64;
+template <typename T>
+cudaError_t launch_dvec_ident_dot(T *kp, const T *p, const long long *seg, const int *active,
+                                  double *part, int ns, cudaStream_t st);
+template <typename T>
+cudaError_t launch_dvec_update(T *x, T *r, const T *p, const T *ap, const long long *seg,
+                               const double *alpha, const int *active, double *part, int ns,
+                               cudaStream_t st);
+template <typename T>
+cudaError_t launch_dvec_xpby(T *p, const T *r, const long long *seg, const double *beta,
+                             const int *active, int ns, cudaStream_t st);
+// q[s][t][N] (dense) = f[s][t][pitched] * ipb2[s][pitched]
+template <typename T>
+cudaError_t launch_scale_to_dense(T *q, const T *f, const T *ipb2, int ns, int nt, int rows,
+                                  int nx, int px, long long sst, cudaStream_t st);
 // alpha = rr / pAp ; flags breakdown
 cudaError_t launch_cg_alpha(const double *rr, const double *pap, double *alpha, int *bad,
                             const int *active, int ns, cudaStream_t st);

@@ -175,6 +175,70 @@ __global__ void cg_beta_kernel(double *rr_old, const double *rr_new, double *bet
     rr_old[s] = rr_new[s];
 }
 
+// ---- data-space CG vectors: one flat traces-layout array, shot s owning [seg[s], seg[s+1])
+// ap = p + kp (in place over kp) with per-shot partials of <p, ap>
+template <typename T>
+__global__ void dvec_ident_dot_kernel(T *kp, const T *p, const long long *seg, const int *active,
+                                      double *part) {
+    const int s = blockIdx.y;
+    if (active && !active[s]) return;
+    double acc = 0.0;
+    for (long long i = seg[s] + (long long)blockIdx.x * RT + threadIdx.x; i < seg[s + 1];
+         i += (long long)gridDim.x * RT) {
+        const T a = p[i] + kp[i];
+        kp[i] = a;
+        acc += double(p[i]) * double(a);
+    }
+    const double t = block_sum_d(acc);
+    if (threadIdx.x == 0) part[(long long)s * gridDim.x + blockIdx.x] = t;
+}
+
+// x += alpha p, r -= alpha ap, per-shot partials of ||r||^2
+template <typename T>
+__global__ void dvec_update_kernel(T *x, T *r, const T *p, const T *ap, const long long *seg,
+                                   const double *alpha, const int *active, double *part) {
+    const int s = blockIdx.y;
+    if (active && !active[s]) return;
+    const T al = T(alpha[s]);
+    double acc = 0.0;
+    for (long long i = seg[s] + (long long)blockIdx.x * RT + threadIdx.x; i < seg[s + 1];
+         i += (long long)gridDim.x * RT) {
+        x[i] += al * p[i];
+        const T rv = r[i] - al * ap[i];
+        r[i] = rv;
+        acc += double(rv) * double(rv);
+    }
+    const double t = block_sum_d(acc);
+    if (threadIdx.x == 0) part[(long long)s * gridDim.x + blockIdx.x] = t;
+}
+
+// p = r + beta p
+template <typename T>
+__global__ void dvec_xpby_kernel(T *p, const T *r, const long long *seg, const double *beta,
+                                 const int *active) {
+    const int s = blockIdx.y;
+    if (active && !active[s]) return;
+    const T b = T(beta[s]);
+    for (long long i = seg[s] + (long long)blockIdx.x * RT + threadIdx.x; i < seg[s + 1];
+         i += (long long)gridDim.x * RT)
+        p[i] = r[i] + b * p[i];
+}
+
+// q[s][t][cell] (caller dense) = f[s][t][pitched cell] * ipb2[s][pitched cell]
+template <typename T>
+__global__ void scale_to_dense_kernel(T *q, const T *f, const T *ipb2, int nt, int rows, int nx,
+                                      int px, long long sst) {
+    const int s = blockIdx.y;
+    const long long N = (long long)rows * nx, len = N * nt;
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < len;
+         i += (long long)gridDim.x * RT) {
+        const long long t = i / N, c = i - t * N;
+        const long long row = c / nx;
+        const long long pc = row * px + (c - row * nx);
+        q[(long long)s * len + i] = f[((long long)s * nt + t) * sst + pc] * ipb2[(long long)s * sst + pc];
+    }
+}
+
 template <typename T>
 __global__ void sub_from_kernel(T *y, const T *x, long long len) {
     for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < len;
@@ -420,6 +484,36 @@ cudaError_t launch_cg_beta(double *rr_old, const double *rr_new, double *beta,
 }
 
 template <typename T>
+cudaError_t launch_dvec_ident_dot(T *kp, const T *p, const long long *seg, const int *active,
+                                  double *part, int ns, cudaStream_t st) {
+    dvec_ident_dot_kernel<T><<<dim3(DVEC_NBLK, ns), RT, 0, st>>>(kp, p, seg, active, part);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_dvec_update(T *x, T *r, const T *p, const T *ap, const long long *seg,
+                               const double *alpha, const int *active, double *part, int ns,
+                               cudaStream_t st) {
+    dvec_update_kernel<T><<<dim3(DVEC_NBLK, ns), RT, 0, st>>>(x, r, p, ap, seg, alpha, active, part);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_dvec_xpby(T *p, const T *r, const long long *seg, const double *beta,
+                             const int *active, int ns, cudaStream_t st) {
+    dvec_xpby_kernel<T><<<dim3(DVEC_NBLK, ns), RT, 0, st>>>(p, r, seg, beta, active);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_scale_to_dense(T *q, const T *f, const T *ipb2, int ns, int nt, int rows,
+                                  int nx, int px, long long sst, cudaStream_t st) {
+    scale_to_dense_kernel<T><<<dim3(blocks_for((long long)rows * nx * nt, 4096), ns), RT, 0, st>>>(
+        q, f, ipb2, nt, rows, nx, px, sst);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_sub_from(T *y, const T *x, long long len, cudaStream_t st) {
     sub_from_kernel<T><<<blocks_for(len, 4096), RT, 0, st>>>(y, x, len);
     return cudaGetLastError();
@@ -560,6 +654,15 @@ cudaError_t launch_dft_output(const T *acc, long long sst, int rows, int nx, int
     template cudaError_t launch_b2_maps<T>(T *, T *, int, int, int, int, int, T, T, T,           \
                                            const double *, int, cudaStream_t);                   \
     template cudaError_t launch_sub_from<T>(T *, const T *, long long, cudaStream_t);            \
+    template cudaError_t launch_dvec_ident_dot<T>(T *, const T *, const long long *, const int *, \
+                                                  double *, int, cudaStream_t);                  \
+    template cudaError_t launch_dvec_update<T>(T *, T *, const T *, const T *, const long long *, \
+                                               const double *, const int *, double *, int,       \
+                                               cudaStream_t);                                    \
+    template cudaError_t launch_dvec_xpby<T>(T *, const T *, const long long *, const double *,   \
+                                             const int *, int, cudaStream_t);                    \
+    template cudaError_t launch_scale_to_dense<T>(T *, const T *, const T *, int, int, int, int,  \
+                                                  int, long long, cudaStream_t);                 \
     template cudaError_t launch_add_b2p<T>(T *, const T *, int, int, int, int, int, T, T, T,     \
                                            const double *, cudaStream_t);                        \
     template cudaError_t launch_residual<T>(T *, const T *, long long, double *, int,            \

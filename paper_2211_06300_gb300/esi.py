@@ -32,7 +32,7 @@ EXPORTS = ["esi_create", "esi_destroy", "esi_set_stream", "esi_set_velocity", "e
            "esi_get_profile", "esi_forward_noalloc", "esi_normal_apply", "esi_pc_param_count",
            "esi_pc_fallbacks", "esi_pc_pack", "esi_pc_create", "esi_pc_destroy",
            "esi_pc_last_error", "esi_pc_set_params", "esi_pc_get_params", "esi_pc_apply",
-           "esi_pc_grad", "esi_pc_train_step", "esi_wri_solve"]
+           "esi_pc_grad", "esi_pc_train_step", "esi_wri_solve", "esi_dscg_solve"]
 
 
 class EsiGrid(ctypes.Structure):
@@ -102,6 +102,7 @@ def load_library(require_gpu: bool = True) -> ctypes.CDLL:
                                   ctypes.POINTER(ctypes.c_float), vp]
     L.esi_cg_solve.argtypes = [vp, d, d, i, vp, vp, i, d, ctypes.POINTER(EsiCgReport)]
     L.esi_wri_solve.argtypes = [vp, d, d, i, vp, vp, vp, ctypes.POINTER(EsiCgReport)]
+    L.esi_dscg_solve.argtypes = [vp, d, d, i, vp, vp, vp, d, ctypes.POINTER(EsiCgReport)]
     L.esi_pc_load.argtypes = [vp, vp, ctypes.c_size_t]
     L.esi_normal_apply.argtypes = [vp, d, d, vp, vp]
     L.esi_pc_param_count.argtypes = []
@@ -134,7 +135,7 @@ def load_library(require_gpu: bool = True) -> ctypes.CDLL:
                  "esi_pc_set_params", "esi_pc_get_params", "esi_pc_apply", "esi_pc_grad",
                  "esi_pc_train_step",
                  "esi_adjoint", "esi_gradient", "esi_dft_extract", "esi_cg_solve",
-                 "esi_pc_load", "esi_wri_solve"):
+                 "esi_pc_load", "esi_wri_solve", "esi_dscg_solve"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -345,9 +346,11 @@ class Context:
         return out, (scales.reshape(self.ns, nf) if scales is not None else None)
 
     def cg_solve(self, dobs, lam: float, tol: float, max_iter: int, precond: str = "none",
-                 eps: float = 0.0, out=None, hist: int = 0, wri_wavelet=None):
+                 eps: float = 0.0, out=None, hist: int = 0, wri_wavelet=None,
+                 data_space: bool = False, w_out=None):
         """ESI normal equation by Algorithm 1; with wri_wavelet (the point sources f) the WRI
-        system (S^T S + lam I) q = S^T (d - S f) instead (esi_wri_solve)."""
+        system (S^T S + lam I) q = S^T (d - S f) instead (esi_wri_solve); with data_space the
+        ESI system through the data-space form (esi_dscg_solve; w_out receives w)."""
         q = self.empty_field() if out is None else out
         rep = EsiCgReport()
         hist = max(int(hist), int(max_iter))
@@ -356,7 +359,11 @@ class Context:
         rep.max_hist = hist
         rep.iters = its.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
         rep.rel_res = rel.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        if wri_wavelet is not None:
+        if data_space:
+            call = self.L.esi_dscg_solve(self.h, float(lam), float(tol), int(max_iter),
+                                         _ptr(dobs), _ptr(q), _ptr(w_out), float(eps),
+                                         ctypes.byref(rep))
+        elif wri_wavelet is not None:
             call = self.L.esi_wri_solve(self.h, float(lam), float(tol), int(max_iter),
                                         _ptr(wri_wavelet), _ptr(dobs), _ptr(q), ctypes.byref(rep))
         else:

@@ -289,8 +289,11 @@ def test_single_step_and_corner_points():
     assert np.allclose(ctx.traces_of(d, 0).cpu().numpy(), ref, rtol=1e-13, atol=1e-300)
 
 
+@pytest.mark.parametrize("tma_cg", [False, True])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_diag_pcg_matches_oracle(prec):
+def test_diag_pcg_matches_oracle(prec, tma_cg, monkeypatch):
+    # tma_cg: the CG product halves by the persistent TMA-fed kernel (ESI_TMA_CG=1)
+    monkeypatch.setenv("ESI_TMA_CG", "1" if tma_cg else "0")
     v, geom, p = _ragged_case(nt=80)
     geom.rec_xyz[geom.rec_offset[1]] = (geom.src_xyz[1, 0] + 55.0, 0.0, 30.0)
     o, shots = _orc(v, geom, p)
@@ -349,3 +352,31 @@ def test_wri_cg_and_gradient_match_oracle(prec):
     g_ref = sum(o.wri_gradient(sh, qh[s].reshape(nt, -1), wav[s], lam, param="v")
                 for s, sh in enumerate(shots))
     assert oracle.rel_l2(g.double().cpu().numpy().ravel(), g_ref) <= tol
+
+
+# ----------------------------------------------------------------------------- data-space CG
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_data_space_cg_matches_oracle(prec):
+    """The data-space form of the ESI solve (Eq. "wd", "q"): iterates of (I + K) w = K d and
+    the extended source q = (beta B^2)^{-1} S^T (d - w) against the oracle, several shots."""
+    v, geom, p = _ragged_case(nt=80)
+    geom.rec_xyz[geom.rec_offset[1]] = (geom.src_xyz[1, 0] + 55.0, 0.0, 30.0)
+    nt = p["nt"]
+    o, shots = _orc(v, geom, p)
+    wav = np.stack([synth.ricker(nt, p["dt"], 25.0)] * geom.ns)
+    d = np.concatenate([o.forward(sh, wavelet=wav[s])["traces"].ravel()
+                        for s, sh in enumerate(shots)])
+    lam, nmax = 2e-4, 5
+    ctx = _ctx(v, geom, p, prec)
+    w = torch.empty(d.size, dtype=_tdt(prec), device="cuda")
+    q, rep = ctx.cg_solve(_dev(d, prec), lam=lam, tol=0.0, max_iter=nmax, data_space=True,
+                          w_out=w)
+    tol = {"f64": 1e-12, "f32": 1e-4}[prec]
+    wh = w.double().cpu().numpy()
+    for s, sh in enumerate(shots):
+        o0, o1 = geom.rec_offset[s], geom.rec_offset[s + 1]
+        ref = o.ds_cg(sh, d[nt * o0:nt * o1].reshape(nt, -1), lam, 0.0, nmax)
+        assert rep["iters"][s] == ref["iters"] == nmax, s
+        assert np.allclose(rep["rel_res"][s], ref["rel_res"], rtol=10 * tol, atol=0), s
+        assert oracle.rel_l2(wh[nt * o0:nt * o1].reshape(nt, -1), ref["w"]) <= tol, s
+        assert oracle.rel_l2(q[s].reshape(nt, -1).double().cpu().numpy(), ref["q"]) <= 10 * tol, s
