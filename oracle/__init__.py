@@ -15,6 +15,8 @@ The heavy loops (stencil, time stepping, transpose solve, DTFT sums) are plain C
   bullet of the CG section) and Algorithm 1 (CG) written step by step;
 * the zero-lag cross-correlation gradient (Eq. "gradient", "gradewi") in both the
   adjoint-state form and the saddle-point form of Algorithm 2 (lambda = beta B^H B q);
+* the frequency-domain ESI system F (S^T S + beta B^T B) F^H qbar = F S^T d (Eq. "dtft",
+  "idtft", "normaldtft") and its CG with the real part of the Hermitian inner product;
 * dense assembly of the normal matrix at tiny sizes and its Cholesky solution;
 * FP16 / BF16 snapshot codecs with a per-snapshot scale.
 
@@ -480,6 +482,53 @@ class Oracle:
         B = self.annihilator(sh.src_xyz, eps)
         q = self.ST(sh, d - x) / (beta * B * B)[None, :]
         return {"w": x, "q": q, "rel_res": np.asarray(hist), "iters": k + 1, "b": b}
+
+    # ---------------------------------------------------------- frequency-domain ESI
+    def dtft_matrix(self, freqs: Sequence[float]) -> np.ndarray:
+        """F of Eq. "dtft" over the source's time index: F[m, n] = exp(+j 2 pi f_m n dt),
+        shape [nf, nt].  The inverse of Eq. "idtft" is F^H / nt."""
+        f = np.asarray(freqs, dtype=np.float64)
+        n = np.arange(self.nt, dtype=np.float64)
+        return np.exp(2j * np.pi * np.outer(f, n) * self.dt)
+
+    def fd_matvec(self, sh: Shot, qbar: np.ndarray, beta: float, freqs: Sequence[float],
+                  eps: Optional[float] = None) -> np.ndarray:
+        """M qbar = F (S^T S + beta B^T B) F^H qbar / nt (left side of Eq. "normaldtft"): the
+        inverse DTFT to a complex time series, the real normal operator on its real and its
+        imaginary part, the DTFT back to the frequencies."""
+        F = self.dtft_matrix(freqs)
+        qb = np.asarray(qbar, dtype=np.complex128).reshape(len(freqs), self.N)
+        q = F.conj().T @ qb / self.nt
+        Aq = self.normal_matvec(sh, q.real, beta, eps) + 1j * self.normal_matvec(sh, q.imag, beta, eps)
+        return F @ Aq
+
+    def fd_cg(self, sh: Shot, d: np.ndarray, beta: float, freqs: Sequence[float], tol: float,
+              n_cg: int, eps: Optional[float] = None) -> Dict:
+        """Algorithm 1 on Eq. "normaldtft", right-hand side F S^T d (the observed data taken
+        as the time series d = F^H dbar / nt), inner products Re <x, y> (M is Hermitian
+        positive definite).  Also returns q = F^H qbar / nt."""
+        F = self.dtft_matrix(freqs)
+        b = F @ self.ST(sh, np.asarray(d, dtype=np.float64).reshape(self.nt, sh.nr))
+        x = np.zeros_like(b)
+        r = b.copy()
+        p = r.copy()
+        rr = float(np.vdot(r, r).real)
+        r0 = math.sqrt(rr)
+        hist = []
+        k = 0
+        for k in range(n_cg):
+            Ap = self.fd_matvec(sh, p, beta, freqs, eps)
+            alpha = rr / float(np.vdot(p, Ap).real)
+            x = x + alpha * p
+            r = r - alpha * Ap
+            rr_new = float(np.vdot(r, r).real)
+            hist.append(math.sqrt(rr_new) / r0 if r0 > 0 else 0.0)
+            if math.sqrt(rr_new) < tol * r0 or k == n_cg - 1:
+                break
+            p = r + (rr_new / rr) * p
+            rr = rr_new
+        return {"qbar": x, "q": F.conj().T @ x / self.nt, "rel_res": np.asarray(hist),
+                "iters": k + 1, "b": b}
 
     def assemble_S(self, sh: Shot) -> np.ndarray:
         """Dense data operator S (columns S e_j over space-time; tiny sizes only)."""
