@@ -244,6 +244,29 @@ ESI_API esi_status esi_cg_solve(esi_ctx *ctx, double lambda, double tol, int max
                                 esi_cg_report *report);
 
 /*
+ * esi_fdcg_solve -- frequency-domain ESI by time-domain modelling (the section "Frequency
+ * domain inversion by time domain modelling"; Eq. "dtft", "idtft", "normaldtft"): Algorithm 1
+ * on the Hermitian positive definite system
+ *   F (S^T S + lambda B^T B) F^H qbar / nt = F S^T d,   F[m][n] = exp(+j 2 pi f_m n dt),
+ * (the inverse DTFT being the adjoint of F scaled by 1/nt) for the extended source at nf
+ * frequencies, qbar: per shot nf complex fields.  The observed data enter as the time series
+ * d.  CG runs in the real representation with Re <x, y> as inner product.  Each product
+ * synthesises the real and the imaginary part of F^H qbar / nt block by block into a
+ * 16-step source stash during two forward modellings, folds the two adjoint modellings of
+ * their traces block by block into the frequency slices, and adds lambda B^2 (F F^H / nt)
+ * qbar per cell; no space-time vector is stored (the CG vectors hold 2 nf values per cell).
+ *   dobs_dev     : device seismogram-layout observed data d
+ *   freqs_hz     : host [nf] frequencies, 1 <= nf <= 8
+ *   qbar_out_dev : device [ns][nf][N][2] (re, im) receives the solution
+ *   eps, report  : as esi_cg_solve (ms_matvec: the products, ms_vector: the vector work)
+ * Per-shot stopping, errors and frozen shots as esi_cg_solve; lambda must be > 0.  The
+ * time-domain source is q = F^H qbar / nt (its real part for a real source).
+ */
+ESI_API esi_status esi_fdcg_solve(esi_ctx *ctx, double lambda, double tol, int max_iter,
+                                  const void *dobs_dev, const double *freqs_hz, int nf,
+                                  void *qbar_out_dev, double eps, esi_cg_report *report);
+
+/*
  * esi_dscg_solve -- the ESI normal equation solved in data space (the section "Switching
  * from the wavefield to data space"; Eq. "wd", "q"): Algorithm 1 on
  *   (I + K) w = K d,   K = S (lambda B^2)^{-1} S^T,   B = ||x - x_s|| + eps,

@@ -98,6 +98,8 @@ struct esi_ctx {
     DBuf pc_dev;                   // learned-PCG dot partials, sums and per-shot theta
     DBuf dftsnap;                  // blocked DTFT: DFT_BLOCK new states [slot][ns][sst]
     DBuf wri_res;                  // WRI: data residual d - S f [traces]
+    DBuf fdv, fdsrc, fdtr;         // frequency-domain CG: 5 complex vectors, source stash, traces
+    DBuf fdsyn, fdfold, fdG;       // its twiddle tables and the Gram matrix F F^H / nt
     DBuf dsv, dseg;                // data-space CG: 5 data vectors; shot segments
     int pc_batch = 0;
     DBuf ckpt, ckpt_scale, absbits, stash, gacc, twid, dftacc;
@@ -534,7 +536,7 @@ esi_status step(esi_ctx *ctx, unsigned flags, const StepArgs<T> &a) {
     if (!state_map(ctx, a.cur, &b.tm) ||
         (ctx->g.ndim == 3 && (!state_map(ctx, a.po, &b.tm_old, 1) || !state_map(ctx, a.cc, &b.tm_cc, 2))))
         return ctx->fail(ESI_ERR_CUDA, "cuTensorMapEncodeTiled failed for a state buffer");
-    if (ctx->g.ndim == 2 && ctx->tma_cg &&
+    if (ctx->g.ndim == 2 && ctx->tma_cg && a.fstp == ctx->sst * ctx->nt &&
         (flags == (F_CGP | F_SMP) || flags == (F_PT | F_AP))) {
         // the CG product halves: every stream by TMA (tile-interior boxes)
         const bool fwd = flags == (F_CGP | F_SMP);
@@ -1706,6 +1708,295 @@ esi_status dscg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, cons
     return conv ? ESI_OK : ESI_ERR_NOT_CONVERGED;
 }
 
+// ------------------------------------------------------------------ frequency-domain ESI
+// The section "Frequency domain inversion by time domain modelling": CG on Eq. "normaldtft",
+//   F (S^T S + lambda B^T B) F^H qbar / nt = F S^T d,
+// over nf complex frequency slices per shot (qbar pitched [ns][nf][sst][2]; the CG works in
+// the real representation, where the Hermitian positive definite operator is symmetric
+// positive definite).  One product: for the real and the imaginary part of the time series
+// F^H qbar / nt, a forward modelling whose source is synthesised block by block from qbar
+// (Eq. "idtft"), then an adjoint modelling of its traces whose output is folded block by
+// block into the frequency slices (Eq. "dtft"; the imaginary part's twiddles turned by j);
+// then lambda B^2 G qbar per cell (G = F F^H / nt).  No space-time vector is stored: the
+// sources and the adjoint output pass through DFT_BLOCK-step stashes.
+template <typename T>
+esi_status fdcg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const void *dobs,
+                     const double *freqs, int nf, void *qbar_out, double eps_in,
+                     esi_cg_report *rep) {
+    using clk = std::chrono::steady_clock;
+    const auto t_start = clk::now();
+    const int ns = ctx->ns, nt = ctx->nt, K = DFT_BLOCK;
+    if (nf < 1 || nf > FD_MAXF)
+        return ctx->fail(ESI_ERR_ARG, "need 1 .. " + std::to_string(FD_MAXF) + " frequencies");
+    for (int m = 0; m < nf; ++m)
+        if (!std::isfinite(freqs[m])) return ctx->fail(ESI_ERR_ARG, "frequencies must be finite");
+    if (!(lambda > 0)) return ctx->fail(ESI_ERR_ARG, "the frequency-domain form needs lambda > 0");
+    if (max_iter < 1) return ctx->fail(ESI_ERR_ARG, "max_iter must be >= 1");
+    esi_status e = ensure_states<T>(ctx, true);
+    if (e != ESI_OK) return e;
+    const long long vl = (long long)ns * nf * ctx->sst * 2;   // one complex unknown vector
+    CK(ctx->fdv.ensure((size_t)5 * vl * sizeof(T)));
+    T *X = ctx->fdv.as<T>(), *R = X + vl, *P = R + vl, *AP = P + vl, *Bv = AP + vl;
+    // source stash [ns][K][sst] and the scratch the fused kernel writes its source to
+    CK(ctx->fdsrc.ensure((size_t)2 * ns * K * ctx->sst * sizeof(T)));
+    T *src = ctx->fdsrc.as<T>(), *psc = src + (size_t)ns * K * ctx->sst;
+    CK(ctx->dftsnap.ensure((size_t)K * ns * ctx->sst * sizeof(T)));
+    const long long tl = std::max<long long>((long long)ctx->total_rec * nt, 4);
+    CK(ctx->fdtr.ensure((size_t)tl * sizeof(T)));
+    T *tr = ctx->fdtr.as<T>();
+    const T eps = T(eps_in > 0 ? eps_in : ctx->g.dx);
+    CK(ctx->pb2.ensure((size_t)ns * ctx->sst * sizeof(T)));
+    CKL(launch_b2_maps<T>(ctx->pb2.as<T>(), nullptr, ns, ctx->g.nz, ctx->g.ny, ctx->g.nx, ctx->px,
+                          T(lambda), eps, T(ctx->g.dx), ctx->src_pos.as<double>(), 0, ctx->st));
+    // twiddle tables [part][n][m][2]: synthesis of the real part (cos, sin) / nt and of the
+    // imaginary part (-sin, cos) / nt; folding of a real series (cos, sin) and of an
+    // imaginary one (-sin, cos); the Gram matrix G[m][k] = 1/nt sum_n e^{j (ph_m - ph_k) n}
+    std::vector<T> syn((size_t)2 * nt * nf * 2), fold((size_t)2 * nt * nf * 2);
+    std::vector<double> G((size_t)nf * nf * 2, 0.0);
+    for (int n = 0; n < nt; ++n)
+        for (int m = 0; m < nf; ++m) {
+            const double ph = 2.0 * M_PI * freqs[m] * n * ctx->dt, c = std::cos(ph), sn = std::sin(ph);
+            const size_t o = ((size_t)n * nf + m) * 2, o1 = (size_t)nt * nf * 2 + o;
+            syn[o] = T(c / nt), syn[o + 1] = T(sn / nt);
+            syn[o1] = T(-sn / nt), syn[o1 + 1] = T(c / nt);
+            fold[o] = T(c), fold[o + 1] = T(sn);
+            fold[o1] = T(-sn), fold[o1 + 1] = T(c);
+            for (int k = 0; k < nf; ++k) {
+                const double d = 2.0 * M_PI * (freqs[m] - freqs[k]) * n * ctx->dt;
+                G[(m * nf + k) * 2] += std::cos(d) / nt;
+                G[(m * nf + k) * 2 + 1] += std::sin(d) / nt;
+            }
+        }
+    CK(upload(ctx->fdsyn, syn, ctx->st));
+    CK(upload(ctx->fdfold, fold, ctx->st));
+    CK(upload(ctx->fdG, G, ctx->st));
+    const T *syn_d = ctx->fdsyn.as<T>(), *fold_d = ctx->fdfold.as<T>();
+    const double *G_d = ctx->fdG.as<double>();
+    std::vector<long long> seg(ns + 1);   // shot segments of the real-representation vectors
+    for (int s = 0; s <= ns; ++s) seg[s] = (long long)s * nf * ctx->sst * 2;
+    CK(upload(ctx->dseg, seg, ctx->st));
+    const long long *dseg = ctx->dseg.as<long long>();
+    const int nb = DVEC_NBLK;
+    CK(ctx->part.ensure(sizeof(double) * (size_t)ns * nb));
+    CK(ctx->scal.ensure(sizeof(double) * 5 * ns + sizeof(int) * 2 * ns));
+    double *rr = ctx->scal.as<double>(), *pap = rr + ns, *alpha = pap + ns, *beta = alpha + ns,
+           *rrn = beta + ns;
+    int *active = reinterpret_cast<int *>(rrn + ns), *bad = active + ns;
+    CK(cudaMemsetAsync(active, 0xff, sizeof(int) * ns, ctx->st));
+    CK(cudaMemsetAsync(bad, 0, sizeof(int) * ns, ctx->st));
+    const double es = double(sizeof(T));
+    const unsigned aflags = ctx->g.ndim == 2 ? (F_PT | F_SMP | F_DFT) : (F_PT | F_DFT);
+    // out += F S^T traces, the j-th part's twiddles (part 1: the series times j)
+    auto adjoint_fold = [&](const T *traces, int part, T *out) -> esi_status {
+        cudaEvent_t ev = prof_mark(ctx);
+        CK(cudaMemsetAsync(ctx->a0.p, 0, ctx->a0.n, ctx->st));
+        CK(cudaMemsetAsync(ctx->a1.p, 0, ctx->a1.n, ctx->st));
+        StepArgs<T> a = base_args<T>(ctx);
+        a.active = active;
+        a.inj = inj_view<T>(ctx->inj_rec);
+        a.inj_trace = traces;
+        a.smp = smp_view<T>(ctx->smp_rec);   // no sampling: tout < 0
+        a.stash_w = ctx->dftsnap.as<T>();
+        a.nf = nf;
+        a.twid = fold_d + (size_t)part * nt * nf * 2;
+        a.dft = out;
+        T *c0 = ctx->a0.as<T>(), *p0 = ctx->a1.as<T>();
+        auto body = [&]() -> esi_status {
+            T *c = c0, *q = p0;
+            for (int jhi = nt; jhi > 0;) {
+                const int jlo = std::max(0, jhi - K);
+                for (int j = jhi; j > jlo; --j) {
+                    a.cur = c;
+                    a.po = q;
+                    a.n = j - 1;
+                    a.tin = j - 1;
+                    a.nout = j - 1;
+                    a.tout = -1;
+                    a.slot_w = (j - 1) - jlo;   // slots in time order within the block
+                    esi_status st = step<T>(ctx, aflags, a);
+                    if (st != ESI_OK) return st;
+                    std::swap(c, q);
+                }
+                CKL(launch_dft_block<T>(a.stash_w, jhi - jlo, ns, ctx->sst, nf,
+                                        a.twid + (size_t)jlo * nf * 2, out, ctx->st));
+                jhi = jlo;
+            }
+            return ESI_OK;
+        };
+        esi_status st;
+        if (ctx->use_graphs && nt >= GRAPH_MIN_STEPS) {
+            auto key = loop_key(a, aflags, -3, part, nt, false, c0, p0);
+            if (!graph_replay(ctx, key, st)) st = graph_capture(ctx, std::move(key), body);
+        } else {
+            st = body();
+        }
+        if (st != ESI_OK) return st;
+        prof_close(ctx, ev, step_name(ctx, aflags) + "+dft_block",
+                   step_bpc(ctx, aflags, nf) + es + 4.0 * nf * es / K, nt + (nt + K - 1) / K,
+                   (long long)nt * ctx->prof_active * ctx->N);
+        return ESI_OK;
+    };
+    // traces of the forward modelling whose source is part `part` of F^H qb / nt
+    auto forward_synth = [&](const T *qb, int part) -> esi_status {
+        cudaEvent_t ev = prof_mark(ctx);
+        CK(cudaMemsetAsync(ctx->u0.p, 0, ctx->u0.n, ctx->st));
+        CK(cudaMemsetAsync(ctx->u1.p, 0, ctx->u1.n, ctx->st));
+        StepArgs<T> a = base_args<T>(ctx);
+        a.active = active;
+        a.cg_r = src;
+        a.cg_p = psc;
+        a.cg_first = 1;   // the source is the stash slot itself
+        a.fstp = (long long)K * ctx->sst;
+        a.smp = smp_view<T>(ctx->smp_rec);
+        a.smp_out = tr;
+        a.ext = qb;       // not read by the step; part of the loop key
+        a.nf = nf;
+        a.twid = syn_d + (size_t)part * nt * nf * 2;
+        T *c0 = ctx->u0.as<T>(), *p0 = ctx->u1.as<T>();
+        auto body = [&]() -> esi_status {
+            T *c = c0, *q = p0;
+            for (int n0 = 0; n0 < nt; n0 += K) {
+                const int n1 = std::min(nt, n0 + K);
+                CKL(launch_idft_block<T>(qb, n1 - n0, ns, ctx->sst, nf, a.twid + (size_t)n0 * nf * 2,
+                                         src, ctx->st));
+                for (int n = n0; n < n1; ++n) {
+                    a.cur = c;
+                    a.po = q;
+                    a.n = n - n0;   // the stash slot
+                    a.tin = n;
+                    a.tout = n - 1;
+                    esi_status st = step<T>(ctx, F_CGP | F_SMP, a);
+                    if (st != ESI_OK) return st;
+                    std::swap(c, q);
+                }
+            }
+            CKL(launch_sample_global<T>(a.smp, c, ctx->sst, tr, nt - 1, ctx->st));
+            return ESI_OK;
+        };
+        esi_status st;
+        if (ctx->use_graphs && nt >= GRAPH_MIN_STEPS) {
+            auto key = loop_key(a, F_CGP | F_SMP, +3, part, nt, false, c0, p0);
+            if (!graph_replay(ctx, key, st)) st = graph_capture(ctx, std::move(key), body);
+        } else {
+            st = body();
+        }
+        if (st != ESI_OK) return st;
+        prof_close(ctx, ev, step_name(ctx, F_CGP | F_SMP) + "+idft_block",
+                   step_bpc(ctx, F_CGP | F_SMP, 0) + es + 2.0 * nf * es / K, nt + (nt + K - 1) / K,
+                   (long long)nt * ctx->prof_active * ctx->N);
+        return ESI_OK;
+    };
+    // out = F (S^T S + lambda B^2) F^H qb / nt, with the partials of Re <qb, out>
+    auto apply_M = [&](const T *qb, T *out) -> esi_status {
+        CK(cudaMemsetAsync(out, 0, vl * sizeof(T), ctx->st));
+        for (int part = 0; part < 2; ++part) {
+            esi_status st = forward_synth(qb, part);
+            if (st != ESI_OK) return st;
+            st = adjoint_fold(tr, part, out);
+            if (st != ESI_OK) return st;
+        }
+        CKL(launch_fd_b2g_dot<T>(out, qb, ctx->pb2.as<T>(), G_d, nf, ns, ctx->sst, active,
+                                 ctx->part.as<double>(), ctx->st));
+        return ESI_OK;
+    };
+    ctx->prof_active = ns;
+    // right-hand side F S^T d
+    CK(cudaMemsetAsync(Bv, 0, vl * sizeof(T), ctx->st));
+    e = adjoint_fold(reinterpret_cast<const T *>(dobs), 0, Bv);
+    if (e != ESI_OK) return e;
+    CK(cudaMemsetAsync(X, 0, vl * sizeof(T), ctx->st));
+    CK(cudaMemcpyAsync(R, Bv, vl * sizeof(T), cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaMemcpyAsync(P, Bv, vl * sizeof(T), cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaMemsetAsync(alpha, 0, sizeof(double) * ns, ctx->st));
+    CKL(launch_dvec_update<T>(X, R, P, P, dseg, alpha, nullptr, ctx->part.as<double>(), ns, ctx->st));
+    CKL(launch_reduce_partials(ctx->part.as<double>(), nb, ns, rr, ctx->st));
+    std::vector<double> rr0(ns), h_rrn(ns);
+    std::vector<int> h_active(ns, 1), h_bad(ns, 0), iters(ns, 0);
+    std::vector<char> h_conv(ns, 0);
+    CK(cudaMemcpyAsync(rr0.data(), rr, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    for (int s = 0; s < ns; ++s)
+        if (!(rr0[s] > 0)) h_active[s] = 0;   // b = 0: qbar = 0 is exact
+    CK(cudaMemcpyAsync(active, h_active.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, ctx->st));
+    const int hist_cap = rep ? rep->max_hist : 0;
+    double ms_mv = 0, ms_vec = 0;
+    struct Events {
+        cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+        ~Events() {
+            for (auto z : e)
+                if (z) cudaEventDestroy(z);
+        }
+    } ev;
+    for (auto &z : ev.e) CK(cudaEventCreate(&z));
+    bool any_bad = false;
+    for (int k = 0; k < max_iter; ++k) {
+        ctx->prof_active = 0;
+        for (int s = 0; s < ns; ++s) ctx->prof_active += h_active[s];
+        if (ctx->prof_active == 0) break;
+        CK(cudaEventRecord(ev.e[0], ctx->st));
+        e = apply_M(P, AP);
+        if (e != ESI_OK) return e;
+        CK(cudaEventRecord(ev.e[1], ctx->st));
+        CKL(launch_reduce_partials(ctx->part.as<double>(), nb, ns, pap, ctx->st));
+        CKL(launch_cg_alpha(rr, pap, alpha, bad, active, ns, ctx->st));
+        CKL(launch_dvec_update<T>(X, R, P, AP, dseg, alpha, active, ctx->part.as<double>(), ns, ctx->st));
+        CKL(launch_reduce_partials(ctx->part.as<double>(), nb, ns, rrn, ctx->st));
+        CK(cudaEventRecord(ev.e[2], ctx->st));
+        CK(cudaMemcpyAsync(h_rrn.data(), rrn, sizeof(double) * ns, cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaMemcpyAsync(h_bad.data(), bad, sizeof(int) * ns, cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        if ((e = check_dev_err(ctx)) != ESI_OK) return e;
+        float m01 = 0, m12 = 0;
+        CK(cudaEventElapsedTime(&m01, ev.e[0], ev.e[1]));
+        CK(cudaEventElapsedTime(&m12, ev.e[1], ev.e[2]));
+        ms_mv += m01;
+        ms_vec += m12;
+        bool any = false;
+        for (int s = 0; s < ns; ++s) {
+            if (!h_active[s]) continue;
+            if (h_bad[s]) {
+                any_bad = true;
+                h_active[s] = 0;
+                continue;
+            }
+            iters[s] = k + 1;
+            if (rep && rep->rel_res && k < hist_cap)
+                rep->rel_res[(size_t)s * hist_cap + k] = std::sqrt(h_rrn[s] / rr0[s]);
+            const bool met = std::sqrt(h_rrn[s]) < tol * std::sqrt(rr0[s]);
+            h_conv[s] = met;
+            if (met || k == max_iter - 1)
+                h_active[s] = 0;
+            else
+                any = true;
+        }
+        if (!any) break;
+        CK(cudaMemcpyAsync(active, h_active.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, ctx->st));
+        CKL(launch_cg_beta(rr, rrn, beta, active, ns, ctx->st));
+        CKL(launch_dvec_xpby<T>(P, R, dseg, beta, active, ns, ctx->st));
+    }
+    // qbar out: pitched complex slices -> dense [ns][nf][N][2]
+    CKL(launch_dft_output<T>(X, ctx->sst, ctx->g.nz * ctx->g.ny, ctx->g.nx, ctx->px, ns, nf, 0,
+                             qbar_out, nullptr, nullptr, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    bool conv = true;
+    int mx = 0;
+    for (int s = 0; s < ns; ++s) {
+        if (rr0[s] > 0 && !(iters[s] > 0 && h_conv[s])) conv = false;
+        mx = std::max(mx, iters[s]);
+    }
+    if (rep) {
+        for (int s = 0; s < ns && rep->iters; ++s) rep->iters[s] = iters[s];
+        rep->iters_max = mx;
+        rep->converged = conv ? 1 : 0;
+        rep->ms_matvec = ms_mv;
+        rep->ms_vector = ms_vec;
+        rep->ms_precond = 0;
+        rep->ms_total = std::chrono::duration<double, std::milli>(clk::now() - t_start).count();
+    }
+    if (any_bad) return ctx->fail(ESI_ERR_BREAKDOWN, "CG breakdown: Re <p, M p> <= 0 or non-finite");
+    return conv ? ESI_OK : ESI_ERR_NOT_CONVERGED;
+}
+
 template <typename T>
 esi_status create_impl(esi_ctx *ctx, const void *vel) {
     CK(ctx->dev_err.ensure(sizeof(int)));
@@ -1928,6 +2219,20 @@ ESI_API esi_status esi_dft_extract(esi_ctx *ctx, const void *wavelet_dev, const 
                                   scales_host, traces_dev)
                : dft_impl<float>(ctx, wavelet_dev, ext_src_dev, freqs_hz, nf, out_dev, out_kind,
                                  scales_host, traces_dev);
+}
+
+ESI_API esi_status esi_fdcg_solve(esi_ctx *ctx, double lambda, double tol, int max_iter,
+                                  const void *dobs_dev, const double *freqs_hz, int nf,
+                                  void *qbar_out_dev, double eps, esi_cg_report *report) {
+    if (!ctx) return ESI_ERR_ARG;
+    if (!dobs_dev || !qbar_out_dev || !freqs_hz || !(lambda > 0) || !(tol >= 0))
+        return ctx->fail(ESI_ERR_ARG, "bad frequency-domain CG arguments");
+    ctx->err.clear();
+    return ctx->g.dtype == ESI_F64
+               ? fdcg_impl<double>(ctx, lambda, tol, max_iter, dobs_dev, freqs_hz, nf, qbar_out_dev,
+                                   eps, report)
+               : fdcg_impl<float>(ctx, lambda, tol, max_iter, dobs_dev, freqs_hz, nf, qbar_out_dev,
+                                  eps, report);
 }
 
 ESI_API esi_status esi_dscg_solve(esi_ctx *ctx, double lambda, double tol, int max_iter,

@@ -263,6 +263,19 @@ template <typename T>
 cudaError_t launch_dft_block(const T *snap, int K, int ns, long long sst, int nf, const T *twid,
                              T *acc, cudaStream_t st);
 
+// Frequency-domain ESI (Eq. "idtft", "normaldtft"), at most FD_MAXF frequencies.
+constexpr int FD_MAXF = 8;
+// inverse DTFT of one block: src[s][k][cell] = sum_m re(qb_m) tw[k][m].x + im(qb_m) tw[k][m].y
+// for the K steps of the block, qb pitched complex slices [ns][nf][sst][2]
+template <typename T>
+cudaError_t launch_idft_block(const T *qb, int K, int ns, long long sst, int nf, const T *tw,
+                              T *src, cudaStream_t st);
+// out_m += pb2 * sum_m' G[m][m'] p_m' per cell (G = F F^H / nt, complex [nf][nf][2]) and the
+// per-block partials of Re <p, out> ([ns][DVEC_NBLK]); inactive shots skipped
+template <typename T>
+cudaError_t launch_fd_b2g_dot(T *out, const T *p, const T *pb2, const double *G, int nf, int ns,
+                              long long sst, const int *active, double *part, cudaStream_t st);
+
 // DTFT output: pitched accumulators [ns][nf][sst][2] -> caller dense [ns][nf][N][2], either
 // copied in the field precision (half == 0) or as half pairs with a per (shot, f) scale
 template <typename T>

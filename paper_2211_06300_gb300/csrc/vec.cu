@@ -617,7 +617,108 @@ __global__ void dft_block_kernel(const T *snap, int K, int ns, long long sst, in
     }
 }
 
+// Inverse DTFT of one block (Eq. "idtft" with its 1/nt folded into tw): the K source samples
+// of a cell from its nf complex values, tw[k][m] = (C, D) such that the sample is
+// sum_m re(qbar_m) C + im(qbar_m) D.  A thread keeps the nf values of 16 bytes of cells.
+template <typename T>
+__global__ void idft_block_kernel(const T *qb, int K, int ns, long long sst, int nf, const T *tw,
+                                  T *src) {
+    constexpr int VEC = V16<T>::n;
+    const int s = blockIdx.y;
+    const long long nch = sst / VEC;
+    for (long long c = (long long)blockIdx.x * RT + threadIdx.x; c < nch;
+         c += (long long)gridDim.x * RT) {
+        const long long cell = c * VEC;
+        T a[FD_MAXF][VEC], b[FD_MAXF][VEC];
+#pragma unroll
+        for (int m = 0; m < FD_MAXF; ++m) {
+            if (m >= nf) break;
+            const V16<T> *q = reinterpret_cast<const V16<T> *>(qb + (((long long)s * nf + m) * sst + cell) * 2);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const V16<T> v = q[h];
+#pragma unroll
+                for (int i = 0; i < VEC / 2; ++i) {
+                    a[m][h * VEC / 2 + i] = v.v[2 * i];
+                    b[m][h * VEC / 2 + i] = v.v[2 * i + 1];
+                }
+            }
+        }
+        for (int k = 0; k < K; ++k) {
+            V16<T> o;
+#pragma unroll
+            for (int i = 0; i < VEC; ++i) o.v[i] = T(0);
+#pragma unroll
+            for (int m = 0; m < FD_MAXF; ++m) {
+                if (m >= nf) break;
+                const T C = tw[((long long)k * nf + m) * 2], D = tw[((long long)k * nf + m) * 2 + 1];
+#pragma unroll
+                for (int i = 0; i < VEC; ++i) o.v[i] += a[m][i] * C + b[m][i] * D;
+            }
+            *reinterpret_cast<V16<T> *>(src + ((long long)s * K + k) * sst + cell) = o;
+        }
+    }
+}
+
+// out_m += pb2 sum_m' G[m][m'] p_m' (the lambda B^2 term of Eq. "normaldtft": B commutes with
+// F, so F lambda B^2 F^H / nt = lambda B^2 G), with the partials of Re <p, out>
+template <typename T>
+__global__ void fd_b2g_dot_kernel(T *out, const T *p, const T *pb2, const double *G, int nf,
+                                  long long sst, const int *active, double *part) {
+    const int s = blockIdx.y;
+    if (active && !active[s]) return;
+    double acc = 0.0;
+    for (long long c = (long long)blockIdx.x * RT + threadIdx.x; c < sst;
+         c += (long long)gridDim.x * RT) {
+        const T w = pb2[(long long)s * sst + c];
+        T pr[FD_MAXF], pi[FD_MAXF];
+#pragma unroll
+        for (int m = 0; m < FD_MAXF; ++m) {
+            if (m >= nf) break;
+            const long long o = (((long long)s * nf + m) * sst + c) * 2;
+            pr[m] = p[o];
+            pi[m] = p[o + 1];
+        }
+#pragma unroll
+        for (int m = 0; m < FD_MAXF; ++m) {
+            if (m >= nf) break;
+            T gr = T(0), gi = T(0);
+#pragma unroll
+            for (int k = 0; k < FD_MAXF; ++k) {
+                if (k >= nf) break;
+                const T Gr = T(G[(m * nf + k) * 2]), Gi = T(G[(m * nf + k) * 2 + 1]);
+                gr += Gr * pr[k] - Gi * pi[k];
+                gi += Gr * pi[k] + Gi * pr[k];
+            }
+            const long long o = (((long long)s * nf + m) * sst + c) * 2;
+            const T orr = out[o] + w * gr, oi = out[o + 1] + w * gi;
+            out[o] = orr;
+            out[o + 1] = oi;
+            acc += double(pr[m]) * double(orr) + double(pi[m]) * double(oi);
+        }
+    }
+    const double t = block_sum_d(acc);
+    if (threadIdx.x == 0) part[(long long)s * gridDim.x + blockIdx.x] = t;
+}
+
 }  // namespace
+
+template <typename T>
+cudaError_t launch_idft_block(const T *qb, int K, int ns, long long sst, int nf, const T *tw,
+                              T *src, cudaStream_t st) {
+    if (nf > FD_MAXF) return cudaErrorInvalidValue;
+    idft_block_kernel<T><<<dim3(blocks_for(sst / V16<T>::n, 1024), ns), RT, 0, st>>>(qb, K, ns, sst,
+                                                                                  nf, tw, src);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fd_b2g_dot(T *out, const T *p, const T *pb2, const double *G, int nf, int ns,
+                              long long sst, const int *active, double *part, cudaStream_t st) {
+    if (nf > FD_MAXF) return cudaErrorInvalidValue;
+    fd_b2g_dot_kernel<T><<<dim3(DVEC_NBLK, ns), RT, 0, st>>>(out, p, pb2, G, nf, sst, active, part);
+    return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t launch_dft_block(const T *snap, int K, int ns, long long sst, int nf, const T *twid,
@@ -678,6 +779,10 @@ cudaError_t launch_dft_output(const T *acc, long long sst, int rows, int nx, int
                                           const float *, T *, cudaStream_t);                     \
     template cudaError_t launch_dft_output<T>(const T *, long long, int, int, int, int, int, int, \
                                               void *, unsigned *, float *, cudaStream_t);       \
+    template cudaError_t launch_idft_block<T>(const T *, int, int, long long, int, const T *, T *, \
+                                              cudaStream_t);                                     \
+    template cudaError_t launch_fd_b2g_dot<T>(T *, const T *, const T *, const double *, int, int, \
+                                              long long, const int *, double *, cudaStream_t);   \
     template cudaError_t launch_dft_block<T>(const T *, int, int, long long, int, const T *, T *, \
                                              cudaStream_t);
 

@@ -32,7 +32,8 @@ EXPORTS = ["esi_create", "esi_destroy", "esi_set_stream", "esi_set_velocity", "e
            "esi_get_profile", "esi_forward_noalloc", "esi_normal_apply", "esi_pc_param_count",
            "esi_pc_fallbacks", "esi_pc_pack", "esi_pc_create", "esi_pc_destroy",
            "esi_pc_last_error", "esi_pc_set_params", "esi_pc_get_params", "esi_pc_apply",
-           "esi_pc_grad", "esi_pc_train_step", "esi_wri_solve", "esi_dscg_solve"]
+           "esi_pc_grad", "esi_pc_train_step", "esi_wri_solve", "esi_dscg_solve",
+           "esi_fdcg_solve"]
 
 
 class EsiGrid(ctypes.Structure):
@@ -103,6 +104,8 @@ def load_library(require_gpu: bool = True) -> ctypes.CDLL:
     L.esi_cg_solve.argtypes = [vp, d, d, i, vp, vp, i, d, ctypes.POINTER(EsiCgReport)]
     L.esi_wri_solve.argtypes = [vp, d, d, i, vp, vp, vp, ctypes.POINTER(EsiCgReport)]
     L.esi_dscg_solve.argtypes = [vp, d, d, i, vp, vp, vp, d, ctypes.POINTER(EsiCgReport)]
+    L.esi_fdcg_solve.argtypes = [vp, d, d, i, vp, ctypes.POINTER(d), i, vp, d,
+                                 ctypes.POINTER(EsiCgReport)]
     L.esi_pc_load.argtypes = [vp, vp, ctypes.c_size_t]
     L.esi_normal_apply.argtypes = [vp, d, d, vp, vp]
     L.esi_pc_param_count.argtypes = []
@@ -135,7 +138,7 @@ def load_library(require_gpu: bool = True) -> ctypes.CDLL:
                  "esi_pc_set_params", "esi_pc_get_params", "esi_pc_apply", "esi_pc_grad",
                  "esi_pc_train_step",
                  "esi_adjoint", "esi_gradient", "esi_dft_extract", "esi_cg_solve",
-                 "esi_pc_load", "esi_wri_solve", "esi_dscg_solve"):
+                 "esi_pc_load", "esi_wri_solve", "esi_dscg_solve", "esi_fdcg_solve"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -347,11 +350,18 @@ class Context:
 
     def cg_solve(self, dobs, lam: float, tol: float, max_iter: int, precond: str = "none",
                  eps: float = 0.0, out=None, hist: int = 0, wri_wavelet=None,
-                 data_space: bool = False, w_out=None):
+                 data_space: bool = False, w_out=None, freqs=None):
         """ESI normal equation by Algorithm 1; with wri_wavelet (the point sources f) the WRI
         system (S^T S + lam I) q = S^T (d - S f) instead (esi_wri_solve); with data_space the
-        ESI system through the data-space form (esi_dscg_solve; w_out receives w)."""
-        q = self.empty_field() if out is None else out
+        ESI system through the data-space form (esi_dscg_solve; w_out receives w); with freqs
+        (Hz) the frequency-domain system F A F^H qbar / nt = F S^T d (esi_fdcg_solve), whose
+        solution qbar is returned as [ns][nf][*shape][2] (re, im)."""
+        if freqs is not None:
+            f = np.ascontiguousarray(np.asarray(freqs, dtype=np.float64).ravel())
+            q = (self.torch.empty((self.ns, f.size) + self.shape + (2,), dtype=self.dtype,
+                                  device=self.device) if out is None else out)
+        else:
+            q = self.empty_field() if out is None else out
         rep = EsiCgReport()
         hist = max(int(hist), int(max_iter))
         rel = np.zeros((self.ns, hist), dtype=np.float64)
@@ -359,7 +369,12 @@ class Context:
         rep.max_hist = hist
         rep.iters = its.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
         rep.rel_res = rel.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        if data_space:
+        if freqs is not None:
+            call = self.L.esi_fdcg_solve(self.h, float(lam), float(tol), int(max_iter),
+                                         _ptr(dobs),
+                                         f.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         int(f.size), _ptr(q), float(eps), ctypes.byref(rep))
+        elif data_space:
             call = self.L.esi_dscg_solve(self.h, float(lam), float(tol), int(max_iter),
                                          _ptr(dobs), _ptr(q), _ptr(w_out), float(eps),
                                          ctypes.byref(rep))

@@ -380,3 +380,53 @@ def test_data_space_cg_matches_oracle(prec):
         assert np.allclose(rep["rel_res"][s], ref["rel_res"], rtol=10 * tol, atol=0), s
         assert oracle.rel_l2(wh[nt * o0:nt * o1].reshape(nt, -1), ref["w"]) <= tol, s
         assert oracle.rel_l2(q[s].reshape(nt, -1).double().cpu().numpy(), ref["q"]) <= 10 * tol, s
+
+
+# ----------------------------------------------------------------------------- frequency domain
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_frequency_domain_cg_matches_oracle(prec):
+    """Frequency-domain ESI by time-domain modelling (Eq. "dtft", "idtft", "normaldtft"):
+    iterates of F A F^H qbar / nt = F S^T d at three frequencies against the oracle, several
+    shots, nt not a multiple of the 16-step DTFT block (a ragged block in both directions)."""
+    v, geom, p = _ragged_case(nt=83)
+    nt = p["nt"]
+    o, shots = _orc(v, geom, p)
+    wav = np.stack([synth.ricker(nt, p["dt"], 25.0)] * geom.ns)
+    d = np.concatenate([o.forward(sh, wavelet=wav[s])["traces"].ravel()
+                        for s, sh in enumerate(shots)])
+    freqs = [8.0, 15.5, 23.0]
+    lam, nmax = 2e-4, 5
+    ctx = _ctx(v, geom, p, prec)
+    qb, rep = ctx.cg_solve(_dev(d, prec), lam=lam, tol=0.0, max_iter=nmax, freqs=freqs)
+    assert tuple(qb.shape) == (geom.ns, len(freqs)) + v.shape + (2,)
+    tol = {"f64": 1e-12, "f32": 1e-4}[prec]
+    qh = qb.double().cpu().numpy()
+    for s, sh in enumerate(shots):
+        o0, o1 = geom.rec_offset[s], geom.rec_offset[s + 1]
+        ref = o.fd_cg(sh, d[nt * o0:nt * o1].reshape(nt, -1), lam, freqs, 0.0, nmax)
+        assert rep["iters"][s] == ref["iters"] == nmax, s
+        assert np.allclose(rep["rel_res"][s], ref["rel_res"], rtol=10 * tol, atol=0), s
+        got = (qh[s, ..., 0] + 1j * qh[s, ..., 1]).reshape(len(freqs), -1)
+        assert oracle.rel_l2(got, ref["qbar"].reshape(len(freqs), -1)) <= 10 * tol, s
+
+
+def test_frequency_domain_cg_3d_fp64():
+    """The same solve on a 3D volume with two z chunks and ragged x / y tiles, nt shorter
+    than three DTFT blocks."""
+    shape = (70, 21, 37)
+    dx, dt, nt, nb = 10.0, 1e-3, 37, 4
+    v = synth.dipping_layers(shape, dx, 3, nlayers=3, vmin=1500, vmax=2500, nanom=1,
+                             sigma=3 * dx)
+    geom = synth.surface_grid_3d((183.0, 96.5, 333.0), np.array([35.0, 122.5, 300.0]),
+                                 np.array([0.0, 101.0, 200.0]), 655.5)
+    p = dict(dx=dx, dt=dt, nt=nt, nb=nb)
+    o, (sh,) = _orc(v, geom, p)
+    d = o.forward(sh, wavelet=synth.ricker(nt, dt, 30.0))["traces"]
+    freqs, lam, nmax = [20.0, 45.0], 1e-3, 3
+    ctx = _ctx(v, geom, p, "f64")
+    qb, rep = ctx.cg_solve(_dev(d.ravel(), "f64"), lam=lam, tol=0.0, max_iter=nmax, freqs=freqs)
+    ref = o.fd_cg(sh, d, lam, freqs, 0.0, nmax)
+    assert np.allclose(rep["rel_res"][0], ref["rel_res"], rtol=1e-10, atol=0)
+    qh = qb.cpu().numpy()[0]
+    got = (qh[..., 0] + 1j * qh[..., 1]).reshape(len(freqs), -1)
+    assert oracle.rel_l2(got, ref["qbar"].reshape(len(freqs), -1)) <= 1e-11
