@@ -180,7 +180,7 @@ typedef struct esi_grad_opts {
  *   given (a vector-Jacobian product, J = <e, d>), otherwise e = R u - dobs and
  *   *misfit = 1/2 ||e||^2 (Eq. "fwi").  The forward states are recomputed per segment of
  *   ckpt_every steps from stored (optionally compressed) checkpoints.
- * Saddle-point mode (Algorithm 2, lines 308-310): ext_src is the ESI solution q, the
+ * Saddle-point mode (Algorithm 2): ext_src is the ESI solution q, the
  *   adjoint field is lambda = beta B^H B q with B = ||x - x_s|| + eps; one forward run.
  * WRI saddle mode (Eq. "newadj2", "gradient2"): ext_src is the WRI solution q and
  *   wavelet_dev the point sources f; u = A^{-1}(f + q), lambda = beta q (B = I); one
@@ -225,7 +225,7 @@ typedef struct esi_cg_report {
 /*
  * esi_cg_solve -- Algorithm 1 (CG) on the ESI normal equation (Eq. "normalewi"):
  *   (S^T S + lambda B^T B) q = S^T d,   B = ||x - x_s|| + eps  (per shot),
- * with the north-star's name lambda for the paper's penalty beta.  Every matrix-vector
+ * with lambda naming the paper's penalty beta.  Every matrix-vector
  * product is one forward modelling with p as the extended source and one adjoint
  * modelling of its traces (CG section, second bullet), plus lambda B^2 p.  Shots are
  * independent systems, each with its own scalars; a shot stops at
