@@ -1857,8 +1857,8 @@ esi_status fdcg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, cons
             T *c = c0, *q = p0;
             for (int n0 = 0; n0 < nt; n0 += K) {
                 const int n1 = std::min(nt, n0 + K);
-                CKL(launch_idft_block<T>(qb, n1 - n0, ns, ctx->sst, nf, a.twid + (size_t)n0 * nf * 2,
-                                         src, ctx->st));
+                CKL(launch_idft_block<T>(qb, n1 - n0, K, ns, ctx->sst, nf,
+                                         a.twid + (size_t)n0 * nf * 2, src, ctx->st));
                 for (int n = n0; n < n1; ++n) {
                     a.cur = c;
                     a.po = q;

@@ -266,10 +266,11 @@ cudaError_t launch_dft_block(const T *snap, int K, int ns, long long sst, int nf
 // Frequency-domain ESI (Eq. "idtft", "normaldtft"), at most FD_MAXF frequencies.
 constexpr int FD_MAXF = 8;
 // inverse DTFT of one block: src[s][k][cell] = sum_m re(qb_m) tw[k][m].x + im(qb_m) tw[k][m].y
-// for the K steps of the block, qb pitched complex slices [ns][nf][sst][2]
+// for the K <= kst steps of the block (kst slots per shot), qb pitched complex slices
+// [ns][nf][sst][2]
 template <typename T>
-cudaError_t launch_idft_block(const T *qb, int K, int ns, long long sst, int nf, const T *tw,
-                              T *src, cudaStream_t st);
+cudaError_t launch_idft_block(const T *qb, int K, int kst, int ns, long long sst, int nf,
+                              const T *tw, T *src, cudaStream_t st);
 // out_m += pb2 * sum_m' G[m][m'] p_m' per cell (G = F F^H / nt, complex [nf][nf][2]) and the
 // per-block partials of Re <p, out> ([ns][DVEC_NBLK]); inactive shots skipped
 template <typename T>

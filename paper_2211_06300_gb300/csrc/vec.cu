@@ -619,10 +619,12 @@ __global__ void dft_block_kernel(const T *snap, int K, int ns, long long sst, in
 
 // Inverse DTFT of one block (Eq. "idtft" with its 1/nt folded into tw): the K source samples
 // of a cell from its nf complex values, tw[k][m] = (C, D) such that the sample is
-// sum_m re(qbar_m) C + im(qbar_m) D.  A thread keeps the nf values of 16 bytes of cells.
+// sum_m re(qbar_m) C + im(qbar_m) D, into src[s][k][cell] with kst slots per shot (kst >= K:
+// a ragged last block fills only its first K slots).  A thread keeps the nf values of 16
+// bytes of cells.
 template <typename T>
-__global__ void idft_block_kernel(const T *qb, int K, int ns, long long sst, int nf, const T *tw,
-                                  T *src) {
+__global__ void idft_block_kernel(const T *qb, int K, int kst, int ns, long long sst, int nf,
+                                  const T *tw, T *src) {
     constexpr int VEC = V16<T>::n;
     const int s = blockIdx.y;
     const long long nch = sst / VEC;
@@ -655,7 +657,7 @@ __global__ void idft_block_kernel(const T *qb, int K, int ns, long long sst, int
 #pragma unroll
                 for (int i = 0; i < VEC; ++i) o.v[i] += a[m][i] * C + b[m][i] * D;
             }
-            *reinterpret_cast<V16<T> *>(src + ((long long)s * K + k) * sst + cell) = o;
+            *reinterpret_cast<V16<T> *>(src + ((long long)s * kst + k) * sst + cell) = o;
         }
     }
 }
@@ -704,11 +706,11 @@ __global__ void fd_b2g_dot_kernel(T *out, const T *p, const T *pb2, const double
 }  // namespace
 
 template <typename T>
-cudaError_t launch_idft_block(const T *qb, int K, int ns, long long sst, int nf, const T *tw,
-                              T *src, cudaStream_t st) {
-    if (nf > FD_MAXF) return cudaErrorInvalidValue;
-    idft_block_kernel<T><<<dim3(blocks_for(sst / V16<T>::n, 1024), ns), RT, 0, st>>>(qb, K, ns, sst,
-                                                                                  nf, tw, src);
+cudaError_t launch_idft_block(const T *qb, int K, int kst, int ns, long long sst, int nf,
+                              const T *tw, T *src, cudaStream_t st) {
+    if (nf > FD_MAXF || K > kst) return cudaErrorInvalidValue;
+    idft_block_kernel<T><<<dim3(blocks_for(sst / V16<T>::n, 1024), ns), RT, 0, st>>>(
+        qb, K, kst, ns, sst, nf, tw, src);
     return cudaGetLastError();
 }
 
@@ -779,8 +781,8 @@ cudaError_t launch_dft_output(const T *acc, long long sst, int rows, int nx, int
                                           const float *, T *, cudaStream_t);                     \
     template cudaError_t launch_dft_output<T>(const T *, long long, int, int, int, int, int, int, \
                                               void *, unsigned *, float *, cudaStream_t);       \
-    template cudaError_t launch_idft_block<T>(const T *, int, int, long long, int, const T *, T *, \
-                                              cudaStream_t);                                     \
+    template cudaError_t launch_idft_block<T>(const T *, int, int, int, long long, int, const T *, \
+                                              T *, cudaStream_t);                                \
     template cudaError_t launch_fd_b2g_dot<T>(T *, const T *, const T *, const double *, int, int, \
                                               long long, const int *, double *, cudaStream_t);   \
     template cudaError_t launch_dft_block<T>(const T *, int, int, long long, int, const T *, T *, \
