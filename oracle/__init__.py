@@ -342,8 +342,8 @@ class Oracle:
         rr = float(np.sum(r * r))
         r0 = math.sqrt(rr)
         hist, alphas, betas = [], [], []
-        k = 0
-        for k in range(n_cg):
+        k = -1   # b = 0: x_0 = 0 is exact and no iteration runs
+        for k in range(n_cg if r0 > 0 else 0):
             Ap = self.normal_matvec(sh, p, beta, eps)
             alpha = rr / float(np.sum(p * Ap))
             x = x + alpha * p
@@ -373,8 +373,8 @@ class Oracle:
         rz = float(np.sum(r * z))
         r0 = math.sqrt(float(np.sum(r * r)))
         hist = []
-        k = 0
-        for k in range(n_cg):
+        k = -1   # b = 0: x_0 = 0 is exact and no iteration runs
+        for k in range(n_cg if r0 > 0 else 0):
             Ap = self.normal_matvec(sh, p, beta, eps)
             alpha = rz / float(np.sum(p * Ap))
             x = x + alpha * p
@@ -414,8 +414,8 @@ class Oracle:
         rr = float(np.sum(r * r))
         r0 = math.sqrt(rr)
         hist = []
-        k = 0
-        for k in range(n_cg):
+        k = -1   # b = 0: x_0 = 0 is exact and no iteration runs
+        for k in range(n_cg if r0 > 0 else 0):
             Ap = self.wri_matvec(sh, p, beta)
             alpha = rr / float(np.sum(p * Ap))
             x = x + alpha * p
@@ -467,8 +467,8 @@ class Oracle:
         rr = float(np.sum(r * r))
         r0 = math.sqrt(rr)
         hist = []
-        k = 0
-        for k in range(n_cg):
+        k = -1   # b = 0: x_0 = 0 is exact and no iteration runs
+        for k in range(n_cg if r0 > 0 else 0):
             Ap = p + self.ds_K(sh, p, beta, eps)
             alpha = rr / float(np.sum(p * Ap))
             x = x + alpha * p
@@ -515,8 +515,8 @@ class Oracle:
         rr = float(np.vdot(r, r).real)
         r0 = math.sqrt(rr)
         hist = []
-        k = 0
-        for k in range(n_cg):
+        k = -1   # b = 0: x_0 = 0 is exact and no iteration runs
+        for k in range(n_cg if r0 > 0 else 0):
             Ap = self.fd_matvec(sh, p, beta, freqs, eps)
             alpha = rr / float(np.vdot(p, Ap).real)
             x = x + alpha * p
