@@ -185,8 +185,12 @@ typedef struct esi_grad_opts {
  * WRI saddle mode (Eq. "newadj2", "gradient2"): ext_src is the WRI solution q and
  *   wavelet_dev the point sources f; u = A^{-1}(f + q), lambda = beta q (B = I); one
  *   forward run.
+ *   With dobs_dev in either saddle mode the same forward run also samples R u and
+ *   *misfit receives the objective at (m, q): Eq. "esi", 1/2 ||R u - d||^2 +
+ *   beta/2 ||B q||^2 (WRI: Eq. "wrimisfit", B = 1), summed over shots; the call then
+ *   synchronises.
  *   grad_dev    : device [N], written (sum over all shots) in the chosen parameter
- *   misfit      : host double, written in adjoint-state mode with dobs (may be NULL)
+ *   misfit      : host double, written with dobs (may be NULL)
  */
 ESI_API esi_status esi_gradient(esi_ctx *ctx, const void *wavelet_dev, const void *ext_src_dev,
                                 const void *dobs_dev, const void *adj_src_dev,

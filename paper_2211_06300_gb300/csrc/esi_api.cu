@@ -1087,10 +1087,46 @@ esi_status gradient_impl(esi_ctx *ctx, const void *wavelet, const void *ext, con
             a.inj = inj_view<T>(ctx->inj_src);
             a.inj_trace = reinterpret_cast<const T *>(wavelet);
         }
+        // with the observed data, the objective at (m, q) from the same run: Eq. "esi"
+        // (WRI: "wrimisfit"), 1/2 ||R u - d||^2 + beta/2 ||B q||^2 (B = 1 for WRI)
+        const bool want_J = misfit && dobs;
+        if (want_J) {
+            CK(ctx->traces.ensure(std::max<size_t>((size_t)ctx->total_rec * nt * sizeof(T), 16)));
+            flags |= F_SMP;
+            a.smp = smp_view<T>(ctx->smp_rec);
+            a.smp_out = ctx->traces.as<T>();
+        }
         T *cur = ctx->u0.as<T>(), *po = ctx->u1.as<T>();
         e = fwd_loop<T>(ctx, a, flags, cur, po, 0, nt);
         if (e != ESI_OK) return e;
         extra = -o->beta;
+        if (want_J) {
+            T *tr = ctx->traces.as<T>();
+            CKL(launch_sample_global<T>(a.smp, cur, ctx->sst, tr, nt - 1, ctx->st));
+            const int nblk = 1024;
+            CK(ctx->part.ensure(sizeof(double) * (size_t)nblk * std::max(ns, 1)));
+            CK(ctx->scal.ensure(sizeof(double) * (1 + ns)));
+            double *sc = ctx->scal.as<double>();
+            CKL(launch_residual<T>(tr, reinterpret_cast<const T *>(dobs),
+                                   (long long)ctx->total_rec * nt, ctx->part.as<double>(), nblk,
+                                   ctx->st));
+            CKL(launch_reduce_partials(ctx->part.as<double>(), nblk, 1, sc, ctx->st));
+            CK(ctx->pb2.ensure((size_t)ns * ctx->sst * sizeof(T)));
+            CKL(launch_b2_maps<T>(ctx->pb2.as<T>(), nullptr, ns, ctx->g.nz, ctx->g.ny, ctx->g.nx,
+                                  ctx->px, T(o->beta), eps, T(ctx->g.dx),
+                                  ctx->src_pos.as<double>(), wri ? 1 : 0, ctx->st));
+            CKL(launch_penalty<T>(reinterpret_cast<const T *>(ext), ctx->pb2.as<T>(), ns, nt,
+                                  (long long)ctx->g.nz * ctx->g.ny, ctx->g.nx, ctx->px, ctx->sst,
+                                  ctx->part.as<double>(), nblk, ctx->st));
+            CKL(launch_reduce_partials(ctx->part.as<double>(), nblk, ns, sc + 1, ctx->st));
+            std::vector<double> h(1 + ns);
+            CK(cudaMemcpyAsync(h.data(), sc, sizeof(double) * (1 + ns), cudaMemcpyDeviceToHost,
+                               ctx->st));
+            CK(cudaStreamSynchronize(ctx->st));
+            double J = h[0];
+            for (int s = 0; s < ns; ++s) J += h[1 + s];
+            *misfit = J;
+        }
     } else {
         if (!wavelet && !ext) return ctx->fail(ESI_ERR_ARG, "no source given");
         if (!adj && !dobs) return ctx->fail(ESI_ERR_ARG, "need observed data or an adjoint source");

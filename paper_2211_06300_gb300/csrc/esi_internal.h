@@ -277,6 +277,21 @@ template <typename T>
 cudaError_t launch_fd_b2g_dot(T *out, const T *p, const T *pb2, const double *G, int nf, int ns,
                               long long sst, const int *active, double *part, cudaStream_t st);
 
+// Objective and outer loop: per-shot partials [ns][nblk] of 1/2 sum pb2 q^2 over the dense
+// field q[ns][nt][rows * nx]; dense model-vector dot and max |a| partials [nblk];
+// z = alpha x + beta y (y may be NULL), clamped to [lo, hi] when lo < hi
+template <typename T>
+cudaError_t launch_penalty(const T *q, const T *pb2, int ns, int nt, long long rows, int nx,
+                           int px, long long sst, double *part, int nblk, cudaStream_t st);
+template <typename T>
+cudaError_t launch_mdot(const T *a, const T *b, long long n, double *part, int nblk,
+                        cudaStream_t st);
+template <typename T>
+cudaError_t launch_mamax(const T *a, long long n, double *part, int nblk, cudaStream_t st);
+template <typename T>
+cudaError_t launch_mlincomb(T *z, double alpha, const T *x, double beta, const T *y, long long n,
+                            double lo, double hi, cudaStream_t st);
+
 // DTFT output: pitched accumulators [ns][nf][sst][2] -> caller dense [ns][nf][N][2], either
 // copied in the field precision (half == 0) or as half pairs with a per (shot, f) scale
 template <typename T>

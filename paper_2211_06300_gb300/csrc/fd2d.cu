@@ -394,6 +394,8 @@ cudaError_t launch_step2(unsigned flags, const StepArgs<T> &a, int ns, cudaStrea
         // saddle-point gradient
         ESI_CASE(F_EXT | F_SAD)
         ESI_CASE(F_EXT | F_PT | F_SAD)   // WRI: u = A^{-1}(f + q)
+        ESI_CASE(F_EXT | F_SMP | F_SAD)  // ... with the traces for the objective
+        ESI_CASE(F_EXT | F_PT | F_SMP | F_SAD)
         // adjoint modelling
         ESI_CASE(F_PT)
         ESI_CASE(F_PT | F_OUT)

@@ -745,6 +745,102 @@ cudaError_t launch_dft_output(const T *acc, long long sst, int rows, int nx, int
     return cudaGetLastError();
 }
 
+namespace {
+
+// The penalty of Eq. "esi" (WRI: "wrimisfit"): per-shot partials of 1/2 sum pb2 q^2 over the
+// caller's dense space-time field q[s][t][rows][nx], pb2 = beta B^2 pitched per shot.  A block
+// walks (t, row) lines; its threads stride along x.
+template <typename T>
+__global__ void penalty_kernel(const T *q, const T *pb2, int nt, long long rows, int nx, int px,
+                               long long sst, double *part) {
+    const int s = blockIdx.y;
+    const long long nlines = (long long)nt * rows;
+    const T *qs = q + (long long)s * nlines * nx;
+    double acc = 0.0;
+    for (long long l = blockIdx.x; l < nlines; l += gridDim.x) {
+        const T *ql = qs + l * nx;
+        const T *wl = pb2 + (long long)s * sst + (l % rows) * px;
+        for (int x = threadIdx.x; x < nx; x += RT) {
+            const T v = ql[x];
+            acc += double(wl[x] * v * v);
+        }
+    }
+    const double t = block_sum_d(acc);
+    if (threadIdx.x == 0) part[(long long)s * gridDim.x + blockIdx.x] = 0.5 * t;
+}
+
+// Model-space vectors of the outer loop (dense, any length): <a, b> and max |a| partials in
+// double, and z = alpha x + beta y, clamped to [lo, hi] when lo < hi.
+template <typename T>
+__global__ void mdot_kernel(const T *a, const T *b, long long n, double *part) {
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n;
+         i += (long long)gridDim.x * RT)
+        acc += double(a[i]) * double(b[i]);
+    const double t = block_sum_d(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+template <typename T>
+__global__ void mamax_kernel(const T *a, long long n, double *part) {
+    __shared__ double red[RT / 32];
+    double m = 0.0;
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n;
+         i += (long long)gridDim.x * RT)
+        m = fmax(m, fabs(double(a[i])));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < RT / 32; ++w) t = fmax(t, red[w]);
+        part[blockIdx.x] = t;
+    }
+}
+
+template <typename T>
+__global__ void mlincomb_kernel(T *z, double alpha, const T *x, double beta, const T *y,
+                                long long n, double lo, double hi) {
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n;
+         i += (long long)gridDim.x * RT) {
+        double v = alpha * double(x[i]);
+        if (y) v += beta * double(y[i]);
+        if (lo < hi) v = fmin(fmax(v, lo), hi);
+        z[i] = T(v);
+    }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_penalty(const T *q, const T *pb2, int ns, int nt, long long rows, int nx,
+                           int px, long long sst, double *part, int nblk, cudaStream_t st) {
+    penalty_kernel<T><<<dim3(nblk, ns), RT, 0, st>>>(q, pb2, nt, rows, nx, px, sst, part);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_mdot(const T *a, const T *b, long long n, double *part, int nblk,
+                        cudaStream_t st) {
+    mdot_kernel<T><<<nblk, RT, 0, st>>>(a, b, n, part);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_mamax(const T *a, long long n, double *part, int nblk, cudaStream_t st) {
+    mamax_kernel<T><<<nblk, RT, 0, st>>>(a, n, part);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_mlincomb(T *z, double alpha, const T *x, double beta, const T *y, long long n,
+                            double lo, double hi, cudaStream_t st) {
+    mlincomb_kernel<T><<<blocks_for(n, 2048), RT, 0, st>>>(z, alpha, x, beta, y, n, lo, hi);
+    return cudaGetLastError();
+}
+
 #define ESI_INST(T)                                                                              \
     template cudaError_t launch_setup_cc<T>(const T *, T *, int, int, int, int, double, double,  \
                                             double *, int, cudaStream_t);                        \
@@ -781,6 +877,13 @@ cudaError_t launch_dft_output(const T *acc, long long sst, int rows, int nx, int
                                           const float *, T *, cudaStream_t);                     \
     template cudaError_t launch_dft_output<T>(const T *, long long, int, int, int, int, int, int, \
                                               void *, unsigned *, float *, cudaStream_t);       \
+    template cudaError_t launch_penalty<T>(const T *, const T *, int, int, long long, int, int,    \
+                                           long long, double *, int, cudaStream_t);              \
+    template cudaError_t launch_mdot<T>(const T *, const T *, long long, double *, int,           \
+                                        cudaStream_t);                                           \
+    template cudaError_t launch_mamax<T>(const T *, long long, double *, int, cudaStream_t);      \
+    template cudaError_t launch_mlincomb<T>(T *, double, const T *, double, const T *, long long,  \
+                                            double, double, cudaStream_t);                       \
     template cudaError_t launch_idft_block<T>(const T *, int, int, int, long long, int, const T *, \
                                               T *, cudaStream_t);                                \
     template cudaError_t launch_fd_b2g_dot<T>(T *, const T *, const T *, const double *, int, int, \
