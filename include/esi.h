@@ -196,6 +196,69 @@ ESI_API esi_status esi_gradient(esi_ctx *ctx, const void *wavelet_dev, const voi
                                 const void *dobs_dev, const void *adj_src_dev,
                                 const esi_grad_opts *opts, void *grad_dev, double *misfit);
 
+/*
+ * esi_invert -- the outer loop, Algorithm "nestedloop" (variable projection between m and
+ * q): per outer iteration i, the inner CG solve for q at the penalty beta_i = beta0 growth^i
+ * (ESI: Eq. "normalewi" with the chosen preconditioner; WRI: Eq. "normalwri"), the objective
+ * (Eq. "esi" / "wrimisfit") and the saddle-point gradient in the velocity (Eq. "gradewi" /
+ * "gradient2") from one forward run, an L-BFGS direction (two-loop recursion over the newest
+ * `memory` pairs, initial matrix (s^T y / y^T y) I; a pair is kept when s^T y > 1e-12 |s| |y|;
+ * a non-descent direction clears the memory and takes -g) and a projected backtracking line
+ * search (trial v_t = clamp(v + alpha d, vmin, vmax); accepted when J(v_t) <= J(v) +
+ * c1 g^T (v_t - v); alpha halved up to max_ls times; first trial alpha = 1 with pairs, else
+ * the step moving the fastest cell by step_frac max|v|).  A new penalty re-evaluates J and g
+ * and clears the memory.  The sponge keeps the reference velocity fixed at creation.
+ *   wavelet_dev  : point sources f (WRI only; else NULL)
+ *   dobs_dev     : device seismogram-layout observed data
+ *   velocity_dev : device [N] velocity: the start model in, the last accepted model out;
+ *                  the context's model is left at it
+ *   grad_dev     : device [N] caller scratch: each evaluation's gradient is written here
+ *                  before `reduce` sees it; on return, the gradient at the output model
+ *   reduce       : (opts) NULL on one rank; for shots sharded over ranks, a callback that
+ *                  sums J (host) and grad_dev (device, n values, stream synchronised) over
+ *                  the ranks in place and returns 0
+ * The context owns the scratch (the inner solution q, [ns][nt][N], and 6 + 2 memory model
+ * vectors).  A failed line search ends the loop with ESI_OK and stop_reason 1.  Errors:
+ * ESI_ERR_ARG (options, a reduce failure), ESI_ERR_CFL (vmax violates the stability limit),
+ * and those of esi_cg_solve and esi_gradient.
+ */
+typedef int (*esi_reduce_fn)(void *user, double *J, void *grad_dev, long long n);
+
+typedef struct esi_invert_opts {
+    int mode;              /* ESI_GRAD_SADDLE_POINT (ESI) or ESI_GRAD_WRI_SADDLE (WRI) */
+    int n_outer;           /* outer iterations (>= 0) */
+    int n_cg;              /* inner CG iterations (cap, >= 1) */
+    double cg_tol;         /* inner relative tolerance; 0 runs n_cg iterations */
+    int precond;           /* ESI inner solve: esi_precond */
+    double beta0, growth;  /* penalty schedule beta_i = beta0 growth^i (> 0) */
+    int memory;            /* L-BFGS pairs, 1 .. 64 */
+    double c1;             /* Armijo constant, (0, 1) */
+    double step_frac;      /* first-trial scale without pairs (> 0) */
+    int max_ls;            /* line-search trials (>= 1) */
+    double vmin, vmax;     /* velocity bounds, 0 < vmin < vmax */
+    double eps;            /* annihilator offset in metres (<= 0: dx) */
+    esi_reduce_fn reduce;  /* cross-rank sum, or NULL */
+    void *reduce_user;
+} esi_invert_opts;
+
+typedef struct esi_invert_report {
+    int max_iters;         /* capacity of the host arrays below (>= n_outer) */
+    double *J_start;       /* per iteration: J at its start and after its step (its penalty) */
+    double *J_end;
+    double *alpha;         /* accepted step */
+    double *beta;          /* penalty */
+    int *trials;           /* line-search trials */
+    int iters_done;        /* accepted steps */
+    int evaluations;       /* objective + gradient evaluations */
+    int cg_iters_total;    /* inner iterations summed over evaluations (max over shots) */
+    int stop_reason;       /* 0 all iterations, 1 line search failed, 2 zero gradient */
+    double ms_total;       /* host wall clock */
+} esi_invert_report;
+
+ESI_API esi_status esi_invert(esi_ctx *ctx, const esi_invert_opts *opts, const void *wavelet_dev,
+                              const void *dobs_dev, void *velocity_dev, void *grad_dev,
+                              esi_invert_report *report);
+
 typedef enum esi_dft_out { ESI_DFT_C64 = 0, ESI_DFT_C32_HALF = 1 } esi_dft_out;
 
 /*

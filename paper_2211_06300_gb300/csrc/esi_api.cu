@@ -98,6 +98,7 @@ struct esi_ctx {
     DBuf pc_dev;                   // learned-PCG dot partials, sums and per-shot theta
     DBuf dftsnap;                  // blocked DTFT: DFT_BLOCK new states [slot][ns][sst]
     DBuf wri_res;                  // WRI: data residual d - S f [traces]
+    DBuf invq, invv, invpart;      // outer loop: inner solution q, model vectors, dot partials
     DBuf fdv, fdsrc, fdtr;         // frequency-domain CG: 5 complex vectors, source stash, traces
     DBuf fdsyn, fdfold, fdG;       // its twiddle tables and the Gram matrix F F^H / nt
     DBuf dsv, dseg;                // data-space CG: 5 data vectors; shot segments
@@ -2033,6 +2034,205 @@ esi_status fdcg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, cons
     return conv ? ESI_OK : ESI_ERR_NOT_CONVERGED;
 }
 
+// ------------------------------------------------------------------ outer loop
+// Algorithm "nestedloop": inner CG solve, objective and saddle-point gradient in v, L-BFGS
+// direction, projected Armijo backtracking, penalty schedule.  Model vectors are dense [N]
+// in the field precision; their dot products and maxima are reduced in double on the host
+// (block partials summed in a fixed order).
+template <typename T>
+esi_status invert_impl(esi_ctx *ctx, const esi_invert_opts *o, const void *wavelet,
+                       const void *dobs, void *vel, void *gwork, esi_invert_report *rep) {
+    using clk = std::chrono::steady_clock;
+    const auto t_start = clk::now();
+    const bool wri = o->mode == ESI_GRAD_WRI_SADDLE;
+    if (o->mode != ESI_GRAD_SADDLE_POINT && !wri)
+        return ctx->fail(ESI_ERR_ARG, "mode must be the ESI or the WRI saddle-point mode");
+    if (wri && !wavelet) return ctx->fail(ESI_ERR_ARG, "WRI needs the point sources f");
+    if (o->n_outer < 0 || o->n_cg < 1 || o->memory < 1 || o->memory > 64 || o->max_ls < 1 ||
+        !(o->beta0 > 0) || !(o->growth > 0) || !(o->c1 > 0 && o->c1 < 1) || !(o->step_frac > 0) ||
+        !(o->vmin > 0) || !(o->vmax > o->vmin) || !std::isfinite(o->vmax) || !(o->cg_tol >= 0))
+        return ctx->fail(ESI_ERR_ARG, "bad outer-loop options");
+    if (rep && rep->max_iters < o->n_outer)
+        return ctx->fail(ESI_ERR_ARG, "report arrays shorter than n_outer");
+    if (!wri && o->precond == ESI_PC_LEARNED && !ctx->pc)
+        return ctx->fail(ESI_ERR_ARG, "the learned preconditioner is not loaded");
+    const long long N = ctx->N;
+    const int M = o->memory;
+    CK(ctx->invq.ensure((size_t)ctx->ns * ctx->nt * N * sizeof(T)));
+    CK(ctx->invv.ensure((size_t)(6 + 2 * M) * N * sizeof(T)));
+    T *q = ctx->invq.as<T>(), *V = ctx->invv.as<T>();
+    T *x = reinterpret_cast<T *>(vel), *gw = reinterpret_cast<T *>(gwork);
+    T *g = V, *gt = V + N, *xt = V + 2 * N, *d = V + 3 * N, *sv = V + 4 * N, *yv = V + 5 * N;
+    T *Sp = V + 6 * N, *Yp = V + (6 + M) * N;   // pair slots
+    const int nblk = 256;
+    CK(ctx->invpart.ensure(sizeof(double) * nblk));
+    std::vector<double> hp(nblk);
+    auto reduce_host = [&](bool is_max, double &out) -> esi_status {
+        CK(cudaMemcpyAsync(hp.data(), ctx->invpart.p, sizeof(double) * nblk, cudaMemcpyDeviceToHost,
+                           ctx->st));
+        CK(cudaStreamSynchronize(ctx->st));
+        out = 0;
+        for (double v : hp) out = is_max ? std::max(out, v) : out + v;
+        return ESI_OK;
+    };
+    auto dot = [&](const T *a, const T *b, double &out) -> esi_status {
+        CKL(launch_mdot<T>(a, b, N, ctx->invpart.as<double>(), nblk, ctx->st));
+        return reduce_host(false, out);
+    };
+    auto amax = [&](const T *a, double &out) -> esi_status {
+        CKL(launch_mamax<T>(a, N, ctx->invpart.as<double>(), nblk, ctx->st));
+        return reduce_host(true, out);
+    };
+    auto lin = [&](T *z, double al, const T *xx, double be, const T *yy, bool clamp) -> esi_status {
+        CKL(launch_mlincomb<T>(z, al, xx, be, yy, N, clamp ? o->vmin : 0.0, clamp ? o->vmax : 0.0,
+                               ctx->st));
+        return ESI_OK;
+    };
+    int evals = 0, cg_total = 0;
+    esi_grad_opts go{};
+    go.mode = o->mode;
+    go.param = ESI_PARAM_V;
+    go.ckpt_every = 1;
+    go.ckpt_kind = ESI_CKPT_F32;
+    go.eps = o->eps;
+    // J and g (into g_out) at the model m
+    auto eval = [&](const T *m, double beta, T *g_out, double &J) -> esi_status {
+        esi_status st = setup_model<T>(ctx, m, false);
+        if (st != ESI_OK) return st;
+        std::vector<int> its(ctx->ns);
+        esi_cg_report cr{};
+        cr.iters = its.data();
+        st = wri ? cg_impl<T>(ctx, beta, o->cg_tol, o->n_cg, dobs, q, ESI_PC_NONE, 0.0, &cr, wavelet)
+                 : cg_impl<T>(ctx, beta, o->cg_tol, o->n_cg, dobs, q, o->precond, o->eps, &cr);
+        if (st != ESI_OK && st != ESI_ERR_NOT_CONVERGED) return st;
+        cg_total += cr.iters_max;
+        go.beta = beta;
+        st = gradient_impl<T>(ctx, wri ? wavelet : nullptr, q, dobs, nullptr, &go, gw, &J);
+        if (st != ESI_OK) return st;
+        if (o->reduce) {
+            CK(cudaStreamSynchronize(ctx->st));
+            if (o->reduce(o->reduce_user, &J, gw, N) != 0)
+                return ctx->fail(ESI_ERR_ARG, "the reduce callback failed");
+        }
+        CK(cudaMemcpyAsync(g_out, gw, N * sizeof(T), cudaMemcpyDeviceToDevice, ctx->st));
+        ++evals;
+        return ESI_OK;
+    };
+    auto beta_of = [&](int i) { return o->beta0 * std::pow(o->growth, i); };
+    std::vector<double> rho, gam;   // per stored pair (oldest first): 1 / y^T s, s^T y / y^T y
+    std::vector<int> slot;          // pair -> slot index
+    int next_slot = 0;
+    double J = 0, Jt = 0;
+    esi_status e = eval(x, beta_of(0), g, J);
+    if (e != ESI_OK) return e;
+    int stop = 0, done = 0;
+    for (int i = 0; i < o->n_outer; ++i) {
+        const double beta = beta_of(i);
+        if (i > 0 && beta != beta_of(i - 1)) {
+            if ((e = eval(x, beta, g, J)) != ESI_OK) return e;
+            rho.clear(), gam.clear(), slot.clear();
+        }
+        if (rep && rep->beta) rep->beta[i] = beta;
+        if (rep && rep->J_start) rep->J_start[i] = J;
+        // two-loop recursion: d = -H g
+        if ((e = lin(d, 1.0, g, 0.0, nullptr, false)) != ESI_OK) return e;
+        const int np = int(slot.size());
+        std::vector<double> a(np);
+        for (int k = np - 1; k >= 0; --k) {
+            double sd;
+            if ((e = dot(Sp + (size_t)slot[k] * N, d, sd)) != ESI_OK) return e;
+            a[k] = rho[k] * sd;
+            if ((e = lin(d, 1.0, d, -a[k], Yp + (size_t)slot[k] * N, false)) != ESI_OK) return e;
+        }
+        if (np > 0 && (e = lin(d, gam[np - 1], d, 0.0, nullptr, false)) != ESI_OK) return e;
+        for (int k = 0; k < np; ++k) {
+            double yd;
+            if ((e = dot(Yp + (size_t)slot[k] * N, d, yd)) != ESI_OK) return e;
+            const double b = rho[k] * yd;
+            if ((e = lin(d, 1.0, d, a[k] - b, Sp + (size_t)slot[k] * N, false)) != ESI_OK) return e;
+        }
+        if ((e = lin(d, -1.0, d, 0.0, nullptr, false)) != ESI_OK) return e;
+        double gd;
+        if ((e = dot(g, d, gd)) != ESI_OK) return e;
+        bool have_pairs = np > 0;
+        if (!(gd < 0)) {   // not a descent direction: steepest descent, memory cleared
+            rho.clear(), gam.clear(), slot.clear();
+            have_pairs = false;
+            if ((e = lin(d, -1.0, g, 0.0, nullptr, false)) != ESI_OK) return e;
+        }
+        double alpha = 1.0;
+        if (!have_pairs) {
+            double dmax, xmax;
+            if ((e = amax(d, dmax)) != ESI_OK) return e;
+            if ((e = amax(x, xmax)) != ESI_OK) return e;
+            if (!(dmax > 0)) {
+                stop = 2;
+                break;
+            }
+            alpha = o->step_frac * xmax / dmax;
+        }
+        bool ok = false;
+        int t = 0;
+        for (t = 0; t < o->max_ls; ++t) {
+            if ((e = lin(xt, 1.0, x, alpha, d, true)) != ESI_OK) return e;
+            if ((e = eval(xt, beta, gt, Jt)) != ESI_OK) return e;
+            if ((e = lin(sv, 1.0, xt, -1.0, x, false)) != ESI_OK) return e;
+            double gs;
+            if ((e = dot(g, sv, gs)) != ESI_OK) return e;
+            if (Jt <= J + o->c1 * gs) {
+                ok = true;
+                break;
+            }
+            alpha *= 0.5;
+        }
+        if (rep && rep->trials) rep->trials[i] = std::min(t + 1, o->max_ls);
+        if (!ok) {
+            stop = 1;
+            break;
+        }
+        // pair (s, y) = (xt - x, gt - g), kept on positive curvature
+        if ((e = lin(yv, 1.0, gt, -1.0, g, false)) != ESI_OK) return e;
+        double sy, yy, ss;
+        if ((e = dot(sv, yv, sy)) != ESI_OK) return e;
+        if ((e = dot(yv, yv, yy)) != ESI_OK) return e;
+        if ((e = dot(sv, sv, ss)) != ESI_OK) return e;
+        if (sy > 1e-12 * std::sqrt(ss) * std::sqrt(yy)) {
+            int sl;
+            if (int(slot.size()) == M) {   // drop the oldest, reuse its slot
+                sl = slot.front();
+                slot.erase(slot.begin());
+                rho.erase(rho.begin());
+                gam.erase(gam.begin());
+            } else {
+                sl = next_slot++;
+            }
+            CK(cudaMemcpyAsync(Sp + (size_t)sl * N, sv, N * sizeof(T), cudaMemcpyDeviceToDevice, ctx->st));
+            CK(cudaMemcpyAsync(Yp + (size_t)sl * N, yv, N * sizeof(T), cudaMemcpyDeviceToDevice, ctx->st));
+            slot.push_back(sl);
+            rho.push_back(1.0 / sy);
+            gam.push_back(sy / yy);
+        }
+        CK(cudaMemcpyAsync(x, xt, N * sizeof(T), cudaMemcpyDeviceToDevice, ctx->st));
+        std::swap(g, gt);
+        J = Jt;
+        ++done;
+        if (rep && rep->J_end) rep->J_end[i] = J;
+        if (rep && rep->alpha) rep->alpha[i] = alpha;
+    }
+    // leave the context at the output model and the caller's gradient at its gradient
+    if ((e = setup_model<T>(ctx, x, false)) != ESI_OK) return e;
+    CK(cudaMemcpyAsync(gw, g, N * sizeof(T), cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (rep) {
+        rep->iters_done = done;
+        rep->evaluations = evals;
+        rep->cg_iters_total = cg_total;
+        rep->stop_reason = stop;
+        rep->ms_total = std::chrono::duration<double, std::milli>(clk::now() - t_start).count();
+    }
+    return check_dev_err(ctx);
+}
+
 template <typename T>
 esi_status create_impl(esi_ctx *ctx, const void *vel) {
     CK(ctx->dev_err.ensure(sizeof(int)));
@@ -2255,6 +2455,18 @@ ESI_API esi_status esi_dft_extract(esi_ctx *ctx, const void *wavelet_dev, const 
                                   scales_host, traces_dev)
                : dft_impl<float>(ctx, wavelet_dev, ext_src_dev, freqs_hz, nf, out_dev, out_kind,
                                  scales_host, traces_dev);
+}
+
+ESI_API esi_status esi_invert(esi_ctx *ctx, const esi_invert_opts *opts, const void *wavelet_dev,
+                              const void *dobs_dev, void *velocity_dev, void *grad_dev,
+                              esi_invert_report *report) {
+    if (!ctx) return ESI_ERR_ARG;
+    if (!opts || !dobs_dev || !velocity_dev || !grad_dev)
+        return ctx->fail(ESI_ERR_ARG, "bad outer-loop arguments");
+    ctx->err.clear();
+    return ctx->g.dtype == ESI_F64
+               ? invert_impl<double>(ctx, opts, wavelet_dev, dobs_dev, velocity_dev, grad_dev, report)
+               : invert_impl<float>(ctx, opts, wavelet_dev, dobs_dev, velocity_dev, grad_dev, report);
 }
 
 ESI_API esi_status esi_fdcg_solve(esi_ctx *ctx, double lambda, double tol, int max_iter,

@@ -33,7 +33,7 @@ EXPORTS = ["esi_create", "esi_destroy", "esi_set_stream", "esi_set_velocity", "e
            "esi_pc_fallbacks", "esi_pc_pack", "esi_pc_create", "esi_pc_destroy",
            "esi_pc_last_error", "esi_pc_set_params", "esi_pc_get_params", "esi_pc_apply",
            "esi_pc_grad", "esi_pc_train_step", "esi_wri_solve", "esi_dscg_solve",
-           "esi_fdcg_solve"]
+           "esi_fdcg_solve", "esi_invert"]
 
 
 class EsiGrid(ctypes.Structure):
@@ -60,6 +60,33 @@ class EsiCgReport(ctypes.Structure):
                 ("rel_res", ctypes.POINTER(ctypes.c_double)), ("ms_matvec", ctypes.c_double),
                 ("ms_vector", ctypes.c_double), ("ms_precond", ctypes.c_double),
                 ("ms_total", ctypes.c_double)]
+
+
+REDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                             ctypes.c_void_p, ctypes.c_longlong)
+
+
+class EsiInvertOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("n_outer", ctypes.c_int), ("n_cg", ctypes.c_int),
+                ("cg_tol", ctypes.c_double), ("precond", ctypes.c_int),
+                ("beta0", ctypes.c_double), ("growth", ctypes.c_double),
+                ("memory", ctypes.c_int), ("c1", ctypes.c_double),
+                ("step_frac", ctypes.c_double), ("max_ls", ctypes.c_int),
+                ("vmin", ctypes.c_double), ("vmax", ctypes.c_double), ("eps", ctypes.c_double),
+                ("reduce", REDUCE_FN), ("reduce_user", ctypes.c_void_p)]
+
+
+class EsiInvertReport(ctypes.Structure):
+    _fields_ = [("max_iters", ctypes.c_int), ("J_start", ctypes.POINTER(ctypes.c_double)),
+                ("J_end", ctypes.POINTER(ctypes.c_double)),
+                ("alpha", ctypes.POINTER(ctypes.c_double)),
+                ("beta", ctypes.POINTER(ctypes.c_double)),
+                ("trials", ctypes.POINTER(ctypes.c_int)), ("iters_done", ctypes.c_int),
+                ("evaluations", ctypes.c_int), ("cg_iters_total", ctypes.c_int),
+                ("stop_reason", ctypes.c_int), ("ms_total", ctypes.c_double)]
+
+
+STOP_REASONS = {0: "ok", 1: "line search failed", 2: "zero gradient"}
 
 
 class EsiKernelStat(ctypes.Structure):
@@ -107,6 +134,8 @@ def load_library(require_gpu: bool = True) -> ctypes.CDLL:
     L.esi_fdcg_solve.argtypes = [vp, d, d, i, vp, ctypes.POINTER(d), i, vp, d,
                                  ctypes.POINTER(EsiCgReport)]
     L.esi_pc_load.argtypes = [vp, vp, ctypes.c_size_t]
+    L.esi_invert.argtypes = [vp, ctypes.POINTER(EsiInvertOpts), vp, vp, vp, vp,
+                             ctypes.POINTER(EsiInvertReport)]
     L.esi_normal_apply.argtypes = [vp, d, d, vp, vp]
     L.esi_pc_param_count.argtypes = []
     L.esi_pc_param_count.restype = ctypes.c_size_t
@@ -138,7 +167,7 @@ def load_library(require_gpu: bool = True) -> ctypes.CDLL:
                  "esi_pc_set_params", "esi_pc_get_params", "esi_pc_apply", "esi_pc_grad",
                  "esi_pc_train_step",
                  "esi_adjoint", "esi_gradient", "esi_dft_extract", "esi_cg_solve",
-                 "esi_pc_load", "esi_wri_solve", "esi_dscg_solve", "esi_fdcg_solve"):
+                 "esi_pc_load", "esi_wri_solve", "esi_dscg_solve", "esi_fdcg_solve", "esi_invert"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -392,6 +421,56 @@ class Context:
                   "ms_precond": rep.ms_precond,
                   "ms_total": rep.ms_total, "status": st}
         return q, report
+
+    def invert(self, dobs, velocity, mode: str = "esi", n_outer: int = 3, n_cg: int = 10,
+               cg_tol: float = 0.0, precond: str = "diag", beta0: float = 1.0,
+               growth: float = 1.0, memory: int = 5, c1: float = 1e-4, step_frac: float = 0.02,
+               max_ls: int = 8, vmin: float = 1.0, vmax: float = 1e9, eps: float = 0.0,
+               wavelet=None, grad=None, reduce=None):
+        """Algorithm "nestedloop" (esi_invert): velocity (tensor, updated in place) from the
+        observed data by n_outer L-BFGS steps on the ESI (mode "esi") or WRI ("wri") reduced
+        objective.  `reduce(J, grad) -> J_total`, for shots sharded over ranks, sums J and the
+        gradient tensor in place over the ranks.  Returns (gradient, report dict)."""
+        g = self.torch.empty(self.shape, dtype=self.dtype, device=self.device) if grad is None else grad
+        o = EsiInvertOpts()
+        o.mode = GRAD_MODES["saddle" if mode == "esi" else mode]
+        o.n_outer, o.n_cg, o.cg_tol = int(n_outer), int(n_cg), float(cg_tol)
+        o.precond = PC[precond]
+        o.beta0, o.growth, o.memory = float(beta0), float(growth), int(memory)
+        o.c1, o.step_frac, o.max_ls = float(c1), float(step_frac), int(max_ls)
+        o.vmin, o.vmax, o.eps = float(vmin), float(vmax), float(eps)
+        cb = None
+        if reduce is not None:
+            def _cb(user, jp, gp, n):
+                try:
+                    jp[0] = float(reduce(float(jp[0]), g))
+                    self.torch.cuda.current_stream().synchronize()
+                    return 0
+                except Exception:   # reported to the caller as ESI_ERR_ARG
+                    return 1
+            cb = REDUCE_FN(_cb)
+            o.reduce = cb
+        k = max(int(n_outer), 1)
+        arr = {n: np.zeros(k) for n in ("J_start", "J_end", "alpha", "beta")}
+        trials = np.zeros(k, dtype=np.int32)
+        rep = EsiInvertReport()
+        rep.max_iters = k
+        for n, a in arr.items():
+            setattr(rep, n, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        rep.trials = trials.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        self._check(self.L.esi_invert(self.h, ctypes.byref(o), _ptr(wavelet), _ptr(dobs),
+                                      _ptr(velocity), _ptr(g), ctypes.byref(rep)))
+        n = rep.iters_done
+        tried = n + (1 if rep.stop_reason == 1 else 0)   # a failed line search was tried
+        out = {"iters_done": n, "evaluations": rep.evaluations,
+               "cg_iters_total": rep.cg_iters_total,
+               "stop": STOP_REASONS.get(rep.stop_reason, str(rep.stop_reason)),
+               "ms_total": rep.ms_total, "trials": trials[:tried].tolist(),
+               "J_start": arr["J_start"][:tried].tolist(), "beta": arr["beta"][:tried].tolist(),
+               "J_end": arr["J_end"][:n].tolist(), "alpha": arr["alpha"][:n].tolist()}
+        del cb
+        return g, out
+
 
 
 class PCNet:

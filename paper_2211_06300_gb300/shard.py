@@ -12,6 +12,8 @@ from __future__ import annotations
 
 from typing import Tuple
 
+import numpy as np
+
 
 def shot_range(ns_total: int, rank: int, world: int) -> Tuple[int, int]:
     """Contiguous shots [lo, hi) of `rank`; the first ns_total % world ranks take one more."""
@@ -53,3 +55,19 @@ def sum_over_ranks(x: float, dist=None, device=None) -> float:
     t = torch.tensor([float(x)], dtype=torch.float64, device=device)
     dist.all_reduce(t)
     return float(t)
+
+
+def reduce_objective(J: float, g, dist=None):
+    """The outer loop's exchange: J and the model gradient `g` summed over the ranks in rank
+    order.  For a torch tensor `g` (updated in place, dtype and device kept) the total J is
+    returned; for a numpy array, (J_total, g_total)."""
+    import torch
+    is_np = not isinstance(g, torch.Tensor)
+    gt = torch.from_numpy(np.ascontiguousarray(g)) if is_np else g
+    t = torch.cat([torch.tensor([J], dtype=torch.float64, device=gt.device),
+                   gt.reshape(-1).to(torch.float64)])
+    tot = ordered_sum(t, dist)
+    if is_np:
+        return float(tot[0]), tot[1:].numpy().reshape(np.shape(g)).astype(np.asarray(g).dtype)
+    gt.copy_(tot[1:].reshape(gt.shape).to(gt.dtype))
+    return float(tot[0])

@@ -1,6 +1,8 @@
 """The N > 1 path on CPU: two gloo ranks split the shots, each computes its shots' misfit
 gradients with the oracle, and the ordered sum over ranks equals the single-process sum over
-all shots (the one exchange of the outer loop); times reduce by max, work by sum."""
+all shots (the one exchange of the outer loop); times reduce by max, work by sum.  The whole
+outer loop (Algorithm "nestedloop") sharded the same way reproduces the single-process
+inversion."""
 import os
 import socket
 
@@ -92,3 +94,52 @@ def test_two_gloo_ranks_reproduce_the_single_process_gradient(tmp_path):
     ref = np.concatenate([[J], g])
     assert np.allclose(r0[:-2], ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
     assert r0[-2] == 2.0 and r0[-1] == 5.0          # max time, total shots
+
+
+def _outer_case():
+    import oracle
+    from oracle import outer
+    from paper_2211_06300_gb300 import synth
+    shape, dx, dt, nt, nb = (14, 16), 10.0, 1e-3, 30, 4
+    v = synth.dipping_layers(shape, dx, 5, nlayers=3, vmin=1500, vmax=2300, nanom=1, sigma=25.0)
+    vt = v + synth.gaussian_blob(shape, dx, 3, amp=60.0, sigma=30.0)
+    srcs = [(25.0, 0.0, 40.0), (75.0, 0.0, 40.0), (125.0, 0.0, 40.0)]
+    recs = [np.array([(x, 0.0, 40.0) for x in np.arange(5.0, 155.0, 10.0)])] * 3
+    f = synth.ricker(nt, dt, 45.0)
+    o_true = oracle.Oracle(vt, dx, dt, nt, nb, vref=2500.0)
+    d = [o_true.forward(o_true.shot(s, r), wavelet=f)["traces"] for s, r in zip(srcs, recs)]
+    pb = outer.Problem(dx, dt, nt, nb, 2500.0, srcs, recs, d, wavelets=[f] * 3)
+    opt = outer.Options(mode="esi", n_outer=3, n_cg=10, beta0=0.1, vmin=1400, vmax=2600)
+    return v, pb, opt
+
+
+def _outer_rank(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from oracle import outer
+        v, pb, opt = _outer_case()
+        lo, hi = shard.shot_range(len(pb.src_xyz), rank, world)
+        h = outer.invert(v, pb, opt, reduce=lambda J, g: shard.reduce_objective(J, g, dist),
+                         shots=range(lo, hi))
+        np.save(os.path.join(out, f"o{rank}.npy"),
+                np.concatenate([h["v"].ravel(), h["J_end"], [len(h["J_end"])]]))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_reproduce_the_single_process_outer_loop(tmp_path):
+    import torch.multiprocessing as mp
+    from oracle import outer
+    world = 2
+    mp.start_processes(_outer_rank, args=(world, _free_port(), str(tmp_path)), nprocs=world,
+                       start_method="spawn", join=True)
+    r0 = np.load(tmp_path / "o0.npy")
+    r1 = np.load(tmp_path / "o1.npy")
+    assert np.array_equal(r0, r1)
+    v, pb, opt = _outer_case()
+    h = outer.invert(v, pb, opt)
+    ref = np.concatenate([h["v"].ravel(), h["J_end"], [len(h["J_end"])]])
+    assert r0.shape == ref.shape
+    assert np.allclose(r0, ref, rtol=1e-10, atol=0)
