@@ -59,10 +59,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-nt", type=int, default=1500, help="oracle sample: steps per bench step")
-    ap.add_argument("--workload", default="esi2d", choices=["esi2d", "dft3d", "wri2d"],
+    ap.add_argument("--workload", default="esi2d",
+                    choices=["esi2d", "dft3d", "wri2d", "invert2d"],
                     help="dft3d: forward modelling with the on-the-fly DTFT (5 frequencies, FP16 "
                          "output) on the 400^3, nt 2000 volume instead of the ESI step; wri2d: "
-                         "the WRI solve (B = I) and its gradient on the ESI step's workload")
+                         "the WRI solve (B = I) and its gradient on the ESI step's workload; "
+                         "invert2d: the ESI outer loop (esi_invert) on that workload")
+    ap.add_argument("--outer", type=int, default=2, help="invert2d: outer iterations per step")
     ap.add_argument("--wri-factor", type=float, default=1e-2,
                     help="WRI penalty: beta = factor * lambda_max(S^T S)")
     ap.add_argument("--n3d", type=int, default=400)
@@ -437,6 +440,117 @@ def run_wri2d(args, rank, world, local):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------- outer loop
+def run_invert2d(args, rank, world, local):
+    """One step = the outer loop (Algorithm "nestedloop", esi_invert) on the 801 x 241, nt 3000,
+    16-shot workload from the smoothed starting model: args.outer L-BFGS iterations, each
+    evaluation 10 diagonally preconditioned CG iterations (the paper's numerical tests use 10)
+    plus the objective and saddle-point gradient from one forward run.  Shots are sharded over
+    ranks; J and the gradient are summed through the reduce callback."""
+    import torch
+    from paper_2211_06300_gb300 import esi, pc_train, shard, synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    ns, nt = args.ns, args.nt
+    wl = synth.workload_esi_2d(nt=nt, ns=ns * world)
+    geom = wl.geom.select(range(*shard.shot_range(ns * world, rank, world)))
+    vref = float(wl.v_true.max())
+    f32 = torch.float32
+    v0 = torch.tensor(wl.v_start, dtype=f32, device=dev)
+    wav = torch.tensor(wl.wavelets()[rank * ns:(rank + 1) * ns], dtype=f32, device=dev).contiguous()
+    ct = esi.Context(torch.tensor(wl.v_true, dtype=f32, device=dev), wl.dx, wl.dt, nt, wl.nb,
+                     geom, vref=vref)
+    dobs = ct.forward(wavelet=wav)
+    ct.close()
+    ctx = esi.Context(v0, wl.dx, wl.dt, nt, wl.nb, geom, vref=vref)
+    c1 = esi.Context(v0, wl.dx, wl.dt, nt, wl.nb, geom.select([0]), vref=vref)
+    beta = pc_train.penalty(c1, wl.shape, wl.dx, nt, dev, factor=args.beta_factor)
+    c1.close()
+    vel = v0.clone()
+    grad = torch.empty_like(v0)
+    N = wl.ncell
+    red = (lambda J, g: shard.reduce_objective(J, g, dist)) if dist is not None else None
+    kw = dict(n_outer=args.outer, n_cg=10, precond="diag", beta0=beta, vmin=1400.0,
+              vmax=4700.0, reduce=red)
+
+    def step(d):
+        vel.copy_(v0)
+        _, rep = ctx.invert(d, vel, grad=grad, **kw)
+        props = 2 * rep["evaluations"] + 2 * rep["cg_iters_total"]   # S^T d, forward; products
+        return rep, props * N * nt * ns
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        step(dobs)
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = ctx.launches
+    ctx.set_profiling(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream(dev)
+    barrier()
+    e0.record(stream)
+    cells, reps = 0, []
+    for _ in range(args.steps):
+        rep, c = step(dobs)
+        cells += c
+        reps.append(rep)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    prof = ctx.profile()
+    ctx.set_profiling(False)
+    launches = ctx.launches - l0
+    clk = clocks.stop()
+    t_max = shard.max_over_ranks(ms, dist, dev)
+    cells_all = shard.sum_over_ranks(cells, dist, dev)
+    d_host = dobs.cpu().pin_memory()
+    d_dev = torch.empty_like(dobs)
+    barrier()
+    t0 = time.perf_counter()
+    ce = 0
+    for _ in range(args.steps):
+        d_dev.copy_(d_host, non_blocking=True)
+        _, c = step(d_dev)
+        v_host = vel.cpu()
+        ce += c
+    te = shard.max_over_ranks(time.perf_counter() - t0, dist, dev)
+    ce = shard.sum_over_ranks(ce, dist, dev)
+    if rank == 0:
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            pass
+        print(json.dumps({
+            "metric": "FD Gcell-updates/s fwd+adj; ESI outer loop (nestedloop)",
+            "value": cells_all / (t_max * 1e-3) / 1e9, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "invert2d-801x241-nt%d-%dshots-fp32" % (nt, ns),
+                       "outer_iterations": args.outer, "inner_cg": 10, "precond": "diag",
+                       "beta": beta, "l2": "inputs larger than L2 (q 37 GB per GPU)"},
+            "outer": [{"J_start": r["J_start"], "J_end": r["J_end"], "trials": r["trials"],
+                       "evaluations": r["evaluations"], "stop": r["stop"],
+                       "ms": r["ms_total"]} for r in reps],
+            "roofline": roofline_of(prof, peaks), "kernels": prof,
+            "e2e": {"value": ce / te / 1e9, "unit": UNIT,
+                    "h2d_bytes_per_step": int(d_host.numel() * d_host.element_size()),
+                    "d2h_bytes_per_step": int(v_host.numel() * v_host.element_size())},
+            "gpu_launches": launches, "clocks": clk}), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 # ----------------------------------------------------------------------------- CUDA arm
 def main():
     args = parse()
@@ -451,6 +565,9 @@ def main():
         return
     if args.workload == "wri2d":
         run_wri2d(args, rank, world, local)
+        return
+    if args.workload == "invert2d":
+        run_invert2d(args, rank, world, local)
         return
     import numpy as np
     import torch
