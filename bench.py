@@ -58,6 +58,9 @@ def parse():
                                                          "pc_weights.npy"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the untimed CG comparison (none / diag / data space / frequency "
+                         "domain / learned)")
     ap.add_argument("--ref-nt", type=int, default=1500, help="oracle sample: steps per bench step")
     ap.add_argument("--workload", default="esi2d",
                     choices=["esi2d", "dft3d", "wri2d", "invert2d"],
@@ -687,66 +690,69 @@ def main():
     iters = [int(max(r["iters"])) for r in reps]
     cg_ms = [r["ms_total"] for r in reps]
 
-    # CG alone on the same system with each preconditioner (untimed by the steps above)
-    # the true residual ||S^T d - (S^T S + beta B^2) q|| / ||S^T d|| of each solution, on the
-    # first and last shot (a two-shot context keeps the extra memory to a few GB)
-    sel = [0, ns - 1]
-    ctx2 = esi.Context(v0, wl.dx, wl.dt, nt, wl.nb, geom.select(sel), vref=vref)
-    d2 = torch.cat([ctx.traces_of(dobs, s).reshape(-1) for s in sel]).contiguous()
-    b_rhs, _ = ctx2.adjoint(d2)
+    def run_compare():
+        # CG alone on the same system with each preconditioner (untimed by the steps above)
+        # the true residual ||S^T d - (S^T S + beta B^2) q|| / ||S^T d|| of each solution, on the
+        # first and last shot (a two-shot context keeps the extra memory to a few GB)
+        sel = [0, ns - 1]
+        ctx2 = esi.Context(v0, wl.dx, wl.dt, nt, wl.nb, geom.select(sel), vref=vref)
+        d2 = torch.cat([ctx.traces_of(dobs, s).reshape(-1) for s in sel]).contiguous()
+        b_rhs, _ = ctx2.adjoint(d2)
 
-    def true_rel_res():
-        q2 = q[sel].contiguous()
-        res = ctx2.normal_apply(q2, beta)
-        torch.sub(b_rhs, res, out=res)
-        num = res.reshape(len(sel), -1).norm(dim=1)
-        den = b_rhs.reshape(len(sel), -1).norm(dim=1)
-        del res, q2
-        return float((num / den).max())
+        def true_rel_res():
+            q2 = q[sel].contiguous()
+            res = ctx2.normal_apply(q2, beta)
+            torch.sub(b_rhs, res, out=res)
+            num = res.reshape(len(sel), -1).norm(dim=1)
+            den = b_rhs.reshape(len(sel), -1).norm(dim=1)
+            del res, q2
+            return float((num / den).max())
 
-    def cg_only(pc, cap, data_space=False):
+        def cg_only(pc, cap, data_space=False):
+            torch.cuda.synchronize()
+            ctx.set_velocity(v0)
+            _, r = ctx.cg_solve(dobs, lam=beta, tol=args.tol, max_iter=cap, out=q, precond=pc,
+                                data_space=data_space)
+            return {"iters_max": int(max(r["iters"])), "time_ms": r["ms_total"],
+                    "true_rel_res_first_last_shot": true_rel_res(),
+                    "reached_tol": bool(r["converged"]),
+                    "rel_res_max_over_shots": float(max(x[-1] for x in r["rel_res"] if x.size)),
+                    "device_ms": {"product": r["ms_matvec"], "vector": r["ms_vector"],
+                                  "precond": r["ms_precond"]}}
+        compare = {}
+        if args.plain_iter > 0:
+            compare["none"] = cg_only("none", args.plain_iter)
+        compare["diag"] = cg_only("diag", args.max_iter)
+        # the same ESI system in data space (section "Switching from the wavefield to data space");
+        # its stopping test is on the data-space residual, so it is also run to tol / 10 to
+        # compare at a matching true residual
+        compare["data_space"] = cg_only("none", args.max_iter, data_space=True)
+        tol0 = args.tol
+        args.tol = tol0 / 10
+        compare["data_space_tol_div10"] = cg_only("none", args.max_iter, data_space=True)
+        args.tol = tol0
+        # frequency-domain ESI by time-domain modelling (section "Frequency domain inversion by
+        # time domain modelling"): CG on F A F^H qbar / nt = F S^T d at the DTFT frequencies, its
+        # vectors nf complex fields per shot instead of nt real ones (the residual is that of the
+        # frequency-domain system)
         torch.cuda.synchronize()
         ctx.set_velocity(v0)
-        _, r = ctx.cg_solve(dobs, lam=beta, tol=args.tol, max_iter=cap, out=q, precond=pc,
-                            data_space=data_space)
-        return {"iters_max": int(max(r["iters"])), "time_ms": r["ms_total"],
-                "true_rel_res_first_last_shot": true_rel_res(),
-                "reached_tol": bool(r["converged"]),
-                "rel_res_max_over_shots": float(max(x[-1] for x in r["rel_res"] if x.size)),
-                "device_ms": {"product": r["ms_matvec"], "vector": r["ms_vector"],
-                              "precond": r["ms_precond"]}}
-    compare = {}
-    if args.plain_iter > 0:
-        compare["none"] = cg_only("none", args.plain_iter)
-    compare["diag"] = cg_only("diag", args.max_iter)
-    # the same ESI system in data space (section "Switching from the wavefield to data space");
-    # its stopping test is on the data-space residual, so it is also run to tol / 10 to
-    # compare at a matching true residual
-    compare["data_space"] = cg_only("none", args.max_iter, data_space=True)
-    tol0 = args.tol
-    args.tol = tol0 / 10
-    compare["data_space_tol_div10"] = cg_only("none", args.max_iter, data_space=True)
-    args.tol = tol0
-    # frequency-domain ESI by time-domain modelling (section "Frequency domain inversion by
-    # time domain modelling"): CG on F A F^H qbar / nt = F S^T d at the DTFT frequencies, its
-    # vectors nf complex fields per shot instead of nt real ones (the residual is that of the
-    # frequency-domain system)
-    torch.cuda.synchronize()
-    ctx.set_velocity(v0)
-    qb, r = ctx.cg_solve(dobs, lam=beta, tol=args.tol, max_iter=args.max_iter, freqs=freqs)
-    compare["frequency_domain"] = {
-        "freqs_hz": freqs, "iters_max": int(max(r["iters"])), "time_ms": r["ms_total"],
-        "reached_tol": bool(r["converged"]),
-        "rel_res_max_over_shots": float(max(x[-1] for x in r["rel_res"] if x.size)),
-        "device_ms": {"product": r["ms_matvec"], "vector": r["ms_vector"]},
-        "cg_vector_bytes_per_shot": int(qb[0].numel() * qb.element_size()),
-        "time_domain_cg_vector_bytes_per_shot": int(q[0].numel() * q.element_size())}
-    del qb
-    if have_pc:
-        compare["learned"] = cg_only("learned", args.max_iter)
-        compare["learned"]["fallbacks"] = ctx.pc_fallbacks
-    del b_rhs
-    ctx2.close()
+        qb, r = ctx.cg_solve(dobs, lam=beta, tol=args.tol, max_iter=args.max_iter, freqs=freqs)
+        compare["frequency_domain"] = {
+            "freqs_hz": freqs, "iters_max": int(max(r["iters"])), "time_ms": r["ms_total"],
+            "reached_tol": bool(r["converged"]),
+            "rel_res_max_over_shots": float(max(x[-1] for x in r["rel_res"] if x.size)),
+            "device_ms": {"product": r["ms_matvec"], "vector": r["ms_vector"]},
+            "cg_vector_bytes_per_shot": int(qb[0].numel() * qb.element_size()),
+            "time_domain_cg_vector_bytes_per_shot": int(q[0].numel() * q.element_size())}
+        del qb
+        if have_pc:
+            compare["learned"] = cg_only("learned", args.max_iter)
+            compare["learned"]["fallbacks"] = ctx.pc_fallbacks
+        del b_rhs
+        ctx2.close()
+        return compare
+    compare = None if args.no_compare else run_compare()
     cb = None
     if not args.no_cpu_baseline and world == 1:
         try:
