@@ -116,8 +116,9 @@ __global__ void __launch_bounds__(NT2, ESI_FD2_MINB) fd2_step_kernel(const __gri
 
     // Per-cell global inputs of both passes are loaded first, so that their latency
     // overlaps the staging of the shared tile instead of following the barrier.
-    Vec<T> p_old[NP], p_cc[NP], p_r[NP], p_p[NP], p_g[NP], p_st[NP];
-    T p_q[NP][VEC];
+    Vec<T> p_old[NP], p_cc[NP], p_r[NP], p_p[NP], p_g[NP], p_st[NP], p_b2[NP];
+    T p_q[NP][VEC], p_kz[NP];
+    const Vec<T> kx = ldv(a.kx + (colok ? gx0 : 0));   // sponge profile, padded to px
 #pragma unroll
     for (int pz = 0; pz < NP; ++pz) {
         const int gz = z0 + ry + pz * RPP;
@@ -127,6 +128,7 @@ __global__ void __launch_bounds__(NT2, ESI_FD2_MINB) fd2_step_kernel(const __gri
         const long long gi = (long long)gz * a.px + gx0;
         p_old[pz] = ldv(po + gi);
         p_cc[pz] = ldv(a.cc + gi);
+        p_kz[pz] = a.kz[gz];
         if constexpr ((F & F_EXT) != 0) {
             const T *e = a.ext + fd + (long long)a.n * a.N + (long long)gz * a.nx + gx0;
 #pragma unroll
@@ -138,7 +140,10 @@ __global__ void __launch_bounds__(NT2, ESI_FD2_MINB) fd2_step_kernel(const __gri
             p_r[pz] = ldv(a.cg_r + vi);
             if (!a.cg_first) p_p[pz] = ldv(a.cg_p + vi);
         }
-        if constexpr ((F & F_AP) != 0) p_p[pz] = ldv(a.ap_p + fb + (long long)a.nout * a.sst + gi);
+        if constexpr ((F & F_AP) != 0) {
+            p_p[pz] = ldv(a.ap_p + fb + (long long)a.nout * a.sst + gi);
+            p_b2[pz] = ldv(a.pb2 + (long long)s * a.sst + gi);
+        }
         if constexpr ((F & (F_GRD | F_SAD)) != 0) p_g[pz] = ldv(a.grad + (long long)s * a.sst + gi);
         if constexpr ((F & F_GRD) != 0)
             p_st[pz] = ldv(a.stash_r + ((long long)a.slot_r * a.ns + s) * a.sst + gi);
@@ -184,7 +189,6 @@ __global__ void __launch_bounds__(NT2, ESI_FD2_MINB) fd2_step_kernel(const __gri
 
     T psum = T(0);
     if (colok) {
-        const Vec<T> kx = ldv(a.kx + gx0);
         T xs = T(0), zs = T(0);
         if constexpr ((F & F_SAD) != 0) {
             xs = T(a.src_pos[3 * s + 0]);
@@ -220,7 +224,7 @@ __global__ void __launch_bounds__(NT2, ESI_FD2_MINB) fd2_step_kernel(const __gri
             const long long gi = (long long)gz * a.px + gx0;
             const Vec<T> old = p_old[pz];
             const Vec<T> cc = p_cc[pz];
-            const T kz = a.kz[gz];
+            const T kz = p_kz[pz];
             T q[VEC], S[VEC];
 #pragma unroll
             for (int i = 0; i < VEC; ++i) q[i] = p_q[pz][i];
@@ -301,7 +305,7 @@ __global__ void __launch_bounds__(NT2, ESI_FD2_MINB) fd2_step_kernel(const __gri
             if constexpr ((F & F_AP) != 0) {   // A p = S^T S p + pen B^2 p
                 const long long vi = fb + (long long)a.nout * a.sst + gi;
                 const Vec<T> pv = p_p[pz];
-                const Vec<T> b2 = ldv(a.pb2 + (long long)s * a.sst + gi);
+                const Vec<T> b2 = p_b2[pz];
                 Vec<T> av;
 #pragma unroll
                 for (int i = 0; i < VEC; ++i) {
