@@ -530,6 +530,37 @@ class Oracle:
         return {"qbar": x, "q": F.conj().T @ x / self.nt, "rel_res": np.asarray(hist),
                 "iters": k + 1, "b": b}
 
+    def fd_pcg(self, sh: Shot, d: np.ndarray, beta: float, freqs: Sequence[float], tol: float,
+               n_cg: int, minv: np.ndarray, eps: Optional[float] = None) -> Dict:
+        """fd_cg with a fixed preconditioner z = minv r per cell, the same at every frequency
+        (minv = 1 / (beta B^2): on the DFT grid F F^H / nt = I, so this is the inverse of the
+        penalty term of Eq. "normaldtft"); beta_k = Re<r', z'> / Re<r, z>, stopping on ||r||."""
+        F = self.dtft_matrix(freqs)
+        b = F @ self.ST(sh, np.asarray(d, dtype=np.float64).reshape(self.nt, sh.nr))
+        x = np.zeros_like(b)
+        r = b.copy()
+        z = r * minv[None, :]
+        p = z.copy()
+        rz = float(np.vdot(r, z).real)
+        r0 = math.sqrt(float(np.vdot(r, r).real))
+        hist = []
+        k = -1   # b = 0: x_0 = 0 is exact and no iteration runs
+        for k in range(n_cg if r0 > 0 else 0):
+            Ap = self.fd_matvec(sh, p, beta, freqs, eps)
+            alpha = rz / float(np.vdot(p, Ap).real)
+            x = x + alpha * p
+            r = r - alpha * Ap
+            rn = math.sqrt(float(np.vdot(r, r).real))
+            hist.append(rn / r0)
+            if rn < tol * r0 or k == n_cg - 1:
+                break
+            z = r * minv[None, :]
+            rz_new = float(np.vdot(r, z).real)
+            p = z + (rz_new / rz) * p
+            rz = rz_new
+        return {"qbar": x, "q": F.conj().T @ x / self.nt, "rel_res": np.asarray(hist),
+                "iters": k + 1, "b": b}
+
     def assemble_S(self, sh: Shot) -> np.ndarray:
         """Dense data operator S (columns S e_j over space-time; tiny sizes only)."""
         n = self.nt * self.N

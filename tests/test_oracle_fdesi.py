@@ -141,3 +141,23 @@ def test_worked_example_with_both_signs_is_exact_for_any_spd_operator():
     exact whatever the (here Toeplitz, not shift-invariant) operator."""
     err, _ = _toeplitz_case(0.5 ** np.arange(200), both_signs=True)
     assert err < 1e-12
+
+
+def test_preconditioned_full_grid_reduces_to_the_time_domain_pcg():
+    """The diagonal preconditioner 1 / (beta B^2) acts per cell, so on the full DFT grid the
+    preconditioned frequency-domain CG is the preconditioned time-domain CG seen through F."""
+    orc, sh = _tiny(nt=8)
+    beta = 2e-3
+    d = synth.normal(13, (orc.nt, sh.nr))
+    B = orc.annihilator(sh.src_xyz)
+    minv = 1.0 / (beta * B * B)
+    freqs = np.arange(orc.nt) / (orc.nt * orc.dt)
+    fd = orc.fd_pcg(sh, d, beta, freqs, 0.0, 6, minv)
+    td = orc.pcg(sh, d, beta, 0.0, 6, minv=minv)
+    assert np.allclose(fd["rel_res"], td["rel_res"], rtol=1e-9, atol=0)
+    assert oracle.rel_l2(fd["q"].real, td["x"]) < 1e-10
+    # and it converges to the unpreconditioned solution off the grid as well
+    fr = [37.0, 120.5]
+    a = orc.fd_pcg(sh, d, beta, fr, 1e-12, 400, minv)
+    c = orc.fd_cg(sh, d, beta, fr, 1e-12, 400)
+    assert oracle.rel_l2(a["qbar"], c["qbar"]) < 1e-8
