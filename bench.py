@@ -737,9 +737,10 @@ def main():
         # frequency-domain system)
         torch.cuda.synchronize()
         ctx.set_velocity(v0)
-        qb, r = ctx.cg_solve(dobs, lam=beta, tol=args.tol, max_iter=args.max_iter, freqs=freqs)
+        qb, r = ctx.cg_solve(dobs, lam=beta, tol=args.tol, max_iter=args.max_iter, freqs=freqs,
+                             precond="diag")
         compare["frequency_domain"] = {
-            "freqs_hz": freqs, "iters_max": int(max(r["iters"])), "time_ms": r["ms_total"],
+            "precond": "diag", "freqs_hz": freqs, "iters_max": int(max(r["iters"])), "time_ms": r["ms_total"],
             "reached_tol": bool(r["converged"]),
             "rel_res_max_over_shots": float(max(x[-1] for x in r["rel_res"] if x.size)),
             "device_ms": {"product": r["ms_matvec"], "vector": r["ms_vector"]},

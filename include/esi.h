@@ -324,6 +324,9 @@ ESI_API esi_status esi_cg_solve(esi_ctx *ctx, double lambda, double tol, int max
  * qbar per cell; no space-time vector is stored (the CG vectors hold 2 nf values per cell).
  *   dobs_dev     : device seismogram-layout observed data d
  *   freqs_hz     : host [nf] frequencies, 1 <= nf <= 8
+ *   precond      : ESI_PC_NONE, or ESI_PC_DIAG: z = r / (lambda B^2) per cell at every
+ *                  frequency (the inverse of the penalty term on the DFT grid, where
+ *                  F F^H / nt = I); ESI_PC_LEARNED gives ESI_ERR_UNSUPPORTED
  *   qbar_out_dev : device [ns][nf][N][2] (re, im) receives the solution
  *   eps, report  : as esi_cg_solve (ms_matvec: the products, ms_vector: the vector work)
  * Per-shot stopping, errors and frozen shots as esi_cg_solve; lambda must be > 0.  The
@@ -331,7 +334,8 @@ ESI_API esi_status esi_cg_solve(esi_ctx *ctx, double lambda, double tol, int max
  */
 ESI_API esi_status esi_fdcg_solve(esi_ctx *ctx, double lambda, double tol, int max_iter,
                                   const void *dobs_dev, const double *freqs_hz, int nf,
-                                  void *qbar_out_dev, double eps, esi_cg_report *report);
+                                  int precond, void *qbar_out_dev, double eps,
+                                  esi_cg_report *report);
 
 /*
  * esi_dscg_solve -- the ESI normal equation solved in data space (the section "Switching

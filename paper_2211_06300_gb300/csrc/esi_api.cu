@@ -1758,7 +1758,7 @@ esi_status dscg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, cons
 // sources and the adjoint output pass through DFT_BLOCK-step stashes.
 template <typename T>
 esi_status fdcg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const void *dobs,
-                     const double *freqs, int nf, void *qbar_out, double eps_in,
+                     const double *freqs, int nf, int precond, void *qbar_out, double eps_in,
                      esi_cg_report *rep) {
     using clk = std::chrono::steady_clock;
     const auto t_start = clk::now();
@@ -1769,11 +1769,14 @@ esi_status fdcg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, cons
         if (!std::isfinite(freqs[m])) return ctx->fail(ESI_ERR_ARG, "frequencies must be finite");
     if (!(lambda > 0)) return ctx->fail(ESI_ERR_ARG, "the frequency-domain form needs lambda > 0");
     if (max_iter < 1) return ctx->fail(ESI_ERR_ARG, "max_iter must be >= 1");
+    if (precond != ESI_PC_NONE && precond != ESI_PC_DIAG)
+        return ctx->fail(ESI_ERR_UNSUPPORTED, "the frequency-domain CG takes no or the diagonal preconditioner");
+    const bool pc = precond == ESI_PC_DIAG;
     esi_status e = ensure_states<T>(ctx, true);
     if (e != ESI_OK) return e;
     const long long vl = (long long)ns * nf * ctx->sst * 2;   // one complex unknown vector
-    CK(ctx->fdv.ensure((size_t)5 * vl * sizeof(T)));
-    T *X = ctx->fdv.as<T>(), *R = X + vl, *P = R + vl, *AP = P + vl, *Bv = AP + vl;
+    CK(ctx->fdv.ensure((size_t)6 * vl * sizeof(T)));
+    T *X = ctx->fdv.as<T>(), *R = X + vl, *P = R + vl, *AP = P + vl, *Bv = AP + vl, *Z = Bv + vl;
     // source stash [ns][K][sst] and the scratch the fused kernel writes its source to
     CK(ctx->fdsrc.ensure((size_t)2 * ns * K * ctx->sst * sizeof(T)));
     T *src = ctx->fdsrc.as<T>(), *psc = src + (size_t)ns * K * ctx->sst;
@@ -1783,7 +1786,12 @@ esi_status fdcg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, cons
     T *tr = ctx->fdtr.as<T>();
     const T eps = T(eps_in > 0 ? eps_in : ctx->g.dx);
     CK(ctx->pb2.ensure((size_t)ns * ctx->sst * sizeof(T)));
-    CKL(launch_b2_maps<T>(ctx->pb2.as<T>(), nullptr, ns, ctx->g.nz, ctx->g.ny, ctx->g.nx, ctx->px,
+    T *ipb2 = nullptr;   // 1 / (lambda B^2) for the diagonal preconditioner
+    if (pc) {
+        CK(ctx->ipb2.ensure((size_t)ns * ctx->sst * sizeof(T)));
+        ipb2 = ctx->ipb2.as<T>();
+    }
+    CKL(launch_b2_maps<T>(ctx->pb2.as<T>(), ipb2, ns, ctx->g.nz, ctx->g.ny, ctx->g.nx, ctx->px,
                           T(lambda), eps, T(ctx->g.dx), ctx->src_pos.as<double>(), 0, ctx->st));
     // twiddle tables [part][n][m][2]: synthesis of the real part (cos, sin) / nt and of the
     // imaginary part (-sin, cos) / nt; folding of a real series (cos, sin) and of an
@@ -1815,10 +1823,10 @@ esi_status fdcg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, cons
     const long long *dseg = ctx->dseg.as<long long>();
     const int nb = DVEC_NBLK;
     CK(ctx->part.ensure(sizeof(double) * (size_t)ns * nb));
-    CK(ctx->scal.ensure(sizeof(double) * 5 * ns + sizeof(int) * 2 * ns));
+    CK(ctx->scal.ensure(sizeof(double) * 7 * ns + sizeof(int) * 2 * ns));
     double *rr = ctx->scal.as<double>(), *pap = rr + ns, *alpha = pap + ns, *beta = alpha + ns,
-           *rrn = beta + ns;
-    int *active = reinterpret_cast<int *>(rrn + ns), *bad = active + ns;
+           *rrn = beta + ns, *rz = rrn + ns, *rzn = rz + ns;   // rz: Re <r, z> (preconditioned)
+    int *active = reinterpret_cast<int *>(rzn + ns), *bad = active + ns;
     CK(cudaMemsetAsync(active, 0xff, sizeof(int) * ns, ctx->st));
     CK(cudaMemsetAsync(bad, 0, sizeof(int) * ns, ctx->st));
     const double es = double(sizeof(T));
@@ -1947,6 +1955,11 @@ esi_status fdcg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, cons
     CK(cudaMemsetAsync(alpha, 0, sizeof(double) * ns, ctx->st));
     CKL(launch_dvec_update<T>(X, R, P, P, dseg, alpha, nullptr, ctx->part.as<double>(), ns, ctx->st));
     CKL(launch_reduce_partials(ctx->part.as<double>(), nb, ns, rr, ctx->st));
+    if (pc) {   // z0 = M^{-1} r0, p0 = z0
+        CKL(launch_fd_precond<T>(Z, R, ipb2, nf, ns, ctx->sst, nullptr, ctx->part.as<double>(), ctx->st));
+        CKL(launch_reduce_partials(ctx->part.as<double>(), nb, ns, rz, ctx->st));
+        CK(cudaMemcpyAsync(P, Z, vl * sizeof(T), cudaMemcpyDeviceToDevice, ctx->st));
+    }
     std::vector<double> rr0(ns), h_rrn(ns);
     std::vector<int> h_active(ns, 1), h_bad(ns, 0), iters(ns, 0);
     std::vector<char> h_conv(ns, 0);
@@ -1975,7 +1988,7 @@ esi_status fdcg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, cons
         if (e != ESI_OK) return e;
         CK(cudaEventRecord(ev.e[1], ctx->st));
         CKL(launch_reduce_partials(ctx->part.as<double>(), nb, ns, pap, ctx->st));
-        CKL(launch_cg_alpha(rr, pap, alpha, bad, active, ns, ctx->st));
+        CKL(launch_cg_alpha(pc ? rz : rr, pap, alpha, bad, active, ns, ctx->st));
         CKL(launch_dvec_update<T>(X, R, P, AP, dseg, alpha, active, ctx->part.as<double>(), ns, ctx->st));
         CKL(launch_reduce_partials(ctx->part.as<double>(), nb, ns, rrn, ctx->st));
         CK(cudaEventRecord(ev.e[2], ctx->st));
@@ -2008,8 +2021,16 @@ esi_status fdcg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, cons
         }
         if (!any) break;
         CK(cudaMemcpyAsync(active, h_active.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, ctx->st));
-        CKL(launch_cg_beta(rr, rrn, beta, active, ns, ctx->st));
-        CKL(launch_dvec_xpby<T>(P, R, dseg, beta, active, ns, ctx->st));
+        if (pc) {   // z = M^{-1} r, beta = <r', z'> / <r, z>, p = z + beta p
+            CKL(launch_fd_precond<T>(Z, R, ipb2, nf, ns, ctx->sst, active, ctx->part.as<double>(),
+                                     ctx->st));
+            CKL(launch_reduce_partials(ctx->part.as<double>(), nb, ns, rzn, ctx->st));
+            CKL(launch_cg_beta(rz, rzn, beta, active, ns, ctx->st));
+            CKL(launch_dvec_xpby<T>(P, Z, dseg, beta, active, ns, ctx->st));
+        } else {
+            CKL(launch_cg_beta(rr, rrn, beta, active, ns, ctx->st));
+            CKL(launch_dvec_xpby<T>(P, R, dseg, beta, active, ns, ctx->st));
+        }
     }
     // qbar out: pitched complex slices -> dense [ns][nf][N][2]
     CKL(launch_dft_output<T>(X, ctx->sst, ctx->g.nz * ctx->g.ny, ctx->g.nx, ctx->px, ns, nf, 0,
@@ -2471,16 +2492,17 @@ ESI_API esi_status esi_invert(esi_ctx *ctx, const esi_invert_opts *opts, const v
 
 ESI_API esi_status esi_fdcg_solve(esi_ctx *ctx, double lambda, double tol, int max_iter,
                                   const void *dobs_dev, const double *freqs_hz, int nf,
-                                  void *qbar_out_dev, double eps, esi_cg_report *report) {
+                                  int precond, void *qbar_out_dev, double eps,
+                                  esi_cg_report *report) {
     if (!ctx) return ESI_ERR_ARG;
     if (!dobs_dev || !qbar_out_dev || !freqs_hz || !(lambda > 0) || !(tol >= 0))
         return ctx->fail(ESI_ERR_ARG, "bad frequency-domain CG arguments");
     ctx->err.clear();
     return ctx->g.dtype == ESI_F64
-               ? fdcg_impl<double>(ctx, lambda, tol, max_iter, dobs_dev, freqs_hz, nf, qbar_out_dev,
-                                   eps, report)
-               : fdcg_impl<float>(ctx, lambda, tol, max_iter, dobs_dev, freqs_hz, nf, qbar_out_dev,
-                                  eps, report);
+               ? fdcg_impl<double>(ctx, lambda, tol, max_iter, dobs_dev, freqs_hz, nf, precond,
+                                   qbar_out_dev, eps, report)
+               : fdcg_impl<float>(ctx, lambda, tol, max_iter, dobs_dev, freqs_hz, nf, precond,
+                                  qbar_out_dev, eps, report);
 }
 
 ESI_API esi_status esi_dscg_solve(esi_ctx *ctx, double lambda, double tol, int max_iter,

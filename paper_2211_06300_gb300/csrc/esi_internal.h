@@ -292,6 +292,12 @@ template <typename T>
 cudaError_t launch_mlincomb(T *z, double alpha, const T *x, double beta, const T *y, long long n,
                             double lo, double hi, cudaStream_t st);
 
+// z = w r per cell at every frequency of the complex slices [ns][nf][sst][2] (w per shot
+// [ns][sst]) with the partials of Re <r, z> ([ns][DVEC_NBLK]); inactive shots skipped
+template <typename T>
+cudaError_t launch_fd_precond(T *z, const T *r, const T *w, int nf, int ns, long long sst,
+                              const int *active, double *part, cudaStream_t st);
+
 // DTFT output: pitched accumulators [ns][nf][sst][2] -> caller dense [ns][nf][N][2], either
 // copied in the field precision (half == 0) or as half pairs with a per (shot, f) scale
 template <typename T>

@@ -703,7 +703,38 @@ __global__ void fd_b2g_dot_kernel(T *out, const T *p, const T *pb2, const double
     if (threadIdx.x == 0) part[(long long)s * gridDim.x + blockIdx.x] = t;
 }
 
+// z = w r per cell at every frequency (w = 1 / (lambda B^2)), with the partials of Re <r, z>:
+// the diagonal preconditioner of the frequency-domain CG
+template <typename T>
+__global__ void fd_precond_kernel(T *z, const T *r, const T *w, int nf, long long sst,
+                                  const int *active, double *part) {
+    const int s = blockIdx.y;
+    if (active && !active[s]) return;
+    double acc = 0.0;
+    for (long long c = (long long)blockIdx.x * RT + threadIdx.x; c < sst;
+         c += (long long)gridDim.x * RT) {
+        const T wc = w[(long long)s * sst + c];
+        for (int m = 0; m < nf; ++m) {
+            const long long o = (((long long)s * nf + m) * sst + c) * 2;
+            const T r0 = r[o], r1 = r[o + 1];
+            const T z0 = wc * r0, z1 = wc * r1;
+            z[o] = z0;
+            z[o + 1] = z1;
+            acc += double(r0) * double(z0) + double(r1) * double(z1);
+        }
+    }
+    const double t = block_sum_d(acc);
+    if (threadIdx.x == 0) part[(long long)s * gridDim.x + blockIdx.x] = t;
+}
+
 }  // namespace
+
+template <typename T>
+cudaError_t launch_fd_precond(T *z, const T *r, const T *w, int nf, int ns, long long sst,
+                              const int *active, double *part, cudaStream_t st) {
+    fd_precond_kernel<T><<<dim3(DVEC_NBLK, ns), RT, 0, st>>>(z, r, w, nf, sst, active, part);
+    return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t launch_idft_block(const T *qb, int K, int kst, int ns, long long sst, int nf,
@@ -884,6 +915,8 @@ cudaError_t launch_mlincomb(T *z, double alpha, const T *x, double beta, const T
     template cudaError_t launch_mamax<T>(const T *, long long, double *, int, cudaStream_t);      \
     template cudaError_t launch_mlincomb<T>(T *, double, const T *, double, const T *, long long,  \
                                             double, double, cudaStream_t);                       \
+    template cudaError_t launch_fd_precond<T>(T *, const T *, const T *, int, int, long long,     \
+                                              const int *, double *, cudaStream_t);              \
     template cudaError_t launch_idft_block<T>(const T *, int, int, int, long long, int, const T *, \
                                               T *, cudaStream_t);                                \
     template cudaError_t launch_fd_b2g_dot<T>(T *, const T *, const T *, const double *, int, int, \

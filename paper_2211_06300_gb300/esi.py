@@ -131,7 +131,7 @@ def load_library(require_gpu: bool = True) -> ctypes.CDLL:
     L.esi_cg_solve.argtypes = [vp, d, d, i, vp, vp, i, d, ctypes.POINTER(EsiCgReport)]
     L.esi_wri_solve.argtypes = [vp, d, d, i, vp, vp, vp, ctypes.POINTER(EsiCgReport)]
     L.esi_dscg_solve.argtypes = [vp, d, d, i, vp, vp, vp, d, ctypes.POINTER(EsiCgReport)]
-    L.esi_fdcg_solve.argtypes = [vp, d, d, i, vp, ctypes.POINTER(d), i, vp, d,
+    L.esi_fdcg_solve.argtypes = [vp, d, d, i, vp, ctypes.POINTER(d), i, i, vp, d,
                                  ctypes.POINTER(EsiCgReport)]
     L.esi_pc_load.argtypes = [vp, vp, ctypes.c_size_t]
     L.esi_invert.argtypes = [vp, ctypes.POINTER(EsiInvertOpts), vp, vp, vp, vp,
@@ -402,7 +402,8 @@ class Context:
             call = self.L.esi_fdcg_solve(self.h, float(lam), float(tol), int(max_iter),
                                          _ptr(dobs),
                                          f.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                         int(f.size), _ptr(q), float(eps), ctypes.byref(rep))
+                                         int(f.size), PC[precond], _ptr(q), float(eps),
+                                         ctypes.byref(rep))
         elif data_space:
             call = self.L.esi_dscg_solve(self.h, float(lam), float(tol), int(max_iter),
                                          _ptr(dobs), _ptr(q), _ptr(w_out), float(eps),

@@ -383,8 +383,9 @@ def test_data_space_cg_matches_oracle(prec):
 
 
 # ----------------------------------------------------------------------------- frequency domain
+@pytest.mark.parametrize("pc", ["none", "diag"])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_frequency_domain_cg_matches_oracle(prec):
+def test_frequency_domain_cg_matches_oracle(prec, pc):
     """Frequency-domain ESI by time-domain modelling (Eq. "dtft", "idtft", "normaldtft"):
     iterates of F A F^H qbar / nt = F S^T d at three frequencies against the oracle, several
     shots, nt not a multiple of the 16-step DTFT block (a ragged block in both directions)."""
@@ -403,13 +404,19 @@ def test_frequency_domain_cg_matches_oracle(prec):
     # finite-precision CG)
     lam, nmax = 2e-4, (5 if prec == "f64" else 3)
     ctx = _ctx(v, geom, p, prec)
-    qb, rep = ctx.cg_solve(_dev(d, prec), lam=lam, tol=0.0, max_iter=nmax, freqs=freqs)
+    qb, rep = ctx.cg_solve(_dev(d, prec), lam=lam, tol=0.0, max_iter=nmax, freqs=freqs,
+                           precond=pc)
     assert tuple(qb.shape) == (geom.ns, len(freqs)) + v.shape + (2,)
     tol = {"f64": 1e-12, "f32": 1e-4}[prec]
     qh = qb.double().cpu().numpy()
     for s, sh in enumerate(shots):
         o0, o1 = geom.rec_offset[s], geom.rec_offset[s + 1]
-        ref = o.fd_cg(sh, d[nt * o0:nt * o1].reshape(nt, -1), lam, freqs, 0.0, nmax)
+        ds = d[nt * o0:nt * o1].reshape(nt, -1)
+        if pc == "diag":
+            B = o.annihilator(sh.src_xyz)
+            ref = o.fd_pcg(sh, ds, lam, freqs, 0.0, nmax, minv=1.0 / (lam * B * B))
+        else:
+            ref = o.fd_cg(sh, ds, lam, freqs, 0.0, nmax)
         assert rep["iters"][s] == ref["iters"] == nmax, s
         assert np.allclose(rep["rel_res"][s], ref["rel_res"], rtol=10 * tol, atol=0), s
         got = (qh[s, ..., 0] + 1j * qh[s, ..., 1]).reshape(len(freqs), -1)
