@@ -117,8 +117,7 @@ __global__ void __launch_bounds__(NT2, ESI_FD2_MINB) fd2_step_kernel(const __gri
     // Per-cell global inputs of both passes are loaded first, so that their latency
     // overlaps the staging of the shared tile instead of following the barrier.
     Vec<T> p_old[NP], p_cc[NP], p_r[NP], p_p[NP], p_g[NP], p_st[NP], p_b2[NP];
-    T p_q[NP][VEC], p_kz[NP];
-    const Vec<T> kx = ldv(a.kx + (colok ? gx0 : 0));   // sponge profile, padded to px
+    T p_q[NP][VEC];
 #pragma unroll
     for (int pz = 0; pz < NP; ++pz) {
         const int gz = z0 + ry + pz * RPP;
@@ -128,7 +127,6 @@ __global__ void __launch_bounds__(NT2, ESI_FD2_MINB) fd2_step_kernel(const __gri
         const long long gi = (long long)gz * a.px + gx0;
         p_old[pz] = ldv(po + gi);
         p_cc[pz] = ldv(a.cc + gi);
-        p_kz[pz] = a.kz[gz];
         if constexpr ((F & F_EXT) != 0) {
             const T *e = a.ext + fd + (long long)a.n * a.N + (long long)gz * a.nx + gx0;
 #pragma unroll
@@ -189,6 +187,7 @@ __global__ void __launch_bounds__(NT2, ESI_FD2_MINB) fd2_step_kernel(const __gri
 
     T psum = T(0);
     if (colok) {
+        const Vec<T> kx = ldv(a.kx + gx0);
         T xs = T(0), zs = T(0);
         if constexpr ((F & F_SAD) != 0) {
             xs = T(a.src_pos[3 * s + 0]);
@@ -224,7 +223,7 @@ __global__ void __launch_bounds__(NT2, ESI_FD2_MINB) fd2_step_kernel(const __gri
             const long long gi = (long long)gz * a.px + gx0;
             const Vec<T> old = p_old[pz];
             const Vec<T> cc = p_cc[pz];
-            const T kz = p_kz[pz];
+            const T kz = a.kz[gz];
             T q[VEC], S[VEC];
 #pragma unroll
             for (int i = 0; i < VEC; ++i) q[i] = p_q[pz][i];
