@@ -408,10 +408,12 @@ ESI_API esi_status esi_pc_load(esi_ctx *ctx, const void *weights_dev, size_t byt
 /* How many learned solves of this context dropped the network and restarted diagonally. */
 ESI_API long long esi_pc_fallbacks(const esi_ctx *ctx);
 
-/* Pack a dense field [ns][nt][N] (scaled by 1 / (lambda B^2) when scale != 0) into the
- * network's BF16 images [ns * ceil(nt/16)][h][w][16] (2D FP32 contexts). */
+/* Pack a field (scaled by 1 / (lambda B^2) when scale != 0) into the network's BF16 images
+ * [ns * ceil(nt/16)][h][w][16] (2D FP32 contexts).  pitched == 0: the field is dense
+ * [ns][nt][nz][nx]; otherwise it has the CG vectors' layout [ns][nt][nz][px], px = nx rounded
+ * up to a multiple of 32, pad columns zero (the form the learned CG packs its residuals in). */
 ESI_API esi_status esi_pc_pack(esi_ctx *ctx, const void *field_dev, double lambda, double eps,
-                               int scale, void *img_dev);
+                               int scale, int pitched, void *img_dev);
 
 /* A stand-alone network for h x w images, batches of up to max_batch, on a stream. */
 ESI_API esi_status esi_pc_create(esi_pc **out, int h, int w, int max_batch, void *stream);

@@ -2591,7 +2591,7 @@ ESI_API esi_status esi_normal_apply(esi_ctx *ctx, double lambda, double eps, con
 }
 
 ESI_API esi_status esi_pc_pack(esi_ctx *ctx, const void *field_dev, double lambda, double eps,
-                               int scale, void *img_dev) {
+                               int scale, int pitched, void *img_dev) {
     if (!ctx) return ESI_ERR_ARG;
     if (!field_dev || !img_dev) return ctx->fail(ESI_ERR_ARG, "bad arguments");
     if (ctx->g.ndim != 2 || ctx->g.dtype != ESI_F32)
@@ -2609,7 +2609,7 @@ ESI_API esi_status esi_pc_pack(esi_ctx *ctx, const void *field_dev, double lambd
     }
     CKL(pcnet::pack_launch(reinterpret_cast<const float *>(field_dev), ipb2,
                            reinterpret_cast<__nv_bfloat16 *>(img_dev), ctx->ns, ctx->nt, ctx->g.nz,
-                           ctx->g.nx, ctx->px, ctx->sst, scale, 1, ctx->st));
+                           ctx->g.nx, ctx->px, ctx->sst, scale, pitched ? 0 : 1, ctx->st));
     return ESI_OK;
 }
 

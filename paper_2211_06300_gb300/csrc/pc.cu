@@ -401,6 +401,64 @@ __global__ void __launch_bounds__(256, 4) pack_kernel(const float *r, const floa
     }
 }
 
+// The same packing for the pitched residual (row stride px, a multiple of 32 floats, pads zero):
+// a thread takes two neighbouring output pixels, i.e. 4 input columns, and reads them as one
+// 16-byte load per row and time sample; a block walks whole output rows.  Columns past nx read
+// the zero pads (4 * ceil(nx / 4) <= px), so no column test is needed.
+__global__ void __launch_bounds__(256, 4) pack4_kernel(const float *r, const float *ipb2,
+                                                       __nv_bfloat16 *img, int ns, int nt, int ng,
+                                                       int nz, int px, long long sst, int hc,
+                                                       int wc, int scale_by_map) {
+    const int nrow = ns * ng * hc, nqd = (wc + 1) / 2;
+    for (int rw = blockIdx.x; rw < nrow; rw += gridDim.x) {
+        const int zc = rw % hc, ig = rw / hc;
+        const int g = ig % ng, s = ig / ng;
+        const float *rs = r + (long long)s * nt * sst;
+        __nv_bfloat16 *orow = img + ((long long)ig * hc + zc) * wc * G;
+        const int iz0 = 2 * zc;
+        const bool row2 = iz0 + 1 < nz;
+        for (int qd = threadIdx.x; qd < nqd; qd += blockDim.x) {
+            const int ix0 = 4 * qd;
+            float4 m[2];
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                m[a] = make_float4(1.0f, 1.0f, 1.0f, 1.0f);
+                if (scale_by_map && (a == 0 || row2))
+                    m[a] = *reinterpret_cast<const float4 *>(ipb2 + (long long)s * sst +
+                                                             (long long)(iz0 + a) * px + ix0);
+            }
+            if (!row2) m[1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            const bool pix2 = 2 * qd + 1 < wc;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float v0[G / 2], v1[G / 2];
+#pragma unroll
+                for (int c = 0; c < G / 2; ++c) {
+                    const int t = G * g + (G / 2) * h + c;
+                    float a0 = 0.0f, a1 = 0.0f;
+                    if (t < nt) {
+                        const float *rt = rs + (long long)t * sst + (long long)iz0 * px + ix0;
+                        const float4 u = *reinterpret_cast<const float4 *>(rt);
+                        a0 = u.x * m[0].x + u.y * m[0].y;
+                        a1 = u.z * m[0].z + u.w * m[0].w;
+                        if (row2) {
+                            const float4 w = *reinterpret_cast<const float4 *>(rt + px);
+                            a0 += w.x * m[1].x + w.y * m[1].y;
+                            a1 += w.z * m[1].z + w.w * m[1].w;
+                        }
+                    }
+                    v0[c] = 0.25f * a0;
+                    v1[c] = 0.25f * a1;
+                }
+                store_row<__nv_bfloat16>(orow + (long long)(2 * qd) * G + (G / 2) * h, v0, G / 2);
+                if (pix2)
+                    store_row<__nv_bfloat16>(orow + (long long)(2 * qd + 1) * G + (G / 2) * h, v1,
+                                             G / 2);
+            }
+        }
+    }
+}
+
 // 2 x 2 average pooling (zero fill at odd edges), BF16 channels-last, C = 32
 __global__ void pool_kernel(const __nv_bfloat16 *in, __nv_bfloat16 *out, long long n, int H, int W,
                             int Ho, int Wo) {
@@ -895,6 +953,11 @@ cudaError_t pack_launch(const float *r, const float *ipb2, __nv_bfloat16 *img, i
                         cudaStream_t st) {
     const int ng = (nt + G - 1) / G, hc = (nz + 1) / 2, wc = (nx + 1) / 2;
     const int nrow = ns * ng * hc;
+    if (!dense) {   // pitched rows: 16-byte loads
+        pack4_kernel<<<std::min(nrow, 4096), 256, 0, st>>>(r, ipb2, img, ns, nt, ng, nz, px, sst,
+                                                              hc, wc, scale_by_map);
+        return cudaGetLastError();
+    }
     pack_kernel<<<std::min(nrow, 4096), 256, 0, st>>>(r, ipb2, img, ns, nt, ng, nz, nx, px, sst,
                                                          hc, wc, scale_by_map, dense);
     return cudaGetLastError();

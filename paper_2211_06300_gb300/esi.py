@@ -141,7 +141,7 @@ def load_library(require_gpu: bool = True) -> ctypes.CDLL:
     L.esi_pc_param_count.restype = ctypes.c_size_t
     L.esi_pc_fallbacks.argtypes = [vp]
     L.esi_pc_fallbacks.restype = ctypes.c_longlong
-    L.esi_pc_pack.argtypes = [vp, vp, d, d, i, vp]
+    L.esi_pc_pack.argtypes = [vp, vp, d, d, i, i, vp]
     L.esi_pc_create.argtypes = [ctypes.POINTER(vp), i, i, i, vp]
     L.esi_pc_destroy.argtypes = [vp]
     L.esi_pc_destroy.restype = None
@@ -312,12 +312,14 @@ class Context:
         ng = (self.nt + 15) // 16
         return (self.ns * ng, (self.shape[0] + 1) // 2, (self.shape[-1] + 1) // 2, 16)
 
-    def pc_pack(self, field, lam: float = 0.0, scale: bool = False, eps: float = 0.0, out=None):
-        """Pack a [ns][nt][...] field into the network's BF16 images (esi_pc_pack)."""
+    def pc_pack(self, field, lam: float = 0.0, scale: bool = False, eps: float = 0.0, out=None,
+                pitched: bool = False):
+        """Pack a [ns][nt][...] field into the network's BF16 images (esi_pc_pack); pitched:
+        the field's rows are px = 32 ceil(nx / 32) wide, pad columns zero."""
         out = self.torch.empty(self.pc_images_shape(), dtype=self.torch.bfloat16,
                                device=self.device) if out is None else out
         self._check(self.L.esi_pc_pack(self.h, _ptr(field), float(lam), float(eps),
-                                       1 if scale else 0, _ptr(out)))
+                                       1 if scale else 0, 1 if pitched else 0, _ptr(out)))
         return out
 
     def pc_load(self, params):

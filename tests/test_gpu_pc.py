@@ -124,9 +124,11 @@ def test_cg_with_learned_preconditioner_reaches_the_true_residual():
         assert np.linalg.norm(r) / np.linalg.norm(b) < 2e-3, s
 
 
-def test_pack_matches_oracle_with_ragged_edges_and_time_padding():
+@pytest.mark.parametrize("pitched", [False, True])
+def test_pack_matches_oracle_with_ragged_edges_and_time_padding(pitched):
     """esi_pc_pack: r / (lambda B^2), 16-sample time groups (zero-padded past nt), 2 x 2
-    averages with zero fill at odd edges, BF16 - against the oracle's pack."""
+    averages with zero fill at odd edges, BF16 - against the oracle's pack; from a dense field
+    and from the CG vectors' pitched layout (the path of the learned CG)."""
     from paper_2211_06300_gb300 import esi
     shape, dx, dt, nt, nb = (23, 37), 10.0, 1e-3, 40, 4     # odd nz, nx; nt = 2.5 groups
     v = synth.dipping_layers(shape, dx, 3, nlayers=3, vmin=1500, vmax=2500, nanom=1, sigma=30.0)
@@ -135,8 +137,13 @@ def test_pack_matches_oracle_with_ragged_edges_and_time_padding():
     rng = np.random.default_rng(13)
     field = rng.standard_normal((2, nt) + shape)
     lam = 3e-4
-    img = ctx.pc_pack(torch.tensor(field, dtype=torch.float32, device="cuda"), lam=lam,
-                      scale=True).double().cpu().numpy()
+    fin = field
+    if pitched:   # rows padded with zeros to a multiple of 32 columns
+        px = (shape[1] + 31) // 32 * 32
+        fin = np.zeros((2, nt, shape[0], px))
+        fin[..., :shape[1]] = field
+    img = ctx.pc_pack(torch.tensor(fin, dtype=torch.float32, device="cuda"), lam=lam,
+                      scale=True, pitched=pitched).double().cpu().numpy()
     o = oracle.Oracle(v, dx, dt, nt, nb)
     ng = (nt + cnn.G - 1) // cnn.G
     for s in range(2):
