@@ -83,13 +83,13 @@ def workload_name(ns, nt):
 # ----------------------------------------------------------------------------- DRAM traffic
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per cell update of a step-kernel variant,
 # from the capture summarised in profiles/fd2_step_801x241_16shots.md (16 shots of 801 x 241,
-# one launch = 3,088,656 cell updates), valid only for the
-# kernel sources it was taken on: the SHA-256 of fd2d.cu and esi_internal.h at capture time.
-_SHA = "a3f13c11fae45243f13514923dd571846149fe34416508ab05ec6fa67b9a66f3"
+# one launch = 3,088,656 cell updates), valid only for the kernel it was taken on: the
+# SHA-256 below of its template source and the header's argument struct (_sources_sha).
+_SHA = "ef6b0c4a12b0c41812cc6bc93c71b90a1236190a0c505df6841b16262935abe7"
 MEASURED_TRAFFIC = {
-    "fd2_step[PT|AP]": ((52.540672e6 + 0.893696e6) / 3088656, _SHA),
-    "fd2_step[CGP|SMP]": ((69.079040e6 + 1.337600e6) / 3088656, _SHA),
-    "fd2_step[EXT|SAD]": ((51.681280e6 + 0.226304e6) / 3088656, _SHA),
+    "fd2_step[PT|AP]": ((52.657664e6 + 0.915456e6) / 3088656, _SHA),
+    "fd2_step[CGP|SMP]": ((69.079040e6 + 1.483008e6) / 3088656, _SHA),
+    "fd2_step[EXT|SAD]": ((51.679232e6 + 0.257792e6) / 3088656, _SHA),
 }
 TRAFFIC_SOURCES = ("paper_2211_06300_gb300/csrc/fd2d.cu", "paper_2211_06300_gb300/csrc/esi_internal.h")
 

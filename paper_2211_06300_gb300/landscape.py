@@ -94,10 +94,12 @@ def _power(ctx, nt, shape, device, iters: int = 8) -> float:
 def scan(v_true: np.ndarray, dx: float, dt: float, nt: int, nb: int, f_peak: float,
          eps_grid: Sequence[float], b_values: Sequence[float] = (100.0, 0.01), n_cg: int = 10,
          dtype: str = "f32", device: str = "cuda", step: int = 2,
-         betas: Optional[Dict] = None) -> Dict:
+         betas: Optional[Dict] = None, cg_tol: float = 1e-6, log=None) -> Dict:
     """The objectives along the scan: {"eps", "fwi", "wri": {b: [...]}, "esi": {b: [...]},
-    "beta", "lambda_max"}.  `betas` ({"wri": {b: beta}, "esi": {b: beta}}) replaces the
-    penalties derived from lambda_max."""
+    "beta", "lambda_max", "breakdowns"}.  `betas` ({"wri": {b: beta}, "esi": {b: beta}})
+    replaces the penalties derived from lambda_max.  An inner solve stops after n_cg
+    iterations or at cg_tol; one that meets a breakdown (p^T A p <= 0 once its residual has
+    vanished in the field precision) keeps its last iterate, and the event is listed."""
     import torch
     from . import esi
     tdt = torch.float64 if dtype == "f64" else torch.float32
@@ -121,21 +123,31 @@ def scan(v_true: np.ndarray, dx: float, dt: float, nt: int, nb: int, f_peak: flo
         b_values = list(betas["wri"])
     out = {"eps": [float(e) for e in eps_grid], "fwi": [],
            "wri": {b: [] for b in b_values}, "esi": {b: [] for b in b_values},
-           "beta": beta, "lambda_max": lam_max}
-    q = None
+           "beta": beta, "lambda_max": lam_max, "breakdowns": []}
+    q = ctx.empty_field()
+
+    def solve(tag, e, b, **kw):
+        try:
+            ctx.cg_solve(dobs, tol=cg_tol, max_iter=n_cg, out=q, **kw)
+        except esi.EsiError as ex:
+            if ex.status != esi.ESI_ERR_BREAKDOWN:
+                raise
+            out["breakdowns"].append({"eps": float(e), "method": tag, "b": b})
     for e in eps_grid:
         ctx.set_velocity(vt * (1.0 + float(e)))
         _, J = ctx.gradient(wavelet=wav, dobs=dobs, mode="adjoint", param="v")
         out["fwi"].append(J)
         for b in b_values:
-            q, _ = ctx.cg_solve(dobs, lam=beta["wri"][b], tol=0.0, max_iter=n_cg,
-                                wri_wavelet=wav, out=q)
+            solve("wri", e, b, lam=beta["wri"][b], wri_wavelet=wav)
             _, J = ctx.gradient(wavelet=wav, ext=q, dobs=dobs, mode="wri", beta=beta["wri"][b])
             out["wri"][b].append(J)
-            q, _ = ctx.cg_solve(dobs, lam=beta["esi"][b], tol=0.0, max_iter=n_cg, precond="diag",
-                                out=q)
+            solve("esi", e, b, lam=beta["esi"][b], precond="diag")
             _, J = ctx.gradient(ext=q, dobs=dobs, mode="saddle", beta=beta["esi"][b])
             out["esi"][b].append(J)
+        if log:
+            print(f"eps {float(e):+.3f} fwi {out['fwi'][-1]:.6e} " +
+                  " ".join(f"{m}{b:g} {out[m][b][-1]:.6e}" for m in ("wri", "esi")
+                           for b in b_values), file=log, flush=True)
     ctx.close()
     return out
 
@@ -154,14 +166,15 @@ def main(argv=None):
     a = ap.parse_args(argv)
     v = layered_model((a.n, a.n), a.dx)
     eps = np.linspace(-0.5, 0.5, a.n_eps)
-    r = scan(v, a.dx, a.dt, a.nt, a.nb, a.f_peak, eps, dtype=a.dtype)
+    import sys
+    r = scan(v, a.dx, a.dt, a.nt, a.nb, a.f_peak, eps, dtype=a.dtype, log=sys.stdout)
     curves = {"fwi": r["fwi"]}
     for m in ("wri", "esi"):
         for b, J in r[m].items():
             curves[f"{m}_b{b:g}"] = J
     res = {"config": vars(a), "eps": r["eps"], "curves": curves,
            "beta": {m: {f"{b:g}": x for b, x in r["beta"][m].items()} for m in ("wri", "esi")},
-           "lambda_max": r["lambda_max"],
+           "lambda_max": r["lambda_max"], "breakdowns": r["breakdowns"],
            "summary": {k: basin(eps, J) for k, J in curves.items()}}
     if a.out:
         with open(a.out, "w") as fh:

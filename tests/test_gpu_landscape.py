@@ -16,7 +16,9 @@ def test_scan_matches_oracle_fp64():
     v = landscape.layered_model(shape, dx, seed=5, nlayers=3)
     eps = [-0.3, 0.0, 0.2]
     betas = {"wri": {100.0: 2e-2, 0.01: 2e-6}, "esi": {100.0: 1e-3, 0.01: 1e-7}}
-    r = landscape.scan(v, dx, dt, nt, nb, fp, eps, n_cg=10, dtype="f64", betas=betas)
+    r = landscape.scan(v, dx, dt, nt, nb, fp, eps, n_cg=10, dtype="f64", betas=betas,
+                       cg_tol=0.0)
+    assert r["breakdowns"] == []
     geom = landscape.acquisition(shape, dx, nb)
     vref = float(v.max()) * 1.3
     f = synth.ricker(nt, dt, fp)
