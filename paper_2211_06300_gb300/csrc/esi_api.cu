@@ -139,6 +139,7 @@ struct esi_ctx {
     // slower than the one-tile-per-block kernel (18.3 / 19.7 us against 14.1 / 17.2 us per
     // step of 16 shots of 801 x 241); ESI_TMA_CG=1 selects it
     bool tma_cg = false;
+    bool pdl = true;               // 2D loop steps after the first start as dependent launches
     unsigned long long graph_clock = 0;
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> evpool;
@@ -532,7 +533,7 @@ StepArgs<T> base_args(esi_ctx *ctx) {
 
 // One step of either kernel.  In 3D the sampling of the input state is a gather launch.
 template <typename T>
-esi_status step(esi_ctx *ctx, unsigned flags, const StepArgs<T> &a) {
+esi_status step(esi_ctx *ctx, unsigned flags, const StepArgs<T> &a, bool chained = false) {
     StepArgs<T> b = a;
     if (!state_map(ctx, a.cur, &b.tm) ||
         (ctx->g.ndim == 3 && (!state_map(ctx, a.po, &b.tm_old, 1) || !state_map(ctx, a.cc, &b.tm_cc, 2))))
@@ -552,7 +553,7 @@ esi_status step(esi_ctx *ctx, unsigned flags, const StepArgs<T> &a) {
         if (!ok) return ctx->fail(ESI_ERR_CUDA, "cuTensorMapEncodeTiled failed for a CG stream");
         CKL(launch_step2_cg<T>(flags, b, ctx->ns, ctx->st));
     } else if (ctx->g.ndim == 2) {
-        CKL(launch_step2<T>(flags, b, ctx->ns, ctx->st));
+        CKL(launch_step2<T>(flags, b, ctx->ns, ctx->st, chained && ctx->pdl));
     } else {
         if ((flags & F_SMP) && a.tout >= 0)
             CKL(launch_sample_global<T>(a.smp, a.cur, ctx->sst, a.smp_out, a.tout, ctx->st));
@@ -760,7 +761,7 @@ esi_status fwd_loop(esi_ctx *ctx, StepArgs<T> a, unsigned flags, T *&cur, T *&po
             a.tin = n;
             a.tout = n - 1;
             a.slot_w = n - n0;
-            esi_status e = step<T>(ctx, flags, a);
+            esi_status e = step<T>(ctx, flags, a, n > n0);
             if (e != ESI_OK) return e;
             std::swap(c, q);
         }
@@ -797,7 +798,7 @@ esi_status fwd_dft_loop(esi_ctx *ctx, StepArgs<T> a, unsigned flags, T *cur, T *
                 a.tin = n;
                 a.tout = n - 1;
                 a.slot_w = n - n0;
-                esi_status e = step<T>(ctx, flags, a);
+                esi_status e = step<T>(ctx, flags, a, n > 0);
                 if (e != ESI_OK) return e;
                 std::swap(c, q);
             }
@@ -966,7 +967,7 @@ esi_status adj_loop(esi_ctx *ctx, StepArgs<T> a, unsigned flags, T *&cur, T *&po
             a.nout = j - 1;
             a.tout = (sample_src && j <= ctx->nt - 1) ? j : -1;
             a.slot_r = (j - 1) - j0;
-            esi_status e = step<T>(ctx, flags, a);
+            esi_status e = step<T>(ctx, flags, a, j < j1);
             if (e != ESI_OK) return e;
             std::swap(c, q);
         }
@@ -1858,7 +1859,7 @@ esi_status fdcg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, cons
                     a.nout = j - 1;
                     a.tout = -1;
                     a.slot_w = (j - 1) - jlo;   // slots in time order within the block
-                    esi_status st = step<T>(ctx, aflags, a);
+                    esi_status st = step<T>(ctx, aflags, a, j < nt);
                     if (st != ESI_OK) return st;
                     std::swap(c, q);
                 }
@@ -1910,7 +1911,7 @@ esi_status fdcg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, cons
                     a.n = n - n0;   // the stash slot
                     a.tin = n;
                     a.tout = n - 1;
-                    esi_status st = step<T>(ctx, F_CGP | F_SMP, a);
+                    esi_status st = step<T>(ctx, F_CGP | F_SMP, a, n > 0);
                     if (st != ESI_OK) return st;
                     std::swap(c, q);
                 }
@@ -2388,6 +2389,7 @@ ESI_API esi_status esi_create(esi_ctx **out, const esi_grid *grid, const esi_geo
     }
     if (const char *ev = std::getenv("ESI_NO_GRAPHS")) ctx->use_graphs = ev[0] == '0';
     if (const char *ev = std::getenv("ESI_TMA_CG")) ctx->tma_cg = ev[0] == '1';
+    if (const char *ev = std::getenv("ESI_PDL")) ctx->pdl = ev[0] != '0';
     esi_ctx *c = ctx.get();
     {
         esi_ctx *ctx = c;  // for CK

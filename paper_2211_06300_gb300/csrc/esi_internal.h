@@ -164,7 +164,8 @@ constexpr long long TMA_WAIT_LIMIT = 1ll << 26;
 
 // ----------------------------------------------------------------------------- launchers
 template <typename T>
-cudaError_t launch_step2(unsigned flags, const StepArgs<T> &a, int ns, cudaStream_t st);
+cudaError_t launch_step2(unsigned flags, const StepArgs<T> &a, int ns, cudaStream_t st,
+                         bool chained = false);
 template <typename T>
 cudaError_t launch_step3(unsigned flags, const StepArgs<T> &a, int ns, cudaStream_t st);
 // the two CG-product variants of the 2D step (F_CGP | F_SMP, F_PT | F_AP), persistent and

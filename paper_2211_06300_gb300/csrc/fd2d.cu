@@ -102,12 +102,6 @@ __global__ void __launch_bounds__(NT2, ESI_FD2_MINB) fd2_step_kernel(const __gri
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (tid == 0) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar)),
-                     "r"((unsigned)(SH2 * SW2 * sizeof(T)))
-                     : "memory");
-        tma_load_3d(&tl[0][0], &a.tm, x0 - HALO, z0 - HALO, s, &bar);
-    }
     const int qx = tid % TPR, ry = tid / TPR;
     const int lx = qx * VEC, gx0 = x0 + lx;
     const bool colok = gx0 < a.nx;
@@ -142,11 +136,29 @@ __global__ void __launch_bounds__(NT2, ESI_FD2_MINB) fd2_step_kernel(const __gri
             p_p[pz] = ldv(a.ap_p + fb + (long long)a.nout * a.sst + gi);
             p_b2[pz] = ldv(a.pb2 + (long long)s * a.sst + gi);
         }
-        if constexpr ((F & (F_GRD | F_SAD)) != 0) p_g[pz] = ldv(a.grad + (long long)s * a.sst + gi);
         if constexpr ((F & F_GRD) != 0)
             p_st[pz] = ldv(a.stash_r + ((long long)a.slot_r * a.ns + s) * a.sst + gi);
     }
 
+    // Everything above reads only what the previous step does not write (u_{n-1} was written
+    // two steps back).  Wait for the previous step, then stage its output u_n and read the
+    // accumulators it updated; then let the next step's blocks start their own prologue.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (tid == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar)),
+                     "r"((unsigned)(SH2 * SW2 * sizeof(T)))
+                     : "memory");
+        tma_load_3d(&tl[0][0], &a.tm, x0 - HALO, z0 - HALO, s, &bar);
+    }
+    if constexpr ((F & (F_GRD | F_SAD)) != 0) {
+#pragma unroll
+        for (int pz = 0; pz < NP; ++pz) {
+            const int gz = z0 + ry + pz * RPP;
+            if (colok && gz < a.nz)
+                p_g[pz] = ldv(a.grad + (long long)s * a.sst + (long long)gz * a.px + gx0);
+        }
+    }
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     (void)CPR;
     bool has_pt = false;
     if constexpr ((F & F_PT) != 0) {
@@ -352,11 +364,22 @@ __global__ void __launch_bounds__(NT2, ESI_FD2_MINB) fd2_step_kernel(const __gri
     }
 }
 
+// chained: the previous launch on the stream is the previous step of the same loop, so the
+// grid may start (programmatic dependent launch) while that step drains: its prologue reads
+// only what that step does not write, and it waits for it before staging u_n.
 template <typename T, unsigned F>
-cudaError_t go(const StepArgs<T> &a, int ns, cudaStream_t st) {
-    dim3 grid(a.ntx, a.ntz, ns);
-    fd2_step_kernel<T, F><<<grid, NT2, 0, st>>>(a);
-    return cudaGetLastError();
+cudaError_t go(const StepArgs<T> &a, int ns, cudaStream_t st, bool chained) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.ntx, a.ntz, ns);
+    cfg.blockDim = dim3(NT2);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = chained ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, fd2_step_kernel<T, F>, a);
 }
 
 template <typename T>
@@ -375,10 +398,11 @@ __global__ void sample_global_kernel(const SmpList<T> l, const T *state, long lo
 
 #define ESI_CASE(FL)        \
     case (FL):              \
-        return go<T, (FL)>(a, ns, st);
+        return go<T, (FL)>(a, ns, st, chained);
 
 template <typename T>
-cudaError_t launch_step2(unsigned flags, const StepArgs<T> &a, int ns, cudaStream_t st) {
+cudaError_t launch_step2(unsigned flags, const StepArgs<T> &a, int ns, cudaStream_t st,
+                         bool chained) {
     switch (flags) {
         // forward modelling (point / extended / both), with and without DTFT; the
         // F_PT | F_SMP variant also serves the adjoint with the wavelet output only
@@ -420,8 +444,8 @@ cudaError_t launch_sample_global(const SmpList<T> &l, const T *state, long long 
     return cudaGetLastError();
 }
 
-template cudaError_t launch_step2<float>(unsigned, const StepArgs<float> &, int, cudaStream_t);
-template cudaError_t launch_step2<double>(unsigned, const StepArgs<double> &, int, cudaStream_t);
+template cudaError_t launch_step2<float>(unsigned, const StepArgs<float> &, int, cudaStream_t, bool);
+template cudaError_t launch_step2<double>(unsigned, const StepArgs<double> &, int, cudaStream_t, bool);
 template cudaError_t launch_sample_global<float>(const SmpList<float> &, const float *, long long,
                                                  float *, int, cudaStream_t);
 template cudaError_t launch_sample_global<double>(const SmpList<double> &, const double *,
