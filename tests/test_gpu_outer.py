@@ -155,3 +155,17 @@ def test_outer_loop_rejects_bad_options():
     with pytest.raises(esi.EsiError):
         ctx.invert(d, vel, memory=0)
     assert np.array_equal(vel.cpu().numpy(), v)  # nothing ran
+
+
+def test_outer_loop_on_zero_data_stops_at_a_zero_gradient():
+    """Zero data: the inner solution is q = 0, so J = 0 and g = 0 and the loop stops before
+    its first step, leaving the model as it was."""
+    v, geom, pb, f = _problem()
+    ctx = _ctx(v, geom, pb, torch.float64)
+    vel = _dev(v, torch.float64)
+    d0 = torch.zeros(sum(x.size for x in pb.d), dtype=torch.float64, device="cuda")
+    g, rep = ctx.invert(d0, vel, n_outer=2, n_cg=5, beta0=0.1, vmin=1400.0, vmax=2600.0)
+    assert rep["stop"] == "zero gradient" and rep["iters_done"] == 0
+    assert rep["evaluations"] == 1
+    assert torch.count_nonzero(g).item() == 0
+    assert np.array_equal(vel.cpu().numpy(), v)

@@ -443,3 +443,21 @@ def test_frequency_domain_cg_3d_fp64():
     qh = qb.cpu().numpy()[0]
     got = (qh[..., 0] + 1j * qh[..., 1]).reshape(len(freqs), -1)
     assert oracle.rel_l2(got, ref["qbar"].reshape(len(freqs), -1)) <= 1e-11
+
+
+def test_frequency_domain_cg_limits_and_zero_data():
+    """At most 8 frequencies; the learned preconditioner is not offered; zero data give
+    qbar = 0 with no iteration (x_0 = 0 is exact), as in the oracle."""
+    esi = _esi()
+    v, geom, p = _ragged_case(nt=40)
+    ctx = _ctx(v, geom, p, "f64")
+    nd = int(geom.rec_offset[-1]) * p["nt"]
+    d0 = torch.zeros(nd, dtype=torch.float64, device="cuda")
+    with pytest.raises(esi.EsiError):
+        ctx.cg_solve(d0, lam=1e-3, tol=0.0, max_iter=3, freqs=[5.0] * 9)
+    with pytest.raises(esi.EsiError):
+        ctx.cg_solve(d0, lam=1e-3, tol=0.0, max_iter=3, freqs=[5.0], precond="learned")
+    qb, rep = ctx.cg_solve(d0, lam=1e-3, tol=0.0, max_iter=3, freqs=[5.0, 9.0],
+                           precond="diag")
+    assert torch.count_nonzero(qb).item() == 0
+    assert list(rep["iters"]) == [0] * geom.ns and rep["converged"]
