@@ -431,7 +431,7 @@ def test_frequency_domain_cg_3d_fp64():
     v = synth.dipping_layers(shape, dx, 3, nlayers=3, vmin=1500, vmax=2500, nanom=1,
                              sigma=3 * dx)
     geom = synth.surface_grid_3d((183.0, 96.5, 333.0), np.array([35.0, 122.5, 300.0]),
-                                 np.array([0.0, 101.0, 200.0]), 655.5)
+                                 np.array([0.0, 101.0, 200.0]), 300.0)
     p = dict(dx=dx, dt=dt, nt=nt, nb=nb)
     o, (sh,) = _orc(v, geom, p)
     d = o.forward(sh, wavelet=synth.ricker(nt, dt, 30.0))["traces"]
@@ -461,3 +461,41 @@ def test_frequency_domain_cg_limits_and_zero_data():
                            precond="diag")
     assert torch.count_nonzero(qb).item() == 0
     assert list(rep["iters"]) == [0] * geom.ns and rep["converged"]
+
+
+def test_3d_cg_gradients_and_objective_fp64():
+    """The 3D kernels' CG product (F_CGP, PT|AP), gradient recompute / correlation (STW, GRD)
+    and saddle-point correlation (EXT|SAD) against the oracle on a volume with two z chunks
+    and ragged x / y tiles."""
+    shape = (70, 21, 37)
+    dx, dt, nt, nb = 10.0, 1e-3, 60, 4
+    v = synth.dipping_layers(shape, dx, 3, nlayers=3, vmin=1500, vmax=2500, nanom=1,
+                             sigma=3 * dx)
+    # receivers 33 m above the source plane, within reach over 60 steps
+    geom = synth.surface_grid_3d((183.0, 96.5, 333.0), np.array([35.0, 122.5, 300.0]),
+                                 np.array([0.0, 101.0, 200.0]), 300.0)
+    p = dict(dx=dx, dt=dt, nt=nt, nb=nb)
+    o, (sh,) = _orc(v, geom, p)
+    wav = synth.ricker(nt, dt, 30.0)
+    d = o.forward(sh, wavelet=wav)["traces"]
+    ctx = _ctx(v, geom, p, "f64")
+    lam, nmax = 1e-3, 3
+    q, rep = ctx.cg_solve(_dev(d.ravel(), "f64"), lam=lam, tol=0.0, max_iter=nmax, precond="diag")
+    B = o.annihilator(sh.src_xyz)
+    ref = o.pcg(sh, d, lam, 0.0, nmax, minv=1.0 / (lam * B * B))
+    assert np.allclose(rep["rel_res"][0], ref["rel_res"], rtol=1e-9, atol=0)
+    assert oracle.rel_l2(q[0].reshape(nt, -1).cpu().numpy(), ref["x"]) <= 1e-9
+    # saddle-point gradient and the objective at this q
+    qh = q.cpu().numpy()[0].reshape(nt, -1)
+    g, J = ctx.gradient(ext=q, dobs=_dev(d.ravel(), "f64"), mode="saddle", beta=lam, param="v")
+    g_ref = o.saddle_gradient(sh, qh, lam, param="v")
+    assert oracle.rel_l2(g.cpu().numpy().ravel(), g_ref) <= 1e-12
+    from oracle import outer
+    assert J == pytest.approx(outer.esi_objective(o, sh, qh, d, lam), rel=1e-12)
+    # adjoint-state gradient of a shifted-wavelet misfit, checkpoints every 5 steps
+    wav2 = synth.ricker(nt, dt, 26.0, delay=0.04)
+    g2, J2 = ctx.gradient(wavelet=_dev(wav2[None, :], "f64"), dobs=_dev(d.ravel(), "f64"),
+                          param="v", ckpt_every=5)
+    J2_ref, g2_ref = o.misfit_gradient(sh, d, wavelet=wav2, param="v")
+    assert oracle.rel_l2(g2.cpu().numpy().ravel(), g2_ref) <= 1e-12
+    assert J2 == pytest.approx(J2_ref, rel=1e-12)
