@@ -63,11 +63,13 @@ def parse():
                          "domain / learned)")
     ap.add_argument("--ref-nt", type=int, default=1500, help="oracle sample: steps per bench step")
     ap.add_argument("--workload", default="esi2d",
-                    choices=["esi2d", "dft3d", "wri2d", "invert2d"],
+                    choices=["esi2d", "dft3d", "wri2d", "invert2d", "grad2d"],
                     help="dft3d: forward modelling with the on-the-fly DTFT (5 frequencies, FP16 "
                          "output) on the 400^3, nt 2000 volume instead of the ESI step; wri2d: "
                          "the WRI solve (B = I) and its gradient on the ESI step's workload; "
-                         "invert2d: the ESI outer loop (esi_invert) on that workload")
+                         "invert2d: the ESI outer loop (esi_invert) on that workload; grad2d: "
+                         "the adjoint-state gradient with BF16 checkpoints on 64 shots of "
+                         "1201 x 301")
     ap.add_argument("--outer", type=int, default=2, help="invert2d: outer iterations per step")
     ap.add_argument("--wri-factor", type=float, default=1e-2,
                     help="WRI penalty: beta = factor * lambda_max(S^T S)")
@@ -554,6 +556,105 @@ def run_invert2d(args, rank, world, local):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------- gradient arm
+def run_grad2d(args, rank, world, local):
+    """One step = the adjoint-state gradient (Eq. "gradient", "FWI_lambda") of the misfit on
+    the 1201 x 301, nt 3000, 64-shot workload of uneven apertures (201-801 receivers): the
+    forward modelling storing BF16 (u_n, u_{n-1}) checkpoints every 20 steps, then per
+    segment the recompute with the stash of Lap u_n + q_n and the adjoint with the
+    correlation.  Shots are sharded over ranks; the gradient is summed in rank order."""
+    import torch
+    from paper_2211_06300_gb300 import esi, shard, synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    nt = args.nt
+    ns_all = 64 * world
+    wl = synth.workload_batched_2d(nt=nt, ns=ns_all)
+    lo, hi = shard.shot_range(ns_all, rank, world)
+    geom = wl.geom.select(range(lo, hi))
+    ns = hi - lo
+    vref = float(wl.v_true.max())
+    f32 = torch.float32
+    wav = torch.tensor(wl.wavelets()[lo:hi], dtype=f32, device=dev).contiguous()
+    ct = esi.Context(torch.tensor(wl.v_true, dtype=f32, device=dev), wl.dx, wl.dt, nt, wl.nb,
+                     geom, vref=vref)
+    dobs = ct.forward(wavelet=wav)
+    ct.close()
+    v0 = torch.tensor(wl.v_start, dtype=f32, device=dev)
+    ctx = esi.Context(v0, wl.dx, wl.dt, nt, wl.nb, geom, vref=vref)
+    N = wl.ncell
+    cells_step = 3 * ns * N * nt      # forward, recompute, adjoint
+
+    def step(d):
+        g, J = ctx.gradient(wavelet=wav, dobs=d, param="v", ckpt_every=20, ckpt="bf16")
+        if dist is not None:
+            J = shard.reduce_objective(J, g, dist)
+        return g, J
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        step(dobs)
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = ctx.launches
+    ctx.set_profiling(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream(dev)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(dobs)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    prof = ctx.profile()
+    ctx.set_profiling(False)
+    launches = ctx.launches - l0
+    clk = clocks.stop()
+    t_max = shard.max_over_ranks(ms, dist, dev)
+    cells_all = shard.sum_over_ranks(cells_step * args.steps, dist, dev)
+    d_host = dobs.cpu().pin_memory()
+    d_dev = torch.empty_like(dobs)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        d_dev.copy_(d_host, non_blocking=True)
+        g, J = step(d_dev)
+        g_host = g.cpu()
+    te = shard.max_over_ranks(time.perf_counter() - t0, dist, dev)
+    if rank == 0:
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            pass
+        print(json.dumps({
+            "metric": "FD Gcell-updates/s fwd+adj; adjoint-state gradient",
+            "value": cells_all / (t_max * 1e-3) / 1e9, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "grad2d-1201x301-nt%d-%dshots-fp32-bf16ckpt" % (nt, ns),
+                       "checkpoint_every": 20, "checkpoints": "bf16",
+                       "l2": "inputs larger than L2 (states 2 x 93 MB, checkpoints 14 GB)"},
+            "misfit": J,
+            "roofline": roofline_of(prof, peaks), "kernels": prof,
+            "e2e": {"value": cells_all / te / 1e9, "unit": UNIT,
+                    "h2d_bytes_per_step": int(d_host.numel() * d_host.element_size()),
+                    "d2h_bytes_per_step": int(g_host.numel() * g_host.element_size())},
+            "gpu_launches": launches, "clocks": clk}), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 # ----------------------------------------------------------------------------- CUDA arm
 def main():
     args = parse()
@@ -571,6 +672,9 @@ def main():
         return
     if args.workload == "invert2d":
         run_invert2d(args, rank, world, local)
+        return
+    if args.workload == "grad2d":
+        run_grad2d(args, rank, world, local)
         return
     import numpy as np
     import torch
