@@ -425,6 +425,24 @@ class Context:
                   "ms_total": rep.ms_total, "status": st}
         return q, report
 
+    def wri_solve(self, wavelet, dobs, lam: float, tol: float, max_iter: int, out=None,
+                  hist: int = 0):
+        """esi_wri_solve: (S^T S + lam I) q = S^T (d - S f) by Algorithm 1."""
+        return self.cg_solve(dobs, lam, tol, max_iter, out=out, hist=hist, wri_wavelet=wavelet)
+
+    def dscg_solve(self, dobs, lam: float, tol: float, max_iter: int, eps: float = 0.0,
+                   out=None, w_out=None, hist: int = 0):
+        """esi_dscg_solve: the ESI normal equation in data space; w_out receives w."""
+        return self.cg_solve(dobs, lam, tol, max_iter, eps=eps, out=out, hist=hist,
+                             data_space=True, w_out=w_out)
+
+    def fdcg_solve(self, dobs, freqs, lam: float, tol: float, max_iter: int,
+                   precond: str = "none", eps: float = 0.0, out=None, hist: int = 0):
+        """esi_fdcg_solve: the frequency-domain ESI system at `freqs` (Hz); returns qbar
+        [ns][nf][*shape][2] (re, im) and the report."""
+        return self.cg_solve(dobs, lam, tol, max_iter, precond=precond, eps=eps, out=out,
+                             hist=hist, freqs=freqs)
+
     def invert(self, dobs, velocity, mode: str = "esi", n_outer: int = 3, n_cg: int = 10,
                cg_tol: float = 0.0, precond: str = "diag", beta0: float = 1.0,
                growth: float = 1.0, memory: int = 5, c1: float = 1e-4, step_frac: float = 0.02,

@@ -457,8 +457,7 @@ def test_frequency_domain_cg_limits_and_zero_data():
         ctx.cg_solve(d0, lam=1e-3, tol=0.0, max_iter=3, freqs=[5.0] * 9)
     with pytest.raises(esi.EsiError):
         ctx.cg_solve(d0, lam=1e-3, tol=0.0, max_iter=3, freqs=[5.0], precond="learned")
-    qb, rep = ctx.cg_solve(d0, lam=1e-3, tol=0.0, max_iter=3, freqs=[5.0, 9.0],
-                           precond="diag")
+    qb, rep = ctx.fdcg_solve(d0, [5.0, 9.0], lam=1e-3, tol=0.0, max_iter=3, precond="diag")
     assert torch.count_nonzero(qb).item() == 0
     assert list(rep["iters"]) == [0] * geom.ns and rep["converged"]
 
