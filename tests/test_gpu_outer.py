@@ -169,3 +169,20 @@ def test_outer_loop_on_zero_data_stops_at_a_zero_gradient():
     assert rep["evaluations"] == 1
     assert torch.count_nonzero(g).item() == 0
     assert np.array_equal(vel.cpu().numpy(), v)
+
+
+def test_failed_line_search_leaves_the_model_and_reports_it():
+    """A strict Armijo constant and two trials of a large first step: the line search fails
+    on both sides, the loop stops with the model unchanged and reports the trials."""
+    v, geom, pb, f = _problem()
+    kw = dict(n_outer=2, n_cg=10, beta0=0.1, vmin=1000.0, vmax=2900.0, step_frac=0.5,
+              max_ls=2, c1=0.9)
+    ref = outer.invert(v, pb, outer.Options(mode="esi", **kw))
+    ctx = _ctx(v, geom, pb, torch.float64)
+    vel = _dev(v, torch.float64)
+    _, rep = ctx.invert(_dcat(pb, torch.float64), vel, **kw)
+    assert ref["status"] == rep["stop"] == "line search failed"
+    assert rep["trials"] == ref["trials"] == [2] and rep["iters_done"] == 0
+    assert rep["evaluations"] == 3
+    assert np.allclose(rep["J_start"], ref["J_start"], rtol=1e-9, atol=0)
+    assert np.array_equal(vel.cpu().numpy(), v)
