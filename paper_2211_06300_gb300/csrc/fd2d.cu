@@ -353,14 +353,15 @@ __global__ void __launch_bounds__(NT2, ESI_FD2_MINB) fd2_step_kernel(const __gri
         }
     }
     if constexpr ((F & F_AP) != 0) {
-        // one partial per warp (deterministic, and no block-wide wait at the end):
-        // dot_part[shot][tile][warp], accumulated over the time steps
+        // one partial per warp (no block-wide wait at the end): dot_part[shot][tile][warp],
+        // accumulated over the time steps.  Each slot has one writer per step and the steps
+        // of a loop complete in order, so the sums are deterministic.
         T v = psum;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((tid & 31) == 0)
-            a.dot_part[((long long)s * (a.ntx * a.ntz) + blockIdx.y * a.ntx + blockIdx.x) *
-                           (NT2 / 32) + (tid >> 5)] += double(v);
+        if ((tid & 31) == 0)   // a reduction without return: no load latency at the block's end
+            atomicAdd(&a.dot_part[((long long)s * (a.ntx * a.ntz) + blockIdx.y * a.ntx + blockIdx.x) *
+                                  (NT2 / 32) + (tid >> 5)], double(v));
     }
 }
 
