@@ -333,8 +333,8 @@ def run_dft3d(args, rank, world, local):
 # ----------------------------------------------------------------------------- WRI arm
 def run_wri2d(args, rank, world, local):
     """One step = WRI on the 801 x 241, nt 3000, 16-shot workload: the data residual of the
-    point sources, CG on (S^T S + beta I) q = S^T (d - S f) to 1e-3 (the CG section's
-    "B = I with a different right hand side"), and the saddle-point gradient with
+    point sources, CG on (S^T S + beta I) q = S^T (d - S f) to 1e-3 (the CG section: the
+    ESI CG with the identity as annihilator and its own right-hand side), and the saddle-point gradient with
     u = A^{-1}(f + q), lambda = beta q.  Shots are sharded over ranks as in the ESI step."""
     import numpy as np
     import torch

@@ -355,8 +355,8 @@ ESI_API esi_status esi_dscg_solve(esi_ctx *ctx, double lambda, double tol, int m
                                   double eps, esi_cg_report *report);
 
 /*
- * esi_wri_solve -- WRI by the same CG (the CG section: "B = I with a different right hand
- * side"; Eq. "normalwri"):
+ * esi_wri_solve -- WRI by the same CG (the CG section: B = I and WRI's own right-hand
+ * side; Eq. "normalwri"):
  *   (S^T S + lambda I) q = S^T (d - S f),
  * f the point sources (wavelet_dev [ns][nt], as in esi_forward) and d the observed traces.
  * One forward modelling with f gives the data residual d - S f (kept in context scratch);

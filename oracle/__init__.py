@@ -390,8 +390,8 @@ class Oracle:
         return {"x": x, "rel_res": np.asarray(hist), "iters": k + 1}
 
     # ---------------------------------------------------------------- WRI (B = I)
-    # The CG section notes that the same CG serves WRI "by simply choosing B = I with a
-    # different right hand side": Eq. "normalwri", (S^H S + beta I) q = S^H (d - S f), with
+    # The CG section notes that the same CG serves WRI once B is the identity and the
+    # right-hand side is WRI's own: Eq. "normalwri", (S^H S + beta I) q = S^H (d - S f), with
     # u = A^{-1}(f + q) (Eq. "newq") and the gradient beta <A u - f, dA/dm u> = <lambda,
     # dA/dm u>, lambda = beta q (Eq. "newadj2", "gradient2").
     def wri_rhs(self, sh: Shot, d: np.ndarray, wavelet: np.ndarray) -> np.ndarray:

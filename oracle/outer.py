@@ -21,7 +21,8 @@ the same ones, in its own code):
   m_t = clip(m + alpha d, vmin, vmax), alpha halved up to max_ls times; first trial alpha = 1
   when the memory holds a pair, else the step that moves the fastest cell by step_frac of the
   largest velocity;
-* penalty schedule: beta_i = beta0 * growth^i (the paper's "start small, increase"); when the
+* penalty schedule: beta_i = beta0 * growth^i (a small penalty first, growing over the
+  iterations, as the section on the role of the penalty advises); when the
   penalty changes the objective changes, so J and g are re-evaluated and the memory cleared;
 * the sponge's reference velocity vref is fixed over the iterations (the damping does not
   follow the model).

@@ -1248,7 +1248,7 @@ esi_status dft_impl(esi_ctx *ctx, const void *wavelet, const void *ext, const do
 // rho; p = z + beta p, where z = r (no preconditioner, Algorithm 1 as printed) or
 // z = r / (lambda B^2) (diagonal preconditioner) and rho = <r, z>.  The work vectors r, p,
 // A p live in the internal pitched layout; x is the caller's dense q_out.
-// WRI (the CG section's "B = I with a different right hand side", Eq. "normalwri"): with
+// WRI (the CG section: the same CG with B = I and its own right-hand side, Eq. "normalwri"): with
 // wri_wavelet the annihilator is the identity and the right-hand side is S^T (d - S f), f the
 // point sources; the rest of Algorithm 1 is unchanged.
 template <typename T>

@@ -324,7 +324,7 @@ def test_diag_pcg_matches_oracle(prec, tma_cg, monkeypatch):
 # ----------------------------------------------------------------------------- WRI (B = I)
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_wri_cg_and_gradient_match_oracle(prec):
-    """WRI through the same CG (the CG section's "B = I with a different right hand side"):
+    """WRI through the same CG (the CG section: B = I and WRI's own right-hand side):
     iterates of (S^T S + beta I) q = S^T (d - S f) and the saddle-point gradient with
     u = A^{-1}(f + q), lambda = beta q, against the oracle, several shots with ragged tiles."""
     v, geom, p = _ragged_case(nt=80)

@@ -1,5 +1,5 @@
-"""Pins of the oracle's WRI operators (the CG section's "B = I with a different right hand
-side", Eq. "normalwri"; Eq. "newq", "wrimisfit", "newadj2", "gradient2") against facts that
+"""Pins of the oracle's WRI operators (the CG section: the same CG with B = I and WRI's own
+right-hand side, Eq. "normalwri"; Eq. "newq", "wrimisfit", "newadj2", "gradient2") against facts that
 do not come from the oracle's WRI code itself: the spectrum of S^T S + beta I, the
 data-space closed form of the reduced objective, the large-beta limit, and a Taylor test of
 the reduced objective's gradient."""
