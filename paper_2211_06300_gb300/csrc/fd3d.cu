@@ -310,9 +310,10 @@ __global__ void __launch_bounds__(block3<T>(), sizeof(T) == 4 ? 3 : 1) fd3_step_
                         for (int c = a.inj.cptr[ip]; c < a.inj.cptr[ip + 1]; ++c)
                             sum += a.inj.w[c] *
                                    a.inj_trace[a.inj.off0[c] + (long long)a.tin * a.inj.tstride[c]];
+                        // a select per cell: an index into S would move S to local memory
+                        const int kk = cx - lx;
 #pragma unroll
-                        for (int k = 0; k < VEC; ++k)
-                            if (k == cx - lx) S[k] += sum;
+                        for (int k = 0; k < VEC; ++k) S[k] = k == kk ? S[k] + sum : S[k];
                     }
                     ++ip;
                 }
