@@ -225,6 +225,7 @@ __global__ void __launch_bounds__(block3<T>(), sizeof(T) == 4 ? 3 : 1) fd3_step_
     for (int i = 0; i < nsteps && !__any_sync(0xffffffffu, late); ++i) {
         const int z = zb + i;
         const long long gi = z * plane + col;
+        const T kzz = a.kz[z];
         // the remaining per-cell global inputs first: their latency overlaps the wait
         T ext[VEC];
         Vec3<T> r_in, p_in, ipb, app;
@@ -319,7 +320,6 @@ __global__ void __launch_bounds__(block3<T>(), sizeof(T) == 4 ? 3 : 1) fd3_step_
                 }
             }
             Vec3<T> nw;
-            const T kzz = a.kz[z];
             if (xy_sponge || kzz != T(0)) {
 #pragma unroll
                 for (int k = 0; k < VEC; ++k) {
