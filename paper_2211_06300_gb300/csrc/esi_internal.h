@@ -307,3 +307,34 @@ cudaError_t launch_dft_output(const T *acc, long long sst, int rows, int nx, int
                               float *scales_dev, cudaStream_t st);
 
 }  // namespace esi
+
+#include <atomic>
+
+namespace esi {
+
+// A launch setting worked out once per device (a kernel's shared-memory attribute, its
+// resident blocks per SM): function attributes belong to each device's context, so a process
+// that drives several devices sets them on each.  Thread-safe; 0 means "not yet computed".
+struct PerDevice {
+    static constexpr int MAXDEV = 64;
+    std::atomic<int> v[MAXDEV];
+};
+
+// *out = the cached value for the current device, computing it with compute(int *) on the
+// first call there (a failing compute is returned and retried on the next call)
+template <typename Fn>
+cudaError_t per_device(PerDevice &c, int *out, Fn &&compute) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= PerDevice::MAXDEV) return cudaErrorInvalidDevice;
+    int v = c.v[dev].load(std::memory_order_acquire);
+    if (v == 0) {
+        if ((e = compute(&v)) != cudaSuccess) return e;
+        c.v[dev].store(v, std::memory_order_release);
+    }
+    *out = v;
+    return cudaSuccess;
+}
+
+}  // namespace esi

@@ -323,28 +323,31 @@ __global__ void __launch_bounds__(NT2, 1) fd2_cg_kernel(const __grid_constant__ 
 }
 
 int sm_count() {
-    static int n = 0;
-    if (!n) {
+    static PerDevice cache;
+    int n = 0;
+    const cudaError_t e = per_device(cache, &n, [](int *v) {
         int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            n = 132;
-    }
-    return n;
+        cudaError_t r = cudaGetDevice(&dev);
+        if (r == cudaSuccess) r = cudaDeviceGetAttribute(v, cudaDevAttrMultiProcessorCount, dev);
+        return r;
+    });
+    return e == cudaSuccess && n > 0 ? n : 152;   // GB300's count if the query failed
 }
 
 template <typename T, bool FWD>
 cudaError_t go_cg(const StepArgs<T> &a, int ns, cudaStream_t st) {
     auto kern = fd2_cg_kernel<T, FWD>;
-    static int per_sm = 0;
-    if (!per_sm) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    static PerDevice cache;
+    int per_sm = 0;
+    cudaError_t e = per_device(cache, &per_sm, [kern](int *v) {
+        cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              cg_smem<T, FWD>());
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT2, cg_smem<T, FWD>());
-        if (e != cudaSuccess) return e;
-        per_sm = std::max(1, per_sm);
-    }
+        if (r != cudaSuccess) return r;
+        r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(v, kern, NT2, cg_smem<T, FWD>());
+        *v = std::max(1, *v);
+        return r;
+    });
+    if (e != cudaSuccess) return e;
     const int total = ns * a.ntx * a.ntz;
     const int grid = std::min(total, sm_count() * per_sm);
     kern<<<grid, NT2, cg_smem<T, FWD>(), st>>>(a, total);

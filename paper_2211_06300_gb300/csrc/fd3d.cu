@@ -424,14 +424,14 @@ __global__ void __launch_bounds__(block3<T>(), sizeof(T) == 4 ? 3 : 1) fd3_step_
 template <typename T, unsigned F>
 cudaError_t go(const StepArgs<T> &a, int ns, cudaStream_t st) {
     const int nzc = (a.nz + ZCH3 - 1) / ZCH3;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(fd3_step_kernel<T, F>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             ring_bytes<T>());
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static PerDevice attr;
+    int set = 0;
+    cudaError_t e = per_device(attr, &set, [](int *v) {
+        *v = 1;
+        return cudaFuncSetAttribute(fd3_step_kernel<T, F>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, ring_bytes<T>());
+    });
+    if (e != cudaSuccess) return e;
     dim3 grid(a.ntx, a.nty, ns * nzc);
     fd3_step_kernel<T, F><<<grid, block3<T>(), ring_bytes<T>(), st>>>(a, nzc);
     return cudaGetLastError();

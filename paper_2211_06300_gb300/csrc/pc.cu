@@ -886,27 +886,31 @@ cudaError_t conv_launch(const void *in, const __nv_bfloat16 *wprep, const float 
     cudaError_t e = make_act_map(&tm, in, CIN, W, H, nimg);
     if (e != cudaSuccess) return e;
     auto kern = conv3x3_tc_kernel<CIN, COUT, RELU, OUT>;
-    static int per_sm = 0;
-    if (!per_sm) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Gm::SMEM);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+    static PerDevice cache;
+    int per_sm = 0;
+    e = per_device(cache, &per_sm, [kern](int *v) {
+        cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             Gm::SMEM);
+        if (r != cudaSuccess) return r;
+        r = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
-        if (e != cudaSuccess) return e;
+        if (r != cudaSuccess) return r;
         // resident CTAs per SM from the shared memory, register and TMEM budgets (a CTA
         // beyond them only waits for its turn: strips are independent)
         int dev = 0, smem_sm = 0, rsv = 0, regs_sm = 0;
         cudaFuncAttributes fa;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
-            (e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess ||
-            (e = cudaDeviceGetAttribute(&rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess ||
-            (e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess ||
-            (e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess)
-            return e;
+        if ((r = cudaGetDevice(&dev)) != cudaSuccess ||
+            (r = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess ||
+            (r = cudaDeviceGetAttribute(&rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess ||
+            (r = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess ||
+            (r = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess)
+            return r;
         const int by_smem = smem_sm / (Gm::SMEM + (int)fa.sharedSizeBytes + rsv);
         const int by_regs = regs_sm / (NTH * std::max(fa.numRegs, 1));
-        per_sm = std::max(1, std::min({by_smem, by_regs, 512 / Gm::TCOLS}));
-    }
+        *v = std::max(1, std::min({by_smem, by_regs, 512 / Gm::TCOLS}));
+        return cudaSuccess;
+    });
+    if (e != cudaSuccess) return e;
     const long long strips = (long long)nimg * ((W + TM - 1) / TM);
     const int grid = (int)std::min<long long>(strips, (long long)nsm * per_sm);
     kern<<<grid, NTH, Gm::SMEM, st>>>(tm, wprep, bias, out, nimg, H, W, dev_err, epi);
