@@ -1,4 +1,4 @@
-"""Register and local-memory budget of the 3D step kernel, from ptxas's resource report.
+"""Register and local-memory budgets of the step kernels, from ptxas's resource report.
 
 The 3D step kernel marches a 9-deep register queue per cell; any per-thread array that the
 compiler cannot keep in registers (a spill, or an array indexed at run time) puts a local-
@@ -50,3 +50,19 @@ def test_3d_step_variants_keep_their_state_in_registers(tmp_path):
         if "fd3_step_kernelIf" in k:
             # 3 blocks x 160 threads within the SM's 65,536 registers
             assert v["regs"] * 160 * 3 <= 65536, (k, v)
+
+
+def test_2d_cg_product_halves_stay_within_their_register_budget(tmp_path):
+    """The two halves of the 2D CG product (`fd2_step[CGP|SMP]`, `fd2_step[PT|AP]`) run at
+    4 blocks of 256 threads per SM, i.e. 64 registers; the forward half fits without spills
+    and the adjoint half spills at most 16 bytes."""
+    rows = _ptxas_report("fd2d.cu", tmp_path)
+    f32 = {k: v for k, v in rows.items() if "fd2_step_kernelIf" in k}
+    assert f32, sorted(rows)
+    for k, v in f32.items():
+        assert v["regs"] <= 64, (k, v)
+    cgp = [v for k, v in f32.items() if "fd2_step_kernelIfLj10E" in k]   # CGP | SMP
+    ap = [v for k, v in f32.items() if "fd2_step_kernelIfLj36E" in k]    # PT | AP
+    assert len(cgp) == 1 and len(ap) == 1
+    assert cgp[0]["stack"] == 0 and cgp[0]["spill"] == 0, cgp
+    assert ap[0]["spill"] <= 32, ap        # 16 bytes stored + 16 loaded
