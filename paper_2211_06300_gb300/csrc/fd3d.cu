@@ -246,7 +246,9 @@ __global__ void __launch_bounds__(block3<T>(), sizeof(T) == 4 ? 3 : 1) fd3_step_
             }
             if constexpr ((F & F_AP) != 0) app = ldv3(a.ap_p + fb + (long long)a.nout * a.sst + gi);
         }
-        late |= !ready(i + HALO);
+        // plane z (sequence index i + 4) has landed: the queue fill waited for it when
+        // i + 4 <= 8, else the refill at the end of step i - 5; its slot is not reused
+        // before this warp releases it at the end of this step
         const Slot3<T> &sl = ring[(i + HALO) % RING3];
         if (rowok) {
             const int sy = ry + HALO;
