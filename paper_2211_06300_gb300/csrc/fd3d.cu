@@ -226,7 +226,8 @@ __global__ void __launch_bounds__(block3<T>(), sizeof(T) == 4 ? 3 : 1) fd3_step_
         const int z = zb + i;
         const long long gi = z * plane + col;
         const T kzz = a.kz[z];
-        // the remaining per-cell global inputs first: their latency overlaps the wait
+        // the per-cell global inputs first: their latency overlaps the shared-memory loads
+        // and the Laplacian below
         T ext[VEC];
         Vec3<T> r_in, p_in, ipb, app;
 #pragma unroll
