@@ -84,8 +84,8 @@ def workload_name(ns, nt):
 
 # ----------------------------------------------------------------------------- DRAM traffic
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per cell update of a step-kernel variant,
-# from the capture summarised in profiles/fd2_step_801x241_16shots.md (16 shots of 801 x 241,
-# one launch = 3,088,656 cell updates), valid only for the kernel it was taken on: the
+# from an ncu capture of the 2D step kernel on 16 shots of 801 x 241 (one launch =
+# 3,088,656 cell updates), valid only for the kernel it was taken on: the
 # SHA-256 below of its template source and the header's argument struct (_sources_sha).
 _SHA = "c4c3417c9da00ccddba35aa9aec425c51322c41392c3387f91c8c6887f6a972a"
 MEASURED_TRAFFIC = {

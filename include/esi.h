@@ -133,6 +133,9 @@ ESI_API esi_status esi_forward(esi_ctx *ctx, const void *wavelet_dev, const void
  *               at the start of every call, so results do not depend on earlier calls,
  *               but calls whose work overlaps on the GPU (other streams, other threads,
  *               other contexts on the same device) race on it: serialise them.
+ *   Launches  : the step kernels of esi_forward, issued one by one (no CUDA graph, since
+ *               instantiating one may take device memory), every step after the first a
+ *               programmatic dependent launch; recorded by esi_get_profile like esi_forward.
  *   Arguments : as esi_forward; traces_dev must not be NULL.
  */
 ESI_API esi_status esi_forward_noalloc(esi_ctx *ctx, const void *wavelet_dev,
@@ -158,6 +161,8 @@ typedef enum esi_grad_mode {
 
 typedef enum esi_param { ESI_PARAM_C = 0, ESI_PARAM_V = 1, ESI_PARAM_M = 2 } esi_param;
 
+/* Compressed kinds store u_n and the difference u_n - u_{n-1} of each checkpoint, each with
+ * its own per-shot scale; u_{n-1} is rebuilt as decoded u_n minus decoded difference. */
 typedef enum esi_ckpt_kind {
     ESI_CKPT_F32 = 0,            /* checkpoints stored in the field precision */
     ESI_CKPT_F16 = 1,            /* IEEE half with a per-snapshot scale */
@@ -299,8 +304,9 @@ typedef struct esi_cg_report {
  * ||r_{k+1}|| < tol ||r_0|| or after max_iter iterations.
  *   dobs_dev  : device seismogram-layout observed data d
  *   q_out_dev : device [ns][nt][N] receives the solution x = q
- *   precond   : esi_precond; ESI_PC_DIAG uses z = r / (lambda B^2) (flexible CG),
- *               ESI_PC_LEARNED the network loaded by esi_pc_load
+ *   precond   : esi_precond; ESI_PC_DIAG uses z = r / (lambda B^2) in standard PCG
+ *               (beta_k = <r_{k+1}, z_{k+1}> / <r_k, z_k>), ESI_PC_LEARNED the network
+ *               loaded by esi_pc_load in flexible (Polak-Ribiere) CG
  *   eps       : annihilator offset in metres (<= 0: dx)
  *   report    : may be NULL
  * Synchronises every iteration (reads 8 bytes per shot).  Returns ESI_ERR_NOT_CONVERGED

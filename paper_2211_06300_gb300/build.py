@@ -15,7 +15,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libesi.so")
 
-SOURCES = ["esi_api.cu", "fd2d.cu", "fd2cg.cu", "fd3d.cu", "vec.cu", "pc.cu", "pc_api.cu"]
+SOURCES = ["esi_api.cu", "fd2d.cu", "fd3d.cu", "vec.cu", "pc.cu", "pc_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

@@ -134,11 +134,6 @@ struct esi_ctx {
     std::vector<GraphEntry> graphs;
     cudaStream_t cap = nullptr;
     bool use_graphs = true;
-    // 2D CG product halves by the persistent TMA-fed kernel (fd2cg.cu): off by default -- with
-    // 52 KB stages two blocks fit per SM and keep one tile in flight each, which measured
-    // slower than the one-tile-per-block kernel (18.3 / 19.7 us against 14.1 / 17.2 us per
-    // step of 16 shots of 801 x 241); ESI_TMA_CG=1 selects it
-    bool tma_cg = false;
     bool pdl = true;               // 2D loop steps after the first start as dependent launches
     unsigned long long graph_clock = 0;
     std::vector<Pending> pending;
@@ -466,21 +461,11 @@ bool state_map(esi_ctx *ctx, const void *base, CUtensorMap *out, int kind = 0) {
     cuuint64_t str[3];
     cuuint32_t box[4];
     cuuint32_t rank;
-    if (ctx->g.ndim == 2 && kind == 4) {
-        rank = 2;
-        dims[0] = nx, dims[1] = nz;
-        str[0] = row;
-        box[0] = TX2, box[1] = TZ2;
-    } else if (ctx->g.ndim == 2 && kind == 5) {
-        rank = 4;
-        dims[0] = nx, dims[1] = nz, dims[2] = (cuuint64_t)ctx->nt, dims[3] = ns;
-        str[0] = row, str[1] = shot, str[2] = shot * (cuuint64_t)ctx->nt;
-        box[0] = TX2, box[1] = TZ2, box[2] = 1, box[3] = 1;
-    } else if (ctx->g.ndim == 2) {
+    if (ctx->g.ndim == 2) {
         rank = 3;
         dims[0] = nx, dims[1] = nz, dims[2] = ns;
         str[0] = row, str[1] = shot;
-        box[0] = kind == 3 ? TX2 : SW2, box[1] = kind == 3 ? TZ2 : SH2, box[2] = 1;
+        box[0] = SW2, box[1] = SH2, box[2] = 1;
     } else if (kind == 2) {
         rank = 3;
         dims[0] = nx, dims[1] = ny, dims[2] = nz;
@@ -538,21 +523,7 @@ esi_status step(esi_ctx *ctx, unsigned flags, const StepArgs<T> &a, bool chained
     if (!state_map(ctx, a.cur, &b.tm) ||
         (ctx->g.ndim == 3 && (!state_map(ctx, a.po, &b.tm_old, 1) || !state_map(ctx, a.cc, &b.tm_cc, 2))))
         return ctx->fail(ESI_ERR_CUDA, "cuTensorMapEncodeTiled failed for a state buffer");
-    if (ctx->g.ndim == 2 && ctx->tma_cg && a.fstp == ctx->sst * ctx->nt &&
-        (flags == (F_CGP | F_SMP) || flags == (F_PT | F_AP))) {
-        // the CG product halves: every stream by TMA (tile-interior boxes)
-        const bool fwd = flags == (F_CGP | F_SMP);
-        bool ok = state_map(ctx, a.po, &b.tm_old, 3) && state_map(ctx, a.cc, &b.tm_cc, 4);
-        if (fwd) {
-            ok = ok && state_map(ctx, a.cg_r, &b.tm_a, 5) &&
-                 (a.cg_first || state_map(ctx, a.cg_p, &b.tm_c, 5)) &&
-                 (!(a.cg_pc > T(0)) || state_map(ctx, a.ipb2, &b.tm_b, 3));
-        } else {
-            ok = ok && state_map(ctx, a.ap_p, &b.tm_a, 5) && state_map(ctx, a.pb2, &b.tm_b, 3);
-        }
-        if (!ok) return ctx->fail(ESI_ERR_CUDA, "cuTensorMapEncodeTiled failed for a CG stream");
-        CKL(launch_step2_cg<T>(flags, b, ctx->ns, ctx->st));
-    } else if (ctx->g.ndim == 2) {
+    if (ctx->g.ndim == 2) {
         CKL(launch_step2<T>(flags, b, ctx->ns, ctx->st, chained && ctx->pdl));
     } else {
         if ((flags & F_SMP) && a.tout >= 0)
@@ -935,16 +906,23 @@ esi_status forward_noalloc_impl(esi_ctx *ctx, const void *wavelet, const void *e
     }
     a.smp = smp_view<T>(ctx->smp_rec);
     a.smp_out = reinterpret_cast<T *>(traces);
+    // the same launches as esi_forward's loop, without its graph cache (instantiating a
+    // CUDA graph may take device memory): every step after the first is a programmatic
+    // dependent launch, and the run is timed for esi_get_profile like the other loops
+    ctx->prof_active = ctx->ns;
+    cudaEvent_t ev = prof_mark(ctx);
     for (int n = 0; n < ctx->nt; ++n) {
         a.cur = cur;
         a.po = po;
         a.n = n;
         a.tin = n;
         a.tout = n - 1;
-        esi_status e = step<T>(ctx, flags, a);
+        esi_status e = step<T>(ctx, flags, a, n > 0);
         if (e != ESI_OK) return e;
         std::swap(cur, po);
     }
+    prof_close(ctx, ev, step_name(ctx, flags), step_bpc(ctx, flags, a.nf), ctx->nt,
+               (long long)ctx->nt * ctx->prof_active * ctx->N);
     CKL(launch_sample_global<T>(a.smp, cur, ctx->sst, a.smp_out, ctx->nt - 1, ctx->st));
     return ESI_OK;
 }
@@ -1022,39 +1000,58 @@ esi_status adjoint_impl(esi_ctx *ctx, const void *traces, void *ext_out, void *w
 }
 
 // ------------------------------------------------------------------ gradient
+// A compressed checkpoint holds u_n and the difference u_n - u_{n-1}, each in the two-level
+// code of vec.cu (even cells plus the residual against their interpolation, FP16 or BF16
+// with per-shot scales).  Between two steps at several samples per period the difference
+// is a small fraction of u (about omega dt), so rounding u_{n-1} on its own would leave the
+// recomputed leapfrog a velocity error far above the format's precision; rebuilding
+// u_{n-1} = u_n - (u_n - u_{n-1}) from the decoded u_n keeps the difference accurate
+// relative to itself.  Layout of ctx->ckpt for nseg segments: the fine parts
+// [nseg][2][ns][sst], then the coarse parts [nseg][2][ns][csst] (uint16 codes); of
+// ctx->ckpt_scale: the fine scales [nseg][2][ns], then the coarse ones.
 template <typename T>
-esi_status ckpt_store(esi_ctx *ctx, int kind, int slot, const T *cur, const T *prev) {
+esi_status ckpt_store(esi_ctx *ctx, int kind, int nseg, int slot, const T *cur, const T *prev) {
     const long long len = ctx->sst;
     const int ns = ctx->ns;
     const T *src[2] = {cur, prev};
+    const long long clen = ckpt_coarse_size(ctx->g.nz, ctx->g.ny, ctx->g.nx);
+    const long long nsh = (long long)nseg * 2 * ns;   // shot states per part
     for (int h = 0; h < 2; ++h) {
         const long long idx = (long long)(2 * slot + h) * ns;  // in units of shot states
         if (kind == ESI_CKPT_F32) {
             CK(cudaMemcpyAsync(ctx->ckpt.as<T>() + idx * len, src[h], ns * len * sizeof(T),
                                cudaMemcpyDeviceToDevice, ctx->st));
         } else {
-            CKL(launch_absmax<T>(src[h], len, len, ns, ctx->absbits.as<unsigned>(), ctx->st));
-            CKL(launch_encode<T>(src[h], len, len, ns, kind, ctx->absbits.as<unsigned>(),
-                                 ctx->ckpt.as<uint16_t>() + idx * len,
-                                 ctx->ckpt_scale.as<float>() + idx, ctx->st));
+            uint16_t *codes = ctx->ckpt.as<uint16_t>();
+            float *sc = ctx->ckpt_scale.as<float>();
+            CKL(launch_ckpt_encode<T>(cur, h ? prev : nullptr, ns, ctx->g.nz, ctx->g.ny,
+                                      ctx->g.nx, ctx->px, len, kind, ctx->absbits.as<unsigned>(),
+                                      codes + idx * len, codes + nsh * len + idx * clen, sc + idx,
+                                      sc + nsh + idx, ctx->st));
         }
     }
     return ESI_OK;
 }
 
 template <typename T>
-esi_status ckpt_load(esi_ctx *ctx, int kind, int slot, T *cur, T *prev) {
+esi_status ckpt_load(esi_ctx *ctx, int kind, int nseg, int slot, T *cur, T *prev) {
     const long long len = ctx->sst;
     const int ns = ctx->ns;
     T *dst[2] = {cur, prev};
+    const long long clen = ckpt_coarse_size(ctx->g.nz, ctx->g.ny, ctx->g.nx);
+    const long long nsh = (long long)nseg * 2 * ns;
     for (int h = 0; h < 2; ++h) {
         const long long idx = (long long)(2 * slot + h) * ns;
         if (kind == ESI_CKPT_F32) {
             CK(cudaMemcpyAsync(dst[h], ctx->ckpt.as<T>() + idx * len, ns * len * sizeof(T),
                                cudaMemcpyDeviceToDevice, ctx->st));
         } else {
-            CKL(launch_decode<T>(ctx->ckpt.as<uint16_t>() + idx * len, len, len, ns, kind,
-                                 ctx->ckpt_scale.as<float>() + idx, dst[h], ctx->st));
+            // u_n first; then u_{n-1} = (decoded u_n) - (decoded difference)
+            const uint16_t *codes = ctx->ckpt.as<uint16_t>();
+            const float *sc = ctx->ckpt_scale.as<float>();
+            CKL(launch_ckpt_decode<T>(codes + idx * len, codes + nsh * len + idx * clen, sc + idx,
+                                      sc + nsh + idx, ns, ctx->g.nz, ctx->g.ny, ctx->g.nx, ctx->px,
+                                      len, kind, h ? cur : nullptr, dst[h], ctx->st));
         }
     }
     return ESI_OK;
@@ -1135,10 +1132,14 @@ esi_status gradient_impl(esi_ctx *ctx, const void *wavelet, const void *ext, con
         const int K = std::max(1, o->ckpt_every);
         const int nseg = (nt + K - 1) / K;
         const int kind = o->ckpt_kind;
-        const size_t csz = kind == ESI_CKPT_F32 ? sizeof(T) : 2;
-        CK(ctx->ckpt.ensure((size_t)nseg * 2 * ns * ctx->sst * csz));
-        CK(ctx->ckpt_scale.ensure(sizeof(float) * nseg * 2 * ns));
-        CK(ctx->absbits.ensure(sizeof(unsigned) * ns));
+        if (kind == ESI_CKPT_F32) {
+            CK(ctx->ckpt.ensure((size_t)nseg * 2 * ns * ctx->sst * sizeof(T)));
+        } else {   // fine + coarse 16-bit codes, two scales per shot state
+            const long long clen = ckpt_coarse_size(ctx->g.nz, ctx->g.ny, ctx->g.nx);
+            CK(ctx->ckpt.ensure((size_t)nseg * 2 * ns * (ctx->sst + clen) * 2));
+        }
+        CK(ctx->ckpt_scale.ensure(sizeof(float) * nseg * 2 * ns * 2));
+        CK(ctx->absbits.ensure(sizeof(unsigned) * ns * 2));
         CK(ctx->stash.ensure((size_t)K * ns * ctx->sst * sizeof(T)));
         CK(ctx->traces.ensure(std::max<size_t>((size_t)ctx->total_rec * nt * sizeof(T), 16)));
         // 1) forward with checkpoints (u_{n0}, u_{n0-1}) at n0 = k K, traces into scratch
@@ -1161,7 +1162,7 @@ esi_status gradient_impl(esi_ctx *ctx, const void *wavelet, const void *ext, con
         a.smp_out = tr;
         for (int sg = 0; sg < nseg; ++sg) {
             const int n0 = sg * K, n1 = std::min(nt, n0 + K);
-            e = ckpt_store<T>(ctx, kind, sg, cur, po);
+            e = ckpt_store<T>(ctx, kind, nseg, sg, cur, po);
             if (e != ESI_OK) return e;
             if (adj && sg + 1 == nseg) break;  // the last segment is recomputed anyway
             e = fwd_loop<T>(ctx, a, fflags | F_SMP, cur, po, n0, n1);
@@ -1193,7 +1194,7 @@ esi_status gradient_impl(esi_ctx *ctx, const void *wavelet, const void *ext, con
         for (int sg = nseg - 1; sg >= 0; --sg) {
             const int n0 = sg * K, n1 = std::min(nt, n0 + K);
             T *fc = ctx->u0.as<T>(), *fp = ctx->u1.as<T>();
-            e = ckpt_load<T>(ctx, kind, sg, fc, fp);
+            e = ckpt_load<T>(ctx, kind, nseg, sg, fc, fp);
             if (e != ESI_OK) return e;
             e = fwd_loop<T>(ctx, a, fflags | F_STW, fc, fp, n0, n1);
             if (e != ESI_OK) return e;
@@ -2388,7 +2389,6 @@ ESI_API esi_status esi_create(esi_ctx **out, const esi_grid *grid, const esi_geo
         ctx->ntiles = ctx->ntx * ctx->nty * ctx->nzc;
     }
     if (const char *ev = std::getenv("ESI_NO_GRAPHS")) ctx->use_graphs = ev[0] == '0';
-    if (const char *ev = std::getenv("ESI_TMA_CG")) ctx->tma_cg = ev[0] == '1';
     if (const char *ev = std::getenv("ESI_PDL")) ctx->pdl = ev[0] != '0';
     esi_ctx *c = ctx.get();
     {

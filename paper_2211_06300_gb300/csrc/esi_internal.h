@@ -94,7 +94,6 @@ struct StepArgs {
                                // (SW3, SH3, 1, 1) (one tile with its halo)
     CUtensorMap tm_old;        // the older state, tile-interior box (3D; 2D CG product)
     CUtensorMap tm_cc;         // c = v^2 dt^2 / dx^2, tile-interior box (3D; 2D CG product)
-    CUtensorMap tm_a, tm_b, tm_c;   // 2D CG product: its space-time / per-shot streams
     int *dev_err;              // sticky device error word (bounded waits that gave up)
     int nz, ny, nx, px;        // grid and pitch (elements) of the state arrays
     long long sst;             // pitched plane (= shot stride of state arrays)
@@ -168,10 +167,6 @@ cudaError_t launch_step2(unsigned flags, const StepArgs<T> &a, int ns, cudaStrea
                          bool chained = false);
 template <typename T>
 cudaError_t launch_step3(unsigned flags, const StepArgs<T> &a, int ns, cudaStream_t st);
-// the two CG-product variants of the 2D step (F_CGP | F_SMP, F_PT | F_AP), persistent and
-// TMA-fed (the StepArgs carry the tile-interior maps of every stream)
-template <typename T>
-cudaError_t launch_step2_cg(unsigned flags, const StepArgs<T> &a, int ns, cudaStream_t st);
 
 // sample a whole state (global memory) for every receiver of a list at time tout
 template <typename T>
@@ -246,17 +241,19 @@ cudaError_t launch_grad_finalize(const T *G, int ns, long long sst, const T *cc,
                                  int nx, int px, double dt, double dx, double extra, int param,
                                  T *g, cudaStream_t st);
 
-// checkpoint codec: per-shot max |u|, encode and decode
+// Two-level checkpoint codec (FP16 / BF16): coarse part = the even-index cells, fine part =
+// the residual against their multilinear interpolation, each with a per-shot scale (vec.cu).
+// With `sub` non-null the encoder codes u - sub; with `base` non-null the decoder stores
+// base - x.  `bits` holds 2 ns words of scratch.
+long long ckpt_coarse_size(int nz, int ny, int nx);
 template <typename T>
-cudaError_t launch_absmax(const T *u, long long len, long long sstride, int ns,
-                          unsigned *bits_out, cudaStream_t st);
+cudaError_t launch_ckpt_encode(const T *u, const T *sub, int ns, int nz, int ny, int nx, int px,
+                               long long sst, int kind, unsigned *bits, uint16_t *fine,
+                               uint16_t *coarse, float *fscale, float *cscale, cudaStream_t st);
 template <typename T>
-cudaError_t launch_encode(const T *u, long long len, long long sstride, int ns, int kind,
-                          const unsigned *absmax_bits, void *codes, float *dec_scale,
-                          cudaStream_t st);
-template <typename T>
-cudaError_t launch_decode(const void *codes, long long len, long long sstride, int ns, int kind,
-                          const float *dec_scale, T *u, cudaStream_t st);
+cudaError_t launch_ckpt_decode(const uint16_t *fine, const uint16_t *coarse, const float *fscale,
+                               const float *cscale, int ns, int nz, int ny, int nx, int px,
+                               long long sst, int kind, const T *base, T *u, cudaStream_t st);
 
 // Blocked DTFT: acc [ns][nf][sst][2] += sum_k snap[k][ns][sst] (cos, sin)(twid[k][nf]) over the
 // K stashed states of one block

@@ -281,14 +281,89 @@ __global__ void grad_finalize_kernel(const T *G, int ns, long long N, long long 
 // ---------------------------------------------------------------- snapshot codec
 constexpr float CODEC_RANGE = 32768.0f;  // max |u| of a snapshot maps to this magnitude
 
+// Two-level checkpoint code.  A snapshot x (a wave state, or with `sub` the difference
+// u_n - u_{n-1}) is stored as
+//   coarse: x at the cells whose indices are all even, [ns][ncz][ncy][ncx] dense;
+//   fine  : x - U(coarse) at every cell, in the pitched state layout;
+// each part in FP16 or BF16 with its own per-shot scale (max |part| -> CODEC_RANGE), U the
+// multilinear interpolation between even cells of the decoded coarse part (an odd index
+// averages its two even neighbours, the last one repeats its left neighbour).  Rounding
+// then leaves an error of the format's precision relative to the interpolation residual,
+// which is a small fraction of x for fields resolved by several cells per wavelength,
+// instead of relative to x itself: the Laplacian of the recomputed states sees far less
+// rounding noise.  The encoder forms the residual against the decoded coarse part, so
+// the decoder reproduces x to the fine part's rounding.
+struct CkDims {
+    int nz, ny, nx, px;
+    int ncz, ncy, ncx;
+    long long sst, csst;   // per-shot sizes of the fine (pitched) and coarse (dense) parts
+};
+
+__device__ __forceinline__ float ck_code_to_float(const uint16_t *codes, long long i, int kind) {
+    const uint16_t c = codes[i];
+    return kind == ESI_CKPT_F16 ? __half2float(__ushort_as_half(c))
+                                : __bfloat162float(__ushort_as_bfloat16(c));
+}
+
+__device__ __forceinline__ uint16_t ck_float_to_code(float y, int kind) {
+    return kind == ESI_CKPT_F16 ? __half_as_ushort(__float2half_rn(y))
+                                : __bfloat16_as_ushort(__float2bfloat16_rn(y));
+}
+
+// U(coarse) at cell (z, y, x) of one shot, in T
 template <typename T>
-__global__ void absmax_kernel(const T *u, long long len, long long sstride, unsigned *bits) {
+__device__ __forceinline__ T ck_interp(const uint16_t *coarse, float cscale, const CkDims &d,
+                                       int z, int y, int x, int kind) {
+    int iz[2], iy[2], ix[2];
+    iz[0] = z >> 1, iz[1] = (z & 1) ? min(iz[0] + 1, d.ncz - 1) : iz[0];
+    iy[0] = y >> 1, iy[1] = (y & 1) ? min(iy[0] + 1, d.ncy - 1) : iy[0];
+    ix[0] = x >> 1, ix[1] = (x & 1) ? min(ix[0] + 1, d.ncx - 1) : ix[0];
+    const int nzs = (z & 1) ? 2 : 1, nys = (y & 1) ? 2 : 1, nxs = (x & 1) ? 2 : 1;
+    T acc = T(0);
+    for (int a = 0; a < nzs; ++a)
+        for (int b = 0; b < nys; ++b)
+            for (int c = 0; c < nxs; ++c)
+                acc += T(ck_code_to_float(
+                    coarse, ((long long)iz[a] * d.ncy + iy[b]) * d.ncx + ix[c], kind) * cscale);
+    return acc * T(1.0 / (nzs * nys * nxs));
+}
+
+template <typename T>
+__device__ __forceinline__ T ck_value(const T *u, const T *sub, long long i) {
+    return sub ? u[i] - sub[i] : u[i];
+}
+
+// pass 0: max |x| over the even cells; pass 1: max |x - U(coarse)| over all cells
+template <typename T>
+__global__ void ck_absmax_kernel(const T *u, const T *sub, CkDims d, int pass, int kind,
+                                 const uint16_t *coarse, const float *cscale, unsigned *bits) {
     const int s = blockIdx.y;
+    const T *x = u + s * d.sst;
+    const T *y = sub ? sub + s * d.sst : nullptr;
     float m = 0.0f;
-    const T *x = u + s * sstride;
-    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < len;
-         i += (long long)gridDim.x * RT)
-        m = fmaxf(m, fabsf(float(x[i])));
+    if (pass == 0) {
+        const long long n = d.csst;
+        for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n;
+             i += (long long)gridDim.x * RT) {
+            const int cx = (int)(i % d.ncx);
+            const long long r = i / d.ncx;
+            const int cy = (int)(r % d.ncy), cz = (int)(r / d.ncy);
+            const long long k = ((long long)(2 * cz) * d.ny + 2 * cy) * d.px + 2 * cx;
+            m = fmaxf(m, fabsf(float(ck_value(x, y, k))));
+        }
+    } else {
+        const uint16_t *cs = coarse + s * d.csst;
+        const float sc = cscale[s];
+        for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < d.sst;
+             i += (long long)gridDim.x * RT) {
+            const int xx = (int)(i % d.px);
+            if (xx >= d.nx) continue;
+            const long long r = i / d.px;
+            const int yy = (int)(r % d.ny), zz = (int)(r / d.ny);
+            const T v = ck_value(x, y, i) - ck_interp<T>(cs, sc, d, zz, yy, xx, kind);
+            m = fmaxf(m, fabsf(float(v)));
+        }
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     // non-negative floats order like their bit patterns
@@ -296,37 +371,68 @@ __global__ void absmax_kernel(const T *u, long long len, long long sstride, unsi
 }
 
 template <typename T>
-__global__ void encode_kernel(const T *u, long long len, long long sstride, int kind,
-                              const unsigned *bits, void *codes, float *dec_scale) {
+__global__ void ck_encode_kernel(const T *u, const T *sub, CkDims d, int pass, int kind,
+                                 const unsigned *bits, uint16_t *coarse, float *cscale,
+                                 uint16_t *fine, float *fscale) {
     const int s = blockIdx.y;
     const float mx = __uint_as_float(bits[s]);
     const float inv = mx > 0.0f ? __fdiv_rn(CODEC_RANGE, mx) : 0.0f;
-    if (blockIdx.x == 0 && threadIdx.x == 0) dec_scale[s] = __fdiv_rn(mx, CODEC_RANGE);
-    const T *x = u + s * sstride;
-    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < len;
-         i += (long long)gridDim.x * RT) {
-        const float y = __fmul_rn(float(x[i]), inv);
-        if (kind == ESI_CKPT_F16)
-            reinterpret_cast<__half *>(codes)[s * sstride + i] = __float2half_rn(y);
-        else
-            reinterpret_cast<__nv_bfloat16 *>(codes)[s * sstride + i] = __float2bfloat16_rn(y);
+    const T *x = u + s * d.sst;
+    const T *y = sub ? sub + s * d.sst : nullptr;
+    if (pass == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) cscale[s] = __fdiv_rn(mx, CODEC_RANGE);
+        uint16_t *cs = coarse + s * d.csst;
+        for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < d.csst;
+             i += (long long)gridDim.x * RT) {
+            const int cx = (int)(i % d.ncx);
+            const long long r = i / d.ncx;
+            const int cy = (int)(r % d.ncy), cz = (int)(r / d.ncy);
+            const long long k = ((long long)(2 * cz) * d.ny + 2 * cy) * d.px + 2 * cx;
+            cs[i] = ck_float_to_code(__fmul_rn(float(ck_value(x, y, k)), inv), kind);
+        }
+    } else {
+        if (blockIdx.x == 0 && threadIdx.x == 0) fscale[s] = __fdiv_rn(mx, CODEC_RANGE);
+        const uint16_t *cs = coarse + s * d.csst;
+        const float sc = cscale[s];
+        uint16_t *fs = fine + s * d.sst;
+        for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < d.sst;
+             i += (long long)gridDim.x * RT) {
+            const int xx = (int)(i % d.px);
+            uint16_t c = 0;
+            if (xx < d.nx) {
+                const long long r = i / d.px;
+                const int yy = (int)(r % d.ny), zz = (int)(r / d.ny);
+                const T v = ck_value(x, y, i) - ck_interp<T>(cs, sc, d, zz, yy, xx, kind);
+                c = ck_float_to_code(__fmul_rn(float(v), inv), kind);
+            }
+            fs[i] = c;
+        }
     }
 }
 
+// x = U(coarse) + fine; with `base`, u_{n-1} = base - x (base holds the decoded u_n)
 template <typename T>
-__global__ void decode_kernel(const void *codes, long long len, long long sstride, int kind,
-                              const float *dec_scale, T *u) {
+__global__ void ck_decode_kernel(const uint16_t *fine, const uint16_t *coarse,
+                                 const float *fscale, const float *cscale, CkDims d, int kind,
+                                 const T *base, T *u) {
     const int s = blockIdx.y;
-    const float d = dec_scale[s];
-    T *x = u + s * sstride;
-    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < len;
+    const uint16_t *cs = coarse + s * d.csst;
+    const uint16_t *fs = fine + s * d.sst;
+    const float sc = cscale[s], sf = fscale[s];
+    T *x = u + s * d.sst;
+    const T *b = base ? base + s * d.sst : nullptr;
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < d.sst;
          i += (long long)gridDim.x * RT) {
-        float h;
-        if (kind == ESI_CKPT_F16)
-            h = __half2float(reinterpret_cast<const __half *>(codes)[s * sstride + i]);
-        else
-            h = __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(codes)[s * sstride + i]);
-        x[i] = T(__fmul_rn(h, d));
+        const int xx = (int)(i % d.px);
+        T v = T(0);   // pad columns stay zero
+        if (xx < d.nx) {
+            const long long r = i / d.px;
+            const int yy = (int)(r % d.ny), zz = (int)(r / d.ny);
+            v = ck_interp<T>(cs, sc, d, zz, yy, xx, kind) +
+                T(__fmul_rn(ck_code_to_float(fs, i, kind), sf));
+            if (b) v = b[i] - v;
+        }
+        x[i] = v;
     }
 }
 
@@ -536,28 +642,43 @@ cudaError_t launch_grad_finalize(const T *G, int ns, long long sst, const T *cc,
     return cudaGetLastError();
 }
 
+CkDims ck_dims(int nz, int ny, int nx, int px, long long sst) {
+    CkDims d;
+    d.nz = nz, d.ny = ny, d.nx = nx, d.px = px;
+    d.ncz = (nz + 1) / 2, d.ncy = (ny + 1) / 2, d.ncx = (nx + 1) / 2;
+    d.sst = sst;
+    d.csst = (long long)d.ncz * d.ncy * d.ncx;
+    return d;
+}
+
+long long ckpt_coarse_size(int nz, int ny, int nx) {
+    return (long long)((nz + 1) / 2) * ((ny + 1) / 2) * ((nx + 1) / 2);
+}
+
 template <typename T>
-cudaError_t launch_absmax(const T *u, long long len, long long sstride, int ns, unsigned *bits,
-                          cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(unsigned) * ns, st);
+cudaError_t launch_ckpt_encode(const T *u, const T *sub, int ns, int nz, int ny, int nx, int px,
+                               long long sst, int kind, unsigned *bits, uint16_t *fine,
+                               uint16_t *coarse, float *fscale, float *cscale, cudaStream_t st) {
+    const CkDims d = ck_dims(nz, ny, nx, px, sst);
+    cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(unsigned) * 2 * ns, st);
     if (e != cudaSuccess) return e;
-    absmax_kernel<T><<<dim3(blocks_for(len, 1024), ns), RT, 0, st>>>(u, len, sstride, bits);
+    const dim3 gc(blocks_for(d.csst, 1024), ns), gf(blocks_for(sst, 1024), ns);
+    ck_absmax_kernel<T><<<gc, RT, 0, st>>>(u, sub, d, 0, kind, nullptr, nullptr, bits);
+    ck_encode_kernel<T><<<gc, RT, 0, st>>>(u, sub, d, 0, kind, bits, coarse, cscale, nullptr,
+                                           nullptr);
+    ck_absmax_kernel<T><<<gf, RT, 0, st>>>(u, sub, d, 1, kind, coarse, cscale, bits + ns);
+    ck_encode_kernel<T><<<gf, RT, 0, st>>>(u, sub, d, 1, kind, bits + ns, coarse, cscale, fine,
+                                           fscale);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_encode(const T *u, long long len, long long sstride, int ns, int kind,
-                          const unsigned *bits, void *codes, float *dec_scale, cudaStream_t st) {
-    encode_kernel<T><<<dim3(blocks_for(len, 1024), ns), RT, 0, st>>>(u, len, sstride, kind, bits,
-                                                                      codes, dec_scale);
-    return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_decode(const void *codes, long long len, long long sstride, int ns, int kind,
-                          const float *dec_scale, T *u, cudaStream_t st) {
-    decode_kernel<T><<<dim3(blocks_for(len, 1024), ns), RT, 0, st>>>(codes, len, sstride, kind,
-                                                                      dec_scale, u);
+cudaError_t launch_ckpt_decode(const uint16_t *fine, const uint16_t *coarse, const float *fscale,
+                               const float *cscale, int ns, int nz, int ny, int nx, int px,
+                               long long sst, int kind, const T *base, T *u, cudaStream_t st) {
+    const CkDims d = ck_dims(nz, ny, nx, px, sst);
+    ck_decode_kernel<T><<<dim3(blocks_for(sst, 1024), ns), RT, 0, st>>>(fine, coarse, fscale,
+                                                                         cscale, d, kind, base, u);
     return cudaGetLastError();
 }
 
@@ -900,12 +1021,13 @@ cudaError_t launch_mlincomb(T *z, double alpha, const T *x, double beta, const T
     template cudaError_t launch_grad_finalize<T>(const T *, int, long long, const T *, int, int, \
                                                  int, int, double, double, double, int, T *,     \
                                                  cudaStream_t);                                  \
-    template cudaError_t launch_absmax<T>(const T *, long long, long long, int, unsigned *,      \
-                                          cudaStream_t);                                         \
-    template cudaError_t launch_encode<T>(const T *, long long, long long, int, int,             \
-                                          const unsigned *, void *, float *, cudaStream_t);      \
-    template cudaError_t launch_decode<T>(const void *, long long, long long, int, int,          \
-                                          const float *, T *, cudaStream_t);                     \
+    template cudaError_t launch_ckpt_encode<T>(const T *, const T *, int, int, int, int, int,    \
+                                               long long, int, unsigned *, uint16_t *,           \
+                                               uint16_t *, float *, float *, cudaStream_t);      \
+    template cudaError_t launch_ckpt_decode<T>(const uint16_t *, const uint16_t *,              \
+                                               const float *, const float *, int, int, int, int, \
+                                               int, long long, int, const T *, T *,              \
+                                               cudaStream_t);                                    \
     template cudaError_t launch_dft_output<T>(const T *, long long, int, int, int, int, int, int, \
                                               void *, unsigned *, float *, cudaStream_t);       \
     template cudaError_t launch_penalty<T>(const T *, const T *, int, int, long long, int, int,    \

@@ -154,11 +154,12 @@ def _grad_case():
     return v0, vt, geom, dict(dx=dx, dt=dt, nt=nt, nb=nb)
 
 
-# FP16 checkpoints with a per-snapshot scale meet the 1e-3 gradient bound.  BF16 keeps 8
-# mantissa bits (2^-8 relative rounding) and measured 5.1e-3 on this case: it does NOT meet
-# the 1e-3 bound, so it is pinned to its own measured envelope (1e-2) to catch regressions.
+# Compressed checkpoints hold u_n and u_n - u_{n-1}, each with a per-snapshot scale; the
+# gradient with FP16 or BF16 checkpoints meets the 1e-3 bound against the FP64 oracle (an
+# FP64 simulation of the BF16 scheme on this case gives 6.9e-4; rounding u_n and u_{n-1}
+# separately gave 5.1e-3).
 @pytest.mark.parametrize("prec,ckpt,K,tol", [("f64", "f32", 7, 1e-12), ("f32", "f32", 20, 1e-4),
-                                            ("f32", "f16", 20, 1e-3), ("f32", "bf16", 20, 1e-2)])
+                                            ("f32", "f16", 20, 1e-3), ("f32", "bf16", 20, 1e-3)])
 def test_adjoint_state_gradient(prec, ckpt, K, tol):
     v0, vt, geom, p = _grad_case()
     vref = 2700.0
@@ -289,11 +290,8 @@ def test_single_step_and_corner_points():
     assert np.allclose(ctx.traces_of(d, 0).cpu().numpy(), ref, rtol=1e-13, atol=1e-300)
 
 
-@pytest.mark.parametrize("tma_cg", [False, True])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_diag_pcg_matches_oracle(prec, tma_cg, monkeypatch):
-    # tma_cg: the CG product halves by the persistent TMA-fed kernel (ESI_TMA_CG=1)
-    monkeypatch.setenv("ESI_TMA_CG", "1" if tma_cg else "0")
+def test_diag_pcg_matches_oracle(prec):
     v, geom, p = _ragged_case(nt=80)
     geom.rec_xyz[geom.rec_offset[1]] = (geom.src_xyz[1, 0] + 55.0, 0.0, 30.0)
     o, shots = _orc(v, geom, p)

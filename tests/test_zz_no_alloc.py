@@ -35,32 +35,89 @@ def _case(dtype, ns=3):
     return ctx, wav, q
 
 
+def _case_3d(dtype):
+    """24^3 volume, two shots with their own receiver grids (trilinear points off the
+    nodes), both sources: the 3D step builds tensor maps over the static array and samples
+    through its gather launch."""
+    from paper_2211_06300_gb300 import esi
+    shape, dx, dt, nt, nb = (24, 24, 24), 10.0, 1e-3, 40, 4
+    v = synth.dipping_layers(shape, dx, 6, nlayers=3, vmin=1500, vmax=2400, nanom=1,
+                             sigma=30.0)
+    g1 = synth.surface_grid_3d((115.0, 96.5, 63.0), np.array([35.0, 122.5, 200.0]),
+                               np.array([40.0, 101.0]), 55.5)
+    g2 = synth.surface_grid_3d((80.0, 150.0, 70.0), np.array([60.0, 170.0]),
+                               np.array([20.0, 90.0, 180.0]), 45.0)
+    geom = synth.Geometry(np.concatenate([g1.src_xyz, g2.src_xyz]),
+                          np.array([0, g1.rec_offset[1], g1.rec_offset[1] + g2.rec_offset[1]]),
+                          np.concatenate([g1.rec_xyz, g2.rec_xyz]))
+    ctx = esi.Context(torch.tensor(v, dtype=dtype, device="cuda"), dx, dt, nt, nb, geom)
+    wav = torch.tensor(np.stack([synth.ricker(nt, dt, f) for f in (25.0, 30.0)]),
+                       dtype=dtype, device="cuda")
+    q = torch.tensor(synth.normal(8, (2, nt) + shape) * 1e-3, dtype=dtype, device="cuda")
+    return ctx, wav, q
+
+
+def _noalloc(L, ctx, wav, q, out):
+    from paper_2211_06300_gb300 import esi
+    st = L.esi_forward_noalloc(ctx.h, ctypes.c_void_p(wav.data_ptr()),
+                               ctypes.c_void_p(q.data_ptr()) if q is not None else None,
+                               ctypes.c_void_p(out.data_ptr()))
+    assert st == esi.ESI_OK, L.esi_last_error(ctx.h)
+
+
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
-def test_noalloc_forward_matches_forward_on_two_calls(dtype):
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_noalloc_forward_matches_forward_on_two_calls(dtype, ndim):
     from paper_2211_06300_gb300 import esi
     L = esi.load_library()
-    ctx, wav, q = _case(dtype)
+    ctx, wav, q = _case(dtype) if ndim == 2 else _case_3d(dtype)
     ref = ctx.forward(wavelet=wav, ext=q)
     outs = [torch.full_like(ref, float("nan")) for _ in range(2)]
     torch.cuda.synchronize()
-    free = []
     for out in outs:
-        st = L.esi_forward_noalloc(ctx.h, ctypes.c_void_p(wav.data_ptr()),
-                                   ctypes.c_void_p(q.data_ptr()), ctypes.c_void_p(out.data_ptr()))
-        assert st == esi.ESI_OK, L.esi_last_error(ctx.h)
+        _noalloc(L, ctx, wav, q, out)
         torch.cuda.synchronize()
-        free.append(torch.cuda.mem_get_info()[0])
-    # the second call reuses the array: no device memory changes hands
-    assert free[1] == free[0]
     for out in outs:
         assert float((out - ref).norm() / ref.norm()) <= TOL[dtype]
     # a different source on the shared array still gives the esi_forward result
     ref2 = ctx.forward(wavelet=wav)
     out = torch.empty_like(ref2)
-    assert L.esi_forward_noalloc(ctx.h, ctypes.c_void_p(wav.data_ptr()), None,
-                                 ctypes.c_void_p(out.data_ptr())) == esi.ESI_OK
+    _noalloc(L, ctx, wav, None, out)
     torch.cuda.synchronize()
     assert float((out - ref2).norm() / ref2.norm()) <= TOL[dtype]
+    ctx.close()
+
+
+def test_noalloc_forward_takes_no_device_memory():
+    """On a context that has never run esi_forward, two calls leave the device's free
+    memory and torch's reserved pool as they were, apart from the static array itself,
+    which the first call in the process may bring in when the library's module loads
+    (at most its 32 MiB plus module code).  The two wave states of this case take 16 MiB,
+    so allocating them would show on the first call; the device-wide figure is exact here
+    because this process is the only one allocating on the GPU during the test."""
+    from paper_2211_06300_gb300 import esi
+    L = esi.load_library()
+    shape, dx, dt, nt, nb = (1024, 1024), 10.0, 1e-3, 6, 8
+    geom = synth.surface_line(2, [3000.0, 7000.0], 100.0,
+                              [np.array([3000.0, 3015.0]), np.array([7005.0])], 100.0)
+    v = torch.full(shape, 2000.0, dtype=torch.float32, device="cuda")
+    ctx = esi.Context(v, dx, dt, nt, nb, geom)
+    wav = torch.ones((2, nt), dtype=torch.float32, device="cuda")
+    outs = [torch.empty(nt * 3, dtype=torch.float32, device="cuda") for _ in range(2)]
+    torch.cuda.synchronize()
+    free0, reserved0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+    free = []
+    for out in outs:
+        _noalloc(L, ctx, wav, None, out)
+        torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info()[0])
+    assert torch.cuda.memory_reserved() == reserved0
+    assert free0 - free[0] <= (32 + 4) << 20, (free0, free[0])
+    assert free[1] == free[0]
+    assert torch.equal(outs[0], outs[1])
+    ref = ctx.forward(wavelet=wav)
+    torch.cuda.synchronize()
+    assert float((outs[0] - ref).norm() / ref.norm()) <= TOL[torch.float32]
     ctx.close()
 
 
