@@ -4,8 +4,9 @@
 One step = the inner problem of Algorithm 2 for a batch of shots on the 801 x 241,
 nt = 3000, 16-shot FP32 workload (seeded dipping layers + anomalies, 8 Hz Ricker data):
   set-up of c = v^2 dt^2 for the current model;
-  b = S^T d and CG on (S^T S + beta B^T B) q = S^T d to ||r|| < 1e-3 ||r_0|| with the best
-  available preconditioner (learned if loaded, else the diagonal z = r / (beta B^2));
+  b = S^T d and CG on (S^T S + beta B^T B) q = S^T d to ||r|| < 1e-3 ||r_0|| with the
+  diagonal preconditioner z = r / (beta B^2) (the learned network, measured beside it,
+  does not reach the tolerance faster);
   the saddle-point gradient of Algorithm 2 (u = A^{-1} q, lambda = beta B^H B q);
   the on-the-fly DTFT of u = A^{-1} q at 2, 4, 6, 8 Hz into FP16.
 The metric is FD cell-updates per second over every forward and adjoint propagation of
@@ -52,8 +53,9 @@ def parse():
     ap.add_argument("--max-iter", type=int, default=60)
     ap.add_argument("--plain-iter", type=int, default=60)
     ap.add_argument("--beta-factor", type=float, default=10.0)
-    ap.add_argument("--precond", default="auto", choices=["auto", "none", "diag", "learned"],
-                    help="auto: the learned preconditioner when its weights are present")
+    ap.add_argument("--precond", default="diag", choices=["auto", "none", "diag", "learned"],
+                    help="preconditioner of the timed solve; auto: the learned one when its "
+                         "weights are present")
     ap.add_argument("--pc-weights", default=os.path.join(ROOT, "paper_2211_06300_gb300",
                                                          "pc_weights.npy"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -321,6 +323,11 @@ def run_dft3d(args, rank, world, local):
             "data": "synthetic",
             "config": {"workload": f"dft3d-{args.n3d}^3-nt{args.nt3d}-5freqs-fp16",
                        "freqs_hz": freqs, "l2": "inputs larger than L2 (states 2 x 256 MB)"},
+            # algorithmic bytes per cell update: accumulating every state into the nf complex
+            # FP32 accumulators directly costs 16 + 16 nf; the blocked DTFT stashes 16 states
+            # and folds them once (16 + 4 stash write + 4 stash read + 4 nf / 16 x 4)
+            "bytes_per_cell": {"per_step_accumulation": 16 + 16 * len(freqs),
+                               "blocked_16_steps": 16 + 4 + 4 + 16 * len(freqs) / 16},
             "roofline": roofline_of(prof, peaks), "kernels": prof,
             "e2e": {"value": cells_all / te / 1e9, "unit": UNIT,
                     "h2d_bytes_per_step": int(wav_h.numel() * 4),
@@ -644,6 +651,10 @@ def run_grad2d(args, rank, world, local):
             "data": "synthetic",
             "config": {"workload": "grad2d-1201x301-nt%d-%dshots-fp32-bf16ckpt" % (nt, ns),
                        "checkpoint_every": 20, "checkpoints": "bf16",
+                       "checkpoint_codec": "u_n and u_n - u_{n-1}, each as BF16 even-index "
+                                           "cells plus the BF16 residual against their "
+                                           "bilinear interpolation, per-shot scales "
+                                           "(5 bytes per cell per checkpoint)",
                        "l2": "inputs larger than L2 (states 2 x 93 MB, checkpoints 14 GB)"},
             "misfit": J,
             "roofline": roofline_of(prof, peaks), "kernels": prof,
@@ -729,7 +740,7 @@ def main():
         g, _ = ctx.gradient(ext=q, mode="saddle", beta=beta, param="v")
         U, _ = ctx.dft_extract(freqs, ext=q, half=True)
         props = sum(1 + 2 * int(k) + 2 for k in rep["iters"])   # b, CG products, grad, DTFT
-        return g, rep, props * N * nt
+        return g, rep, props * N * nt, U
 
     for _ in range(args.warmup):
         step(dobs)
@@ -744,7 +755,7 @@ def main():
     e0.record(stream)
     cells, reps = 0, []
     for _ in range(args.steps):
-        _, rep, c = step(dobs)
+        _, rep, c, _ = step(dobs)
         cells += c
         reps.append(rep)
     e1.record(stream)
@@ -758,7 +769,9 @@ def main():
     cells_all = shard.sum_over_ranks(cells, dist, dev)
     value = cells_all / (t_max * 1e-3) / 1e9
 
-    # end to end through the public API with host buffers: pinned d_obs in, gradient out
+    # end to end through the public API with host buffers: pinned d_obs in; the gradient and
+    # the FP16 DTFT fields with their scales out (the CG solution q stays on the device: it
+    # is the step's intermediate, consumed by the gradient and the DTFT)
     e2e = None
     if not args.no_e2e:
         d_host = dobs.cpu().pin_memory()
@@ -766,18 +779,20 @@ def main():
         barrier()
         t0 = time.perf_counter()
         ce = 0
-        g_host = None
+        g_host = U_host = None
         for _ in range(args.steps):
             d_dev.copy_(d_host, non_blocking=True)
-            g, rep, c = step(d_dev)
-            g_host = g.cpu()
+            g, rep, c, U = step(d_dev)
+            g_host, U_host = g.cpu(), U.cpu()
             ce += c
         barrier()
         te = shard.max_over_ranks(time.perf_counter() - t0, dist, dev)
         ce = shard.sum_over_ranks(ce, dist, dev)
         e2e = {"value": ce / te / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(d_host.numel() * d_host.element_size()),
-               "d2h_bytes_per_step": int(g_host.numel() * g_host.element_size())}
+               "d2h_bytes_per_step": int(g_host.numel() * g_host.element_size() +
+                                         U_host.numel() * U_host.element_size()),
+               "outputs_copied": "gradient (FP32) and DTFT fields (FP16)"}
 
     if rank != 0:
         if dist is not None:

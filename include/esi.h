@@ -435,6 +435,13 @@ ESI_API esi_status esi_pc_apply(esi_pc *pc, const void *in_dev, int n, float *y_
  * parameter gradient (device FP32, may be NULL) and the loss (host, may be NULL). */
 ESI_API esi_status esi_pc_grad(esi_pc *pc, const void *in_dev, const void *target_dev, int n,
                                float *grad_dev, double *loss);
+/* Vector-Jacobian product of the network: grad_dev (FP32, esi_pc_param_count() values,
+ * overwritten) = d<gy, y(in)>/d(parameters) for the output gradient gy_dev (device FP32,
+ * the layout of esi_pc_apply's y) of the n images in_dev.  Lets a caller train the network
+ * on an objective the library does not compute itself (the preconditioner section of the
+ * conclusion leaves the objective open). */
+ESI_API esi_status esi_pc_vjp(esi_pc *pc, const void *in_dev, const float *gy_dev, int n,
+                              float *grad_dev);
 /* esi_pc_grad followed by one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at rate lr. */
 ESI_API esi_status esi_pc_train_step(esi_pc *pc, const void *in_dev, const void *target_dev,
                                      int n, double lr, double *loss);

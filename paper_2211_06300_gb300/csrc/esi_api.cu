@@ -211,14 +211,17 @@ std::string step_name(const esi_ctx *ctx, unsigned f) {
 }
 
 // algorithmic HBM bytes per cell update of a step variant: the stencil reads u_n, u_{n-1}
-// and c and writes u_{n+1}; each fused stream adds its own reads / writes
-double step_bpc(const esi_ctx *ctx, unsigned f, int nf) {
+// and c and writes u_{n+1}; each fused stream adds its own reads / writes.  The CG forward
+// half reads r and p and writes p (+ the 1/(beta B^2) map under a preconditioner, + a
+// quarter float of the learned correction); the CG product epilogue reads p and the
+// beta B^2 map and writes A p.
+double step_bpc(const esi_ctx *ctx, unsigned f, int nf, bool pc = false, bool learned = false) {
     const double e = ctx->esz;
     double b = 4 * e;
     if (f & F_EXT) b += e;
-    if (f & F_CGP) b += 3 * e;
+    if (f & F_CGP) b += 3 * e + (pc ? e : 0.0) + (learned ? 1.0 : 0.0);
     if (f & F_OUT) b += e;
-    if (f & F_AP) b += 2 * e;
+    if (f & F_AP) b += 3 * e;
     if (f & F_STW) b += e;
     if (f & F_GRD) b += 3 * e;
     if (f & F_SAD) b += 2 * e;
@@ -284,7 +287,9 @@ void tile_of(const esi_ctx *c, int s, int iz, int iy, int ix, int &tile, int &ce
         tile = (s * c->ntz + bz) * c->ntx + bx;
         cell = (iz - bz * TZ2) * TX2 + (ix - bx * TX2);
     } else {
-        const int zc = iz / ZCH3, by = iy / TY3, bx = ix / TX3;
+        int zc = 0;
+        while (zc + 1 < c->nzc && chunk_begin3(zc + 1, c->nzc, c->g.nz) <= iz) ++zc;
+        const int by = iy / TY3, bx = ix / TX3;
         tile = ((s * c->nzc + zc) * c->nty + by) * c->ntx + bx;
         cell = iz * (TX3 * TY3) + (iy - by * TY3) * TX3 + (ix - bx * TX3);
     }
@@ -747,7 +752,8 @@ esi_status fwd_loop(esi_ctx *ctx, StepArgs<T> a, unsigned flags, T *&cur, T *&po
     }
     if (e != ESI_OK) return e;
     if ((n1 - n0) & 1) std::swap(cur, po);
-    prof_close(ctx, ev, step_name(ctx, flags), step_bpc(ctx, flags, a.nf), n1 - n0,
+    prof_close(ctx, ev, step_name(ctx, flags),
+               step_bpc(ctx, flags, a.nf, a.cg_pc > T(0), a.pc_y != nullptr), n1 - n0,
                (long long)(n1 - n0) * ctx->prof_active * ctx->N);
     return ESI_OK;
 }
@@ -2384,7 +2390,7 @@ ESI_API esi_status esi_create(esi_ctx **out, const esi_grid *grid, const esi_geo
     } else {
         ctx->ntx = (g.nx + TX3 - 1) / TX3;
         ctx->nty = (g.ny + TY3 - 1) / TY3;
-        ctx->nzc = (g.nz + ZCH3 - 1) / ZCH3;
+        ctx->nzc = step3_chunks(g.nz, (long long)ctx->ntx * ctx->nty * geom->ns, ctx->esz);
         ctx->ntz = ctx->nzc;
         ctx->ntiles = ctx->ntx * ctx->nty * ctx->nzc;
     }

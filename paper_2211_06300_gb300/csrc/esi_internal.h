@@ -43,9 +43,17 @@ constexpr int PITCH = 32;           // x pitch multiple of the state / internal 
 // 3D kernel tile (xy plane, marching along z)
 constexpr int TX3 = 32, TY3 = 16;
 constexpr int SW3 = TX3 + 2 * HALO, SH3 = TY3 + 2 * HALO;
-constexpr int ZCH3 = 80;            // planes per block (z chunk)
+// z chunks: each block marches one chunk of planes; the chunk count of a context is chosen
+// at creation (step3_chunks) so that the grid fills whole waves of resident blocks, with
+// chunks of ZCH3_MIN .. ZCH3_MAX planes
+constexpr int ZCH3_MIN = 40, ZCH3_MAX = 100;
 constexpr int RING3 = 8;            // staged planes (shared-memory ring of TMA boxes)
 constexpr int DFT_BLOCK = 16;       // time steps per blocked DTFT pass
+
+// first plane of z chunk zc when nz planes are split into nzc chunks of near-equal length
+__host__ __device__ inline int chunk_begin3(int zc, int nzc, int nz) {
+    return (int)((long long)zc * nz / nzc);
+}
 
 // ----------------------------------------------------------------------------- feature flags
 enum : unsigned {
@@ -167,6 +175,9 @@ cudaError_t launch_step2(unsigned flags, const StepArgs<T> &a, int ns, cudaStrea
                          bool chained = false);
 template <typename T>
 cudaError_t launch_step3(unsigned flags, const StepArgs<T> &a, int ns, cudaStream_t st);
+// number of z chunks for a 3D context: cols = x tiles * y tiles * shots, element size esz
+// (the resident blocks per SM of the step kernel on the current device enter the choice)
+int step3_chunks(int nz, long long cols, int esz);
 
 // sample a whole state (global memory) for every receiver of a list at time tout
 template <typename T>

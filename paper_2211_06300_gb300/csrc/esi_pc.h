@@ -101,6 +101,9 @@ cudaError_t pcnet_forward(PcNet *p, const __nv_bfloat16 *x, int n, float *y, cud
 // optional copy of the gradient to grad_out (FP32, parameter layout)
 cudaError_t pcnet_grad(PcNet *p, const __nv_bfloat16 *x, const __nv_bfloat16 *e, int n,
                        double *loss, float *grad_out, cudaStream_t st);
+// parameter gradient of <gy, y(x)> for an output gradient gy (channels-last FP32)
+cudaError_t pcnet_vjp(PcNet *p, const __nv_bfloat16 *x, const float *gy, int n, float *grad_out,
+                      cudaStream_t st);
 cudaError_t pcnet_adam(PcNet *p, double lr, cudaStream_t st);
 int *pcnet_dev_err(PcNet *p);
 

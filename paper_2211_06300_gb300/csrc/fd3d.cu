@@ -13,6 +13,10 @@
 // global-load latency on the marching path.  Receiver sampling is a separate gather launch
 // (trilinear points straddle two planes); point injection walks a per-tile node list sorted
 // by z.
+#include <algorithm>
+#include <cstdlib>
+#include <type_traits>
+
 #include "esi_internal.h"
 
 namespace esi {
@@ -96,8 +100,22 @@ constexpr int ring_bytes() {
     return RING3 * (int)sizeof(Slot3<T>) + 128;   // + slack for the 128-byte alignment
 }
 
+// resident blocks per SM the FP32 register allocation must allow
+#ifndef ESI_FD3_MINB
+#define ESI_FD3_MINB 3
+#endif
+// planes marched per loop iteration (1..3): the register queue shifts once per group
+#ifndef ESI_FD3_UNROLL
+#define ESI_FD3_UNROLL 3
+#endif
+static_assert(ESI_FD3_UNROLL >= 1 && ESI_FD3_UNROLL <= 3, "unroll 1..3");
+// the centre cells of a row come from the register queue (else from shared memory)
+#ifndef ESI_FD3_WQ
+#define ESI_FD3_WQ 1
+#endif
+
 template <typename T, unsigned F>
-__global__ void __launch_bounds__(block3<T>(), sizeof(T) == 4 ? 3 : 1) fd3_step_kernel(const __grid_constant__ StepArgs<T> a,
+__global__ void __launch_bounds__(block3<T>(), sizeof(T) == 4 ? ESI_FD3_MINB : 1) fd3_step_kernel(const __grid_constant__ StepArgs<T> a,
                                                                   int nzc) {
     constexpr int VEC = Vec3<T>::n;        // cells per consumer thread
     constexpr int NC = consumers3<T>();
@@ -108,11 +126,13 @@ __global__ void __launch_bounds__(block3<T>(), sizeof(T) == 4 ? 3 : 1) fd3_step_
     // full[k]: the planes of slot k have landed; empty[k]: every consumer warp is done with them
     __shared__ __align__(8) unsigned long long full[RING3], empty[RING3];
     __shared__ double red[NC / 32];
+    // per consumer warp: one value per cell of its rows (the point-source sums of a plane)
+    __shared__ __align__(16) T scr_all[(F & F_PT) ? NC * VEC : 1];
     const int tid = threadIdx.x;
     const int s = blockIdx.z / nzc, zc = blockIdx.z - s * nzc;
     if (a.active && !a.active[s]) return;
     const int x0 = blockIdx.x * TX3, y0 = blockIdx.y * TY3;
-    const int zb = zc * ZCH3, ze = min(a.nz, zb + ZCH3);
+    const int zb = chunk_begin3(zc, nzc, a.nz), ze = chunk_begin3(zc + 1, nzc, a.nz);
     const int nsteps = ze - zb;
     const int J = nsteps + 2 * HALO;   // planes zb - 4 .. ze + 3 pass through the ring
     constexpr unsigned BOXU = SH3 * SW3 * sizeof(T), BOXI = TY3 * TX3 * sizeof(T);
@@ -171,6 +191,8 @@ __global__ void __launch_bounds__(block3<T>(), sizeof(T) == 4 ? 3 : 1) fd3_step_
     // ---- consumer warps: one 16-byte row segment per thread, marching up the chunk
     const int lane = tid & 31;
     const int qx = tid % TPR, ry = tid / TPR;
+    T *scr = scr_all + ((F & F_PT) ? (tid >> 5) * 32 * VEC : 0);
+    (void)scr;
     const int lx = qx * VEC, gx0 = x0 + lx, gy = y0 + ry;
     const bool rowok = gy < a.ny && gx0 < a.nx;   // px >= x0 + TX3: the segment is in the pitch
     const long long plane = (long long)a.ny * a.px;
@@ -184,7 +206,8 @@ __global__ void __launch_bounds__(block3<T>(), sizeof(T) == 4 ? 3 : 1) fd3_step_
                          : "memory");
     };
     bool late = false;
-    T q[9][VEC];
+    constexpr int UN = ESI_FD3_UNROLL;
+    T q[2 * HALO + UN][VEC];   // u(z - 4 .. z + 4) of the row segment, + UN - 1 planes ahead
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         late |= !ready(k);
@@ -222,7 +245,9 @@ __global__ void __launch_bounds__(block3<T>(), sizeof(T) == 4 ? 3 : 1) fd3_step_
     const long long dcol = (long long)gy * a.nx + gx0;
     constexpr double WK[5] = {0.0, W1, W2, W3, W4};
 
-    for (int i = 0; i < nsteps && !__any_sync(0xffffffffu, late); ++i) {
+    // one marching step: plane z = zb + i, its z neighbours in q[O .. O + 8]
+    auto plane_step = [&](auto offc, int i) {
+        constexpr int O = decltype(offc)::value;
         const int z = zb + i;
         const long long gi = z * plane + col;
         const T kzz = a.kz[z];
@@ -251,20 +276,74 @@ __global__ void __launch_bounds__(block3<T>(), sizeof(T) == 4 ? 3 : 1) fd3_step_
         // i + 4 <= 8, else the refill at the end of step i - 5; its slot is not reused
         // before this warp releases it at the end of this step
         const Slot3<T> &sl = ring[(i + HALO) % RING3];
+        // point sources of this plane (entries sorted by z, then row, then column): the
+        // warp scans them 32 at a time, each lane sums the entries of the warp's rows it
+        // holds and leaves the sum in the owner's slot of the warp's scratch
+        bool has_inj = false;
+        if constexpr ((F & F_PT) != 0) {
+            if (ip < ie && a.inj.cell[ip] / (TX3 * TY3) == z) {   // uniform in the warp
+                has_inj = true;
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) scr[lane * VEC + k] = T(0);
+                __syncwarp();
+                constexpr int RPW = 32 / TPR;   // tile rows per warp
+                const int r0 = (tid >> 5) * RPW;
+                int e0 = ip;
+                for (;;) {
+                    const int e = e0 + lane;
+                    int cell = -1;
+                    if (e < ie) cell = a.inj.cell[e];
+                    const bool in = cell >= 0 && cell / (TX3 * TY3) == z;
+                    const unsigned m = __ballot_sync(0xffffffffu, in);
+                    if (in) {
+                        const int rem = cell - z * (TX3 * TY3);
+                        const int cy = rem / TX3, cx = rem - cy * TX3;
+                        if (cy >= r0 && cy < r0 + RPW) {
+                            T sum = T(0);
+                            for (int c = a.inj.cptr[e]; c < a.inj.cptr[e + 1]; ++c)
+                                sum += a.inj.w[c] *
+                                       a.inj_trace[a.inj.off0[c] + (long long)a.tin * a.inj.tstride[c]];
+                            scr[((cy - r0) * TPR + cx / VEC) * VEC + cx % VEC] = sum;   // one entry per cell
+                        }
+                    }
+                    const int cnt = __popc(m);   // the plane's entries form a prefix
+                    e0 += cnt;
+                    if (cnt < 32) break;
+                }
+                ip = e0;
+                __syncwarp();
+            }
+        }
         if (rowok) {
             const int sy = ry + HALO;
-            // x neighbours: the shared row segment [lx, lx + VEC + 8)
+            // x neighbours: the shared row segment [lx, lx + VEC + 8); its centre part is the
+            // plane's own cells, already in the register queue
             T w[VEC + 2 * HALO];
+#if ESI_FD3_WQ
+#pragma unroll
+            for (int c = 0; c < HALO / VEC; ++c) {
+                const Vec3<T> tl = ldv3(&sl.u[sy][lx + c * VEC]);
+                const Vec3<T> tr = ldv3(&sl.u[sy][lx + HALO + VEC + c * VEC]);
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) {
+                    w[c * VEC + k] = tl.v[k];
+                    w[HALO + VEC + c * VEC + k] = tr.v[k];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) w[HALO + k] = q[O + HALO][k];
+#else
 #pragma unroll
             for (int c = 0; c < (VEC + 2 * HALO) / VEC; ++c) {
                 const Vec3<T> t = ldv3(&sl.u[sy][lx + c * VEC]);
 #pragma unroll
                 for (int k = 0; k < VEC; ++k) w[c * VEC + k] = t.v[k];
             }
+#endif
             // Laplacian sum: 3 w0 u + sum_k w_k (6 neighbours at distance k)
             T L[VEC];
 #pragma unroll
-            for (int k = 0; k < VEC; ++k) L[k] = T(3.0 * W0) * q[HALO][k];
+            for (int k = 0; k < VEC; ++k) L[k] = T(3.0 * W0) * q[O + HALO][k];
 #pragma unroll
             for (int d = 1; d <= HALO; ++d) {
                 const Vec3<T> up = ldv3(&sl.u[sy - d][lx + HALO]);
@@ -272,7 +351,7 @@ __global__ void __launch_bounds__(block3<T>(), sizeof(T) == 4 ? 3 : 1) fd3_step_
 #pragma unroll
                 for (int k = 0; k < VEC; ++k)
                     L[k] += T(WK[d]) * (((w[k + HALO - d] + w[k + HALO + d]) + (up.v[k] + dn.v[k])) +
-                                        (q[HALO - d][k] + q[HALO + d][k]));
+                                        (q[O + HALO - d][k] + q[O + HALO + d][k]));
             }
             const Vec3<T> old = ldv3(&sl.old[ry][lx]);
             const Vec3<T> cz = ldv3(&sl.c[ry][lx]);
@@ -302,24 +381,9 @@ __global__ void __launch_bounds__(block3<T>(), sizeof(T) == 4 ? 3 : 1) fd3_step_
 #pragma unroll
             for (int k = 0; k < VEC; ++k) S[k] = L[k] + a.dx2 * src[k];
             if constexpr ((F & F_PT) != 0) {
-                // entries sorted by z: consume those of this plane
-                while (ip < ie) {
-                    const int cell = a.inj.cell[ip];
-                    const int cz3 = cell / (TX3 * TY3);
-                    if (cz3 != z) break;
-                    const int rem = cell - cz3 * (TX3 * TY3);
-                    const int cy = rem / TX3, cx = rem - cy * TX3;
-                    if (cy == ry && cx / VEC == qx) {
-                        T sum = T(0);
-                        for (int c = a.inj.cptr[ip]; c < a.inj.cptr[ip + 1]; ++c)
-                            sum += a.inj.w[c] *
-                                   a.inj_trace[a.inj.off0[c] + (long long)a.tin * a.inj.tstride[c]];
-                        // a select per cell: an index into S would move S to local memory
-                        const int kk = cx - lx;
+                if (has_inj) {   // this plane's point sums, gathered by the warp
 #pragma unroll
-                        for (int k = 0; k < VEC; ++k) S[k] = k == kk ? S[k] + sum : S[k];
-                    }
-                    ++ip;
+                    for (int k = 0; k < VEC; ++k) S[k] += scr[lane * VEC + k];
                 }
             }
             Vec3<T> nw;
@@ -329,13 +393,13 @@ __global__ void __launch_bounds__(block3<T>(), sizeof(T) == 4 ? 3 : 1) fd3_step_
                     const T kap = kzz + kxy[k];
                     const T al = T(1) / (T(1) + kap);
                     const T ga = (T(1) - kap) * al;
-                    const T u = q[HALO][k];
+                    const T u = q[O + HALO][k];
                     nw.v[k] = u + ga * (u - old.v[k]) + al * cz.v[k] * S[k];
                 }
             } else {   // interior: alpha = gamma = 1
 #pragma unroll
                 for (int k = 0; k < VEC; ++k) {
-                    const T u = q[HALO][k];
+                    const T u = q[O + HALO][k];
                     nw.v[k] = u + (u - old.v[k]) + cz.v[k] * S[k];
                 }
             }
@@ -392,21 +456,46 @@ __global__ void __launch_bounds__(block3<T>(), sizeof(T) == 4 ? 3 : 1) fd3_step_
             }
             if constexpr ((F & F_DFT) != 0)   // the DTFT's block stash (slot n - n0)
                 stv3(a.stash_w + ((long long)a.slot_w * a.ns + s) * a.sst + gi, nw);
-        } else if constexpr ((F & F_PT) != 0) {
-            while (ip < ie && a.inj.cell[ip] / (TX3 * TY3) == z) ++ip;
         }
-        if (i + 1 < nsteps) {
-            // the queue moves one plane down; plane z + 5 comes from the ring
-            late |= !ready(i + 2 * HALO + 1);
+    };
+    // after step O of the group that starts at plane i: the next plane into the queue (once
+    // per group the queue moves UN planes down), and release of the plane just updated
+    auto refill_after = [&](auto offc, int i) {
+        constexpr int O = decltype(offc)::value;
+        if constexpr (O + 1 < UN) {
+            if (i + O + 1 < nsteps) {   // plane z + 5 of the next step into entry O + 9
+                late |= !ready(i + O + 2 * HALO + 1);
+                const Vec3<T> c = ldv3(&ring[(i + O + 2 * HALO + 1) % RING3].u[ry + HALO][lx + HALO]);
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
+                for (int e = 0; e < VEC; ++e) q[O + 2 * HALO + 1][e] = c.v[e];
+            }
+        } else {
+            if (i + UN < nsteps) {
+                late |= !ready(i + UN + 2 * HALO);
 #pragma unroll
-                for (int e = 0; e < VEC; ++e) q[k][e] = q[k + 1][e];
-            const Vec3<T> c = ldv3(&ring[(i + 2 * HALO + 1) % RING3].u[ry + HALO][lx + HALO]);
+                for (int k = 0; k < 2 * HALO; ++k)
 #pragma unroll
-            for (int e = 0; e < VEC; ++e) q[8][e] = c.v[e];
+                    for (int e = 0; e < VEC; ++e) q[k][e] = q[k + UN][e];
+                const Vec3<T> c = ldv3(&ring[(i + UN + 2 * HALO) % RING3].u[ry + HALO][lx + HALO]);
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) q[2 * HALO][e] = c.v[e];
+            }
         }
-        release(i + HALO);   // plane z: its neighbours and centre were last read in this step
+        release(i + O + HALO);   // plane z: its neighbours and centre were last read in this step
+    };
+    for (int i = 0; i < nsteps && !__any_sync(0xffffffffu, late); i += UN) {
+        plane_step(std::integral_constant<int, 0>(), i);
+        refill_after(std::integral_constant<int, 0>(), i);
+        if constexpr (UN >= 2) {
+            if (i + 1 >= nsteps || __any_sync(0xffffffffu, late)) break;
+            plane_step(std::integral_constant<int, 1>(), i + 1);
+            refill_after(std::integral_constant<int, 1>(), i);
+        }
+        if constexpr (UN >= 3) {
+            if (i + 2 >= nsteps || __any_sync(0xffffffffu, late)) break;
+            plane_step(std::integral_constant<int, 2>(), i + 2);
+            refill_after(std::integral_constant<int, 2>(), i);
+        }
     }
     if (late) atomicExch(a.dev_err, DEV_ERR_TMA_TIMEOUT);
     if constexpr ((F & F_AP) != 0) {
@@ -425,15 +514,20 @@ __global__ void __launch_bounds__(block3<T>(), sizeof(T) == 4 ? 3 : 1) fd3_step_
 }
 
 template <typename T, unsigned F>
-cudaError_t go(const StepArgs<T> &a, int ns, cudaStream_t st) {
-    const int nzc = (a.nz + ZCH3 - 1) / ZCH3;
-    static PerDevice attr;
+cudaError_t set_smem(PerDevice &attr) {
     int set = 0;
-    cudaError_t e = per_device(attr, &set, [](int *v) {
+    return per_device(attr, &set, [](int *v) {
         *v = 1;
         return cudaFuncSetAttribute(fd3_step_kernel<T, F>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, ring_bytes<T>());
     });
+}
+
+template <typename T, unsigned F>
+cudaError_t go(const StepArgs<T> &a, int ns, cudaStream_t st) {
+    const int nzc = a.ntz;
+    static PerDevice attr;
+    cudaError_t e = set_smem<T, F>(attr);
     if (e != cudaSuccess) return e;
     dim3 grid(a.ntx, a.nty, ns * nzc);
     fd3_step_kernel<T, F><<<grid, block3<T>(), ring_bytes<T>(), st>>>(a, nzc);
@@ -469,6 +563,53 @@ cudaError_t launch_step3(unsigned flags, const StepArgs<T> &a, int ns, cudaStrea
     }
 }
 #undef ESI_CASE
+
+namespace {
+// SMs x resident blocks per SM of the step kernel (the point-source variant stands for all:
+// every FP32 variant keeps three blocks per SM, every FP64 one one)
+template <typename T>
+int step3_slots() {
+    static PerDevice slots;
+    int v = 0;
+    cudaError_t e = per_device(slots, &v, [](int *out) {
+        static PerDevice a2;
+        cudaError_t r = set_smem<T, F_PT>(a2);
+        if (r != cudaSuccess) return r;
+        int dev = 0, nsm = 0, nb = 0;
+        if ((r = cudaGetDevice(&dev)) != cudaSuccess) return r;
+        if ((r = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return r;
+        if ((r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fd3_step_kernel<T, F_PT>,
+                                                               block3<T>(), ring_bytes<T>())) !=
+            cudaSuccess)
+            return r;
+        *out = std::max(1, nb) * std::max(1, nsm);
+        return cudaSuccess;
+    });
+    return e == cudaSuccess ? v : 1;   // unknown: the model then prefers the longest chunks
+}
+}  // namespace
+
+// The chunk count that minimises (waves of resident blocks) x (planes per chunk + the
+// chunk's z halo at about half the cost of a plane), with chunks of ZCH3_MIN .. ZCH3_MAX
+// planes: a grid that ends in a part-filled wave leaves SMs idle at the end of every step.
+int step3_chunks(int nz, long long cols, int esz) {
+    const int slots = esz == 8 ? step3_slots<double>() : step3_slots<float>();
+    const int lo = std::max(1, (nz + ZCH3_MAX - 1) / ZCH3_MAX);
+    const int hi = std::max(lo, (nz + ZCH3_MIN - 1) / ZCH3_MIN);
+    int best = lo;
+    double best_cost = 1e300;
+    for (int n = lo; n <= hi; ++n) {
+        const long long waves = (cols * n + slots - 1) / slots;
+        const double cost = (double)waves * ((double)nz / n + HALO);
+        if (cost < best_cost * (1 - 1e-9)) {
+            best_cost = cost;
+            best = n;
+        }
+    }
+    if (const char *ev = std::getenv("ESI_NZC3")) best = std::max(1, std::atoi(ev));
+    return best;
+}
 
 template cudaError_t launch_step3<float>(unsigned, const StepArgs<float> &, int, cudaStream_t);
 template cudaError_t launch_step3<double>(unsigned, const StepArgs<double> &, int, cudaStream_t);

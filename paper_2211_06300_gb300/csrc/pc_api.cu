@@ -177,11 +177,10 @@ cudaError_t pcnet_forward(PcNet *p, const __nv_bfloat16 *x, int n, float *y, cud
     return cudaSuccess;
 }
 
-cudaError_t pcnet_grad(PcNet *p, const __nv_bfloat16 *x, const __nv_bfloat16 *e, int n,
-                       double *loss, float *grad_out, cudaStream_t st) {
-    if (n > p->max_batch || n < 1) return cudaErrorInvalidValue;
-    using bf = __nv_bfloat16;
-    const int *H = p->H, *W = p->W;
+namespace {
+
+// scratch of the backward pass for n images
+cudaError_t ensure_grad_buffers(PcNet *p, int n) {
     const long long n0 = px_of(p, 0, n), n1 = px_of(p, 1, n), n2 = px_of(p, 2, n), n3 = px_of(p, 3, n);
     RET(p->yscratch.ensure((size_t)n0 * G * 4));
     RET(p->gy.ensure((size_t)n0 * G * 4));
@@ -195,11 +194,17 @@ cudaError_t pcnet_grad(PcNet *p, const __nv_bfloat16 *x, const __nv_bfloat16 *e,
     RET(p->gBT.ensure((size_t)n3 * C * 4));
     RET(p->gP3.ensure((size_t)n3 * C * 4));
     RET(p->gbf.ensure((size_t)n0 * C * 2));
+    RET(p->dwpart.ensure((size_t)9 * 2 * p->nsm * C * C * 4));
+    return cudaSuccess;
+}
+
+// Parameter gradient of <gy, y(x)> into p->grads (overwritten), gy = dL/dy in p->gy
+// (channels-last FP32), after pcnet_forward(x, keep_xn = true) of the same n images.
+cudaError_t backward_from_gy(PcNet *p, int n, cudaStream_t st) {
+    using bf = __nv_bfloat16;
+    const int *H = p->H, *W = p->W;
+    const long long n0 = px_of(p, 0, n), n1 = px_of(p, 1, n), n2 = px_of(p, 2, n), n3 = px_of(p, 3, n);
     const int nblk = 2 * p->nsm;
-    RET(p->dwpart.ensure((size_t)9 * nblk * C * C * 4));
-    float *y = p->yscratch.as<float>();
-    RET(pcnet_forward(p, x, n, y, st, false, true));
-    RET(cos_loss_launch(x, y, e, p->dots.as<double>(), p->gy.as<float>(), (long long)H[0] * W[0] * G, n, st));
     // y = rms * U(xn): the network's output gradient carries the per-image scale
     RET(img_mul_launch(p->gy.as<float>(), p->rms.as<float>(), n, (long long)H[0] * W[0] * G, st));
     const bf *xin = p->xn.as<bf>();   // the first layer saw the normalised images
@@ -250,6 +255,20 @@ cudaError_t pcnet_grad(PcNet *p, const __nv_bfloat16 *x, const __nv_bfloat16 *e,
     RET(mask_launch(p->gL1.as<float>(), p->e1.as<bf>(), gb, n0 * C, st));
     RET((dw_launch<G, C>(xin, gb, dw, gW(0), n, H[0], W[0], nblk, st)));
     RET(bias_grad_launch(p->gL1.as<float>(), gB(0), n0, C, st));
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t pcnet_grad(PcNet *p, const __nv_bfloat16 *x, const __nv_bfloat16 *e, int n,
+                       double *loss, float *grad_out, cudaStream_t st) {
+    if (n > p->max_batch || n < 1) return cudaErrorInvalidValue;
+    const int *H = p->H, *W = p->W;
+    RET(ensure_grad_buffers(p, n));
+    float *y = p->yscratch.as<float>();
+    RET(pcnet_forward(p, x, n, y, st, false, true));
+    RET(cos_loss_launch(x, y, e, p->dots.as<double>(), p->gy.as<float>(), (long long)H[0] * W[0] * G, n, st));
+    RET(backward_from_gy(p, n, st));
     if (grad_out)
         RET(cudaMemcpyAsync(grad_out, p->grads.p, (size_t)param_count() * 4, cudaMemcpyDeviceToDevice, st));
     if (loss) {
@@ -263,6 +282,18 @@ cudaError_t pcnet_grad(PcNet *p, const __nv_bfloat16 *x, const __nv_bfloat16 *e,
         }
         *loss = s / n;
     }
+    return cudaSuccess;
+}
+
+cudaError_t pcnet_vjp(PcNet *p, const __nv_bfloat16 *x, const float *gy, int n, float *grad_out,
+                      cudaStream_t st) {
+    if (n > p->max_batch || n < 1) return cudaErrorInvalidValue;
+    RET(ensure_grad_buffers(p, n));
+    RET(pcnet_forward(p, x, n, p->yscratch.as<float>(), st, false, true));
+    RET(cudaMemcpyAsync(p->gy.p, gy, (size_t)px_of(p, 0, n) * G * 4, cudaMemcpyDeviceToDevice, st));
+    RET(backward_from_gy(p, n, st));
+    if (grad_out)
+        RET(cudaMemcpyAsync(grad_out, p->grads.p, (size_t)param_count() * 4, cudaMemcpyDeviceToDevice, st));
     return cudaSuccess;
 }
 
@@ -361,6 +392,15 @@ ESI_API esi_status esi_pc_grad(esi_pc *pc, const void *in_dev, const void *targe
                                     grad_dev, pc->st);
     if (e != cudaSuccess) return pc_fail(pc, e, "grad");
     return pc_check_err(pc);
+}
+
+ESI_API esi_status esi_pc_vjp(esi_pc *pc, const void *in_dev, const float *gy_dev, int n,
+                              float *grad_dev) {
+    if (!pc || !in_dev || !gy_dev || !grad_dev || n < 1) return ESI_ERR_ARG;
+    cudaError_t e = esi::pcnet_vjp(pc->net, reinterpret_cast<const __nv_bfloat16 *>(in_dev), gy_dev,
+                                   n, grad_dev, pc->st);
+    if (e != cudaSuccess) return pc_fail(pc, e, "vjp");
+    return ESI_OK;
 }
 
 ESI_API esi_status esi_pc_train_step(esi_pc *pc, const void *in_dev, const void *target_dev, int n,

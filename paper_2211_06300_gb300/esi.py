@@ -32,7 +32,7 @@ EXPORTS = ["esi_create", "esi_destroy", "esi_set_stream", "esi_set_velocity", "e
            "esi_get_profile", "esi_forward_noalloc", "esi_normal_apply", "esi_pc_param_count",
            "esi_pc_fallbacks", "esi_pc_pack", "esi_pc_create", "esi_pc_destroy",
            "esi_pc_last_error", "esi_pc_set_params", "esi_pc_get_params", "esi_pc_apply",
-           "esi_pc_grad", "esi_pc_train_step", "esi_wri_solve", "esi_dscg_solve",
+           "esi_pc_grad", "esi_pc_vjp", "esi_pc_train_step", "esi_wri_solve", "esi_dscg_solve",
            "esi_fdcg_solve", "esi_invert"]
 
 
@@ -151,6 +151,7 @@ def load_library(require_gpu: bool = True) -> ctypes.CDLL:
     L.esi_pc_get_params.argtypes = [vp, vp]
     L.esi_pc_apply.argtypes = [vp, vp, i, vp]
     L.esi_pc_grad.argtypes = [vp, vp, vp, i, vp, ctypes.POINTER(d)]
+    L.esi_pc_vjp.argtypes = [vp, vp, vp, i, vp]
     L.esi_pc_train_step.argtypes = [vp, vp, vp, i, d, ctypes.POINTER(d)]
     L.esi_status_string.argtypes = [i]
     L.esi_status_string.restype = ctypes.c_char_p
@@ -165,7 +166,7 @@ def load_library(require_gpu: bool = True) -> ctypes.CDLL:
     for name in ("esi_create", "esi_set_stream", "esi_set_velocity", "esi_forward",
                  "esi_forward_noalloc", "esi_normal_apply", "esi_pc_pack", "esi_pc_create",
                  "esi_pc_set_params", "esi_pc_get_params", "esi_pc_apply", "esi_pc_grad",
-                 "esi_pc_train_step",
+                 "esi_pc_vjp", "esi_pc_train_step",
                  "esi_adjoint", "esi_gradient", "esi_dft_extract", "esi_cg_solve",
                  "esi_pc_load", "esi_wri_solve", "esi_dscg_solve", "esi_fdcg_solve", "esi_invert"):
         getattr(L, name).restype = ctypes.c_int
@@ -540,6 +541,13 @@ class PCNet:
         self._check(self.L.esi_pc_grad(self.h, _ptr(x), _ptr(e), int(x.shape[0]), _ptr(g),
                                        ctypes.byref(loss)))
         return g, float(loss.value)
+
+    def vjp(self, x, gy, out=None):
+        """Parameter gradient of <gy, y(x)> (esi_pc_vjp)."""
+        g = self.torch.empty(self.param_count(), dtype=self.torch.float32, device=x.device) \
+            if out is None else out
+        self._check(self.L.esi_pc_vjp(self.h, _ptr(x), _ptr(gy), int(x.shape[0]), _ptr(g)))
+        return g
 
     def train_step(self, x, e, lr: float) -> float:
         loss = ctypes.c_double(0.0)

@@ -83,6 +83,27 @@ def test_network_gradient_matches_oracle():
         o += k + co
 
 
+def test_network_vjp_matches_oracle():
+    """esi_pc_vjp: the parameter gradient of <gy, y(x)> for a given output gradient gy,
+    against the oracle's backward of the normalised network (dL/dU = rho gy)."""
+    rng = np.random.default_rng(8)
+    H, W, n = 9, 70, 3
+    x = _bf16(rng.standard_normal((n, H, W, cnn.G)))
+    gy = rng.standard_normal((n, H, W, cnn.G))
+    p = _params(9, dec1=0.2)
+    net = _net(H, W, n, p)
+    g = net.vjp(_img(x), torch.tensor(gy, dtype=torch.float32, device="cuda")).double().cpu().numpy()
+    y, a, rho = cnn.normalized_forward(x, _as_stored(p), store=_bf16)
+    _, g_ref = cnn.unet_backward(gy * rho[:, None, None, None], _as_stored(p), a)
+    rv = cnn.param_vector(g_ref)
+    o = 0
+    for name, ci, co, _ in cnn.LAYERS:
+        k = 9 * ci * co
+        assert oracle.rel_l2(g[o:o + k], rv[o:o + k]) < 3e-2, name + ".W"
+        assert oracle.rel_l2(g[o + k:o + k + co], rv[o + k:o + k + co]) < 3e-2, name + ".b"
+        o += k + co
+
+
 def test_training_reduces_the_loss():
     rng = np.random.default_rng(5)
     H, W, n = 12, 40, 8
