@@ -779,7 +779,7 @@ esi_status fwd_dft_loop(esi_ctx *ctx, StepArgs<T> a, unsigned flags, T *cur, T *
                 if (e != ESI_OK) return e;
                 std::swap(c, q);
             }
-            CKL(launch_dft_block<T>(a.stash_w, n1 - n0, ctx->ns, ctx->sst, a.nf,
+            CKL(launch_dft_block<T>(a.stash_w, n1 - n0, ctx->ns, ctx->sst, ctx->g.nx, ctx->px, a.nf,
                                     a.twid + (size_t)n0 * a.nf * 2, a.dft, ctx->st));
         }
         CKL(launch_sample_global<T>(a.smp, c, ctx->sst, tr, nt - 1, ctx->st));
@@ -1870,7 +1870,7 @@ esi_status fdcg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, cons
                     if (st != ESI_OK) return st;
                     std::swap(c, q);
                 }
-                CKL(launch_dft_block<T>(a.stash_w, jhi - jlo, ns, ctx->sst, nf,
+                CKL(launch_dft_block<T>(a.stash_w, jhi - jlo, ns, ctx->sst, ctx->g.nx, ctx->px, nf,
                                         a.twid + (size_t)jlo * nf * 2, out, ctx->st));
                 jhi = jlo;
             }

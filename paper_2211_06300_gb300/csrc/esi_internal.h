@@ -267,10 +267,12 @@ cudaError_t launch_ckpt_decode(const uint16_t *fine, const uint16_t *coarse, con
                                long long sst, int kind, const T *base, T *u, cudaStream_t st);
 
 // Blocked DTFT: acc [ns][nf][sst][2] += sum_k snap[k][ns][sst] (cos, sin)(twid[k][nf]) over the
-// K stashed states of one block
+// K stashed states of one block.  Rows of px cells of which nx are real: 16-byte chunks that
+// lie wholly in the pad are skipped (the step kernels never write them, so the stash holds
+// whatever the memory held there; the accumulators keep their zero pads).
 template <typename T>
-cudaError_t launch_dft_block(const T *snap, int K, int ns, long long sst, int nf, const T *twid,
-                             T *acc, cudaStream_t st);
+cudaError_t launch_dft_block(const T *snap, int K, int ns, long long sst, int nx, int px, int nf,
+                             const T *twid, T *acc, cudaStream_t st);
 
 // Frequency-domain ESI (Eq. "idtft", "normaldtft"), at most FD_MAXF frequencies.
 constexpr int FD_MAXF = 8;

@@ -7,7 +7,9 @@
 // input state is staged in shared memory with a 4-cell halo by 16-byte loads; cells
 // outside the grid read as zero, the homogeneous extension under which the 8th-order
 // Laplacian is a symmetric matrix (what makes the time-reversed run the exact adjoint).
-// Pad columns (nx <= x < px) of the pitched arrays are kept at zero by masked stores.
+// Pad columns (nx <= x < px) of the pitched arrays: the cells of a thread's 16-byte segment
+// that fall in the pad are stored as zero; segments wholly in the pad are not written, so
+// kernels that read whole pitched planes skip them.
 //
 // Fused work per step (each optional, selected at compile time):
 //   prologue : point injection (source wavelet, or R^T e at receivers) through a per-tile

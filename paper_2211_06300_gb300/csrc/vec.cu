@@ -690,14 +690,15 @@ namespace {
 constexpr int DFT_MCH = 4;
 
 template <typename T>
-__global__ void dft_block_kernel(const T *snap, int K, int ns, long long sst, int nf,
-                                 const T *twid, T *acc) {
+__global__ void dft_block_kernel(const T *snap, int K, int ns, long long sst, int nx, int px,
+                                 int nf, const T *twid, T *acc) {
     constexpr int VEC = V16<T>::n;
     const int s = blockIdx.y;
     const long long nch = sst / VEC;
     for (long long c = (long long)blockIdx.x * RT + threadIdx.x; c < nch;
          c += (long long)gridDim.x * RT) {
         const long long cell = c * VEC;
+        if ((int)(cell % px) >= nx) continue;   // a chunk of pad cells only: never written
         for (int m0 = 0; m0 < nf; m0 += DFT_MCH) {
             T re[DFT_MCH][VEC], im[DFT_MCH][VEC];
 #pragma unroll
@@ -875,10 +876,10 @@ cudaError_t launch_fd_b2g_dot(T *out, const T *p, const T *pb2, const double *G,
 }
 
 template <typename T>
-cudaError_t launch_dft_block(const T *snap, int K, int ns, long long sst, int nf, const T *twid,
-                             T *acc, cudaStream_t st) {
-    dft_block_kernel<T><<<dim3(blocks_for(sst / V16<T>::n, 1024), ns), RT, 0, st>>>(snap, K, ns, sst,
-                                                                                 nf, twid, acc);
+cudaError_t launch_dft_block(const T *snap, int K, int ns, long long sst, int nx, int px, int nf,
+                             const T *twid, T *acc, cudaStream_t st) {
+    dft_block_kernel<T><<<dim3(blocks_for(sst / V16<T>::n, 1024), ns), RT, 0, st>>>(
+        snap, K, ns, sst, nx, px, nf, twid, acc);
     return cudaGetLastError();
 }
 
@@ -1043,8 +1044,8 @@ cudaError_t launch_mlincomb(T *z, double alpha, const T *x, double beta, const T
                                               T *, cudaStream_t);                                \
     template cudaError_t launch_fd_b2g_dot<T>(T *, const T *, const T *, const double *, int, int, \
                                               long long, const int *, double *, cudaStream_t);   \
-    template cudaError_t launch_dft_block<T>(const T *, int, int, long long, int, const T *, T *, \
-                                             cudaStream_t);
+    template cudaError_t launch_dft_block<T>(const T *, int, int, long long, int, int, int,      \
+                                             const T *, T *, cudaStream_t);
 
 ESI_INST(float)
 ESI_INST(double)
