@@ -284,48 +284,63 @@ constexpr float CODEC_RANGE = 32768.0f;  // max |u| of a snapshot maps to this m
 // Two-level checkpoint code.  A snapshot x (a wave state, or with `sub` the difference
 // u_n - u_{n-1}) is stored as
 //   coarse: x at the cells whose indices are all even, [ns][ncz][ncy][ncx] dense;
-//   fine  : x - U(coarse) at every cell, in the pitched state layout;
-// each part in FP16 or BF16 with its own per-shot scale (max |part| -> CODEC_RANGE), U the
-// multilinear interpolation between even cells of the decoded coarse part (an odd index
-// averages its two even neighbours, the last one repeats its left neighbour).  Rounding
-// then leaves an error of the format's precision relative to the interpolation residual,
-// which is a small fraction of x for fields resolved by several cells per wavelength,
-// instead of relative to x itself: the Laplacian of the recomputed states sees far less
-// rounding noise.  The encoder forms the residual against the decoded coarse part, so
-// the decoder reproduces x to the fine part's rounding.
+//   fine  : x - U(coarse) at every cell, in the pitched state layout (pad cells 0);
+// each part in FP16 or BF16, U the multilinear interpolation between even cells of the
+// decoded coarse part (an odd index averages its two even neighbours, the last one repeats
+// its left neighbour).  Rounding then leaves an error of the format's precision relative
+// to the interpolation residual, which is a small fraction of x for fields resolved by
+// several cells per wavelength, instead of relative to x itself: the Laplacian of the
+// recomputed states sees far less rounding noise.  The encoder forms the residual against
+// the decoded coarse part, so the decoder reproduces x to the fine part's rounding.  FP16
+// parts carry a per-shot scale (max |part| -> CODEC_RANGE, for FP16's narrow exponent
+// range); BF16 has the exponent range of FP32 and is stored unscaled (scale 1).
+// Kernels walk rows of x (one (z, y) row per block iteration): no per-element division.
 struct CkDims {
     int nz, ny, nx, px;
     int ncz, ncy, ncx;
     long long sst, csst;   // per-shot sizes of the fine (pitched) and coarse (dense) parts
 };
 
-__device__ __forceinline__ float ck_code_to_float(const uint16_t *codes, long long i, int kind) {
-    const uint16_t c = codes[i];
+__device__ __forceinline__ float ck_dec(uint16_t c, int kind) {
     return kind == ESI_CKPT_F16 ? __half2float(__ushort_as_half(c))
                                 : __bfloat162float(__ushort_as_bfloat16(c));
 }
 
-__device__ __forceinline__ uint16_t ck_float_to_code(float y, int kind) {
+__device__ __forceinline__ uint16_t ck_enc(float y, int kind) {
     return kind == ESI_CKPT_F16 ? __half_as_ushort(__float2half_rn(y))
                                 : __bfloat16_as_ushort(__float2bfloat16_rn(y));
 }
 
-// U(coarse) at cell (z, y, x) of one shot, in T
+// The coarse rows that row (z, y) interpolates from: one or two along z times one or two
+// along y (an odd index takes its even neighbours, the last one its left one twice).
+struct CkRows {
+    const uint16_t *r[4];
+    int n;
+};
+
+__device__ __forceinline__ CkRows ck_rows(const uint16_t *cs, const CkDims &d, int z, int y) {
+    const int z0 = z >> 1, z1 = (z & 1) ? min(z0 + 1, d.ncz - 1) : z0;
+    const int y0 = y >> 1, y1 = (y & 1) ? min(y0 + 1, d.ncy - 1) : y0;
+    CkRows c;
+    c.n = 0;
+    const int zs[2] = {z0, z1}, ys[2] = {y0, y1};
+    for (int a = 0; a < ((z & 1) ? 2 : 1); ++a)
+        for (int b = 0; b < ((y & 1) ? 2 : 1); ++b)
+            c.r[c.n++] = cs + ((long long)zs[a] * d.ncy + ys[b]) * d.ncx;
+    return c;
+}
+
+// U(coarse) at column x of a row, in T (the same arithmetic in the encoder and the decoder)
 template <typename T>
-__device__ __forceinline__ T ck_interp(const uint16_t *coarse, float cscale, const CkDims &d,
-                                       int z, int y, int x, int kind) {
-    int iz[2], iy[2], ix[2];
-    iz[0] = z >> 1, iz[1] = (z & 1) ? min(iz[0] + 1, d.ncz - 1) : iz[0];
-    iy[0] = y >> 1, iy[1] = (y & 1) ? min(iy[0] + 1, d.ncy - 1) : iy[0];
-    ix[0] = x >> 1, ix[1] = (x & 1) ? min(ix[0] + 1, d.ncx - 1) : ix[0];
-    const int nzs = (z & 1) ? 2 : 1, nys = (y & 1) ? 2 : 1, nxs = (x & 1) ? 2 : 1;
+__device__ __forceinline__ T ck_interp(const CkRows &c, float cscale, const CkDims &d, int x,
+                                       int kind) {
+    const int x0 = x >> 1, x1 = (x & 1) ? min(x0 + 1, d.ncx - 1) : x0;
     T acc = T(0);
-    for (int a = 0; a < nzs; ++a)
-        for (int b = 0; b < nys; ++b)
-            for (int c = 0; c < nxs; ++c)
-                acc += T(ck_code_to_float(
-                    coarse, ((long long)iz[a] * d.ncy + iy[b]) * d.ncx + ix[c], kind) * cscale);
-    return acc * T(1.0 / (nzs * nys * nxs));
+    for (int j = 0; j < c.n; ++j) {
+        acc += T(ck_dec(c.r[j][x0], kind) * cscale);
+        if (x & 1) acc += T(ck_dec(c.r[j][x1], kind) * cscale);
+    }
+    return acc * T(1.0 / (c.n * ((x & 1) ? 2 : 1)));
 }
 
 template <typename T>
@@ -333,80 +348,82 @@ __device__ __forceinline__ T ck_value(const T *u, const T *sub, long long i) {
     return sub ? u[i] - sub[i] : u[i];
 }
 
-// pass 0: max |x| over the even cells; pass 1: max |x - U(coarse)| over all cells
+// the coarse part: pass 0 max |x| over the even cells (FP16 only), pass 1 the codes
 template <typename T>
-__global__ void ck_absmax_kernel(const T *u, const T *sub, CkDims d, int pass, int kind,
-                                 const uint16_t *coarse, const float *cscale, unsigned *bits) {
+__global__ void ck_coarse_kernel(const T *u, const T *sub, CkDims d, int pass, int kind,
+                                 unsigned *bits, uint16_t *coarse, float *cscale) {
     const int s = blockIdx.y;
     const T *x = u + s * d.sst;
     const T *y = sub ? sub + s * d.sst : nullptr;
+    float inv = 1.0f;
+    if (pass == 1 && kind == ESI_CKPT_F16) {
+        const float mx = __uint_as_float(bits[s]);
+        inv = mx > 0.0f ? __fdiv_rn(CODEC_RANGE, mx) : 0.0f;
+        if (blockIdx.x == 0 && threadIdx.x == 0) cscale[s] = __fdiv_rn(mx, CODEC_RANGE);
+    } else if (pass == 1 && blockIdx.x == 0 && threadIdx.x == 0) {
+        cscale[s] = 1.0f;
+    }
+    uint16_t *cs = coarse + s * d.csst;
     float m = 0.0f;
-    if (pass == 0) {
-        const long long n = d.csst;
-        for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n;
-             i += (long long)gridDim.x * RT) {
-            const int cx = (int)(i % d.ncx);
-            const long long r = i / d.ncx;
-            const int cy = (int)(r % d.ncy), cz = (int)(r / d.ncy);
-            const long long k = ((long long)(2 * cz) * d.ny + 2 * cy) * d.px + 2 * cx;
-            m = fmaxf(m, fabsf(float(ck_value(x, y, k))));
-        }
-    } else {
-        const uint16_t *cs = coarse + s * d.csst;
-        const float sc = cscale[s];
-        for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < d.sst;
-             i += (long long)gridDim.x * RT) {
-            const int xx = (int)(i % d.px);
-            if (xx >= d.nx) continue;
-            const long long r = i / d.px;
-            const int yy = (int)(r % d.ny), zz = (int)(r / d.ny);
-            const T v = ck_value(x, y, i) - ck_interp<T>(cs, sc, d, zz, yy, xx, kind);
-            m = fmaxf(m, fabsf(float(v)));
+    for (int row = blockIdx.x; row < d.ncz * d.ncy; row += gridDim.x) {
+        const int cz = row / d.ncy, cy = row - cz * d.ncy;
+        const long long src = ((long long)(2 * cz) * d.ny + 2 * cy) * d.px;
+        for (int cx = threadIdx.x; cx < d.ncx; cx += blockDim.x) {
+            const float v = float(ck_value(x, y, src + 2 * cx));
+            if (pass == 0)
+                m = fmaxf(m, fabsf(v));
+            else
+                cs[(long long)row * d.ncx + cx] = ck_enc(kind == ESI_CKPT_F16 ? __fmul_rn(v, inv) : v, kind);
         }
     }
+    if (pass == 0) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    // non-negative floats order like their bit patterns
-    if ((threadIdx.x & 31) == 0) atomicMax(bits + s, __float_as_uint(m));
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        // non-negative floats order like their bit patterns
+        if ((threadIdx.x & 31) == 0) atomicMax(bits + s, __float_as_uint(m));
+    }
 }
 
+// the fine part: pass 0 max |x - U(coarse)| (FP16 only), pass 1 the codes (pads 0)
 template <typename T>
-__global__ void ck_encode_kernel(const T *u, const T *sub, CkDims d, int pass, int kind,
-                                 const unsigned *bits, uint16_t *coarse, float *cscale,
-                                 uint16_t *fine, float *fscale) {
+__global__ void ck_fine_kernel(const T *u, const T *sub, CkDims d, int pass, int kind,
+                               unsigned *bits, const uint16_t *coarse, const float *cscale,
+                               uint16_t *fine, float *fscale) {
     const int s = blockIdx.y;
-    const float mx = __uint_as_float(bits[s]);
-    const float inv = mx > 0.0f ? __fdiv_rn(CODEC_RANGE, mx) : 0.0f;
     const T *x = u + s * d.sst;
     const T *y = sub ? sub + s * d.sst : nullptr;
-    if (pass == 0) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) cscale[s] = __fdiv_rn(mx, CODEC_RANGE);
-        uint16_t *cs = coarse + s * d.csst;
-        for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < d.csst;
-             i += (long long)gridDim.x * RT) {
-            const int cx = (int)(i % d.ncx);
-            const long long r = i / d.ncx;
-            const int cy = (int)(r % d.ncy), cz = (int)(r / d.ncy);
-            const long long k = ((long long)(2 * cz) * d.ny + 2 * cy) * d.px + 2 * cx;
-            cs[i] = ck_float_to_code(__fmul_rn(float(ck_value(x, y, k)), inv), kind);
-        }
-    } else {
+    const uint16_t *cs = coarse + s * d.csst;
+    const float sc = cscale[s];
+    float inv = 1.0f;
+    if (pass == 1 && kind == ESI_CKPT_F16) {
+        const float mx = __uint_as_float(bits[s]);
+        inv = mx > 0.0f ? __fdiv_rn(CODEC_RANGE, mx) : 0.0f;
         if (blockIdx.x == 0 && threadIdx.x == 0) fscale[s] = __fdiv_rn(mx, CODEC_RANGE);
-        const uint16_t *cs = coarse + s * d.csst;
-        const float sc = cscale[s];
-        uint16_t *fs = fine + s * d.sst;
-        for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < d.sst;
-             i += (long long)gridDim.x * RT) {
-            const int xx = (int)(i % d.px);
-            uint16_t c = 0;
-            if (xx < d.nx) {
-                const long long r = i / d.px;
-                const int yy = (int)(r % d.ny), zz = (int)(r / d.ny);
-                const T v = ck_value(x, y, i) - ck_interp<T>(cs, sc, d, zz, yy, xx, kind);
-                c = ck_float_to_code(__fmul_rn(float(v), inv), kind);
+    } else if (pass == 1 && blockIdx.x == 0 && threadIdx.x == 0) {
+        fscale[s] = 1.0f;
+    }
+    uint16_t *fs = fine + s * d.sst;
+    float m = 0.0f;
+    for (int row = blockIdx.x; row < d.nz * d.ny; row += gridDim.x) {
+        const int z = row / d.ny, yy = row - z * d.ny;
+        const CkRows c = ck_rows(cs, d, z, yy);
+        const long long base = (long long)row * d.px;
+        for (int xx = threadIdx.x; xx < d.px; xx += blockDim.x) {
+            if (xx >= d.nx) {
+                if (pass == 1) fs[base + xx] = 0;
+                continue;
             }
-            fs[i] = c;
+            const float v = float(ck_value(x, y, base + xx) - ck_interp<T>(c, sc, d, xx, kind));
+            if (pass == 0)
+                m = fmaxf(m, fabsf(v));
+            else
+                fs[base + xx] = ck_enc(kind == ESI_CKPT_F16 ? __fmul_rn(v, inv) : v, kind);
         }
+    }
+    if (pass == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(bits + s, __float_as_uint(m));
     }
 }
 
@@ -421,18 +438,18 @@ __global__ void ck_decode_kernel(const uint16_t *fine, const uint16_t *coarse,
     const float sc = cscale[s], sf = fscale[s];
     T *x = u + s * d.sst;
     const T *b = base ? base + s * d.sst : nullptr;
-    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < d.sst;
-         i += (long long)gridDim.x * RT) {
-        const int xx = (int)(i % d.px);
-        T v = T(0);   // pad columns stay zero
-        if (xx < d.nx) {
-            const long long r = i / d.px;
-            const int yy = (int)(r % d.ny), zz = (int)(r / d.ny);
-            v = ck_interp<T>(cs, sc, d, zz, yy, xx, kind) +
-                T(__fmul_rn(ck_code_to_float(fs, i, kind), sf));
-            if (b) v = b[i] - v;
+    for (int row = blockIdx.x; row < d.nz * d.ny; row += gridDim.x) {
+        const int z = row / d.ny, yy = row - z * d.ny;
+        const CkRows c = ck_rows(cs, d, z, yy);
+        const long long base_i = (long long)row * d.px;
+        for (int xx = threadIdx.x; xx < d.px; xx += blockDim.x) {
+            T v = T(0);   // pad columns stay zero
+            if (xx < d.nx) {
+                v = ck_interp<T>(c, sc, d, xx, kind) + T(__fmul_rn(ck_dec(fs[base_i + xx], kind), sf));
+                if (b) v = b[base_i + xx] - v;
+            }
+            x[base_i + xx] = v;
         }
-        x[i] = v;
     }
 }
 
@@ -660,15 +677,19 @@ cudaError_t launch_ckpt_encode(const T *u, const T *sub, int ns, int nz, int ny,
                                long long sst, int kind, unsigned *bits, uint16_t *fine,
                                uint16_t *coarse, float *fscale, float *cscale, cudaStream_t st) {
     const CkDims d = ck_dims(nz, ny, nx, px, sst);
-    cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(unsigned) * 2 * ns, st);
-    if (e != cudaSuccess) return e;
-    const dim3 gc(blocks_for(d.csst, 1024), ns), gf(blocks_for(sst, 1024), ns);
-    ck_absmax_kernel<T><<<gc, RT, 0, st>>>(u, sub, d, 0, kind, nullptr, nullptr, bits);
-    ck_encode_kernel<T><<<gc, RT, 0, st>>>(u, sub, d, 0, kind, bits, coarse, cscale, nullptr,
-                                           nullptr);
-    ck_absmax_kernel<T><<<gf, RT, 0, st>>>(u, sub, d, 1, kind, coarse, cscale, bits + ns);
-    ck_encode_kernel<T><<<gf, RT, 0, st>>>(u, sub, d, 1, kind, bits + ns, coarse, cscale, fine,
-                                           fscale);
+    const bool scaled = kind == ESI_CKPT_F16;
+    const dim3 gc(std::min(d.ncz * d.ncy, 2048), ns), gf(std::min(nz * ny, 4096), ns);
+    if (scaled) {
+        cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(unsigned) * 2 * ns, st);
+        if (e != cudaSuccess) return e;
+        ck_coarse_kernel<T><<<gc, RT, 0, st>>>(u, sub, d, 0, kind, bits, coarse, cscale);
+    }
+    ck_coarse_kernel<T><<<gc, RT, 0, st>>>(u, sub, d, 1, kind, bits, coarse, cscale);
+    if (scaled)
+        ck_fine_kernel<T><<<gf, RT, 0, st>>>(u, sub, d, 0, kind, bits + ns, coarse, cscale, fine,
+                                             fscale);
+    ck_fine_kernel<T><<<gf, RT, 0, st>>>(u, sub, d, 1, kind, bits + ns, coarse, cscale, fine,
+                                         fscale);
     return cudaGetLastError();
 }
 
@@ -677,8 +698,8 @@ cudaError_t launch_ckpt_decode(const uint16_t *fine, const uint16_t *coarse, con
                                const float *cscale, int ns, int nz, int ny, int nx, int px,
                                long long sst, int kind, const T *base, T *u, cudaStream_t st) {
     const CkDims d = ck_dims(nz, ny, nx, px, sst);
-    ck_decode_kernel<T><<<dim3(blocks_for(sst, 1024), ns), RT, 0, st>>>(fine, coarse, fscale,
-                                                                         cscale, d, kind, base, u);
+    ck_decode_kernel<T><<<dim3(std::min(nz * ny, 4096), ns), RT, 0, st>>>(fine, coarse, fscale,
+                                                                          cscale, d, kind, base, u);
     return cudaGetLastError();
 }
 
