@@ -104,11 +104,11 @@ constexpr int ring_bytes() {
 #ifndef ESI_FD3_MINB
 #define ESI_FD3_MINB 3
 #endif
-// planes marched per loop iteration (1..3): the register queue shifts once per group
+// planes marched per loop iteration (1..4): the register queue shifts once per group
 #ifndef ESI_FD3_UNROLL
-#define ESI_FD3_UNROLL 3
+#define ESI_FD3_UNROLL 4
 #endif
-static_assert(ESI_FD3_UNROLL >= 1 && ESI_FD3_UNROLL <= 3, "unroll 1..3");
+static_assert(ESI_FD3_UNROLL >= 1 && ESI_FD3_UNROLL <= 4, "unroll 1..4");
 // the centre cells of a row come from the register queue (else from shared memory)
 #ifndef ESI_FD3_WQ
 #define ESI_FD3_WQ 1
@@ -495,6 +495,11 @@ __global__ void __launch_bounds__(block3<T>(), sizeof(T) == 4 ? ESI_FD3_MINB : 1
             if (i + 2 >= nsteps || __any_sync(0xffffffffu, late)) break;
             plane_step(std::integral_constant<int, 2>(), i + 2);
             refill_after(std::integral_constant<int, 2>(), i);
+        }
+        if constexpr (UN >= 4) {
+            if (i + 3 >= nsteps || __any_sync(0xffffffffu, late)) break;
+            plane_step(std::integral_constant<int, 3>(), i + 3);
+            refill_after(std::integral_constant<int, 3>(), i);
         }
     }
     if (late) atomicExch(a.dev_err, DEV_ERR_TMA_TIMEOUT);
