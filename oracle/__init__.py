@@ -18,7 +18,9 @@ The heavy loops (stencil, time stepping, transpose solve, DTFT sums) are plain C
 * the frequency-domain ESI system F (S^T S + beta B^T B) F^H qbar = F S^T d (Eq. "dtft",
   "idtft", "normaldtft") and its CG with the real part of the Hermitian inner product;
 * dense assembly of the normal matrix at tiny sizes and its Cholesky solution;
-* FP16 / BF16 snapshot codecs with a per-snapshot scale.
+* FP16 / BF16 snapshot codecs with a per-snapshot scale, the two-level checkpoint code
+  (all-even cells plus the interpolation residual) and the gradient recomputed from
+  checkpoints in that code.
 
 Where the paper leaves a point open, this module takes one reading and states it
 where it is used: state u_{n+1} is produced by step n from q_n; sample n of a trace is
@@ -628,6 +630,87 @@ def decode_snapshot(codes: np.ndarray, dec: np.float32, kind: str) -> np.ndarray
     else:
         h = bf16_to_f32(codes)
     return (h * np.float32(dec)).astype(np.float32)
+
+
+def _code16(x: np.ndarray, kind: str) -> np.ndarray:
+    """x taken to FP32, then to a 16-bit format and back (FP64 result): BF16 unscaled,
+    FP16 through the per-part scale of encode_snapshot."""
+    if kind == "bf16":
+        return bf16_to_f32(_bf16_rne(np.asarray(x, dtype=np.float32))).astype(np.float64)
+    if kind == "f16":
+        codes, dec = encode_snapshot(x, "f16")
+        return decode_snapshot(codes, dec, "f16").astype(np.float64)
+    raise ValueError(kind)
+
+
+def upsample_even(c: np.ndarray, shape: Sequence[int]) -> np.ndarray:
+    """Multilinear prolongation from the cells whose indices are all even to the whole grid:
+    along each axis an even index 2k takes c[k], an odd index the mean of its even
+    neighbours, and an odd last index (even axis length) repeats its left neighbour."""
+    u = np.asarray(c, dtype=np.float64)
+    for ax, n in enumerate(shape):
+        u = np.moveaxis(u, ax, 0)
+        out = np.empty((n,) + u.shape[1:])
+        out[0::2] = u
+        right = np.concatenate([u[1:], u[-1:]])
+        out[1::2] = (0.5 * (u + right))[: n // 2]
+        u = np.moveaxis(out, 0, ax)
+    return u
+
+
+def checkpoint_code(x: np.ndarray, shape: Sequence[int], kind: str) -> np.ndarray:
+    """Round trip of one snapshot through the two-level 16-bit checkpoint code.
+
+    The paper replaces the stored wavefield history by recomputation from checkpoints
+    (storage section, time-reversal discussion); it fixes no checkpoint format, so this is
+    the library's: the coarse part is x at the all-even cells, coded to 16 bits; the fine
+    part is x - U(decoded coarse) at every cell, coded to 16 bits; the decoded snapshot is
+    U(decoded coarse) + decoded fine, U the prolongation of upsample_even.  Rounding then
+    errs by the 16-bit precision of the interpolation residual, not of x.  kind "f32" keeps
+    the snapshot as it is (an uncompressed copy in the working precision)."""
+    x = np.asarray(x, dtype=np.float64).reshape(tuple(shape))
+    if kind == "f32":
+        return x.ravel().copy()
+    coarse = _code16(x[tuple(slice(0, None, 2) for _ in shape)], kind)
+    up = upsample_even(coarse, shape)
+    return (up + _code16(x - up, kind)).ravel()
+
+
+def _oracle_checkpointed_gradient(self: "Oracle", sh: Shot, dobs: np.ndarray, wavelet,
+                                  every: int, kind: str, param: str = "c"
+                                  ) -> Tuple[float, np.ndarray]:
+    """misfit_gradient with the forward history recomputed from checkpoints (storage
+    section: recompute instead of storing every step).  Every `every` steps n0 the pair
+    (u_n0, u_n0-1) is kept: u_n0 and the difference u_n0 - u_n0-1 each through
+    checkpoint_code (kind "f32": both states as they are); each segment restarts step n0
+    from the decoded pair, u_n0-1 = decoded u_n0 - decoded difference, and its steps'
+    s_n = Lap u_n + q_n (the same update as ``forward``) enter the correlation.  The
+    residual and J come from the uncompressed forward run."""
+    nt, N = self.nt, self.N
+    fw = self.forward(sh, wavelet=wavelet, want_u=True)
+    e = fw["traces"] - np.asarray(dobs, dtype=np.float64).reshape(nt, sh.nr)
+    U = fw["u"]                      # U[n] = u_n, U[0] = u_0 = 0; u_{-1} = 0
+    wav = np.asarray(wavelet, dtype=np.float64)
+    s_hist = np.empty((nt, N))
+    for n0 in range(0, nt, int(every)):
+        u_prev_true = U[n0 - 1] if n0 > 0 else np.zeros(N)
+        cur = checkpoint_code(U[n0], self.shape, kind)
+        if kind == "f32":
+            prev = checkpoint_code(u_prev_true, self.shape, kind)
+        else:
+            prev = cur - checkpoint_code(U[n0] - u_prev_true, self.shape, kind)
+        for n in range(n0, min(nt, n0 + int(every))):
+            q = np.zeros(N)
+            np.add.at(q, sh.src_node, sh.src_w * wav[n])
+            s = laplacian(cur.reshape(self.shape), self.dx).ravel() + q
+            s_hist[n] = s
+            nxt = (2.0 * cur - (1.0 - self.kappa) * prev + self.c * s) / (1.0 + self.kappa)
+            prev, cur = cur, nxt
+    ad = self.adjoint(sh, e, want_out=False, s_hist=s_hist)
+    return 0.5 * float(np.sum(e * e)), self.to_param(ad["grad_c"], param)
+
+
+Oracle.checkpointed_gradient = _oracle_checkpointed_gradient
 
 
 def rel_l2(a, b) -> float:
