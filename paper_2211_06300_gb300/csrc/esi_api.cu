@@ -134,7 +134,7 @@ struct esi_ctx {
     std::vector<GraphEntry> graphs;
     cudaStream_t cap = nullptr;
     bool use_graphs = true;
-    bool pdl = true;               // 2D loop steps after the first start as dependent launches
+    bool pdl = true;               // loop steps after the first start as dependent launches
     unsigned long long graph_clock = 0;
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> evpool;
@@ -521,7 +521,8 @@ StepArgs<T> base_args(esi_ctx *ctx) {
     return a;
 }
 
-// One step of either kernel.  In 3D the sampling of the input state is a gather launch.
+// One step of either kernel.  In 3D the step kernel samples its input state itself when
+// F_SMP is set (a.tout >= 0), by a gather of the receivers of each block's tile.
 template <typename T>
 esi_status step(esi_ctx *ctx, unsigned flags, const StepArgs<T> &a, bool chained = false) {
     StepArgs<T> b = a;
@@ -531,9 +532,8 @@ esi_status step(esi_ctx *ctx, unsigned flags, const StepArgs<T> &a, bool chained
     if (ctx->g.ndim == 2) {
         CKL(launch_step2<T>(flags, b, ctx->ns, ctx->st, chained && ctx->pdl));
     } else {
-        if ((flags & F_SMP) && a.tout >= 0)
-            CKL(launch_sample_global<T>(a.smp, a.cur, ctx->sst, a.smp_out, a.tout, ctx->st));
-        CKL(launch_step3<T>(flags & ~F_SMP, b, ctx->ns, ctx->st));
+        if (!(flags & F_SMP) || a.smp.nrec == 0) b.tout = -1;
+        CKL(launch_step3<T>(flags & ~F_SMP, b, ctx->ns, ctx->st, chained && ctx->pdl));
     }
     return ESI_OK;
 }

@@ -174,7 +174,8 @@ template <typename T>
 cudaError_t launch_step2(unsigned flags, const StepArgs<T> &a, int ns, cudaStream_t st,
                          bool chained = false);
 template <typename T>
-cudaError_t launch_step3(unsigned flags, const StepArgs<T> &a, int ns, cudaStream_t st);
+cudaError_t launch_step3(unsigned flags, const StepArgs<T> &a, int ns, cudaStream_t st,
+                         bool chained);
 // number of z chunks for a 3D context: cols = x tiles * y tiles * shots, element size esz
 // (the resident blocks per SM of the step kernel on the current device enter the choice)
 int step3_chunks(int nz, long long cols, int esz);

@@ -10,9 +10,11 @@
 // those cells in registers, refilled from the ring.  So every cell of the input state
 // crosses from HBM once per chunk (plus the z halo of the chunk and the xy halo, mostly
 // served by L2), the older state and c once, and the new state is written once, with no
-// global-load latency on the marching path.  Receiver sampling is a separate gather launch
-// (trilinear points straddle two planes); point injection walks a per-tile node list sorted
-// by z.
+// global-load latency on the marching path.  Receiver sampling of the input state is a
+// gather from global memory by the consumer threads of the block whose tile and chunk hold
+// the receiver's base node, issued while the first planes are in flight (trilinear points
+// straddle two planes, possibly two chunks); point injection walks a per-tile node list
+// sorted by z.
 #include <algorithm>
 #include <cstdlib>
 #include <type_traits>
@@ -130,7 +132,31 @@ __global__ void __launch_bounds__(block3<T>(), sizeof(T) == 4 ? ESI_FD3_MINB : 1
     __shared__ __align__(16) T scr_all[(F & F_PT) ? NC * VEC : 1];
     const int tid = threadIdx.x;
     const int s = blockIdx.z / nzc, zc = blockIdx.z - s * nzc;
-    if (a.active && !a.active[s]) return;
+    const int tile = ((s * nzc + zc) * a.nty + blockIdx.y) * a.ntx + blockIdx.x;
+    // Receiver sampling R u_n of the input state (a.tout >= 0): the receivers whose base
+    // node lies in this block's column tile and chunk, gathered from global memory by the
+    // consumer threads (u_n is never written by this launch).  Point order and sums as in
+    // the stand-alone gather, so the traces are the same to the bit.
+    auto sample_input = [&]() {
+        if (a.tout < 0 || tid >= consumers3<T>()) return;
+        const T *u = a.cur + (long long)s * a.sst;
+        const int r1 = a.smp.tile_ptr[tile + 1];
+        for (int r = a.smp.tile_ptr[tile] + tid; r < r1; r += consumers3<T>()) {
+            T v = T(0);
+#pragma unroll
+            for (int j = 0; j < MAXP; ++j) v += a.smp.w[r * MAXP + j] * u[a.smp.gidx[r * MAXP + j]];
+            a.smp_out[a.smp.off0[r] + (long long)a.tout * a.smp.tstride[r]] = v;
+        }
+    };
+    // Launched as a dependent of the previous step of the same loop (programmatic dependent
+    // launch), everything before griddepcontrol.wait reads only what stays fixed during the
+    // loop (flags, lists, sponge profiles); each thread waits for the previous step before
+    // it touches a state, a field or an accumulator, and the next step may then launch.
+    if (a.active && !a.active[s]) {   // a frozen shot: sampled, not stepped
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        sample_input();
+        return;
+    }
     const int x0 = blockIdx.x * TX3, y0 = blockIdx.y * TY3;
     const int zb = chunk_begin3(zc, nzc, a.nz), ze = chunk_begin3(zc + 1, nzc, a.nz);
     const int nsteps = ze - zb;
@@ -154,6 +180,8 @@ __global__ void __launch_bounds__(block3<T>(), sizeof(T) == 4 ? ESI_FD3_MINB : 1
     if (tid >= NC) {
         // ---- producer warp: one thread keeps the ring filled ahead of use
         if (tid != NC) return;
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
         bool ok = true;
         int j = 0;
         for (; j < J; ++j) {
@@ -198,7 +226,10 @@ __global__ void __launch_bounds__(block3<T>(), sizeof(T) == 4 ? ESI_FD3_MINB : 1
     const long long plane = (long long)a.ny * a.px;
     T *po = a.po + (long long)s * a.sst;
     const long long col = (long long)gy * a.px + gx0;
-    const int tile = ((s * nzc + zc) * a.nty + blockIdx.y) * a.ntx + blockIdx.x;
+    // the gather's loads overlap the producer's first TMA copies
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    sample_input();
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     auto release = [&](int j) {   // this warp is done with plane j
         __syncwarp();
         if (lane == 0)
@@ -528,25 +559,37 @@ cudaError_t set_smem(PerDevice &attr) {
     });
 }
 
+// chained: the previous launch on the stream is the previous step of the same loop, so the
+// grid may be launched (programmatic dependent launch) while that step drains; its blocks
+// wait for it before they read its output or write over its input.
 template <typename T, unsigned F>
-cudaError_t go(const StepArgs<T> &a, int ns, cudaStream_t st) {
+cudaError_t go(const StepArgs<T> &a, int ns, cudaStream_t st, bool chained) {
     const int nzc = a.ntz;
     static PerDevice attr;
     cudaError_t e = set_smem<T, F>(attr);
     if (e != cudaSuccess) return e;
-    dim3 grid(a.ntx, a.nty, ns * nzc);
-    fd3_step_kernel<T, F><<<grid, block3<T>(), ring_bytes<T>(), st>>>(a, nzc);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.ntx, a.nty, ns * nzc);
+    cfg.blockDim = dim3(block3<T>());
+    cfg.dynamicSmemBytes = ring_bytes<T>();
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = chained ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, fd3_step_kernel<T, F>, a, nzc);
 }
 
 }  // namespace
 
 #define ESI_CASE(FL)        \
     case (FL):              \
-        return go<T, (FL)>(a, ns, st);
+        return go<T, (FL)>(a, ns, st, chained);
 
 template <typename T>
-cudaError_t launch_step3(unsigned flags, const StepArgs<T> &a, int ns, cudaStream_t st) {
+cudaError_t launch_step3(unsigned flags, const StepArgs<T> &a, int ns, cudaStream_t st,
+                         bool chained) {
     switch (flags) {
         ESI_CASE(F_PT)
         ESI_CASE(F_EXT)
@@ -616,7 +659,7 @@ int step3_chunks(int nz, long long cols, int esz) {
     return best;
 }
 
-template cudaError_t launch_step3<float>(unsigned, const StepArgs<float> &, int, cudaStream_t);
-template cudaError_t launch_step3<double>(unsigned, const StepArgs<double> &, int, cudaStream_t);
+template cudaError_t launch_step3<float>(unsigned, const StepArgs<float> &, int, cudaStream_t, bool);
+template cudaError_t launch_step3<double>(unsigned, const StepArgs<double> &, int, cudaStream_t, bool);
 
 }  // namespace esi
