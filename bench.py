@@ -323,7 +323,9 @@ def run_dft3d(args, rank, world, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"dft3d-{args.n3d}^3-nt{args.nt3d}-5freqs-fp16",
-                       "freqs_hz": freqs, "l2": "inputs larger than L2 (states 2 x 256 MB)"},
+                       "freqs_hz": freqs,
+                       "l2": "inputs larger than L2 (states 2 x %.0f MB, DTFT stash %.1f GB)"
+                             % (4 * w.ncell / 1e6, 16 * 4 * w.ncell / 1e9)},
             # algorithmic bytes per cell update: accumulating every state into the nf complex
             # FP32 accumulators directly costs 16 + 16 nf; the blocked DTFT stashes 16 states
             # and folds them once (16 + 4 stash write + 4 stash read + 4 nf / 16 x 4)
@@ -440,7 +442,8 @@ def run_wri2d(args, rank, world, local):
             "data": "synthetic",
             "config": {"workload": "wri2d-801x241-nt%d-%dshots-fp32" % (nt, ns), "beta": beta,
                        "wri_factor": args.wri_factor, "tol": args.tol,
-                       "l2": "inputs larger than L2 (CG vectors 4 x 37 GB per GPU)"},
+                       "l2": "inputs larger than L2 (CG vectors 4 x %.2f GB per GPU)"
+                             % (4 * ns * nt * N / 1e9)},
             "cg": {"iters_max_per_step": [int(max(r["iters"])) for r in reps],
                    "time_to_tol_ms": [r["ms_total"] for r in reps],
                    "converged": [bool(r["converged"]) for r in reps]},
@@ -551,7 +554,8 @@ def run_invert2d(args, rank, world, local):
             "data": "synthetic",
             "config": {"workload": "invert2d-801x241-nt%d-%dshots-fp32" % (nt, ns),
                        "outer_iterations": args.outer, "inner_cg": 10, "precond": "diag",
-                       "beta": beta, "l2": "inputs larger than L2 (q 37 GB per GPU)"},
+                       "beta": beta,
+                       "l2": "inputs larger than L2 (q %.2f GB per GPU)" % (4 * ns * nt * N / 1e9)},
             "outer": [{"J_start": r["J_start"], "J_end": r["J_end"], "trials": r["trials"],
                        "evaluations": r["evaluations"], "stop": r["stop"],
                        "ms": r["ms_total"]} for r in reps],
@@ -654,9 +658,10 @@ def run_grad2d(args, rank, world, local):
                        "checkpoint_every": 20, "checkpoints": "bf16",
                        "checkpoint_codec": "u_n and u_n - u_{n-1}, each as BF16 even-index "
                                            "cells plus the BF16 residual against their "
-                                           "bilinear interpolation, per-shot scales "
+                                           "bilinear interpolation, unscaled "
                                            "(5 bytes per cell per checkpoint)",
-                       "l2": "inputs larger than L2 (states 2 x 93 MB, checkpoints 14 GB)"},
+                       "l2": "inputs larger than L2 (states 2 x %.1f MB, checkpoints %.1f GB)"
+                             % (4 * ns * N / 1e6, 5 * ns * N * ((nt + 19) // 20) / 1e9)},
             "misfit": J,
             "roofline": roofline_of(prof, peaks), "kernels": prof,
             "e2e": {"value": cells_all / te / 1e9, "unit": UNIT,
@@ -887,7 +892,8 @@ def main():
         "config": {"workload": workload_name(ns, nt), "grid": "801x241 (z 241, x 801)",
                    "nt": nt, "shots_per_gpu": ns, "tol": args.tol, "beta": beta,
                    "freqs_hz": freqs, "precond": precond, "beta_factor": args.beta_factor,
-                   "l2": "inputs larger than L2 (CG vectors 4 x 37 GB per GPU)"},
+                   "l2": "inputs larger than L2 (CG vectors 4 x %.2f GB per GPU)"
+                         % (4 * ns * nt * N / 1e9)},
         "cg": {"precond": precond, "iters_max_per_step": iters, "time_to_tol_ms": cg_ms,
                "converged": [bool(r["converged"]) for r in reps],
                "rel_res_max_over_shots": float(max(r[-1] for r in reps[-1]["rel_res"] if r.size)),
