@@ -500,6 +500,44 @@ def test_data_space_cg_matches_oracle(prec):
         assert oracle.rel_l2(q[s].reshape(nt, -1).double().cpu().numpy(), ref["q"]) <= 10 * tol, s
 
 
+def test_3d_wri_and_data_space_fp64():
+    """The WRI solve and its saddle-point gradient (3D: EXT|PT|SAD), and the data-space form
+    of the ESI solve, on the three-shot volume against the oracle."""
+    v, geom, p = _multishot_3d()
+    nt = p["nt"]
+    o, shots = _orc(v, geom, p, vref=float(v.max()))
+    wav = np.stack([synth.ricker(nt, p["dt"], 30.0)] * geom.ns)
+    Sf = np.concatenate([o.forward(sh, wavelet=wav[s])["traces"].ravel()
+                         for s, sh in enumerate(shots)])
+    d = Sf + synth.normal(43, Sf.shape) * np.abs(Sf).max()
+    ctx = _ctx(v, geom, p, "f64", vref=float(v.max()))
+    lam, nmax = 0.05, 4
+    q, rep = ctx.cg_solve(_dev(d, "f64"), lam=lam, tol=0.0, max_iter=nmax,
+                          wri_wavelet=_dev(wav, "f64"))
+    qh = q.cpu().numpy()
+    for s, sh in enumerate(shots):
+        o0, o1 = geom.rec_offset[s], geom.rec_offset[s + 1]
+        ref = o.wri_cg(sh, d[nt * o0:nt * o1].reshape(nt, -1), wav[s], lam, 0.0, nmax)
+        assert np.allclose(rep["rel_res"][s], ref["rel_res"], rtol=1e-12, atol=0), s
+        assert oracle.rel_l2(qh[s].reshape(nt, -1), ref["x"]) <= 1e-12, s
+    g, _ = ctx.gradient(wavelet=_dev(wav, "f64"), ext=q, mode="wri", beta=lam, param="v")
+    g_ref = sum(o.wri_gradient(sh, qh[s].reshape(nt, -1), wav[s], lam, param="v")
+                for s, sh in enumerate(shots))
+    assert oracle.rel_l2(g.cpu().numpy().ravel(), g_ref) <= 1e-12
+    # data space on the noise-free data: (I + K) w = K d, q = (beta B^2)^-1 S^T (d - w)
+    lam_d = 2e-4
+    w = torch.empty(Sf.size, dtype=torch.float64, device="cuda")
+    q2, rep2 = ctx.cg_solve(_dev(Sf, "f64"), lam=lam_d, tol=0.0, max_iter=nmax, data_space=True,
+                            w_out=w)
+    wh = w.cpu().numpy()
+    for s, sh in enumerate(shots):
+        o0, o1 = geom.rec_offset[s], geom.rec_offset[s + 1]
+        ref = o.ds_cg(sh, Sf[nt * o0:nt * o1].reshape(nt, -1), lam_d, 0.0, nmax)
+        assert np.allclose(rep2["rel_res"][s], ref["rel_res"], rtol=1e-12, atol=0), s
+        assert oracle.rel_l2(wh[nt * o0:nt * o1].reshape(nt, -1), ref["w"]) <= 1e-12, s
+        assert oracle.rel_l2(q2[s].reshape(nt, -1).cpu().numpy(), ref["q"]) <= 1e-11, s
+
+
 # ----------------------------------------------------------------------------- frequency domain
 @pytest.mark.parametrize("pc", ["none", "diag"])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
