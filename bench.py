@@ -130,6 +130,14 @@ def traffic_per_launch(entry):
     return m[0] * entry["cells"] / max(entry["launches"], 1)
 
 
+def pinned_like(t):
+    """A page-locked host buffer of t's shape and type, made before a timed loop: copies
+    from the device into it run at the link's speed (a pageable target goes through a
+    staging buffer)."""
+    import torch
+    return torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+
+
 # ----------------------------------------------------------------------------- clocks
 class Clocks:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -303,12 +311,15 @@ def run_dft3d(args, rank, world, local):
     cells_all = shard.sum_over_ranks(cells, dist, dev)
     # end to end: the wavelet from pinned host memory in, traces and the FP16 wavefields out
     wav_h = wav.cpu().pin_memory()
+    tr_h, U_h = pinned_like(tr), pinned_like(U)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         wav.copy_(wav_h, non_blocking=True)
         U, _ = ctx.dft_extract(freqs, wavelet=wav, half=True, traces=tr)
-        tr_h, U_h = tr.cpu(), U.cpu()
+        tr_h.copy_(tr, non_blocking=True)
+        U_h.copy_(U, non_blocking=True)
+        torch.cuda.synchronize()
     te = shard.max_over_ranks(time.perf_counter() - t0, dist, dev)
     if rank == 0:
         peaks = {}
@@ -415,6 +426,7 @@ def run_wri2d(args, rank, world, local):
     cells_all = shard.sum_over_ranks(cells, dist, dev)
     d_host = dobs.cpu().pin_memory()
     d_dev = torch.empty_like(dobs)
+    g_host = pinned_like(v0)
     barrier()
     t0 = time.perf_counter()
     ce = 0
@@ -424,7 +436,8 @@ def run_wri2d(args, rank, world, local):
         _, rep = ctx.cg_solve(d_dev, lam=beta, tol=args.tol, max_iter=args.max_iter, out=q,
                               wri_wavelet=wav)
         g, _ = ctx.gradient(wavelet=wav, ext=q, mode="wri", beta=beta, param="v")
-        g_host = g.cpu()
+        g_host.copy_(g, non_blocking=True)
+        torch.cuda.synchronize()
         ce += sum(3 + 2 * int(k) for k in rep["iters"]) * N * nt
     te = shard.max_over_ranks(time.perf_counter() - t0, dist, dev)
     ce = shard.sum_over_ranks(ce, dist, dev)
@@ -530,13 +543,15 @@ def run_invert2d(args, rank, world, local):
     cells_all = shard.sum_over_ranks(cells, dist, dev)
     d_host = dobs.cpu().pin_memory()
     d_dev = torch.empty_like(dobs)
+    v_host = pinned_like(vel)
     barrier()
     t0 = time.perf_counter()
     ce = 0
     for _ in range(args.steps):
         d_dev.copy_(d_host, non_blocking=True)
         _, c = step(d_dev)
-        v_host = vel.cpu()
+        v_host.copy_(vel, non_blocking=True)
+        torch.cuda.synchronize()
         ce += c
     te = shard.max_over_ranks(time.perf_counter() - t0, dist, dev)
     ce = shard.sum_over_ranks(ce, dist, dev)
@@ -635,12 +650,14 @@ def run_grad2d(args, rank, world, local):
     cells_all = shard.sum_over_ranks(cells_step * args.steps, dist, dev)
     d_host = dobs.cpu().pin_memory()
     d_dev = torch.empty_like(dobs)
+    g_host = pinned_like(v0)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         d_dev.copy_(d_host, non_blocking=True)
         g, J = step(d_dev)
-        g_host = g.cpu()
+        g_host.copy_(g, non_blocking=True)
+        torch.cuda.synchronize()
     te = shard.max_over_ranks(time.perf_counter() - t0, dist, dev)
     if rank == 0:
         peaks = {}
@@ -744,9 +761,9 @@ def main():
         _, rep = ctx.cg_solve(d_obs, lam=beta, tol=args.tol, max_iter=max_iter, out=q,
                               precond=precond)
         g, _ = ctx.gradient(ext=q, mode="saddle", beta=beta, param="v")
-        U, _ = ctx.dft_extract(freqs, ext=q, half=True)
+        U, sc = ctx.dft_extract(freqs, ext=q, half=True)
         props = sum(1 + 2 * int(k) + 2 for k in rep["iters"])   # b, CG products, grad, DTFT
-        return g, rep, props * N * nt, U
+        return g, rep, props * N * nt, U, sc
 
     for _ in range(args.warmup):
         step(dobs)
@@ -761,7 +778,7 @@ def main():
     e0.record(stream)
     cells, reps = 0, []
     for _ in range(args.steps):
-        _, rep, c, _ = step(dobs)
+        g, rep, c, U, sc = step(dobs)
         cells += c
         reps.append(rep)
     e1.record(stream)
@@ -782,14 +799,16 @@ def main():
     if not args.no_e2e:
         d_host = dobs.cpu().pin_memory()
         d_dev = torch.empty_like(dobs)
+        g_host, U_host = pinned_like(g), pinned_like(U)
         barrier()
         t0 = time.perf_counter()
         ce = 0
-        g_host = U_host = None
         for _ in range(args.steps):
             d_dev.copy_(d_host, non_blocking=True)
-            g, rep, c, U = step(d_dev)
-            g_host, U_host = g.cpu(), U.cpu()
+            g, rep, c, U, sc = step(d_dev)   # the call returns the scales on the host
+            g_host.copy_(g, non_blocking=True)
+            U_host.copy_(U, non_blocking=True)
+            torch.cuda.synchronize()
             ce += c
         barrier()
         te = shard.max_over_ranks(time.perf_counter() - t0, dist, dev)
@@ -797,8 +816,8 @@ def main():
         e2e = {"value": ce / te / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(d_host.numel() * d_host.element_size()),
                "d2h_bytes_per_step": int(g_host.numel() * g_host.element_size() +
-                                         U_host.numel() * U_host.element_size()),
-               "outputs_copied": "gradient (FP32) and DTFT fields (FP16)"}
+                                         U_host.numel() * U_host.element_size() + sc.nbytes),
+               "outputs_copied": "gradient (FP32), DTFT fields (FP16) and their scales"}
 
     if rank != 0:
         if dist is not None:
