@@ -706,33 +706,67 @@ cudaError_t launch_ckpt_decode(const uint16_t *fine, const uint16_t *coarse, con
 namespace {
 
 // Blocked DTFT (Eq. "dtft"): acc[s][m][cell] += sum_k snap[k][s][cell] e^{+j 2 pi f_m t_k} for
-// the K states of one block, twid[k][m] = (cos, sin) of their phases.  A thread takes 16 bytes
-// of cells (pads included: they hold zeros) and up to DFT_MCH frequencies at a time in registers.
-constexpr int DFT_MCH = 4;
+// the K <= DFT_BLOCK states of one block, twid[k][m] = (cos, sin) of their phases.  A thread
+// takes 16 bytes of cells (pads included: they hold zeros, chunks wholly in the pad are
+// skipped) and M frequencies in registers, so the K stash planes are read once for up to
+// M = 8 frequencies; the block's twiddles of those frequencies are staged in shared memory,
+// and the states are loaded four at a time ahead of their sums (accumulated in step order).
+// The grid holds as many blocks as are resident at once and strides over the cells.
+constexpr int DFT_MCH = 8;
 
-template <typename T>
-__global__ void dft_block_kernel(const T *snap, int K, int ns, long long sst, int nx, int px,
-                                 int nf, const T *twid, T *acc) {
+template <typename T, int M>
+__global__ void __launch_bounds__(RT) dft_block_kernel(const T *snap, int K, int ns, long long sst,
+                                                       int nx, int px, int nf, const T *twid,
+                                                       T *acc) {
     constexpr int VEC = V16<T>::n;
+    __shared__ T tw[DFT_BLOCK][M][2];
     const int s = blockIdx.y;
     const long long nch = sst / VEC;
-    for (long long c = (long long)blockIdx.x * RT + threadIdx.x; c < nch;
-         c += (long long)gridDim.x * RT) {
-        const long long cell = c * VEC;
-        if ((int)(cell % px) >= nx) continue;   // a chunk of pad cells only: never written
-        for (int m0 = 0; m0 < nf; m0 += DFT_MCH) {
-            T re[DFT_MCH][VEC], im[DFT_MCH][VEC];
+    const T *sn0 = snap + (long long)s * sst;
+    const long long kst = (long long)ns * sst;   // stash slot stride
+    for (int m0 = 0; m0 < nf; m0 += M) {
+        __syncthreads();   // the previous chunk's twiddles are no longer read
+        for (int t = threadIdx.x; t < K * M; t += RT) {
+            const int k = t / M, j = t - k * M;
+            const bool in = m0 + j < nf;
+            tw[k][j][0] = in ? twid[((long long)k * nf + m0 + j) * 2] : T(0);
+            tw[k][j][1] = in ? twid[((long long)k * nf + m0 + j) * 2 + 1] : T(0);
+        }
+        __syncthreads();
+        const int mn = min(M, nf - m0);
+        for (long long c = (long long)blockIdx.x * RT + threadIdx.x; c < nch;
+             c += (long long)gridDim.x * RT) {
+            const long long cell = c * VEC;
+            if ((int)(cell % px) >= nx) continue;   // a chunk of pad cells only: never written
+            T re[M][VEC], im[M][VEC];
 #pragma unroll
-            for (int j = 0; j < DFT_MCH; ++j)
+            for (int j = 0; j < M; ++j)
 #pragma unroll
                 for (int i = 0; i < VEC; ++i) re[j][i] = im[j][i] = T(0);
-            for (int k = 0; k < K; ++k) {
-                const V16<T> u = *reinterpret_cast<const V16<T> *>(snap + ((long long)k * ns + s) * sst + cell);
+            const T *src = sn0 + cell;
+            int k = 0;
+            for (; k + 4 <= K; k += 4) {
+                V16<T> u[4];
 #pragma unroll
-                for (int j = 0; j < DFT_MCH; ++j) {
-                    if (m0 + j >= nf) break;
-                    const T cs = twid[((long long)k * nf + m0 + j) * 2];
-                    const T sn = twid[((long long)k * nf + m0 + j) * 2 + 1];
+                for (int q = 0; q < 4; ++q)
+                    u[q] = *reinterpret_cast<const V16<T> *>(src + (long long)(k + q) * kst);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int j = 0; j < M; ++j) {
+                        const T cs = tw[k + q][j][0], sn = tw[k + q][j][1];
+#pragma unroll
+                        for (int i = 0; i < VEC; ++i) {
+                            re[j][i] += u[q].v[i] * cs;
+                            im[j][i] += u[q].v[i] * sn;
+                        }
+                    }
+            }
+            for (; k < K; ++k) {
+                const V16<T> u = *reinterpret_cast<const V16<T> *>(src + (long long)k * kst);
+#pragma unroll
+                for (int j = 0; j < M; ++j) {
+                    const T cs = tw[k][j][0], sn = tw[k][j][1];
 #pragma unroll
                     for (int i = 0; i < VEC; ++i) {
                         re[j][i] += u.v[i] * cs;
@@ -741,8 +775,8 @@ __global__ void dft_block_kernel(const T *snap, int K, int ns, long long sst, in
                 }
             }
 #pragma unroll
-            for (int j = 0; j < DFT_MCH; ++j) {
-                if (m0 + j >= nf) break;
+            for (int j = 0; j < M; ++j) {
+                if (j >= mn) break;
                 // VEC complex values = 32 bytes = two 16-byte vectors
                 V16<T> *a = reinterpret_cast<V16<T> *>(acc + (((long long)s * nf + m0 + j) * sst + cell) * 2);
 #pragma unroll
@@ -760,11 +794,6 @@ __global__ void dft_block_kernel(const T *snap, int K, int ns, long long sst, in
     }
 }
 
-// Inverse DTFT of one block (Eq. "idtft" with its 1/nt folded into tw): the K source samples
-// of a cell from its nf complex values, tw[k][m] = (C, D) such that the sample is
-// sum_m re(qbar_m) C + im(qbar_m) D, into src[s][k][cell] with kst slots per shot (kst >= K:
-// a ragged last block fills only its first K slots).  A thread keeps the nf values of 16
-// bytes of cells.
 template <typename T>
 __global__ void idft_block_kernel(const T *qb, int K, int kst, int ns, long long sst, int nf,
                                   const T *tw, T *src) {
@@ -896,12 +925,52 @@ cudaError_t launch_fd_b2g_dot(T *out, const T *p, const T *pb2, const double *G,
     return cudaGetLastError();
 }
 
+namespace {
+// resident blocks of one fold instantiation on the current device (SMs x blocks per SM)
+template <typename T, int M>
+int dft_block_slots() {
+    static PerDevice slots;
+    int v = 0;
+    cudaError_t e = per_device(slots, &v, [](int *out) {
+        int dev = 0, nsm = 0, nb = 0;
+        cudaError_t r;
+        if ((r = cudaGetDevice(&dev)) != cudaSuccess) return r;
+        if ((r = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return r;
+        if ((r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dft_block_kernel<T, M>, RT, 0)) !=
+            cudaSuccess)
+            return r;
+        *out = std::max(1, nb) * std::max(1, nsm);
+        return cudaSuccess;
+    });
+    return e == cudaSuccess ? v : 1024;
+}
+
+template <typename T, int M>
+cudaError_t go_dft_block(const T *snap, int K, int ns, long long sst, int nx, int px, int nf,
+                         const T *twid, T *acc, cudaStream_t st) {
+    // the resident blocks, shared among the shots
+    const int per_shot = std::max(1, dft_block_slots<T, M>() / std::max(1, ns));
+    dft_block_kernel<T, M><<<dim3(blocks_for(sst / V16<T>::n, per_shot), ns), RT, 0, st>>>(
+        snap, K, ns, sst, nx, px, nf, twid, acc);
+    return cudaGetLastError();
+}
+}  // namespace
+
 template <typename T>
 cudaError_t launch_dft_block(const T *snap, int K, int ns, long long sst, int nx, int px, int nf,
                              const T *twid, T *acc, cudaStream_t st) {
-    dft_block_kernel<T><<<dim3(blocks_for(sst / V16<T>::n, 1024), ns), RT, 0, st>>>(
-        snap, K, ns, sst, nx, px, nf, twid, acc);
-    return cudaGetLastError();
+    if (K < 1 || K > DFT_BLOCK || nf < 1) return cudaErrorInvalidValue;
+    switch (std::min(nf, DFT_MCH)) {
+        case 1: return go_dft_block<T, 1>(snap, K, ns, sst, nx, px, nf, twid, acc, st);
+        case 2: return go_dft_block<T, 2>(snap, K, ns, sst, nx, px, nf, twid, acc, st);
+        case 3: return go_dft_block<T, 3>(snap, K, ns, sst, nx, px, nf, twid, acc, st);
+        case 4: return go_dft_block<T, 4>(snap, K, ns, sst, nx, px, nf, twid, acc, st);
+        case 5: return go_dft_block<T, 5>(snap, K, ns, sst, nx, px, nf, twid, acc, st);
+        case 6: return go_dft_block<T, 6>(snap, K, ns, sst, nx, px, nf, twid, acc, st);
+        case 7: return go_dft_block<T, 7>(snap, K, ns, sst, nx, px, nf, twid, acc, st);
+        default: return go_dft_block<T, 8>(snap, K, ns, sst, nx, px, nf, twid, acc, st);
+    }
 }
 
 template <typename T>
