@@ -309,6 +309,10 @@ def run_dft3d(args, rank, world, local):
     cells = args.steps * w.ncell * w.nt
     t_max = shard.max_over_ranks(ms, dist, dev)
     cells_all = shard.sum_over_ranks(cells, dist, dev)
+    # the blocked DTFT's bytes per cell update and block length, from the library's profile
+    # entry of the step + fold (FP32: 24 + 16 nf / K bytes)
+    bpc_blk = next(k["bytes_per_cell"] for k in prof if k["name"].endswith("+dft_block"))
+    kblk = int(round(16 * len(freqs) / (bpc_blk - 24)))
     # end to end: the wavelet from pinned host memory in, traces and the FP16 wavefields out
     wav_h = wav.cpu().pin_memory()
     tr_h, U_h = pinned_like(tr), pinned_like(U)
@@ -336,12 +340,13 @@ def run_dft3d(args, rank, world, local):
             "config": {"workload": f"dft3d-{args.n3d}^3-nt{args.nt3d}-5freqs-fp16",
                        "freqs_hz": freqs,
                        "l2": "inputs larger than L2 (states 2 x %.0f MB, DTFT stash %.1f GB)"
-                             % (4 * w.ncell / 1e6, 16 * 4 * w.ncell / 1e9)},
+                             % (4 * w.ncell / 1e6, kblk * 4 * w.ncell / 1e9)},
             # algorithmic bytes per cell update: accumulating every state into the nf complex
-            # FP32 accumulators directly costs 16 + 16 nf; the blocked DTFT stashes 16 states
-            # and folds them once (16 + 4 stash write + 4 stash read + 4 nf / 16 x 4)
+            # FP32 accumulators directly costs 16 + 16 nf; the blocked DTFT stashes the states
+            # of a block of K steps and folds them once (16 + 4 stash write + 4 stash read +
+            # 16 nf / K), K chosen by the library for the context's memory (from its profile)
             "bytes_per_cell": {"per_step_accumulation": 16 + 16 * len(freqs),
-                               "blocked_16_steps": 16 + 4 + 4 + 16 * len(freqs) / 16},
+                               "blocked": bpc_blk, "block_steps": kblk},
             "roofline": roofline_of(prof, peaks), "kernels": prof,
             "e2e": {"value": cells_all / te / 1e9, "unit": UNIT,
                     "h2d_bytes_per_step": int(wav_h.numel() * 4),

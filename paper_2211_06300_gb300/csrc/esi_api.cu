@@ -77,6 +77,7 @@ struct esi_ctx {
     std::vector<double> rec_xyz;
     double vmax = 0, vref = 0, kappa_max = 0;
     int ntx = 0, nty = 1, ntz = 0, nzc = 1, ntiles = 0;
+    int dft_k = DFT_BLOCK;         // steps per blocked DTFT pass (dft_block_steps)
     DBuf cc, kz, ky, kx, src_pos;
     DBuf dev_err;                  // sticky device error word (int)
     struct TMap {
@@ -96,7 +97,7 @@ struct esi_ctx {
     PcNet *pc = nullptr;           // learned preconditioner (esi_pc_load)
     DBuf pc_img, pc_y;             // network input images (BF16) and output (FP32)
     DBuf pc_dev;                   // learned-PCG dot partials, sums and per-shot theta
-    DBuf dftsnap;                  // blocked DTFT: DFT_BLOCK new states [slot][ns][sst]
+    DBuf dftsnap;                  // blocked DTFT: dft_k new states [slot][ns][sst]
     DBuf wri_res;                  // WRI: data residual d - S f [traces]
     DBuf invq, invv, invpart;      // outer loop: inner solution q, model vectors, dot partials
     DBuf fdv, fdsrc, fdtr;         // frequency-domain CG: 5 complex vectors, source stash, traces
@@ -766,8 +767,8 @@ esi_status fwd_dft_loop(esi_ctx *ctx, StepArgs<T> a, unsigned flags, T *cur, T *
     const int nt = ctx->nt;
     auto body = [&]() -> esi_status {
         T *c = cur, *q = po;
-        for (int n0 = 0; n0 < nt; n0 += DFT_BLOCK) {
-            const int n1 = std::min(nt, n0 + DFT_BLOCK);
+        for (int n0 = 0; n0 < nt; n0 += ctx->dft_k) {
+            const int n1 = std::min(nt, n0 + ctx->dft_k);
             for (int n = n0; n < n1; ++n) {
                 a.cur = c;
                 a.po = q;
@@ -797,7 +798,7 @@ esi_status fwd_dft_loop(esi_ctx *ctx, StepArgs<T> a, unsigned flags, T *cur, T *
     // and the accumulators' read and write once per block
     const double es = double(sizeof(T));
     prof_close(ctx, ev, step_name(ctx, flags) + "+dft_block",
-               step_bpc(ctx, flags, a.nf) + es + 4.0 * a.nf * es / DFT_BLOCK, nt + (nt + DFT_BLOCK - 1) / DFT_BLOCK,
+               step_bpc(ctx, flags, a.nf) + es + 4.0 * a.nf * es / ctx->dft_k, nt + (nt + ctx->dft_k - 1) / ctx->dft_k,
                (long long)nt * ctx->prof_active * ctx->N);
     return ESI_OK;
 }
@@ -831,9 +832,9 @@ esi_status forward_impl(esi_ctx *ctx, const void *wavelet, const void *ext, void
     a.smp_out = tr;
     T *cur = ctx->u0.as<T>(), *po = ctx->u1.as<T>();
     if (nf > 0) {
-        // blocked DTFT: each step stores u_{n+1} in a DFT_BLOCK-slot stash, and one pass per
-        // block adds the block's terms to the accumulators (80 -> ~13 bytes per cell update
-        // for five frequencies)
+        // blocked DTFT: each step stores u_{n+1} in a dft_k-slot stash, and one pass per
+        // block adds the block's terms to the accumulators (80 -> 8 + 80 / dft_k bytes per
+        // cell update for five frequencies)
         flags |= F_DFT;
         std::vector<T> tw((size_t)ctx->nt * nf * 2);
         for (int n = 0; n < ctx->nt; ++n)
@@ -843,7 +844,7 @@ esi_status forward_impl(esi_ctx *ctx, const void *wavelet, const void *ext, void
                 tw[((size_t)n * nf + m) * 2 + 1] = T(std::sin(ph));
             }
         CK(upload(ctx->twid, tw, ctx->st));
-        CK(ctx->dftsnap.ensure((size_t)DFT_BLOCK * ctx->ns * ctx->sst * sizeof(T)));
+        CK(ctx->dftsnap.ensure((size_t)ctx->dft_k * ctx->ns * ctx->sst * sizeof(T)));
         a.nf = nf;
         a.twid = ctx->twid.as<T>();
         a.dft = dft_acc;
@@ -1763,14 +1764,14 @@ esi_status dscg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, cons
 // (Eq. "idtft"), then an adjoint modelling of its traces whose output is folded block by
 // block into the frequency slices (Eq. "dtft"; the imaginary part's twiddles turned by j);
 // then lambda B^2 G qbar per cell (G = F F^H / nt).  No space-time vector is stored: the
-// sources and the adjoint output pass through DFT_BLOCK-step stashes.
+// sources and the adjoint output pass through dft_k-step stashes.
 template <typename T>
 esi_status fdcg_impl(esi_ctx *ctx, double lambda, double tol, int max_iter, const void *dobs,
                      const double *freqs, int nf, int precond, void *qbar_out, double eps_in,
                      esi_cg_report *rep) {
     using clk = std::chrono::steady_clock;
     const auto t_start = clk::now();
-    const int ns = ctx->ns, nt = ctx->nt, K = DFT_BLOCK;
+    const int ns = ctx->ns, nt = ctx->nt, K = ctx->dft_k;
     if (nf < 1 || nf > FD_MAXF)
         return ctx->fail(ESI_ERR_ARG, "need 1 .. " + std::to_string(FD_MAXF) + " frequencies");
     for (int m = 0; m < nf; ++m)
@@ -2393,6 +2394,11 @@ ESI_API esi_status esi_create(esi_ctx **out, const esi_grid *grid, const esi_geo
         ctx->nzc = step3_chunks(g.nz, (long long)ctx->ntx * ctx->nty * geom->ns, ctx->esz);
         ctx->ntz = ctx->nzc;
         ctx->ntiles = ctx->ntx * ctx->nty * ctx->nzc;
+    }
+    {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) total_b = 0;
+        ctx->dft_k = dft_block_steps((long long)ctx->ns * ctx->sst * ctx->esz, total_b);
     }
     if (const char *ev = std::getenv("ESI_NO_GRAPHS")) ctx->use_graphs = ev[0] == '0';
     if (const char *ev = std::getenv("ESI_PDL")) ctx->pdl = ev[0] != '0';

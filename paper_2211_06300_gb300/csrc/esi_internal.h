@@ -267,10 +267,16 @@ cudaError_t launch_ckpt_decode(const uint16_t *fine, const uint16_t *coarse, con
                                const float *cscale, int ns, int nz, int ny, int nx, int px,
                                long long sst, int kind, const T *base, T *u, cudaStream_t st);
 
+// Blocked DTFT: a context stashes the new states of DFT_BLOCK_MAX, 32 or DFT_BLOCK steps at a
+// time, the longest block whose stash fits its budget (dft_block_steps); longer blocks read
+// and write the accumulators less often.
+constexpr int DFT_BLOCK_MAX = 64;
+int dft_block_steps(long long stash_plane_bytes, size_t device_bytes);
+
 // Blocked DTFT: acc [ns][nf][sst][2] += sum_k snap[k][ns][sst] (cos, sin)(twid[k][nf]) over the
-// K stashed states of one block.  Rows of px cells of which nx are real: 16-byte chunks that
-// lie wholly in the pad are skipped (the step kernels never write them, so the stash holds
-// whatever the memory held there; the accumulators keep their zero pads).
+// K <= DFT_BLOCK_MAX stashed states of one block.  Rows of px cells of which nx are real:
+// 16-byte chunks that lie wholly in the pad are skipped (the step kernels never write them,
+// so the stash holds whatever the memory held there; the accumulators keep their zero pads).
 template <typename T>
 cudaError_t launch_dft_block(const T *snap, int K, int ns, long long sst, int nx, int px, int nf,
                              const T *twid, T *acc, cudaStream_t st);

@@ -706,7 +706,7 @@ cudaError_t launch_ckpt_decode(const uint16_t *fine, const uint16_t *coarse, con
 namespace {
 
 // Blocked DTFT (Eq. "dtft"): acc[s][m][cell] += sum_k snap[k][s][cell] e^{+j 2 pi f_m t_k} for
-// the K <= DFT_BLOCK states of one block, twid[k][m] = (cos, sin) of their phases.  A thread
+// the K <= DFT_BLOCK_MAX states of one block, twid[k][m] = (cos, sin) of their phases.  A thread
 // takes 16 bytes of cells (pads included: they hold zeros, chunks wholly in the pad are
 // skipped) and M frequencies in registers, so the K stash planes are read once for up to
 // M = 8 frequencies; the block's twiddles of those frequencies are staged in shared memory,
@@ -719,7 +719,7 @@ __global__ void __launch_bounds__(RT) dft_block_kernel(const T *snap, int K, int
                                                        int nx, int px, int nf, const T *twid,
                                                        T *acc) {
     constexpr int VEC = V16<T>::n;
-    __shared__ T tw[DFT_BLOCK][M][2];
+    __shared__ T tw[DFT_BLOCK_MAX][M][2];
     const int s = blockIdx.y;
     const long long nch = sst / VEC;
     const T *sn0 = snap + (long long)s * sst;
@@ -957,10 +957,19 @@ cudaError_t go_dft_block(const T *snap, int K, int ns, long long sst, int nx, in
 }
 }  // namespace
 
+// The longest block (DFT_BLOCK_MAX, 32 or DFT_BLOCK steps) whose stash, steps x the bytes of
+// one stashed state of every shot, takes at most 1/16 of the device's memory: the
+// accumulators are read and written once per block, the stash twice per step.
+int dft_block_steps(long long stash_plane_bytes, size_t device_bytes) {
+    int k = DFT_BLOCK_MAX;
+    while (k > DFT_BLOCK && (double)k * (double)stash_plane_bytes > (double)device_bytes / 16.0) k /= 2;
+    return k;
+}
+
 template <typename T>
 cudaError_t launch_dft_block(const T *snap, int K, int ns, long long sst, int nx, int px, int nf,
                              const T *twid, T *acc, cudaStream_t st) {
-    if (K < 1 || K > DFT_BLOCK || nf < 1) return cudaErrorInvalidValue;
+    if (K < 1 || K > DFT_BLOCK_MAX || nf < 1) return cudaErrorInvalidValue;
     switch (std::min(nf, DFT_MCH)) {
         case 1: return go_dft_block<T, 1>(snap, K, ns, sst, nx, px, nf, twid, acc, st);
         case 2: return go_dft_block<T, 2>(snap, K, ns, sst, nx, px, nf, twid, acc, st);

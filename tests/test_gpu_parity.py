@@ -544,7 +544,8 @@ def test_3d_wri_and_data_space_fp64():
 def test_frequency_domain_cg_matches_oracle(prec, pc):
     """Frequency-domain ESI by time-domain modelling (Eq. "dtft", "idtft", "normaldtft"):
     iterates of F A F^H qbar / nt = F S^T d at three frequencies against the oracle, several
-    shots, nt not a multiple of the 16-step DTFT block (a ragged block in both directions)."""
+    shots, nt not a multiple of the DTFT block (64 steps at this size: one full block and a
+    ragged one, in both directions)."""
     v, geom, p = _ragged_case(nt=83)
     # the second shot's single receiver (bottom-right corner) records nothing above FP32
     # resolution within 83 steps (1e-43): move it within reach of its source
@@ -620,10 +621,10 @@ def test_stale_device_memory_does_not_reach_results():
 
 
 def test_frequency_domain_cg_3d_fp64():
-    """The same solve on a 3D volume with two z chunks and ragged x / y tiles, nt shorter
-    than three DTFT blocks."""
+    """The same solve on a 3D volume with two z chunks and ragged x / y tiles, nt not a
+    multiple of the DTFT block (one full 64-step block and a ragged one)."""
     shape = (70, 21, 37)
-    dx, dt, nt, nb = 10.0, 1e-3, 37, 4
+    dx, dt, nt, nb = 10.0, 1e-3, 83, 4
     v = synth.dipping_layers(shape, dx, 3, nlayers=3, vmin=1500, vmax=2500, nanom=1,
                              sigma=3 * dx)
     geom = synth.surface_grid_3d((183.0, 96.5, 333.0), np.array([35.0, 122.5, 300.0]),
