@@ -294,7 +294,8 @@ constexpr float CODEC_RANGE = 32768.0f;  // max |u| of a snapshot maps to this m
 // the decoded coarse part, so the decoder reproduces x to the fine part's rounding.  FP16
 // parts carry a per-shot scale (max |part| -> CODEC_RANGE, for FP16's narrow exponent
 // range); BF16 has the exponent range of FP32 and is stored unscaled (scale 1).
-// Kernels walk rows of x (one (z, y) row per block iteration): no per-element division.
+// The fine and decode kernels give each thread 8 cells of a row (16-byte loads and stores);
+// the coarse kernel walks the rows of the even cells.
 struct CkDims {
     int nz, ny, nx, px;
     int ncz, ncy, ncx;
@@ -311,36 +312,69 @@ __device__ __forceinline__ uint16_t ck_enc(float y, int kind) {
                                 : __bfloat16_as_ushort(__float2bfloat16_rn(y));
 }
 
-// The coarse rows that row (z, y) interpolates from: one or two along z times one or two
-// along y (an odd index takes its even neighbours, the last one its left one twice).
+// The coarse rows that row (z, y) interpolates from: (z0, y0), (z0, y1), (z1, y0), (z1, y1),
+// where an odd index takes its even neighbours (the last one its left one twice) and an even
+// one its own row; zo / yo: whether the second row along z / y enters the mean.
 struct CkRows {
-    const uint16_t *r[4];
-    int n;
+    const uint16_t *r00, *r01, *r10, *r11;
+    bool zo, yo;
 };
 
 __device__ __forceinline__ CkRows ck_rows(const uint16_t *cs, const CkDims &d, int z, int y) {
     const int z0 = z >> 1, z1 = (z & 1) ? min(z0 + 1, d.ncz - 1) : z0;
     const int y0 = y >> 1, y1 = (y & 1) ? min(y0 + 1, d.ncy - 1) : y0;
     CkRows c;
-    c.n = 0;
-    const int zs[2] = {z0, z1}, ys[2] = {y0, y1};
-    for (int a = 0; a < ((z & 1) ? 2 : 1); ++a)
-        for (int b = 0; b < ((y & 1) ? 2 : 1); ++b)
-            c.r[c.n++] = cs + ((long long)zs[a] * d.ncy + ys[b]) * d.ncx;
+    c.r00 = cs + ((long long)z0 * d.ncy + y0) * d.ncx;
+    c.r01 = cs + ((long long)z0 * d.ncy + y1) * d.ncx;
+    c.r10 = cs + ((long long)z1 * d.ncy + y0) * d.ncx;
+    c.r11 = cs + ((long long)z1 * d.ncy + y1) * d.ncx;
+    c.zo = (z & 1) != 0;
+    c.yo = (y & 1) != 0;
     return c;
 }
 
-// U(coarse) at column x of a row, in T (the same arithmetic in the encoder and the decoder)
+// Cells per thread of the fine and decode kernels: 16 bytes of codes, 16-byte loads of the
+// state (rows are px = a multiple of 32 cells long, so chunks never straddle rows).
+constexpr int CK_CH = 8;
+
+// U(coarse) at the CK_CH cells x0 .. x0 + 7 of a row (x0 a multiple of 8), in T, the same
+// arithmetic in the encoder and the decoder: the decoded coarse values of columns
+// x0/2 .. x0/2 + 4 (clamped to the last column) summed over the row's coarse rows; an even
+// cell takes its column's mean, an odd one the mean of its two columns.
 template <typename T>
-__device__ __forceinline__ T ck_interp(const CkRows &c, float cscale, const CkDims &d, int x,
-                                       int kind) {
-    const int x0 = x >> 1, x1 = (x & 1) ? min(x0 + 1, d.ncx - 1) : x0;
-    T acc = T(0);
-    for (int j = 0; j < c.n; ++j) {
-        acc += T(ck_dec(c.r[j][x0], kind) * cscale);
-        if (x & 1) acc += T(ck_dec(c.r[j][x1], kind) * cscale);
+__device__ __forceinline__ void ck_interp8(const CkRows &c, float cscale, const CkDims &d, int x0,
+                                           int kind, T out[CK_CH]) {
+    const int k0 = x0 >> 1;
+    T col[CK_CH / 2 + 1];
+#pragma unroll
+    for (int j = 0; j <= CK_CH / 2; ++j) {
+        const int k = min(k0 + j, d.ncx - 1);
+        T acc = T(ck_dec(c.r00[k], kind) * cscale);
+        if (c.yo) acc += T(ck_dec(c.r01[k], kind) * cscale);
+        if (c.zo) {
+            acc += T(ck_dec(c.r10[k], kind) * cscale);
+            if (c.yo) acc += T(ck_dec(c.r11[k], kind) * cscale);
+        }
+        col[j] = acc;
     }
-    return acc * T(1.0 / (c.n * ((x & 1) ? 2 : 1)));
+    const int n = (c.zo ? 2 : 1) * (c.yo ? 2 : 1);
+    const T w1 = T(1.0 / n), w2 = T(0.5 / n);
+#pragma unroll
+    for (int m = 0; m < CK_CH / 2; ++m) {
+        out[2 * m] = col[m] * w1;
+        out[2 * m + 1] = (col[m] + col[m + 1]) * w2;
+    }
+}
+
+// CK_CH consecutive values of a state (16-byte aligned)
+template <typename T>
+__device__ __forceinline__ void ck_load8(const T *p, T v[CK_CH]) {
+#pragma unroll
+    for (int h = 0; h < CK_CH / V16<T>::n; ++h) {
+        const V16<T> t = reinterpret_cast<const V16<T> *>(p)[h];
+#pragma unroll
+        for (int i = 0; i < V16<T>::n; ++i) v[h * V16<T>::n + i] = t.v[i];
+    }
 }
 
 template <typename T>
@@ -384,7 +418,8 @@ __global__ void ck_coarse_kernel(const T *u, const T *sub, CkDims d, int pass, i
     }
 }
 
-// the fine part: pass 0 max |x - U(coarse)| (FP16 only), pass 1 the codes (pads 0)
+// the fine part: pass 0 max |x - U(coarse)| (FP16 only), pass 1 the codes (pads 0); a thread
+// takes CK_CH cells of a row at a time
 template <typename T>
 __global__ void ck_fine_kernel(const T *u, const T *sub, CkDims d, int pass, int kind,
                                unsigned *bits, const uint16_t *coarse, const float *cscale,
@@ -403,21 +438,40 @@ __global__ void ck_fine_kernel(const T *u, const T *sub, CkDims d, int pass, int
         fscale[s] = 1.0f;
     }
     uint16_t *fs = fine + s * d.sst;
+    const int cpr = d.px / CK_CH;   // chunks per row
+    const long long nch = (long long)d.nz * d.ny * cpr;
     float m = 0.0f;
-    for (int row = blockIdx.x; row < d.nz * d.ny; row += gridDim.x) {
-        const int z = row / d.ny, yy = row - z * d.ny;
-        const CkRows c = ck_rows(cs, d, z, yy);
-        const long long base = (long long)row * d.px;
-        for (int xx = threadIdx.x; xx < d.px; xx += blockDim.x) {
-            if (xx >= d.nx) {
-                if (pass == 1) fs[base + xx] = 0;
-                continue;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nch;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long row = q / cpr;
+        const int x0 = (int)(q - row * cpr) * CK_CH;
+        const long long base = row * d.px + x0;
+        uint16_t code[CK_CH];
+#pragma unroll
+        for (int i = 0; i < CK_CH; ++i) code[i] = 0;
+        if (x0 < d.nx) {
+            const int z = (int)(row / d.ny), yy = (int)(row - (long long)z * d.ny);
+            T ip[CK_CH], xv[CK_CH], yv[CK_CH];
+            ck_interp8<T>(ck_rows(cs, d, z, yy), sc, d, x0, kind, ip);
+            ck_load8<T>(x + base, xv);
+            if (y) ck_load8<T>(y + base, yv);
+#pragma unroll
+            for (int i = 0; i < CK_CH; ++i) {
+                if (x0 + i >= d.nx) continue;   // pad cells: code 0
+                const float v = float((y ? xv[i] - yv[i] : xv[i]) - ip[i]);
+                if (pass == 0)
+                    m = fmaxf(m, fabsf(v));
+                else
+                    code[i] = ck_enc(kind == ESI_CKPT_F16 ? __fmul_rn(v, inv) : v, kind);
             }
-            const float v = float(ck_value(x, y, base + xx) - ck_interp<T>(c, sc, d, xx, kind));
-            if (pass == 0)
-                m = fmaxf(m, fabsf(v));
-            else
-                fs[base + xx] = ck_enc(kind == ESI_CKPT_F16 ? __fmul_rn(v, inv) : v, kind);
+        }
+        if (pass == 1) {
+            uint4 w;
+            w.x = code[0] | ((unsigned)code[1] << 16);
+            w.y = code[2] | ((unsigned)code[3] << 16);
+            w.z = code[4] | ((unsigned)code[5] << 16);
+            w.w = code[6] | ((unsigned)code[7] << 16);
+            *reinterpret_cast<uint4 *>(fs + base) = w;
         }
     }
     if (pass == 0) {
@@ -427,7 +481,8 @@ __global__ void ck_fine_kernel(const T *u, const T *sub, CkDims d, int pass, int
     }
 }
 
-// x = U(coarse) + fine; with `base`, u_{n-1} = base - x (base holds the decoded u_n)
+// x = U(coarse) + fine; with `base`, u_{n-1} = base - x (base holds the decoded u_n); a thread
+// takes CK_CH cells of a row at a time
 template <typename T>
 __global__ void ck_decode_kernel(const uint16_t *fine, const uint16_t *coarse,
                                  const float *fscale, const float *cscale, CkDims d, int kind,
@@ -438,17 +493,37 @@ __global__ void ck_decode_kernel(const uint16_t *fine, const uint16_t *coarse,
     const float sc = cscale[s], sf = fscale[s];
     T *x = u + s * d.sst;
     const T *b = base ? base + s * d.sst : nullptr;
-    for (int row = blockIdx.x; row < d.nz * d.ny; row += gridDim.x) {
-        const int z = row / d.ny, yy = row - z * d.ny;
-        const CkRows c = ck_rows(cs, d, z, yy);
-        const long long base_i = (long long)row * d.px;
-        for (int xx = threadIdx.x; xx < d.px; xx += blockDim.x) {
-            T v = T(0);   // pad columns stay zero
-            if (xx < d.nx) {
-                v = ck_interp<T>(c, sc, d, xx, kind) + T(__fmul_rn(ck_dec(fs[base_i + xx], kind), sf));
-                if (b) v = b[base_i + xx] - v;
+    const int cpr = d.px / CK_CH;
+    const long long nch = (long long)d.nz * d.ny * cpr;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nch;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long row = q / cpr;
+        const int x0 = (int)(q - row * cpr) * CK_CH;
+        const long long off = row * d.px + x0;
+        T v[CK_CH];
+#pragma unroll
+        for (int i = 0; i < CK_CH; ++i) v[i] = T(0);   // pad columns stay zero
+        if (x0 < d.nx) {
+            const int z = (int)(row / d.ny), yy = (int)(row - (long long)z * d.ny);
+            T ip[CK_CH], bv[CK_CH];
+            ck_interp8<T>(ck_rows(cs, d, z, yy), sc, d, x0, kind, ip);
+            const uint4 w = *reinterpret_cast<const uint4 *>(fs + off);
+            const unsigned wd[4] = {w.x, w.y, w.z, w.w};
+            if (b) ck_load8<T>(b + off, bv);
+#pragma unroll
+            for (int i = 0; i < CK_CH; ++i) {
+                if (x0 + i >= d.nx) continue;
+                const uint16_t code = (uint16_t)(wd[i >> 1] >> ((i & 1) * 16));
+                const T t = ip[i] + T(__fmul_rn(ck_dec(code, kind), sf));
+                v[i] = b ? bv[i] - t : t;
             }
-            x[base_i + xx] = v;
+        }
+#pragma unroll
+        for (int h = 0; h < CK_CH / V16<T>::n; ++h) {
+            V16<T> o;
+#pragma unroll
+            for (int i = 0; i < V16<T>::n; ++i) o.v[i] = v[h * V16<T>::n + i];
+            reinterpret_cast<V16<T> *>(x + off)[h] = o;
         }
     }
 }
@@ -678,7 +753,9 @@ cudaError_t launch_ckpt_encode(const T *u, const T *sub, int ns, int nz, int ny,
                                uint16_t *coarse, float *fscale, float *cscale, cudaStream_t st) {
     const CkDims d = ck_dims(nz, ny, nx, px, sst);
     const bool scaled = kind == ESI_CKPT_F16;
-    const dim3 gc(std::min(d.ncz * d.ncy, 2048), ns), gf(std::min(nz * ny, 4096), ns);
+    if (px % CK_CH != 0) return cudaErrorInvalidValue;
+    const dim3 gc(std::min(d.ncz * d.ncy, 2048), ns),
+        gf(blocks_for((long long)nz * ny * (px / CK_CH), 4096), ns);
     if (scaled) {
         cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(unsigned) * 2 * ns, st);
         if (e != cudaSuccess) return e;
@@ -698,8 +775,9 @@ cudaError_t launch_ckpt_decode(const uint16_t *fine, const uint16_t *coarse, con
                                const float *cscale, int ns, int nz, int ny, int nx, int px,
                                long long sst, int kind, const T *base, T *u, cudaStream_t st) {
     const CkDims d = ck_dims(nz, ny, nx, px, sst);
-    ck_decode_kernel<T><<<dim3(std::min(nz * ny, 4096), ns), RT, 0, st>>>(fine, coarse, fscale,
-                                                                          cscale, d, kind, base, u);
+    if (px % CK_CH != 0) return cudaErrorInvalidValue;
+    ck_decode_kernel<T><<<dim3(blocks_for((long long)nz * ny * (px / CK_CH), 4096), ns), RT, 0,
+                          st>>>(fine, coarse, fscale, cscale, d, kind, base, u);
     return cudaGetLastError();
 }
 
