@@ -131,11 +131,11 @@ def traffic_per_launch(entry):
 
 
 def pinned_like(t):
-    """A page-locked host buffer of t's shape and type, made before a timed loop: copies
-    from the device into it run at the link's speed (a pageable target goes through a
-    staging buffer)."""
+    """A page-locked host buffer of t's shape and type, made (and its pages touched, by the
+    zero fill) before a timed loop: copies from the device into it run at the link's speed
+    (a pageable target goes through a staging buffer)."""
     import torch
-    return torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+    return torch.zeros(t.shape, dtype=t.dtype, pin_memory=True)
 
 
 # ----------------------------------------------------------------------------- clocks
