@@ -103,8 +103,32 @@ ESI_API void esi_destroy(esi_ctx *ctx);
 /* Replace the context's stream (cudaStream_t). */
 ESI_API esi_status esi_set_stream(esi_ctx *ctx, void *stream);
 
-/* Replace the velocity model (same grid, same sponge reference); device pointer. */
+/* Replace the velocity model (same grid, same sponge reference); device pointer.  Shot
+ * groups (esi_set_shot_groups) follow it. */
 ESI_API esi_status esi_set_velocity(esi_ctx *ctx, const void *velocity_dev);
+
+/*
+ * esi_set_shot_groups -- run the context's shots as `groups` concurrent groups.  The paper's
+ * shots are independent systems (one extended source q and one normal equation per shot),
+ * so the batch can be split: the context makes child contexts over contiguous shot ranges
+ * (shot s in group k when k ns / groups <= s < (k + 1) ns / groups), each with a stream of
+ * its own, and esi_cg_solve (plain or diagonal preconditioner), esi_gradient and
+ * esi_dft_extract then run every group in a host thread of its own: their launches, host
+ * synchronisations and the partly filled last wave of each step launch overlap.  Per-shot
+ * outputs are those of the ungrouped context (each group writes its shots' slices); the
+ * gradient, a sum over shots, is the groups' partial sums added in group order by a
+ * kernel, and the misfit likewise.  The CG report gives per-shot iterations and residual
+ * histories as before; its phase times are the longest group's.  The other calls, and the
+ * learned preconditioner, run on the context itself.  Each call's groups start after the
+ * work already queued on the context stream, which then waits for all of them.
+ * esi_set_profiling, esi_get_profile (entries merged by name, times summed over the groups'
+ * streams) and esi_launch_count include the groups.
+ *   groups       : 1 .. ns (1 removes the groups)
+ *   velocity_dev : the current velocity model, as for esi_create (device pointer)
+ * The groups own their scratch (per shot, as the context would).  Synchronises the context
+ * stream.  Errors: ESI_ERR_ARG (groups outside 1 .. ns, no velocity), those of esi_create.
+ */
+ESI_API esi_status esi_set_shot_groups(esi_ctx *ctx, int groups, const void *velocity_dev);
 
 /*
  * esi_forward -- forward modelling d = R A^{-1} q for every shot (Eq. "fwi", "wave").
@@ -325,7 +349,8 @@ ESI_API esi_status esi_cg_solve(esi_ctx *ctx, double lambda, double tol, int max
  * frequencies, qbar: per shot nf complex fields.  The observed data enter as the time series
  * d.  CG runs in the real representation with Re <x, y> as inner product.  Each product
  * synthesises the real and the imaginary part of F^H qbar / nt block by block into a
- * 16-step source stash during two forward modellings, folds the two adjoint modellings of
+ * K-step source stash (K = 16, 32 or 64 steps, the longest whose stash fits in 1/16 of the
+ * device memory) during two forward modellings, folds the two adjoint modellings of
  * their traces block by block into the frequency slices, and adds lambda B^2 (F F^H / nt)
  * qbar per cell; no space-time vector is stored (the CG vectors hold 2 nf values per cell).
  *   dobs_dev     : device seismogram-layout observed data d

@@ -11,6 +11,8 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
+#include <type_traits>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -26,6 +28,11 @@ namespace {
 // second difference is -4 (W1 + W3) / dx^2 per axis, which fixes the leapfrog CFL bound.
 constexpr double CFL_W1 = 8.0 / 5.0, CFL_W3 = 8.0 / 315.0;
 
+// Device allocations and graph captures are serialised over the threads of the process:
+// contexts of concurrent shot groups run in threads of their own, and freeing device memory
+// synchronises the device, which must not meet another thread's stream capture.
+std::recursive_mutex g_dev_mu;
+
 struct DBuf {
     void *p = nullptr;
     size_t n = 0;
@@ -33,10 +40,14 @@ struct DBuf {
     DBuf(const DBuf &) = delete;
     DBuf &operator=(const DBuf &) = delete;
     ~DBuf() {
-        if (p) cudaFree(p);
+        if (p) {
+            std::lock_guard<std::recursive_mutex> lk(g_dev_mu);
+            cudaFree(p);
+        }
     }
     cudaError_t ensure(size_t bytes) {
         if (bytes <= n && p) return cudaSuccess;
+        std::lock_guard<std::recursive_mutex> lk(g_dev_mu);
         if (p) cudaFree(p);
         p = nullptr;
         n = 0;
@@ -140,8 +151,26 @@ struct esi_ctx {
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> evpool;
     std::vector<Stat> stats;
+    // concurrent shot groups (esi_set_shot_groups): child contexts over contiguous shot
+    // ranges, each on a stream of its own; the batch calls fan out to them
+    std::vector<esi_ctx *> grp;
+    std::vector<int> grp_s0;           // first shot of each group, then ns
+    std::vector<cudaStream_t> grp_st;
+    std::vector<cudaEvent_t> grp_ev;   // [0] fork, [1 + g] join of group g
+    DBuf grp_grad;                     // the groups' partial gradients [G][N]
+
+    void clear_groups() {
+        for (auto *c : grp) esi_destroy(c);
+        for (auto st : grp_st) cudaStreamDestroy(st);
+        for (auto ev : grp_ev) cudaEventDestroy(ev);
+        grp.clear();
+        grp_s0.clear();
+        grp_st.clear();
+        grp_ev.clear();
+    }
 
     ~esi_ctx() {
+        clear_groups();
         if (pc) pcnet_destroy(pc);
         for (auto &g : graphs) cudaGraphExecDestroy(g.exec);
         if (cap) cudaStreamDestroy(cap);
@@ -686,6 +715,7 @@ bool graph_replay(esi_ctx *ctx, const std::vector<unsigned char> &key, esi_statu
 template <typename F>
 esi_status graph_capture(esi_ctx *ctx, std::vector<unsigned char> &&key, F &&body) {
     if (!ctx->cap) CK(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
+    std::lock_guard<std::recursive_mutex> lk(g_dev_mu);   // no allocation meets the capture
     cudaStream_t user = ctx->st;
     const long long l0 = ctx->launches;
     CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
@@ -2280,6 +2310,72 @@ esi_status create_impl(esi_ctx *ctx, const void *vel) {
 #define DISPATCH(ctx, call)                                          \
     ((ctx)->g.dtype == ESI_F64 ? call<double> : call<float>)
 
+namespace {
+// Runs fn(g, child) for every shot group, the first in the calling thread and the others in
+// threads of their own, so that the groups' launches, host syncs and tails overlap.  Each
+// group's stream first waits for the work queued so far on the context stream (the caller's
+// inputs), and the context stream then waits for every group.  A failing group's status and
+// message become the call's (ESI_ERR_NOT_CONVERGED only when no group failed otherwise).
+template <typename Fn>
+esi_status run_groups(esi_ctx *ctx, Fn &&fn) {
+    const int G = (int)ctx->grp.size();
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaEventRecord(ctx->grp_ev[0], ctx->st));
+    for (int g = 0; g < G; ++g) CK(cudaStreamWaitEvent(ctx->grp_st[g], ctx->grp_ev[0], 0));
+    std::vector<esi_status> st(G, ESI_OK);
+    std::vector<std::string> msg(G);
+    auto one = [&](int g) {
+        try {
+            st[g] = fn(g, ctx->grp[g]);
+        } catch (const std::exception &ex) {
+            st[g] = ESI_ERR_CUDA;
+            msg[g] = ex.what();
+        }
+    };
+    std::vector<std::thread> th;
+    for (int g = 1; g < G; ++g)
+        th.emplace_back([&, g]() {
+            if (cudaSetDevice(dev) != cudaSuccess) {
+                st[g] = ESI_ERR_CUDA;
+                msg[g] = "cudaSetDevice failed in a shot-group thread";
+                return;
+            }
+            one(g);
+        });
+    one(0);
+    for (auto &t : th) t.join();
+    for (int g = 0; g < G; ++g) {
+        CK(cudaEventRecord(ctx->grp_ev[1 + g], ctx->grp_st[g]));
+        CK(cudaStreamWaitEvent(ctx->st, ctx->grp_ev[1 + g], 0));
+    }
+    esi_status out = ESI_OK;
+    for (int g = 0; g < G; ++g) {
+        if (st[g] == ESI_OK) continue;
+        if (st[g] == ESI_ERR_NOT_CONVERGED) {
+            out = ESI_ERR_NOT_CONVERGED;
+            continue;
+        }
+        return ctx->fail(st[g], "shot group " + std::to_string(g) + ": " +
+                                    (msg[g].empty() ? ctx->grp[g]->err : msg[g]));
+    }
+    return out;
+}
+
+// byte offset of shot s in a seismogram-layout buffer and in a [ns][nt][N] field
+inline size_t trace_off(const esi_ctx *ctx, int s) {
+    return (size_t)ctx->rec_off[s] * ctx->nt * ctx->esz;
+}
+inline size_t field_off(const esi_ctx *ctx, int s) {
+    return (size_t)s * ctx->nt * ctx->N * ctx->esz;
+}
+template <typename P>
+P *at(P *p, size_t bytes) {   // p + bytes, NULL stays NULL
+    using B = typename std::conditional<std::is_const<P>::value, const char, char>::type;
+    return p ? reinterpret_cast<P *>(reinterpret_cast<B *>(p) + bytes) : nullptr;
+}
+}  // namespace
+
 extern "C" {
 
 ESI_API const char *esi_status_string(esi_status s) {
@@ -2305,7 +2401,12 @@ ESI_API const char *esi_last_error(const esi_ctx *ctx) {
     return ctx ? ctx->err.c_str() : g_create_error.c_str();
 }
 
-ESI_API long long esi_launch_count(const esi_ctx *ctx) { return ctx ? ctx->launches : 0; }
+ESI_API long long esi_launch_count(const esi_ctx *ctx) {
+    if (!ctx) return 0;
+    long long n = ctx->launches;
+    for (const auto *c : ctx->grp) n += c->launches;
+    return n;
+}
 
 ESI_API esi_status esi_set_profiling(esi_ctx *ctx, int on) {
     if (!ctx) return ESI_ERR_ARG;
@@ -2317,6 +2418,7 @@ ESI_API esi_status esi_set_profiling(esi_ctx *ctx, int on) {
     ctx->pending.clear();
     ctx->stats.clear();
     ctx->prof = on != 0;
+    for (auto *c : ctx->grp) esi_set_profiling(c, on);
     return ESI_OK;
 }
 
@@ -2342,6 +2444,28 @@ ESI_API int esi_get_profile(esi_ctx *ctx, esi_kernel_stat *out, int max) {
         ctx->evpool.push_back(p.b);
     }
     ctx->pending.clear();
+    // the shot groups' runs, merged by name (their times are per group stream: groups run
+    // at the same time, so a merged time is the sum over groups of overlapping spans)
+    for (auto *c : ctx->grp) {
+        const int nc = esi_get_profile(c, nullptr, 0);
+        std::vector<esi_kernel_stat> tmp(nc);
+        esi_get_profile(c, tmp.data(), nc);
+        for (const auto &k : tmp) {
+            esi_ctx::Stat *st = nullptr;
+            for (auto &x : ctx->stats)
+                if (x.name == k.name) st = &x;
+            if (!st) {
+                ctx->stats.push_back(esi_ctx::Stat());
+                st = &ctx->stats.back();
+                st->name = k.name;
+                st->bpc = k.bytes_per_cell;
+            }
+            st->launches += k.launches;
+            st->cells += k.cells;
+            st->ms += k.ms;
+        }
+        esi_set_profiling(c, c->prof);   // consumed: the group's stats start again
+    }
     const int n = (int)ctx->stats.size();
     for (int i = 0; i < n && i < max && out; ++i) {
         std::memset(out[i].name, 0, sizeof(out[i].name));
@@ -2428,10 +2552,72 @@ ESI_API esi_status esi_set_stream(esi_ctx *ctx, void *stream) {
     return ESI_OK;
 }
 
+
+ESI_API esi_status esi_set_shot_groups(esi_ctx *ctx, int groups, const void *velocity_dev) {
+    if (!ctx) return ESI_ERR_ARG;
+    if (groups < 1 || groups > ctx->ns)
+        return ctx->fail(ESI_ERR_ARG, "groups must lie in 1 .. the number of shots");
+    if (groups > 1 && !velocity_dev) return ctx->fail(ESI_ERR_ARG, "velocity_dev is NULL");
+    ctx->err.clear();
+    CK(cudaStreamSynchronize(ctx->st));
+    ctx->clear_groups();
+    if (groups == 1) return ESI_OK;
+    esi_grid g = ctx->g;
+    g.sponge_vref = ctx->vref;   // the groups' sponges take the context's reference velocity
+    for (int k = 0; k < groups; ++k) {
+        const int s0 = (int)((long long)k * ctx->ns / groups);
+        const int s1 = (int)((long long)(k + 1) * ctx->ns / groups);
+        std::vector<long long> off(s1 - s0 + 1);
+        for (int s = s0; s <= s1; ++s) off[s - s0] = ctx->rec_off[s] - ctx->rec_off[s0];
+        esi_geometry sub;
+        sub.ns = s1 - s0;
+        sub.src_xyz = ctx->src_xyz.data() + 3 * (size_t)s0;
+        sub.rec_offset = off.data();
+        sub.rec_xyz = ctx->rec_xyz.data() + 3 * (size_t)ctx->rec_off[s0];
+        cudaStream_t st = nullptr;
+        cudaError_t ce = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (ce != cudaSuccess) {
+            ctx->clear_groups();
+            return ctx->fail(ESI_ERR_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(ce));
+        }
+        ctx->grp_st.push_back(st);
+        esi_ctx *c = nullptr;
+        const esi_status e = esi_create(&c, &g, &sub, velocity_dev, ctx->dt, ctx->nt, st);
+        if (e != ESI_OK) {
+            const std::string m = esi_last_error(nullptr);
+            ctx->clear_groups();
+            return ctx->fail(e, "shot group " + std::to_string(k) + ": " + m);
+        }
+        c->use_graphs = ctx->use_graphs;
+        c->pdl = ctx->pdl;
+        c->prof = ctx->prof;
+        ctx->grp.push_back(c);
+        ctx->grp_s0.push_back(s0);
+    }
+    ctx->grp_s0.push_back(ctx->ns);
+    for (int k = 0; k <= groups; ++k) {
+        cudaEvent_t ev = nullptr;
+        cudaError_t ce = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (ce != cudaSuccess) {
+            ctx->clear_groups();
+            return ctx->fail(ESI_ERR_CUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(ce));
+        }
+        ctx->grp_ev.push_back(ev);
+    }
+    return ESI_OK;
+}
+
 ESI_API esi_status esi_set_velocity(esi_ctx *ctx, const void *velocity_dev) {
     if (!ctx || !velocity_dev) return ESI_ERR_ARG;
-    return ctx->g.dtype == ESI_F64 ? setup_model<double>(ctx, velocity_dev, false)
-                                   : setup_model<float>(ctx, velocity_dev, false);
+    const esi_status e = ctx->g.dtype == ESI_F64 ? setup_model<double>(ctx, velocity_dev, false)
+                                                 : setup_model<float>(ctx, velocity_dev, false);
+    if (e != ESI_OK) return e;
+    for (size_t k = 0; k < ctx->grp.size(); ++k) {
+        CK(cudaStreamSynchronize(ctx->st));   // the new model is the caller's; groups follow it
+        const esi_status ek = esi_set_velocity(ctx->grp[k], velocity_dev);
+        if (ek != ESI_OK) return ctx->fail(ek, "shot group " + std::to_string(k) + ": " + ctx->grp[k]->err);
+    }
+    return ESI_OK;
 }
 
 ESI_API esi_status esi_forward(esi_ctx *ctx, const void *wavelet_dev, const void *ext_src_dev,
@@ -2473,6 +2659,33 @@ ESI_API esi_status esi_gradient(esi_ctx *ctx, const void *wavelet_dev, const voi
         opts->ckpt_kind < ESI_CKPT_F32 || opts->ckpt_kind > ESI_CKPT_BF16)
         return ctx->fail(ESI_ERR_ARG, "bad gradient options");
     ctx->err.clear();
+    if (!ctx->grp.empty()) {
+        // each group's gradient (the sum over its shots) into [G][N] scratch, then their sum
+        const int G = (int)ctx->grp.size();
+        const size_t gb = (size_t)ctx->N * ctx->esz;
+        CK(ctx->grp_grad.ensure(G * gb));
+        std::vector<double> mis(G, 0.0);
+        const esi_status e = run_groups(ctx, [&](int k, esi_ctx *c) {
+            const int s0 = ctx->grp_s0[k];
+            return esi_gradient(c, at(wavelet_dev, (size_t)s0 * ctx->nt * ctx->esz),
+                                at(ext_src_dev, field_off(ctx, s0)), at(dobs_dev, trace_off(ctx, s0)),
+                                at(adj_src_dev, trace_off(ctx, s0)), opts,
+                                at(ctx->grp_grad.p, k * gb), misfit ? &mis[k] : nullptr);
+        });
+        if (e != ESI_OK) return e;
+        if (ctx->g.dtype == ESI_F64)
+            CKL(launch_sum_parts<double>(reinterpret_cast<double *>(grad_dev), ctx->grp_grad.as<double>(),
+                                         G, ctx->N, ctx->st));
+        else
+            CKL(launch_sum_parts<float>(reinterpret_cast<float *>(grad_dev), ctx->grp_grad.as<float>(), G,
+                                        ctx->N, ctx->st));
+        if (misfit) {
+            double t = 0.0;
+            for (double m : mis) t += m;
+            *misfit = t;
+        }
+        return ESI_OK;
+    }
     return ctx->g.dtype == ESI_F64
                ? gradient_impl<double>(ctx, wavelet_dev, ext_src_dev, dobs_dev, adj_src_dev, opts,
                                        grad_dev, misfit)
@@ -2485,6 +2698,17 @@ ESI_API esi_status esi_dft_extract(esi_ctx *ctx, const void *wavelet_dev, const 
                                    float *scales_host, void *traces_dev) {
     if (!ctx) return ESI_ERR_ARG;
     ctx->err.clear();
+    if (!ctx->grp.empty() && nf > 0) {
+        const size_t cell = out_kind == ESI_DFT_C32_HALF ? 4 : 2 * (size_t)ctx->esz;
+        return run_groups(ctx, [&](int k, esi_ctx *c) {
+            const int s0 = ctx->grp_s0[k];
+            return esi_dft_extract(c, at(wavelet_dev, (size_t)s0 * ctx->nt * ctx->esz),
+                                   at(ext_src_dev, field_off(ctx, s0)), freqs_hz, nf,
+                                   at(out_dev, (size_t)s0 * nf * ctx->N * cell), out_kind,
+                                   scales_host ? scales_host + (size_t)s0 * nf : nullptr,
+                                   at(traces_dev, trace_off(ctx, s0)));
+        });
+    }
     return ctx->g.dtype == ESI_F64
                ? dft_impl<double>(ctx, wavelet_dev, ext_src_dev, freqs_hz, nf, out_dev, out_kind,
                                   scales_host, traces_dev)
@@ -2554,6 +2778,39 @@ ESI_API esi_status esi_cg_solve(esi_ctx *ctx, double lambda, double tol, int max
     if (!dobs_dev || !q_out_dev || !(lambda >= 0) || !(tol >= 0))
         return ctx->fail(ESI_ERR_ARG, "bad CG arguments");
     ctx->err.clear();
+    if (!ctx->grp.empty() && precond != ESI_PC_LEARNED) {
+        // the network's buffers belong to this context: the learned solve runs here
+        const auto t0 = std::chrono::steady_clock::now();
+        const int G = (int)ctx->grp.size();
+        std::vector<esi_cg_report> reps(G);
+        const esi_status e = run_groups(ctx, [&](int k, esi_ctx *c) {
+            const int s0 = ctx->grp_s0[k];
+            esi_cg_report *r = nullptr;
+            if (report) {
+                reps[k] = *report;
+                reps[k].iters = report->iters ? report->iters + s0 : nullptr;
+                reps[k].rel_res = report->rel_res ? report->rel_res + (size_t)s0 * report->max_hist : nullptr;
+                r = &reps[k];
+            }
+            return esi_cg_solve(c, lambda, tol, max_iter, at(dobs_dev, trace_off(ctx, s0)),
+                                at(q_out_dev, field_off(ctx, s0)), precond, eps, r);
+        });
+        if (report && (e == ESI_OK || e == ESI_ERR_NOT_CONVERGED)) {
+            // groups ran at the same time: the phase times are the longest group's
+            report->iters_max = 0;
+            report->converged = 1;
+            report->ms_matvec = report->ms_vector = report->ms_precond = 0.0;
+            for (const auto &r : reps) {
+                report->iters_max = std::max(report->iters_max, r.iters_max);
+                report->converged &= r.converged;
+                report->ms_matvec = std::max(report->ms_matvec, r.ms_matvec);
+                report->ms_vector = std::max(report->ms_vector, r.ms_vector);
+                report->ms_precond = std::max(report->ms_precond, r.ms_precond);
+            }
+            report->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        }
+        return e;
+    }
     return ctx->g.dtype == ESI_F64
                ? cg_impl<double>(ctx, lambda, tol, max_iter, dobs_dev, q_out_dev, precond, eps, report)
                : cg_impl<float>(ctx, lambda, tol, max_iter, dobs_dev, q_out_dev, precond, eps, report);

@@ -214,6 +214,9 @@ cudaError_t launch_b2_maps(T *pb2, T *ipb2, int ns, int nz, int ny, int nx, int 
 // y = x - y over len elements
 template <typename T>
 cudaError_t launch_sub_from(T *y, const T *x, long long len, cudaStream_t st);
+// out = the sum of G consecutive partial vectors of length n (in order)
+template <typename T>
+cudaError_t launch_sum_parts(T *out, const T *parts, int G, long long n, cudaStream_t st);
 // data-space CG vectors (traces layout; shot s owns [seg[s], seg[s+1])), partials [ns][64]:
 // ap = p + kp in place over kp with <p, ap>; x += alpha p, r -= alpha ap with ||r||^2; p = r + beta p
 constexpr int DVEC_NBLK = 64;

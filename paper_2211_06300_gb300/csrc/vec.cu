@@ -1060,6 +1060,24 @@ cudaError_t launch_dft_block(const T *snap, int K, int ns, long long sst, int nx
     }
 }
 
+// out[i] = sum_g parts[g][i], g in order (the shot groups' partial gradients)
+template <typename T>
+__global__ void sum_parts_kernel(T *out, const T *parts, int G, long long n) {
+    for (long long i = (long long)blockIdx.x * RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT) {
+        T v = parts[i];
+        for (int g = 1; g < G; ++g) v += parts[(long long)g * n + i];
+        out[i] = v;
+    }
+}
+
+template <typename T>
+cudaError_t launch_sum_parts(T *out, const T *parts, int G, long long n, cudaStream_t st) {
+    sum_parts_kernel<T><<<blocks_for(n, 2048), RT, 0, st>>>(out, parts, G, n);
+    return cudaGetLastError();
+}
+template cudaError_t launch_sum_parts<float>(float *, const float *, int, long long, cudaStream_t);
+template cudaError_t launch_sum_parts<double>(double *, const double *, int, long long, cudaStream_t);
+
 template <typename T>
 cudaError_t launch_dft_output(const T *acc, long long sst, int rows, int nx, int px, int ns,
                               int nf, int half, void *out, unsigned *bits, float *scales_dev,

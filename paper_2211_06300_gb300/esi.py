@@ -33,7 +33,7 @@ EXPORTS = ["esi_create", "esi_destroy", "esi_set_stream", "esi_set_velocity", "e
            "esi_pc_fallbacks", "esi_pc_pack", "esi_pc_create", "esi_pc_destroy",
            "esi_pc_last_error", "esi_pc_set_params", "esi_pc_get_params", "esi_pc_apply",
            "esi_pc_grad", "esi_pc_vjp", "esi_pc_train_step", "esi_wri_solve", "esi_dscg_solve",
-           "esi_fdcg_solve", "esi_invert"]
+           "esi_fdcg_solve", "esi_invert", "esi_set_shot_groups"]
 
 
 class EsiGrid(ctypes.Structure):
@@ -121,6 +121,7 @@ def load_library(require_gpu: bool = True) -> ctypes.CDLL:
     L.esi_destroy.restype = None
     L.esi_set_stream.argtypes = [vp, vp]
     L.esi_set_velocity.argtypes = [vp, vp]
+    L.esi_set_shot_groups.argtypes = [vp, i, vp]
     L.esi_forward.argtypes = [vp, vp, vp, vp]
     L.esi_forward_noalloc.argtypes = [vp, vp, vp, vp]
     L.esi_adjoint.argtypes = [vp, vp, vp, vp]
@@ -168,7 +169,8 @@ def load_library(require_gpu: bool = True) -> ctypes.CDLL:
                  "esi_pc_set_params", "esi_pc_get_params", "esi_pc_apply", "esi_pc_grad",
                  "esi_pc_vjp", "esi_pc_train_step",
                  "esi_adjoint", "esi_gradient", "esi_dft_extract", "esi_cg_solve",
-                 "esi_pc_load", "esi_wri_solve", "esi_dscg_solve", "esi_fdcg_solve", "esi_invert"):
+                 "esi_pc_load", "esi_wri_solve", "esi_dscg_solve", "esi_fdcg_solve", "esi_invert",
+                 "esi_set_shot_groups"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -297,6 +299,11 @@ class Context:
     def set_velocity(self, v):
         self._v = v.contiguous()
         self._check(self.L.esi_set_velocity(self.h, _ptr(self._v)))
+
+    def set_shot_groups(self, groups: int):
+        """esi_set_shot_groups: run the shots as `groups` concurrent groups (1 removes them)."""
+        with self.torch.cuda.device(self.device):
+            self._check(self.L.esi_set_shot_groups(self.h, int(groups), _ptr(self._v)))
 
     def forward(self, wavelet=None, ext=None, out=None):
         out = self.empty_traces() if out is None else out
