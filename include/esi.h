@@ -112,14 +112,16 @@ ESI_API esi_status esi_set_velocity(esi_ctx *ctx, const void *velocity_dev);
  * shots are independent systems (one extended source q and one normal equation per shot),
  * so the batch can be split: the context makes child contexts over contiguous shot ranges
  * (shot s in group k when k ns / groups <= s < (k + 1) ns / groups), each with a stream of
- * its own, and esi_cg_solve (plain or diagonal preconditioner), esi_gradient and
+ * its own, and esi_forward, esi_adjoint, esi_normal_apply, esi_cg_solve (plain or diagonal
+ * preconditioner), esi_wri_solve, esi_dscg_solve, esi_fdcg_solve, esi_gradient and
  * esi_dft_extract then run every group in a host thread of its own: their launches, host
  * synchronisations and the partly filled last wave of each step launch overlap.  Per-shot
  * outputs are those of the ungrouped context (each group writes its shots' slices); the
  * gradient, a sum over shots, is the groups' partial sums added in group order by a
- * kernel, and the misfit likewise.  The CG report gives per-shot iterations and residual
- * histories as before; its phase times are the longest group's.  The other calls, and the
- * learned preconditioner, run on the context itself.  Each call's groups start after the
+ * kernel, and the misfit likewise.  A CG report gives per-shot iterations and residual
+ * histories as before; its phase times are the longest group's.  esi_forward_noalloc (whose
+ * fixed scratch the groups would share), esi_invert and the learned preconditioner run on
+ * the context itself.  Each call's groups start after the
  * work already queued on the context stream, which then waits for all of them.
  * esi_set_profiling, esi_get_profile (entries merged by name, times summed over the groups'
  * streams) and esi_launch_count include the groups.

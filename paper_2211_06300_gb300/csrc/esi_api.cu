@@ -2374,6 +2374,43 @@ P *at(P *p, size_t bytes) {   // p + bytes, NULL stays NULL
     using B = typename std::conditional<std::is_const<P>::value, const char, char>::type;
     return p ? reinterpret_cast<P *>(reinterpret_cast<B *>(p) + bytes) : nullptr;
 }
+
+// A CG-type solve over the groups: solve(k, child, report of group k) with the caller's
+// report arrays offset to the group's shots; the merged report has the per-shot entries of
+// every group, the largest iteration count, convergence of all, the longest group's phase
+// times and the wall clock of the whole call.
+template <typename Solve>
+esi_status run_group_solves(esi_ctx *ctx, esi_cg_report *report, Solve &&solve) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const int G = (int)ctx->grp.size();
+    std::vector<esi_cg_report> reps(G);
+    const esi_status e = run_groups(ctx, [&](int k, esi_ctx *c) {
+        const int s0 = ctx->grp_s0[k];
+        esi_cg_report *r = nullptr;
+        if (report) {
+            reps[k] = *report;
+            reps[k].iters = report->iters ? report->iters + s0 : nullptr;
+            reps[k].rel_res = report->rel_res ? report->rel_res + (size_t)s0 * report->max_hist : nullptr;
+            r = &reps[k];
+        }
+        return solve(k, c, r);
+    });
+    if (report && (e == ESI_OK || e == ESI_ERR_NOT_CONVERGED)) {
+        report->iters_max = 0;
+        report->converged = 1;
+        report->ms_matvec = report->ms_vector = report->ms_precond = 0.0;
+        for (const auto &r : reps) {
+            report->iters_max = std::max(report->iters_max, r.iters_max);
+            report->converged &= r.converged;
+            report->ms_matvec = std::max(report->ms_matvec, r.ms_matvec);
+            report->ms_vector = std::max(report->ms_vector, r.ms_vector);
+            report->ms_precond = std::max(report->ms_precond, r.ms_precond);
+        }
+        report->ms_total =
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return e;
+}
 }  // namespace
 
 extern "C" {
@@ -2625,6 +2662,12 @@ ESI_API esi_status esi_forward(esi_ctx *ctx, const void *wavelet_dev, const void
     if (!ctx) return ESI_ERR_ARG;
     if (!traces_dev) return ctx->fail(ESI_ERR_ARG, "traces_dev is NULL");
     ctx->err.clear();
+    if (!ctx->grp.empty())
+        return run_groups(ctx, [&](int k, esi_ctx *c) {
+            const int s0 = ctx->grp_s0[k];
+            return esi_forward(c, at(wavelet_dev, (size_t)s0 * ctx->nt * ctx->esz),
+                               at(ext_src_dev, field_off(ctx, s0)), at(traces_dev, trace_off(ctx, s0)));
+        });
     return ctx->g.dtype == ESI_F64
                ? forward_impl<double>(ctx, wavelet_dev, ext_src_dev, traces_dev, nullptr, 0, nullptr)
                : forward_impl<float>(ctx, wavelet_dev, ext_src_dev, traces_dev, nullptr, 0, nullptr);
@@ -2646,6 +2689,12 @@ ESI_API esi_status esi_adjoint(esi_ctx *ctx, const void *traces_dev, void *ext_o
     if (!traces_dev || (!ext_out_dev && !wavelet_out_dev))
         return ctx->fail(ESI_ERR_ARG, "need adjoint data and at least one output");
     ctx->err.clear();
+    if (!ctx->grp.empty())
+        return run_groups(ctx, [&](int k, esi_ctx *c) {
+            const int s0 = ctx->grp_s0[k];
+            return esi_adjoint(c, at(traces_dev, trace_off(ctx, s0)), at(ext_out_dev, field_off(ctx, s0)),
+                               at(wavelet_out_dev, (size_t)s0 * ctx->nt * ctx->esz));
+        });
     return ctx->g.dtype == ESI_F64 ? adjoint_impl<double>(ctx, traces_dev, ext_out_dev, wavelet_out_dev)
                                    : adjoint_impl<float>(ctx, traces_dev, ext_out_dev, wavelet_out_dev);
 }
@@ -2736,6 +2785,13 @@ ESI_API esi_status esi_fdcg_solve(esi_ctx *ctx, double lambda, double tol, int m
     if (!dobs_dev || !qbar_out_dev || !freqs_hz || !(lambda > 0) || !(tol >= 0))
         return ctx->fail(ESI_ERR_ARG, "bad frequency-domain CG arguments");
     ctx->err.clear();
+    if (!ctx->grp.empty() && nf >= 1)
+        return run_group_solves(ctx, report, [&](int k, esi_ctx *c, esi_cg_report *r) {
+            const int s0 = ctx->grp_s0[k];
+            return esi_fdcg_solve(c, lambda, tol, max_iter, at(dobs_dev, trace_off(ctx, s0)),
+                                  freqs_hz, nf, precond,
+                                  at(qbar_out_dev, (size_t)s0 * nf * ctx->N * 2 * ctx->esz), eps, r);
+        });
     return ctx->g.dtype == ESI_F64
                ? fdcg_impl<double>(ctx, lambda, tol, max_iter, dobs_dev, freqs_hz, nf, precond,
                                    qbar_out_dev, eps, report)
@@ -2750,6 +2806,13 @@ ESI_API esi_status esi_dscg_solve(esi_ctx *ctx, double lambda, double tol, int m
     if (!dobs_dev || !q_out_dev || !(lambda > 0) || !(tol >= 0))
         return ctx->fail(ESI_ERR_ARG, "bad data-space CG arguments");
     ctx->err.clear();
+    if (!ctx->grp.empty())
+        return run_group_solves(ctx, report, [&](int k, esi_ctx *c, esi_cg_report *r) {
+            const int s0 = ctx->grp_s0[k];
+            return esi_dscg_solve(c, lambda, tol, max_iter, at(dobs_dev, trace_off(ctx, s0)),
+                                  at(q_out_dev, field_off(ctx, s0)), at(w_out_dev, trace_off(ctx, s0)),
+                                  eps, r);
+        });
     return ctx->g.dtype == ESI_F64
                ? dscg_impl<double>(ctx, lambda, tol, max_iter, dobs_dev, q_out_dev, w_out_dev, eps,
                                    report)
@@ -2764,6 +2827,12 @@ ESI_API esi_status esi_wri_solve(esi_ctx *ctx, double lambda, double tol, int ma
     if (!wavelet_dev || !dobs_dev || !q_out_dev || !(lambda >= 0) || !(tol >= 0))
         return ctx->fail(ESI_ERR_ARG, "bad WRI arguments");
     ctx->err.clear();
+    if (!ctx->grp.empty())
+        return run_group_solves(ctx, report, [&](int k, esi_ctx *c, esi_cg_report *r) {
+            const int s0 = ctx->grp_s0[k];
+            return esi_wri_solve(c, lambda, tol, max_iter, at(wavelet_dev, (size_t)s0 * ctx->nt * ctx->esz),
+                                 at(dobs_dev, trace_off(ctx, s0)), at(q_out_dev, field_off(ctx, s0)), r);
+        });
     return ctx->g.dtype == ESI_F64
                ? cg_impl<double>(ctx, lambda, tol, max_iter, dobs_dev, q_out_dev, ESI_PC_NONE, 0.0,
                                  report, wavelet_dev)
@@ -2780,36 +2849,11 @@ ESI_API esi_status esi_cg_solve(esi_ctx *ctx, double lambda, double tol, int max
     ctx->err.clear();
     if (!ctx->grp.empty() && precond != ESI_PC_LEARNED) {
         // the network's buffers belong to this context: the learned solve runs here
-        const auto t0 = std::chrono::steady_clock::now();
-        const int G = (int)ctx->grp.size();
-        std::vector<esi_cg_report> reps(G);
-        const esi_status e = run_groups(ctx, [&](int k, esi_ctx *c) {
+        return run_group_solves(ctx, report, [&](int k, esi_ctx *c, esi_cg_report *r) {
             const int s0 = ctx->grp_s0[k];
-            esi_cg_report *r = nullptr;
-            if (report) {
-                reps[k] = *report;
-                reps[k].iters = report->iters ? report->iters + s0 : nullptr;
-                reps[k].rel_res = report->rel_res ? report->rel_res + (size_t)s0 * report->max_hist : nullptr;
-                r = &reps[k];
-            }
             return esi_cg_solve(c, lambda, tol, max_iter, at(dobs_dev, trace_off(ctx, s0)),
                                 at(q_out_dev, field_off(ctx, s0)), precond, eps, r);
         });
-        if (report && (e == ESI_OK || e == ESI_ERR_NOT_CONVERGED)) {
-            // groups ran at the same time: the phase times are the longest group's
-            report->iters_max = 0;
-            report->converged = 1;
-            report->ms_matvec = report->ms_vector = report->ms_precond = 0.0;
-            for (const auto &r : reps) {
-                report->iters_max = std::max(report->iters_max, r.iters_max);
-                report->converged &= r.converged;
-                report->ms_matvec = std::max(report->ms_matvec, r.ms_matvec);
-                report->ms_vector = std::max(report->ms_vector, r.ms_vector);
-                report->ms_precond = std::max(report->ms_precond, r.ms_precond);
-            }
-            report->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-        }
-        return e;
     }
     return ctx->g.dtype == ESI_F64
                ? cg_impl<double>(ctx, lambda, tol, max_iter, dobs_dev, q_out_dev, precond, eps, report)
@@ -2840,6 +2884,12 @@ ESI_API esi_status esi_normal_apply(esi_ctx *ctx, double lambda, double eps, con
     if (!ctx) return ESI_ERR_ARG;
     if (!p_dev || !out_dev || !(lambda >= 0)) return ctx->fail(ESI_ERR_ARG, "bad arguments");
     ctx->err.clear();
+    if (!ctx->grp.empty())
+        return run_groups(ctx, [&](int k, esi_ctx *c) {
+            const int s0 = ctx->grp_s0[k];
+            return esi_normal_apply(c, lambda, eps, at(p_dev, field_off(ctx, s0)),
+                                    at(out_dev, field_off(ctx, s0)));
+        });
     CK(ctx->traces.ensure(std::max<size_t>((size_t)ctx->total_rec * ctx->nt * ctx->esz, 16)));
     const double ep = eps > 0 ? eps : ctx->g.dx;
     esi_status e;

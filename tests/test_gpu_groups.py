@@ -152,3 +152,46 @@ def test_groups_follow_the_velocity_and_report_their_work():
     ctx.set_shot_groups(1)   # removes the groups: the context solves alone again
     q1, _ = ctx.cg_solve(_dev(d, "f64"), lam=2e-4, tol=0.0, max_iter=3)
     assert torch.allclose(q1, q, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_grouped_modelling_and_normal_operator_equal_the_single_context(prec):
+    """Forward modelling (point and extended sources), the adjoint with its source-point
+    output, and the normal operator, three shots in two groups: per shot, the same numbers."""
+    v, geom, p = _case()
+    nt = p["nt"]
+    wav = _dev(np.stack([synth.ricker(nt, p["dt"], f) for f in (25.0, 21.0, 30.0)]), prec)
+    q = _dev(synth.normal(9, (geom.ns, nt) + v.shape) * 1e-3, prec)
+    ctx1, ctxg = _ctx(v, geom, p, prec), _ctx(v, geom, p, prec)
+    ctxg.set_shot_groups(2)
+    d1, dg = ctx1.forward(wavelet=wav, ext=q), ctxg.forward(wavelet=wav, ext=q)
+    assert torch.equal(d1, dg)
+    f1, w1 = ctx1.adjoint(d1, want_wavelet=True)
+    fg, wg = ctxg.adjoint(d1, want_wavelet=True)
+    assert torch.equal(f1, fg) and torch.equal(w1, wg)
+    a1, ag = ctx1.normal_apply(q, 3e-4), ctxg.normal_apply(q, 3e-4)
+    assert torch.equal(a1, ag)
+
+
+def test_grouped_wri_data_space_and_frequency_domain_solves_fp64():
+    """The WRI, data-space and frequency-domain solves with three shots in three groups:
+    iterates and residual histories of the single context."""
+    v, geom, p = _case()
+    nt = p["nt"]
+    o, shots = _orc(v, geom, p, vref=float(v.max()))
+    wav = np.stack([synth.ricker(nt, p["dt"], 25.0)] * geom.ns)
+    d = np.concatenate([o.forward(sh, wavelet=wav[s])["traces"].ravel() for s, sh in enumerate(shots)])
+    dn = d + synth.normal(44, d.shape) * np.abs(d).max()
+    ctx1 = _ctx(v, geom, p, "f64", vref=float(v.max()))
+    ctxg = _ctx(v, geom, p, "f64", vref=float(v.max()))
+    ctxg.set_shot_groups(3)
+    runs = [dict(d=dn, lam=0.05, kw=dict(wri_wavelet=_dev(wav, "f64"))),
+            dict(d=d, lam=2e-4, kw=dict(data_space=True)),
+            dict(d=d, lam=2e-4, kw=dict(freqs=[8.0, 15.5, 23.0], precond="diag"))]
+    for run in runs:
+        x1, r1 = ctx1.cg_solve(_dev(run["d"], "f64"), lam=run["lam"], tol=0.0, max_iter=4, **run["kw"])
+        xg, rg = ctxg.cg_solve(_dev(run["d"], "f64"), lam=run["lam"], tol=0.0, max_iter=4, **run["kw"])
+        assert list(rg["iters"]) == list(r1["iters"]), run["kw"]
+        for s in range(geom.ns):
+            assert np.allclose(rg["rel_res"][s], r1["rel_res"][s], rtol=1e-12, atol=0), (run["kw"], s)
+        assert torch.allclose(xg, x1, rtol=1e-12, atol=1e-300), run["kw"]
