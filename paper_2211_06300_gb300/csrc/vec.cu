@@ -873,9 +873,12 @@ __global__ void __launch_bounds__(RT) dft_block_kernel(const T *snap, int K, int
 }
 
 template <typename T>
-__global__ void idft_block_kernel(const T *qb, int K, int kst, int ns, long long sst, int nf,
-                                  const T *tw, T *src) {
+__global__ void __launch_bounds__(RT) idft_block_kernel(const T *qb, int K, int kst, int ns,
+                                                        long long sst, int nf, const T *tw, T *src) {
     constexpr int VEC = V16<T>::n;
+    __shared__ T tws[DFT_BLOCK_MAX * FD_MAXF * 2];   // the block's twiddles, staged once
+    for (int t = threadIdx.x; t < K * nf * 2; t += RT) tws[t] = tw[t];
+    __syncthreads();
     const int s = blockIdx.y;
     const long long nch = sst / VEC;
     for (long long c = (long long)blockIdx.x * RT + threadIdx.x; c < nch;
@@ -903,7 +906,7 @@ __global__ void idft_block_kernel(const T *qb, int K, int kst, int ns, long long
 #pragma unroll
             for (int m = 0; m < FD_MAXF; ++m) {
                 if (m >= nf) break;
-                const T C = tw[((long long)k * nf + m) * 2], D = tw[((long long)k * nf + m) * 2 + 1];
+                const T C = tws[(k * nf + m) * 2], D = tws[(k * nf + m) * 2 + 1];
 #pragma unroll
                 for (int i = 0; i < VEC; ++i) o.v[i] += a[m][i] * C + b[m][i] * D;
             }
@@ -989,8 +992,25 @@ cudaError_t launch_fd_precond(T *z, const T *r, const T *w, int nf, int ns, long
 template <typename T>
 cudaError_t launch_idft_block(const T *qb, int K, int kst, int ns, long long sst, int nf,
                               const T *tw, T *src, cudaStream_t st) {
-    if (nf > FD_MAXF || K > kst) return cudaErrorInvalidValue;
-    idft_block_kernel<T><<<dim3(blocks_for(sst / V16<T>::n, 1024), ns), RT, 0, st>>>(
+    if (nf < 1 || nf > FD_MAXF || K < 1 || K > kst || K > DFT_BLOCK_MAX) return cudaErrorInvalidValue;
+    // the resident blocks, shared among the shots (grid-stride over the cells)
+    static PerDevice slots;
+    int nres = 0;
+    if (per_device(slots, &nres, [](int *out) {
+            int dev = 0, nsm = 0, nb = 0;
+            cudaError_t r;
+            if ((r = cudaGetDevice(&dev)) != cudaSuccess) return r;
+            if ((r = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+                return r;
+            if ((r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, idft_block_kernel<T>, RT, 0)) !=
+                cudaSuccess)
+                return r;
+            *out = std::max(1, nb) * std::max(1, nsm);
+            return cudaSuccess;
+        }) != cudaSuccess)
+        nres = 1024;
+    const int per_shot = std::max(1, nres / std::max(1, ns));
+    idft_block_kernel<T><<<dim3(blocks_for(sst / V16<T>::n, per_shot), ns), RT, 0, st>>>(
         qb, K, kst, ns, sst, nf, tw, src);
     return cudaGetLastError();
 }
