@@ -92,7 +92,7 @@ def workload_name(ns, nt):
 # from an ncu capture of the 2D step kernel on 16 shots of 801 x 241 (one launch =
 # 3,088,656 cell updates), valid only for the kernel it was taken on: the
 # SHA-256 below of its template source and the header's argument struct (_sources_sha).
-_SHA = "31ad353fc381d3d0d5344841d269001cf79624d5929e7db4d69d0d4a83218ca8"
+_SHA = "5e1d3b4d18ef73966c665b764822e8bfd92c3349c58d284ccc6d45b8206ddf0a"
 MEASURED_TRAFFIC = {
     "fd2_step[PT|AP]": ((52.655616e6 + 1.062656e6) / 3088656, _SHA),
     "fd2_step[CGP|SMP]": ((65.971712e6 + 1.078528e6) / 3088656, _SHA),

@@ -48,7 +48,7 @@ constexpr int SW3 = TX3 + 2 * HALO, SH3 = TY3 + 2 * HALO;
 // chunks of ZCH3_MIN .. ZCH3_MAX planes
 constexpr int ZCH3_MIN = 40, ZCH3_MAX = 100;
 constexpr int RING3 = 8;            // staged planes (shared-memory ring of TMA boxes)
-constexpr int DFT_BLOCK = 16;       // time steps per blocked DTFT pass
+constexpr int DFT_BLOCK = 16;       // shortest block of a blocked DTFT pass (steps)
 
 // first plane of z chunk zc when nz planes are split into nzc chunks of near-equal length
 __host__ __device__ inline int chunk_begin3(int zc, int nzc, int nz) {

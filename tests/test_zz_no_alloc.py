@@ -37,8 +37,8 @@ def _case(dtype, ns=3):
 
 def _case_3d(dtype):
     """24^3 volume, two shots with their own receiver grids (trilinear points off the
-    nodes), both sources: the 3D step builds tensor maps over the static array and samples
-    through its gather launch."""
+    nodes), both sources: the 3D step builds tensor maps over the static array and its
+    consumer threads gather the receivers from it."""
     from paper_2211_06300_gb300 import esi
     shape, dx, dt, nt, nb = (24, 24, 24), 10.0, 1e-3, 40, 4
     v = synth.dipping_layers(shape, dx, 6, nlayers=3, vmin=1500, vmax=2400, nanom=1,
