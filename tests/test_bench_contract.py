@@ -44,3 +44,19 @@ def test_parser_offers_every_workload(monkeypatch):
         monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", w, "--no-compare"])
         a = bench.parse()
         assert a.workload == w and a.gpus == 1 and a.warmup >= 3
+
+
+def test_roofline_of_concurrent_groups_and_the_whole_step():
+    """With shot groups the per-launch rate is one group's (marked, no traffic scaling),
+    and `step` divides the algorithmic bytes of every kernel by the step's device time."""
+    prof = [{"name": "fd2_step[PT|AP]", "launches": 400, "cells": 4000, "bytes_per_cell": 28.0,
+             "ms": 8.0},
+            {"name": "cg_update", "launches": 4, "cells": 4000, "bytes_per_cell": 24.0, "ms": 3.0}]
+    r1 = bench.roofline_of(prof, {"hbm_gbs": 1000.0}, 1, step_ms=5.0, steps=2)
+    r4 = bench.roofline_of(prof, {"hbm_gbs": 1000.0}, 4, step_ms=5.0, steps=2)
+    assert r1["achieved"] == r4["achieved"] == pytest.approx(4000 * 28 / 8e-3 / 1e9)
+    assert "groups" not in r1 and r4["groups"] == 4 and r4["traffic"] is None
+    step_bytes = (4000 * 28 + 4000 * 24) / 2
+    assert r4["step"]["bytes_per_step"] == pytest.approx(step_bytes)
+    assert r4["step"]["achieved"] == pytest.approx(step_bytes / 5e-3 / 1e9)
+    assert r4["step"]["frac"] == pytest.approx(r4["step"]["achieved"] / 1000.0)
