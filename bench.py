@@ -76,7 +76,7 @@ def parse():
     ap.add_argument("--wri-factor", type=float, default=1e-2,
                     help="WRI penalty: beta = factor * lambda_max(S^T S)")
     ap.add_argument("--groups", type=int, default=1,
-                    help="esi2d: run the shots as this many concurrent groups "
+                    help="esi2d, wri2d, grad2d: run the shots as this many concurrent groups "
                          "(esi_set_shot_groups) in the timed steps")
     ap.add_argument("--n3d", type=int, default=400)
     ap.add_argument("--nt3d", type=int, default=2000)
@@ -408,6 +408,8 @@ def run_wri2d(args, rank, world, local):
     c1.close()
     q = ctx.empty_field()
     N = wl.ncell
+    if args.groups > 1:
+        ctx.set_shot_groups(args.groups)
 
     def step():
         ctx.set_velocity(v0)
@@ -476,13 +478,14 @@ def run_wri2d(args, rank, world, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": "wri2d-801x241-nt%d-%dshots-fp32" % (nt, ns), "beta": beta,
-                       "wri_factor": args.wri_factor, "tol": args.tol,
+                       "wri_factor": args.wri_factor, "tol": args.tol, "shot_groups": args.groups,
                        "l2": "inputs larger than L2 (CG vectors 4 x %.2f GB per GPU)"
                              % (4 * ns * nt * N / 1e9)},
             "cg": {"iters_max_per_step": [int(max(r["iters"])) for r in reps],
                    "time_to_tol_ms": [r["ms_total"] for r in reps],
                    "converged": [bool(r["converged"]) for r in reps]},
-            "roofline": roofline_of(prof, peaks), "kernels": prof,
+            "roofline": roofline_of(prof, peaks, args.groups, t_max / args.steps, args.steps),
+            "kernels": prof,
             "e2e": {"value": ce / te / 1e9, "unit": UNIT,
                     "h2d_bytes_per_step": int(d_host.numel() * d_host.element_size()),
                     "d2h_bytes_per_step": int(g_host.numel() * g_host.element_size())},
@@ -637,6 +640,8 @@ def run_grad2d(args, rank, world, local):
     ctx = esi.Context(v0, wl.dx, wl.dt, nt, wl.nb, geom, vref=vref)
     N = wl.ncell
     cells_step = 3 * ns * N * nt      # forward, recompute, adjoint
+    if args.groups > 1:
+        ctx.set_shot_groups(args.groups)
 
     def step(d):
         g, J = ctx.gradient(wavelet=wav, dobs=d, param="v", ckpt_every=20, ckpt="bf16")
@@ -694,7 +699,7 @@ def run_grad2d(args, rank, world, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": "grad2d-1201x301-nt%d-%dshots-fp32-bf16ckpt" % (nt, ns),
-                       "checkpoint_every": 20, "checkpoints": "bf16",
+                       "checkpoint_every": 20, "checkpoints": "bf16", "shot_groups": args.groups,
                        "checkpoint_codec": "u_n and u_n - u_{n-1}, each as BF16 even-index "
                                            "cells plus the BF16 residual against their "
                                            "bilinear interpolation, unscaled "
@@ -702,7 +707,8 @@ def run_grad2d(args, rank, world, local):
                        "l2": "inputs larger than L2 (states 2 x %.1f MB, checkpoints %.1f GB)"
                              % (4 * ns * N / 1e6, 5 * ns * N * ((nt + 19) // 20) / 1e9)},
             "misfit": J,
-            "roofline": roofline_of(prof, peaks), "kernels": prof,
+            "roofline": roofline_of(prof, peaks, args.groups, t_max / args.steps, args.steps),
+            "kernels": prof,
             "e2e": {"value": cells_all / te / 1e9, "unit": UNIT,
                     "h2d_bytes_per_step": int(d_host.numel() * d_host.element_size()),
                     "d2h_bytes_per_step": int(g_host.numel() * g_host.element_size())},
