@@ -76,7 +76,7 @@ def parse():
     ap.add_argument("--wri-factor", type=float, default=1e-2,
                     help="WRI penalty: beta = factor * lambda_max(S^T S)")
     ap.add_argument("--groups", type=int, default=1,
-                    help="esi2d, wri2d, grad2d: run the shots as this many concurrent groups "
+                    help="esi2d, wri2d, invert2d, grad2d: run the shots as this many concurrent groups "
                          "(esi_set_shot_groups) in the timed steps")
     ap.add_argument("--n3d", type=int, default=400)
     ap.add_argument("--nt3d", type=int, default=2000)
@@ -527,6 +527,8 @@ def run_invert2d(args, rank, world, local):
     vel = v0.clone()
     grad = torch.empty_like(v0)
     N = wl.ncell
+    if args.groups > 1:
+        ctx.set_shot_groups(args.groups)
     red = (lambda J, g: shard.reduce_objective(J, g, dist)) if dist is not None else None
     kw = dict(n_outer=args.outer, n_cg=10, precond="diag", beta0=beta, vmin=1400.0,
               vmax=4700.0, reduce=red)
@@ -594,12 +596,13 @@ def run_invert2d(args, rank, world, local):
             "data": "synthetic",
             "config": {"workload": "invert2d-801x241-nt%d-%dshots-fp32" % (nt, ns),
                        "outer_iterations": args.outer, "inner_cg": 10, "precond": "diag",
-                       "beta": beta,
+                       "beta": beta, "shot_groups": args.groups,
                        "l2": "inputs larger than L2 (q %.2f GB per GPU)" % (4 * ns * nt * N / 1e9)},
             "outer": [{"J_start": r["J_start"], "J_end": r["J_end"], "trials": r["trials"],
                        "evaluations": r["evaluations"], "stop": r["stop"],
                        "ms": r["ms_total"]} for r in reps],
-            "roofline": roofline_of(prof, peaks), "kernels": prof,
+            "roofline": roofline_of(prof, peaks, args.groups, t_max / args.steps, args.steps),
+            "kernels": prof,
             "e2e": {"value": ce / te / 1e9, "unit": UNIT,
                     "h2d_bytes_per_step": int(d_host.numel() * d_host.element_size()),
                     "d2h_bytes_per_step": int(v_host.numel() * v_host.element_size())},

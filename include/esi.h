@@ -119,9 +119,10 @@ ESI_API esi_status esi_set_velocity(esi_ctx *ctx, const void *velocity_dev);
  * outputs are those of the ungrouped context (each group writes its shots' slices); the
  * gradient, a sum over shots, is the groups' partial sums added in group order by a
  * kernel, and the misfit likewise.  A CG report gives per-shot iterations and residual
- * histories as before; its phase times are the longest group's.  esi_forward_noalloc (whose
- * fixed scratch the groups would share), esi_invert and the learned preconditioner run on
- * the context itself.  Each call's groups start after the
+ * histories as before; its phase times are the longest group's.  esi_invert's evaluations
+ * (inner solve, objective and gradient) go through these calls and so run on the groups;
+ * esi_forward_noalloc (whose fixed scratch the groups would share) and the learned
+ * preconditioner run on the context itself.  Each call's groups start after the
  * work already queued on the context stream, which then waits for all of them.
  * esi_set_profiling, esi_get_profile (entries merged by name, times summed over the groups'
  * streams) and esi_launch_count include the groups.

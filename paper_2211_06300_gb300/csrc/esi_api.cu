@@ -2155,19 +2155,20 @@ esi_status invert_impl(esi_ctx *ctx, const esi_invert_opts *o, const void *wavel
     go.ckpt_every = 1;
     go.ckpt_kind = ESI_CKPT_F32;
     go.eps = o->eps;
-    // J and g (into g_out) at the model m
+    // J and g (into g_out) at the model m, through the entry points: with shot groups
+    // (esi_set_shot_groups) the inner solve and the gradient run on them
     auto eval = [&](const T *m, double beta, T *g_out, double &J) -> esi_status {
-        esi_status st = setup_model<T>(ctx, m, false);
+        esi_status st = esi_set_velocity(ctx, m);
         if (st != ESI_OK) return st;
         std::vector<int> its(ctx->ns);
         esi_cg_report cr{};
         cr.iters = its.data();
-        st = wri ? cg_impl<T>(ctx, beta, o->cg_tol, o->n_cg, dobs, q, ESI_PC_NONE, 0.0, &cr, wavelet)
-                 : cg_impl<T>(ctx, beta, o->cg_tol, o->n_cg, dobs, q, o->precond, o->eps, &cr);
+        st = wri ? esi_wri_solve(ctx, beta, o->cg_tol, o->n_cg, wavelet, dobs, q, &cr)
+                 : esi_cg_solve(ctx, beta, o->cg_tol, o->n_cg, dobs, q, o->precond, o->eps, &cr);
         if (st != ESI_OK && st != ESI_ERR_NOT_CONVERGED) return st;
         cg_total += cr.iters_max;
         go.beta = beta;
-        st = gradient_impl<T>(ctx, wri ? wavelet : nullptr, q, dobs, nullptr, &go, gw, &J);
+        st = esi_gradient(ctx, wri ? wavelet : nullptr, q, dobs, nullptr, &go, gw, &J);
         if (st != ESI_OK) return st;
         if (o->reduce) {
             CK(cudaStreamSynchronize(ctx->st));
@@ -2279,8 +2280,9 @@ esi_status invert_impl(esi_ctx *ctx, const esi_invert_opts *o, const void *wavel
         if (rep && rep->J_end) rep->J_end[i] = J;
         if (rep && rep->alpha) rep->alpha[i] = alpha;
     }
-    // leave the context at the output model and the caller's gradient at its gradient
-    if ((e = setup_model<T>(ctx, x, false)) != ESI_OK) return e;
+    // leave the context (and its shot groups) at the output model and the caller's gradient
+    // at its gradient
+    if ((e = esi_set_velocity(ctx, x)) != ESI_OK) return e;
     CK(cudaMemcpyAsync(gw, g, N * sizeof(T), cudaMemcpyDeviceToDevice, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     if (rep) {

@@ -195,3 +195,29 @@ def test_grouped_wri_data_space_and_frequency_domain_solves_fp64():
         for s in range(geom.ns):
             assert np.allclose(rg["rel_res"][s], r1["rel_res"][s], rtol=1e-12, atol=0), (run["kw"], s)
         assert torch.allclose(xg, x1, rtol=1e-12, atol=1e-300), run["kw"]
+
+
+@pytest.mark.parametrize("mode", ["esi", "wri"])
+def test_grouped_outer_loop_follows_the_single_context_fp64(mode):
+    """esi_invert with two shot groups: its inner solves and gradients run on the groups (the
+    gradient's partial sums are added in group order, a rounding-order difference), and the
+    loop takes the same steps as on the single context."""
+    from test_gpu_outer import _ctx as _octx, _dcat, _dev as _odev, _problem
+    v, geom, pb, f = _problem()
+    kw = dict(mode=mode, n_outer=3, n_cg=10, precond="diag", beta0=0.1, growth=1.0,
+              vmin=1400.0, vmax=2600.0)
+    outs = []
+    for groups in (1, 2):
+        ctx = _octx(v, geom, pb, torch.float64)
+        if groups > 1:
+            ctx.set_shot_groups(groups)
+        vel = _odev(v, torch.float64)
+        wav = _odev(np.stack([f] * geom.ns), torch.float64) if mode == "wri" else None
+        g, rep = ctx.invert(_dcat(pb, torch.float64), vel, wavelet=wav, **kw)
+        outs.append((vel.cpu().numpy(), g.cpu().numpy(), rep))
+    (v1, g1, r1), (v2, g2, r2) = outs
+    assert r2["stop"] == r1["stop"] and r2["trials"] == r1["trials"]
+    assert np.allclose(r2["J_start"], r1["J_start"], rtol=1e-10, atol=0)
+    assert np.allclose(r2["J_end"], r1["J_end"], rtol=1e-10, atol=0)
+    assert oracle.rel_l2(v2 - v, v1 - v) < 1e-8
+    assert oracle.rel_l2(g2.ravel(), g1.ravel()) < 1e-8
