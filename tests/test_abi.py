@@ -52,4 +52,5 @@ def test_status_strings_and_argument_checks_need_no_gpu(lib):
                         ctypes.c_void_p(16), 1e-3, 10, None)
     assert st == esi.ESI_ERR_ARG
     assert lib.esi_forward(None, None, None, None) == esi.ESI_ERR_ARG
+    assert lib.esi_set_shot_groups(None, 2, None) == esi.ESI_ERR_ARG
     assert lib.esi_launch_count(None) == 0
