@@ -2650,13 +2650,9 @@ ESI_API esi_status esi_set_velocity(esi_ctx *ctx, const void *velocity_dev) {
     if (!ctx || !velocity_dev) return ESI_ERR_ARG;
     const esi_status e = ctx->g.dtype == ESI_F64 ? setup_model<double>(ctx, velocity_dev, false)
                                                  : setup_model<float>(ctx, velocity_dev, false);
-    if (e != ESI_OK) return e;
-    for (size_t k = 0; k < ctx->grp.size(); ++k) {
-        CK(cudaStreamSynchronize(ctx->st));   // the new model is the caller's; groups follow it
-        const esi_status ek = esi_set_velocity(ctx->grp[k], velocity_dev);
-        if (ek != ESI_OK) return ctx->fail(ek, "shot group " + std::to_string(k) + ": " + ctx->grp[k]->err);
-    }
-    return ESI_OK;
+    if (e != ESI_OK || ctx->grp.empty()) return e;
+    // the groups follow the caller's model, each in its own thread (each set-up synchronises)
+    return run_groups(ctx, [&](int, esi_ctx *c) { return esi_set_velocity(c, velocity_dev); });
 }
 
 ESI_API esi_status esi_forward(esi_ctx *ctx, const void *wavelet_dev, const void *ext_src_dev,
